@@ -1,0 +1,196 @@
+"""Discrete boundary integral operators for N rigid spheres (Sec. 4.1, 4.3;
+Problems 2 and 5 of Sec. 5).  Test infrastructure only.
+
+An operator apply splits into (Sec. 4.3):
+  self  analysis -> signature (Theorem 2) -> synthesis on the same sphere (Sec. 4.1, Eqs. 4.6-4.7);
+  far   the smooth quadrature (Eq. 4.4) over nodes of every well-separated sphere (Eq. 4.5);
+  near  the exterior expansion of each close source sphere evaluated at the
+        target nodes (Sec. 4.1, Eqs. 3.6-3.11, 3.18).
+
+Readings of points the paper leaves open (each also listed in the design notes):
+  * close pairs: sphere k is near sphere i (i != k) when
+      |c_i - c_k| - a_i - a_k < eta * max(2 a_i, 2 a_k)       (negation of Eq. 4.5);
+  * radius scaling: the signatures and exterior formulas are for the unit
+    sphere; S scales by the source radius a, D and K are scale free;
+  * the self term of D and K is the principal value (D+ + D-)/2, and the 1/2 I
+    of the BIEs is added nodally;
+  * L_k (Eq. 5.8) acts on Gamma_k only, about the centre of sphere k;
+  * N_k (Eq. 5.19) is a Stokeslet of strength int psi and a rotlet of strength
+    int (y - c_k) x psi, both at c_k, evaluated at every node.
+"""
+import numpy as np
+
+from . import kernels, offsurface, quadrature, signatures, vsh
+
+
+class OverlapError(ValueError):
+    pass
+
+
+class Geometry:
+    def __init__(self, centres, radii, p, eta=1.0):
+        self.c = np.asarray(centres, float).reshape(-1, 3)
+        self.a = np.asarray(radii, float).reshape(-1)
+        self.p = int(p)
+        self.eta = float(eta)
+        n = len(self.a)
+        self.n = n
+        if p < 1:
+            raise ValueError("p >= 1 required")
+        if np.any(self.a <= 0):
+            raise ValueError("radii must be positive")
+        self.npn = (p + 1) * (2 * p + 2)
+        xs, ns, ws = [], [], []
+        for i in range(n):
+            x, nr, w = quadrature.sphere_nodes(self.c[i], self.a[i], p)
+            xs.append(x)
+            ns.append(nr)
+            ws.append(w)
+        self.x = np.concatenate(xs)
+        self.nrm = np.concatenate(ns)
+        self.w = np.concatenate(ws)
+        self.near = [[] for _ in range(n)]
+        for i in range(n):
+            for k in range(n):
+                if k == i:
+                    continue
+                gap = np.linalg.norm(self.c[i] - self.c[k]) - self.a[i] - self.a[k]
+                if gap <= 0:
+                    raise OverlapError(f"spheres {i} and {k} overlap or touch")
+                if gap < self.eta * 2.0 * max(self.a[i], self.a[k]):
+                    self.near[i].append(k)
+
+    @property
+    def N(self):
+        return self.n * self.npn
+
+    def sl(self, i):
+        return slice(i * self.npn, (i + 1) * self.npn)
+
+    def n_near_pairs(self):
+        return sum(len(v) for v in self.near)
+
+
+def _signature(op, n, a):
+    if op == "S":
+        s = signatures.S(n)
+        return tuple(a * v for v in s)
+    if op == "D":
+        return signatures.D_pv(n)
+    if op == "K":
+        return signatures.K_pv(n)
+    raise ValueError(op)
+
+
+def coefficients(g, dens):
+    """VSH coefficients of the density on every sphere (as a function on the unit sphere)."""
+    return [vsh.analysis(dens[g.sl(i)], g.p) for i in range(g.n)]
+
+
+def self_term(g, op, dens, coefs=None):
+    """Self interaction: synthesis of (signature x coefficients), Sec. 4.1 (Eqs. 4.6-4.7)."""
+    coefs = coefs or coefficients(g, dens)
+    out = np.zeros_like(dens)
+    for i in range(g.n):
+        c = coefs[i].copy()
+        for n in range(g.p + 1):
+            lam = _signature(op, n, g.a[i])
+            for t in range(3):
+                c[t, n, :] *= lam[t]
+        c[1, 0, 0] = 0.0
+        c[2, 0, 0] = 0.0
+        out[g.sl(i)] = vsh.synthesis(c)
+    return out
+
+
+def far_term(g, op, dens):
+    """Smooth quadrature (Eq. 4.4) over all nodes of well-separated spheres."""
+    out = np.zeros_like(dens)
+    dw = dens * g.w[:, None]
+    for i in range(g.n):
+        excl = set(g.near[i]) | {i}
+        src = np.concatenate([np.arange(g.sl(k).start, g.sl(k).stop) for k in range(g.n) if k not in excl]
+                             ) if len(excl) < g.n else np.zeros(0, int)
+        if len(src) == 0:
+            continue
+        xt = g.x[g.sl(i)]
+        if op == "S":
+            out[g.sl(i)] = kernels.stokeslet_sum(xt, g.x[src], dw[src])
+        elif op == "D":
+            out[g.sl(i)] = kernels.stresslet_sum_D(xt, g.x[src], g.nrm[src], dw[src])
+        elif op == "K":
+            out[g.sl(i)] = kernels.stresslet_sum_K(xt, g.nrm[g.sl(i)], g.x[src], dw[src])
+        else:
+            raise ValueError(op)
+    return out
+
+
+def near_term(g, op, dens, coefs=None):
+    """Exterior expansion of each close source sphere at the target nodes (Sec. 4.1)."""
+    coefs = coefs or coefficients(g, dens)
+    out = np.zeros_like(dens)
+    for i in range(g.n):
+        xt = g.x[g.sl(i)]
+        for k in g.near[i]:
+            xh = (xt - g.c[k][None, :]) / g.a[k]
+            if op == "S":
+                out[g.sl(i)] += g.a[k] * offsurface.S_velocity(coefs[k], xh)
+            elif op == "D":
+                out[g.sl(i)] += offsurface.D_velocity(coefs[k], xh)
+            elif op == "K":
+                out[g.sl(i)] += offsurface.S_traction(coefs[k], xh, g.nrm[g.sl(i)])
+            else:
+                raise ValueError(op)
+    return out
+
+
+def layer(g, op, dens):
+    """Raw sum over k of S_k, D_k or K_k at every node (self by its signature)."""
+    dens = np.asarray(dens, float).reshape(-1, 3)
+    coefs = coefficients(g, dens)
+    return self_term(g, op, dens, coefs) + far_term(g, op, dens) + near_term(g, op, dens, coefs)
+
+
+def moments(g, dens):
+    """Per sphere M0 = int psi and M1 = int (y - c_k) x psi by the node quadrature."""
+    dens = np.asarray(dens, float).reshape(-1, 3)
+    M0 = np.zeros((g.n, 3))
+    M1 = np.zeros((g.n, 3))
+    for k in range(g.n):
+        s = g.sl(k)
+        M0[k] = np.sum(g.w[s, None] * dens[s], axis=0)
+        M1[k] = np.sum(g.w[s, None] * np.cross(g.x[s] - g.c[k], dens[s]), axis=0)
+    return M0, M1
+
+
+def completion_N(g, dens):
+    """Sum_k N_k[psi]: Stokeslet (Eq. 2.19) with strength M0_k plus rotlet with
+    strength M1_k, both at the centre of sphere k, at every node (Eq. 5.19)."""
+    M0, M1 = moments(g, dens)
+    out = np.zeros((g.N, 3))
+    for k in range(g.n):
+        out += kernels.stokeslet(g.x, g.c[k], M0[k]) + kernels.rotlet(g.x, g.c[k], M1[k])
+    return out
+
+
+def rigid_L(g, dens):
+    """L_k[mu](x) = int mu + (int (y - c_k) x mu) x (x - c_k) for x on Gamma_k (Eq. 5.8)."""
+    M0, M1 = moments(g, dens)
+    out = np.zeros((g.N, 3))
+    for k in range(g.n):
+        s = g.sl(k)
+        out[s] = M0[k][None, :] + np.cross(M1[k][None, :], g.x[s] - g.c[k])
+    return out
+
+
+def apply(g, op, dens):
+    """Operators of the C interface: 'S', 'D', 'K' (raw sums), 'mobility'
+    = 1/2 I + K + L (Eq. 5.8), 'resistance' = 1/2 I + D + N (Eq. 5.19)."""
+    dens = np.asarray(dens, float).reshape(-1, 3)
+    if op in ("S", "D", "K"):
+        return layer(g, op, dens)
+    if op == "mobility":
+        return 0.5 * dens + layer(g, "K", dens) + rigid_L(g, dens)
+    if op == "resistance":
+        return 0.5 * dens + layer(g, "D", dens) + completion_N(g, dens)
+    raise ValueError(op)

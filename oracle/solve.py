@@ -1,0 +1,78 @@
+"""Mobility (Problem 2, Eqs. 5.5-5.8) and resistance (Problem 5, Eqs. 5.18-5.19)
+drivers.  Test infrastructure only.
+
+Readings (the paper defers rho to its reference [9] and does not say how the
+rigid motions or forces are read off):
+  * rho_k = F_k / (4 pi a^2) + (3 / (8 pi a^4)) T_k x (x - c_k), the rigid-form
+    density with int rho = F_k and int (y - c_k) x rho = T_k;
+  * mobility: u = sum_k S_k[mu + rho] on Gamma_k (Eq. 5.7), then
+    v_k = int u / (4 pi a^2) and w_k = (3 / (8 pi a^4)) int (x - c_k) x u;
+  * resistance: right-hand side v_i + w_i x (x - c_i) - u_inf(x) with
+    u_inf(x) = u0 + G x; F_k = int psi, T_k = int (y - c_k) x psi.
+F and T are the force and torque the particle exerts on the fluid.
+"""
+import numpy as np
+
+from . import gmres as _gmres
+from . import operators as ops
+
+
+def rho_density(g, F, T):
+    F = np.asarray(F, float).reshape(-1, 3)
+    T = np.asarray(T, float).reshape(-1, 3)
+    out = np.zeros((g.N, 3))
+    for k in range(g.n):
+        s = g.sl(k)
+        a = g.a[k]
+        out[s] = F[k] / (4 * np.pi * a * a) + (3.0 / (8 * np.pi * a ** 4)) * np.cross(T[k][None, :], g.x[s] - g.c[k])
+    return out
+
+
+def rigid_projection(g, u):
+    """(v_k, w_k) of a nodal field u by the node quadrature."""
+    v = np.zeros((g.n, 3))
+    w = np.zeros((g.n, 3))
+    for k in range(g.n):
+        s = g.sl(k)
+        a = g.a[k]
+        v[k] = np.sum(g.w[s, None] * u[s], axis=0) / (4 * np.pi * a * a)
+        w[k] = 3.0 / (8 * np.pi * a ** 4) * np.sum(g.w[s, None] * np.cross(g.x[s] - g.c[k], u[s]), axis=0)
+    return v, w
+
+
+def mobility_rhs(g, F, T):
+    rho = rho_density(g, F, T)
+    return -(0.5 * rho + ops.layer(g, "K", rho)), rho
+
+
+def solve_mobility(g, F, T, tol=1e-10, restart=200, max_iter=1000):
+    b, rho = mobility_rhs(g, F, T)
+    mu, info = _gmres.gmres(lambda v: ops.apply(g, "mobility", v.reshape(-1, 3)), b.ravel(),
+                            tol=tol, restart=restart, max_iter=max_iter)
+    mu = mu.reshape(-1, 3)
+    u = ops.layer(g, "S", mu + rho)
+    v, w = rigid_projection(g, u)
+    return v, w, dict(info, mu=mu, u=u)
+
+
+def resistance_rhs(g, v, w, u0=None, G=None):
+    v = np.asarray(v, float).reshape(-1, 3)
+    w = np.asarray(w, float).reshape(-1, 3)
+    b = np.zeros((g.N, 3))
+    for k in range(g.n):
+        s = g.sl(k)
+        b[s] = v[k][None, :] + np.cross(w[k][None, :], g.x[s] - g.c[k])
+    if u0 is not None:
+        b -= np.asarray(u0, float)[None, :]
+    if G is not None:
+        b -= g.x @ np.asarray(G, float).T
+    return b
+
+
+def solve_resistance(g, v, w, u0=None, G=None, tol=1e-10, restart=200, max_iter=1000, rhs=None):
+    b = resistance_rhs(g, v, w, u0, G) if rhs is None else np.asarray(rhs, float).reshape(-1, 3)
+    psi, info = _gmres.gmres(lambda x: ops.apply(g, "resistance", x.reshape(-1, 3)), b.ravel(),
+                             tol=tol, restart=restart, max_iter=max_iter)
+    psi = psi.reshape(-1, 3)
+    F, T = ops.moments(g, psi)
+    return F, T, dict(info, psi=psi)

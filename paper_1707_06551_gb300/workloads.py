@@ -1,0 +1,176 @@
+"""Seeded synthetic suspensions (sphere placements, forces, background flows).
+
+This module holds geometry and random draws only -- none of the method's
+arithmetic -- so that the CUDA path and the CPU oracle can be fed identical
+inputs.  All randomness comes from numpy.random.default_rng(seed).
+
+Workloads (the paper uses no public data set):
+  mobility_8      8 unit spheres, centres uniform in [0, 12]^3 with minimum
+                  centre distance 2.5, F, T ~ N(0, 1), p = 6.
+  resistance_256  256 unit spheres, random sequential addition at volume
+                  fraction 0.10 in a cube, then 20% of the spheres moved towards
+                  their nearest neighbour to a surface gap ~ U[0.05, 0.2];
+                  p = 10; background shear u_inf = (y, 0, 0); spheres held fixed.
+  batched_512     512 independent mobility problems with n ~ U{4..64},
+                  p ~ U{6, 8, 10, 12}, radii log-uniform in [0.5, 2], RSA at
+                  volume fraction 0.05 with minimum gap 0.1 (a_i + a_k).
+  dense_1024      1024 unit spheres, RSA at volume fraction 0.30, nearest gap of
+                  each sphere pushed to log-uniform [0.01, 0.5], p = 12.
+  large_4096      4096 spheres, radii ~ U[0.8, 1.2], RSA at volume fraction
+                  0.20, p = 12, resistance in a random linear flow u0 + G x
+                  (G traceless).
+"""
+import math
+
+import numpy as np
+
+
+class _Cells:
+    """Uniform cell list for overlap queries during placement."""
+
+    def __init__(self, L, h):
+        self.h = h
+        self.n = max(1, int(math.ceil(L / h)))
+        self.cells = {}
+
+    def key(self, x):
+        return tuple(np.clip((np.asarray(x) // self.h).astype(int), -1, self.n))
+
+    def add(self, idx, x):
+        self.cells.setdefault(self.key(x), []).append(idx)
+
+    def remove(self, idx, x):
+        self.cells[self.key(x)].remove(idx)
+
+    def around(self, x):
+        k = self.key(x)
+        out = []
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    out.extend(self.cells.get((k[0] + dx, k[1] + dy, k[2] + dz), ()))
+        return out
+
+
+def rsa(rng, radii, L, min_gap_fn=lambda ai, ak: 0.0, max_tries=2_000_000):
+    """Random sequential addition of spheres with the given radii, centres
+    uniform in [0, L]^3, rejecting any draw closer than min_gap_fn to a placed
+    sphere.  Radii are placed in the given order."""
+    radii = np.asarray(radii, float)
+    amax = float(np.max(radii))
+    cells = _Cells(L, 2.0 * amax + min_gap_fn(amax, amax) + 1e-9)
+    c = np.zeros((len(radii), 3))
+    tries = 0
+    for i, a in enumerate(radii):
+        while True:
+            tries += 1
+            if tries > max_tries:
+                raise RuntimeError("placement failed; volume fraction too high")
+            x = rng.uniform(0.0, L, size=3)
+            ok = True
+            for k in cells.around(x):
+                if np.linalg.norm(x - c[k]) - a - radii[k] < min_gap_fn(a, radii[k]):
+                    ok = False
+                    break
+            if ok:
+                c[i] = x
+                cells.add(i, x)
+                break
+    return c
+
+
+def push_gaps(rng, c, radii, frac, gap_sampler, min_gap, L):
+    """Move a fraction of spheres along the line to their nearest neighbour so
+    that their surface gap becomes gap_sampler(); moves that would bring any
+    other pair below min_gap are rejected (the sphere then stays put)."""
+    c = c.copy()
+    n = len(radii)
+    chosen = rng.choice(n, size=int(round(frac * n)), replace=False)
+    for i in chosen:
+        d = np.linalg.norm(c - c[i], axis=1) - radii - radii[i]
+        d[i] = np.inf
+        j = int(np.argmin(d))
+        g = gap_sampler()
+        u = c[i] - c[j]
+        u /= np.linalg.norm(u)
+        x = c[j] + u * (radii[i] + radii[j] + g)
+        dd = np.linalg.norm(c - x, axis=1) - radii - radii[i]
+        dd[i] = np.inf
+        dd[j] = np.inf
+        if np.all(dd >= min_gap):
+            c[i] = x
+    return c
+
+
+def mobility_8(seed=0):
+    rng = np.random.default_rng(seed)
+    radii = np.ones(8)
+    c = rsa(rng, radii, 12.0, lambda ai, ak: 0.5)
+    F = rng.normal(size=(8, 3))
+    T = rng.normal(size=(8, 3))
+    return dict(name="mobility_8", centres=c, radii=radii, p=6, forces=F, torques=T, tol=1e-10)
+
+
+def resistance_256(seed=1):
+    rng = np.random.default_rng(seed)
+    n = 256
+    radii = np.ones(n)
+    L = (n * 4.0 / 3.0 * math.pi / 0.10) ** (1.0 / 3.0)
+    c = rsa(rng, radii, L, lambda ai, ak: 0.05)
+    c = push_gaps(rng, c, radii, 0.20, lambda: rng.uniform(0.05, 0.2), 0.05, L)
+    G = np.zeros((3, 3))
+    G[0, 1] = 1.0
+    return dict(name="resistance_256", centres=c, radii=radii, p=10, vel=np.zeros((n, 3)),
+                omega=np.zeros((n, 3)), u0=np.zeros(3), G=G, tol=1e-8)
+
+
+def small_suspension(n, p, seed, box=None, radius_range=(1.0, 1.0), min_gap=0.05, push=0.3,
+                     gap_range=(0.05, 0.3)):
+    """A small random suspension for parity tests: RSA in a cube sized for a
+    volume fraction near 0.1, then a fraction `push` of spheres moved to gaps
+    U[gap_range] so that near pairs exist."""
+    rng = np.random.default_rng(seed)
+    radii = rng.uniform(radius_range[0], radius_range[1], size=n)
+    if box is None:
+        box = (np.sum(4.0 / 3.0 * math.pi * radii ** 3) / 0.10) ** (1.0 / 3.0) + 2.0
+    c = rsa(rng, radii, box, lambda ai, ak: min_gap)
+    if push > 0:
+        c = push_gaps(rng, c, radii, push, lambda: rng.uniform(*gap_range), min_gap, box)
+    return dict(centres=c, radii=radii, p=p)
+
+
+def batched_512(seed=2, n_problems=512):
+    rng = np.random.default_rng(seed)
+    probs = []
+    for _ in range(n_problems):
+        n = int(rng.integers(4, 65))
+        p = int(rng.choice([6, 8, 10, 12]))
+        radii = np.exp(rng.uniform(math.log(0.5), math.log(2.0), size=n))
+        L = (np.sum(4.0 / 3.0 * math.pi * radii ** 3) / 0.05) ** (1.0 / 3.0)
+        c = rsa(rng, radii, L, lambda ai, ak: 0.1 * (ai + ak))
+        probs.append(dict(centres=c, radii=radii, p=p, forces=rng.normal(size=(n, 3)),
+                          torques=rng.normal(size=(n, 3))))
+    return probs
+
+
+def dense_1024(seed=3):
+    rng = np.random.default_rng(seed)
+    n = 1024
+    radii = np.ones(n)
+    L = (n * 4.0 / 3.0 * math.pi / 0.30) ** (1.0 / 3.0)
+    c = rsa(rng, radii, L, lambda ai, ak: 0.01)
+    c = push_gaps(rng, c, radii, 1.0, lambda: math.exp(rng.uniform(math.log(0.01), math.log(0.5))), 0.01, L)
+    return dict(name="dense_1024", centres=c, radii=radii, p=12, forces=rng.normal(size=(n, 3)),
+                torques=rng.normal(size=(n, 3)))
+
+
+def large_4096(seed=4):
+    rng = np.random.default_rng(seed)
+    n = 4096
+    radii = rng.uniform(0.8, 1.2, size=n)
+    L = (np.sum(4.0 / 3.0 * math.pi * radii ** 3) / 0.20) ** (1.0 / 3.0)
+    c = rsa(rng, radii, L, lambda ai, ak: 0.01)
+    G = rng.normal(size=(3, 3))
+    G -= np.trace(G) / 3.0 * np.eye(3)
+    return dict(name="large_4096", centres=c, radii=radii, p=12, vel=np.zeros((n, 3)),
+                omega=np.zeros((n, 3)), u0=rng.normal(size=3), G=G)

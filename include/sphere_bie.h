@@ -1,0 +1,161 @@
+/*
+ * sphere_bie.h -- C interface of the GB300 (sm_103a) library for the spectral
+ * boundary integral method for N rigid spheres in Stokes flow
+ * (Corona & Veerapaneni, arXiv:1707.06551).
+ *
+ * Conventions shared by every call
+ *   - Viscosity is 1 (Sec. 5, Eq. 5.1).
+ *   - Each sphere k (centre c_k, radius a_k) carries the (p+1) x (2p+2) grid of
+ *     Eq. 4.2: Gauss-Legendre nodes t_j in cos(theta), j = 0..p, ordered from the
+ *     north pole (theta ascending), and phi_k = 2 pi k / (2p+2).  Node order is
+ *     sphere-major, then latitude j, then longitude k; the node count is
+ *     N = n_spheres (p+1)(2p+2).
+ *   - Densities and nodal outputs are arrays of N x 3 doubles (x, y, z per node,
+ *     row-major).  Per-sphere quantities are n_spheres x 3 doubles.
+ *   - Memory: with opts.mem_kind = 0 every pointer argument is host memory; the
+ *     library copies in and out and returns after the result is on the host.
+ *     With mem_kind = 1 the data pointers of apply/solve calls are device
+ *     pointers on the current CUDA device; work is ordered on opts.stream (or
+ *     the context's own stream if NULL) and the call returns when the result is
+ *     in place (the stream is synchronised).  Geometry passed to
+ *     sphere_bie_create is always host memory.
+ *   - Ownership: the caller owns every array it passes; the context owns all of
+ *     its device memory and frees it in sphere_bie_destroy.
+ *   - Errors: every call returns sbie_status; SBIE_OK == 0.  No exception or
+ *     CUDA error crosses the interface.  sphere_bie_last_error(ctx) returns a
+ *     message for the last failure on that context (a static string for NULL).
+ *     Nothing on any path falls back to the CPU.
+ */
+#ifndef SPHERE_BIE_H
+#define SPHERE_BIE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbie_ctx sbie_ctx;
+
+typedef enum {
+    SBIE_OK = 0,
+    SBIE_ERR_ARG = 1,           /* bad argument (size, p, radius, NULL pointer, NaN) */
+    SBIE_ERR_OVERLAP = 2,       /* two spheres overlap or touch (gap <= 0)          */
+    SBIE_ERR_CUDA = 3,          /* a CUDA runtime call failed                        */
+    SBIE_ERR_OOM = 4,           /* device allocation failed                          */
+    SBIE_ERR_NOT_CONVERGED = 5, /* solve stopped at max_iter; outputs still filled   */
+    SBIE_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                     */
+    SBIE_ERR_NUMERIC = 7        /* NaN/Inf met in a solve                            */
+} sbie_status;
+
+typedef enum {
+    SBIE_FP64 = 0,  /* every kernel in FP64                                          */
+    SBIE_MIXED = 1  /* far field and near-field evaluation in FP32 with compensated
+                       accumulation; tables, coefficients, Arnoldi and the
+                       outer residual in FP64 (iterative refinement)               */
+} sbie_precision;
+
+typedef enum {
+    SBIE_OP_S = 0,          /* sum_k S_k: single layer, Eq. 2.21; self by Theorem 2           */
+    SBIE_OP_D = 1,          /* sum_k D_k: double layer, Eq. 2.21, self = principal value        */
+    SBIE_OP_K = 2,          /* sum_k K_k: traction of the single layer, Eq. 2.22, self = PV     */
+    SBIE_OP_MOBILITY = 3,   /* 1/2 I + sum_k (K_k + L_k), the mobility BIE operator, Eq. 5.8     */
+    SBIE_OP_RESISTANCE = 4  /* 1/2 I + sum_k (D_k + N_k), completed double layer, Eq. 5.19       */
+} sbie_op;
+
+typedef struct {
+    int p;                  /* VSH order (Sec. 2.1); 1 <= p <= 24                              */
+    double eta;             /* close-pair parameter of Eq. 4.5: spheres i != k are "near" when
+                               |c_i - c_k| - a_i - a_k < eta * max(2 a_i, 2 a_k); default 1.0   */
+    int prec;               /* sbie_precision                                                  */
+    double tol;             /* GMRES stop: ||b - A x||_2 / ||b||_2 <= tol (nodal l2)            */
+    int restart;            /* GMRES restart length                                            */
+    int max_iter;           /* total GMRES iterations allowed                                  */
+    int use_learned_precond;/* reserved; must be 0                                             */
+    const char* mlp_weights_path; /* reserved; may be NULL                                     */
+    int mem_kind;           /* 0 host pointers, 1 device pointers                              */
+    void* stream;           /* cudaStream_t for mem_kind = 1, or NULL                          */
+} sbie_opts;
+
+typedef struct {
+    int iters;              /* inner GMRES iterations (all restarts / refinements)             */
+    int restarts;
+    int refinements;        /* outer FP64 residual corrections (SBIE_MIXED)                    */
+    double rel_residual_true; /* ||b - A x|| / ||b|| recomputed with the FP64 operator        */
+    double t_setup_ms, t_solve_ms;
+    long long n_near_pairs; /* directed close pairs (i, k)                                     */
+} sbie_solve_info;
+
+/* Fills *opts with defaults: p = 8, eta = 1, FP64, tol = 1e-8, restart = 60,
+ * max_iter = 600, host memory, NULL stream. */
+sbie_status sphere_bie_default_opts(sbie_opts* opts);
+
+/* Builds the grid (Eq. 4.2), smooth weights (Eq. 4.4), close-pair lists
+ * (Eq. 4.5) and device tables for n_spheres spheres.  centres: host [n][3],
+ * radii: host [n].  Fails with SBIE_ERR_OVERLAP on overlapping spheres and
+ * SBIE_ERR_ARG on bad sizes.  On success *out owns all device memory. */
+sbie_status sphere_bie_create(int n_spheres, const double* centres, const double* radii,
+                              const sbie_opts* opts, sbie_ctx** out);
+
+/* Number of quadrature nodes N = n_spheres (p+1)(2p+2). */
+sbie_status sphere_bie_num_nodes(const sbie_ctx* ctx, long long* n_nodes);
+
+/* Host copies of node positions, outward normals ([N][3] each) and smooth
+ * quadrature weights ([N], Eq. 4.4).  Any pointer may be NULL to skip it. */
+sbie_status sphere_bie_nodes(const sbie_ctx* ctx, double* xyz, double* normals, double* weights);
+
+/* out = A density for the chosen operator, at every node (Sec. 4.3): self term
+ * by VSH analysis, signature and synthesis (Sec. 4.1, Theorem 2); far field by
+ * the smooth quadrature of Eq. 4.4 over well-separated spheres; close pairs by
+ * the exterior expansions of Eqs. 3.6-3.11 and the traction of Eq. 3.18.
+ * density, out: [N][3]; host or device per opts.mem_kind; must not alias.
+ * Precision per opts.prec. */
+sbie_status sphere_bie_apply_operator(sbie_ctx* ctx, sbie_op op, const double* density, double* out);
+
+/* Mobility problem (Problem 2, Eqs. 5.5-5.8): given force F_k and torque T_k
+ * on each sphere ([n][3] each), solve (1/2 I + K + L) mu = -(1/2 I + K) rho
+ * with rho_k = F_k / (4 pi a^2) + 3 / (8 pi a^4) T_k x (x - c_k), evaluate
+ * u = S[mu + rho] on every sphere and return its rigid part: vel_k =
+ * int u / (4 pi a^2) and omega_k = 3 / (8 pi a^4) int (x - c_k) x u.
+ * info may be NULL.  Returns SBIE_ERR_NOT_CONVERGED (outputs still filled)
+ * when the tolerance is not met within max_iter. */
+sbie_status sphere_bie_solve_mobility(sbie_ctx* ctx, const double* forces, const double* torques,
+                                      double* vel, double* omega, sbie_solve_info* info);
+
+/* Resistance problem (Problem 5, Eqs. 5.18-5.19): given rigid motions
+ * (vel_k, omega_k) and an optional background flow u_inf(x) = u0 + G x
+ * (bg_u0: [3] or NULL; bg_grad: G as [3][3] row-major or NULL), solve
+ * (1/2 I + D + N) psi = vel_k + omega_k x (x - c_k) - u_inf(x) and return
+ * forces F_k = int psi and torques T_k = int (y - c_k) x psi (the force and
+ * torque each sphere exerts on the fluid).  bg_u0 / bg_grad are host memory
+ * for either mem_kind. */
+sbie_status sphere_bie_solve_resistance(sbie_ctx* ctx, const double* vel, const double* omega,
+                                        const double* bg_u0, const double* bg_grad,
+                                        double* forces, double* torques, sbie_solve_info* info);
+
+/* Stage timing.  Stages: 0 far field (Eq. 4.4 sum, including the density
+ * pack and the split reduction), 1 close pairs (Sec. 4.1), 2 self term
+ * (analysis, signature, synthesis), 3 completion / rigid-mode terms and
+ * 1/2 I, 4 Arnoldi vector work, 5 other.  ms[s] is the total device time
+ * between CUDA events recorded on the context stream around each launch of
+ * that stage; launches[s] counts them.  far_pairs counts the (target node,
+ * source node) kernel evaluations of the far-field launches. */
+typedef struct {
+    double ms[6];
+    long long launches[6];
+    long long far_pairs;
+} sbie_profile;
+
+/* enable != 0 starts recording (and resets the counters); 0 stops. */
+sbie_status sphere_bie_profile(sbie_ctx* ctx, int enable);
+/* Synchronises the context stream and returns the totals since the last reset. */
+sbie_status sphere_bie_profile_read(sbie_ctx* ctx, sbie_profile* out);
+
+/* Frees every device buffer and the context.  NULL is accepted. */
+sbie_status sphere_bie_destroy(sbie_ctx* ctx);
+
+/* Message for the last failure on ctx (or the last create failure if ctx is NULL). */
+const char* sphere_bie_last_error(const sbie_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPHERE_BIE_H */

@@ -20,7 +20,9 @@ pressure.
 """
 import numpy as np
 
-BLOCK = 512
+def _block(n_src):
+    """Targets per block so that one (targets x sources x 3) temporary stays near 48 MB."""
+    return max(1, min(512, 2_000_000 // max(1, n_src)))
 
 
 def _pairs(xt, ys):
@@ -32,6 +34,7 @@ def _pairs(xt, ys):
 def stokeslet_sum(xt, ys, dens_w):
     """S of the weighted density dens_w (density times weight) at targets xt."""
     out = np.zeros((len(xt), 3))
+    BLOCK = _block(len(ys))
     for b in range(0, len(xt), BLOCK):
         r, r2 = _pairs(xt[b:b + BLOCK], ys)
         rinv = 1.0 / np.sqrt(r2)
@@ -44,6 +47,7 @@ def stokeslet_sum(xt, ys, dens_w):
 def stresslet_sum_D(xt, ys, ny, dens_w):
     """D of the weighted density with SOURCE normals ny."""
     out = np.zeros((len(xt), 3))
+    BLOCK = _block(len(ys))
     for b in range(0, len(xt), BLOCK):
         r, r2 = _pairs(xt[b:b + BLOCK], ys)
         rf = np.einsum("tsi,si->ts", r, dens_w)
@@ -55,6 +59,7 @@ def stresslet_sum_D(xt, ys, ny, dens_w):
 def stresslet_sum_K(xt, nx, ys, dens_w):
     """K of the weighted density with TARGET normals nx (traction of S)."""
     out = np.zeros((len(xt), 3))
+    BLOCK = _block(len(ys))
     for b in range(0, len(xt), BLOCK):
         r, r2 = _pairs(xt[b:b + BLOCK], ys)
         rf = np.einsum("tsi,si->ts", r, dens_w)

@@ -87,11 +87,15 @@ def coefficients(g, dens):
     return [vsh.analysis(dens[g.sl(i)], g.p) for i in range(g.n)]
 
 
-def self_term(g, op, dens, coefs=None):
+def _targets(g, targets):
+    return range(g.n) if targets is None else list(targets)
+
+
+def self_term(g, op, dens, coefs=None, targets=None):
     """Self interaction: synthesis of (signature x coefficients), Sec. 4.1 (Eqs. 4.6-4.7)."""
-    coefs = coefs or coefficients(g, dens)
+    coefs = coefficients(g, dens) if coefs is None else coefs
     out = np.zeros_like(dens)
-    for i in range(g.n):
+    for i in _targets(g, targets):
         c = coefs[i].copy()
         for n in range(g.p + 1):
             lam = _signature(op, n, g.a[i])
@@ -103,11 +107,11 @@ def self_term(g, op, dens, coefs=None):
     return out
 
 
-def far_term(g, op, dens):
+def far_term(g, op, dens, targets=None):
     """Smooth quadrature (Eq. 4.4) over all nodes of well-separated spheres."""
     out = np.zeros_like(dens)
     dw = dens * g.w[:, None]
-    for i in range(g.n):
+    for i in _targets(g, targets):
         excl = set(g.near[i]) | {i}
         src = np.concatenate([np.arange(g.sl(k).start, g.sl(k).stop) for k in range(g.n) if k not in excl]
                              ) if len(excl) < g.n else np.zeros(0, int)
@@ -125,11 +129,11 @@ def far_term(g, op, dens):
     return out
 
 
-def near_term(g, op, dens, coefs=None):
+def near_term(g, op, dens, coefs=None, targets=None):
     """Exterior expansion of each close source sphere at the target nodes (Sec. 4.1)."""
-    coefs = coefs or coefficients(g, dens)
+    coefs = coefficients(g, dens) if coefs is None else coefs
     out = np.zeros_like(dens)
-    for i in range(g.n):
+    for i in _targets(g, targets):
         xt = g.x[g.sl(i)]
         for k in g.near[i]:
             xh = (xt - g.c[k][None, :]) / g.a[k]
@@ -144,11 +148,19 @@ def near_term(g, op, dens, coefs=None):
     return out
 
 
-def layer(g, op, dens):
-    """Raw sum over k of S_k, D_k or K_k at every node (self by its signature)."""
+def layer(g, op, dens, targets=None):
+    """Raw sum over k of S_k, D_k or K_k at every node (self by its signature);
+    with `targets`, only the rows of those target spheres are filled."""
     dens = np.asarray(dens, float).reshape(-1, 3)
-    coefs = coefficients(g, dens)
-    return self_term(g, op, dens, coefs) + far_term(g, op, dens) + near_term(g, op, dens, coefs)
+    if targets is None:
+        coefs = coefficients(g, dens)
+    else:
+        need = set(targets)
+        for i in targets:
+            need |= set(g.near[i])
+        coefs = [vsh.analysis(dens[g.sl(k)], g.p) if k in need else None for k in range(g.n)]
+    return (self_term(g, op, dens, coefs, targets) + far_term(g, op, dens, targets)
+            + near_term(g, op, dens, coefs, targets))
 
 
 def moments(g, dens):
@@ -171,6 +183,22 @@ def completion_N(g, dens):
     for k in range(g.n):
         out += kernels.stokeslet(g.x, g.c[k], M0[k]) + kernels.rotlet(g.x, g.c[k], M1[k])
     return out
+
+
+def apply_at(g, op, dens, targets):
+    """apply() restricted to the nodes of the target spheres `targets` (rows of
+    other spheres are zero); used to check large problems on sampled spheres."""
+    dens = np.asarray(dens, float).reshape(-1, 3)
+    rows = np.concatenate([np.arange(g.sl(i).start, g.sl(i).stop) for i in targets])
+    mask = np.zeros((g.N, 1))
+    mask[rows] = 1.0
+    if op in ("S", "D", "K"):
+        return layer(g, op, dens, targets)
+    if op == "mobility":
+        return mask * (0.5 * dens + rigid_L(g, dens)) + layer(g, "K", dens, targets)
+    if op == "resistance":
+        return mask * (0.5 * dens + completion_N(g, dens)) + layer(g, "D", dens, targets)
+    raise ValueError(op)
 
 
 def rigid_L(g, dens):

@@ -1,0 +1,158 @@
+// Internal declarations of the sphere BIE library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/sphere_bie.h"
+
+namespace sbie {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxP = 24;
+
+enum class Kern { S = 0, D = 1, K = 2 };
+
+// Offsets into the packed FP64 table of one order p (device copy in Ctx::tab).
+struct TabLayout {
+    int p, nlat, nlon, npn;
+    int o_ct, o_st, o_w;       // [nlat]   cos theta_j, sin theta_j, 2 pi lambda_j / (2p+2)
+    int o_cph, o_sph;          // [nlon]   cos phi_k, sin phi_k
+    int o_cmk, o_smk;          // [p+1][nlon] cos(m phi_k), sin(m phi_k)
+    int o_P, o_dP, o_mS;       // [p+1 (m)][p+1 (n)][nlat]: Pbar_n^m, d/dtheta Pbar_n^m, m Pbar_n^m / sin
+    int total;
+};
+
+TabLayout tab_layout(int p);
+// Fills host table (size layout.total) for order p: Gauss-Legendre grid and
+// normalised associated Legendre functions (normalised recurrences).
+void build_tables(int p, std::vector<double>& host);
+
+// Real solid-harmonic basis used by the close-pair kernels: functions
+// Re/Im J_nm, J_nm = P_n^m(cos th) e^{i m ph} / r^{n+1} (no Condon-Shortley),
+// ordered m-major: for m = 0..L, for n = m..L: Re (m >= 1: Re, Im).
+__host__ __device__ inline int sh_offset_m(int L, int m) {
+    // entries before order m
+    if (m == 0) return 0;
+    // (L+1) for m = 0, then 2 (L+1-mm) for mm = 1..m-1
+    return (L + 1) + 2 * ((m - 1) * (L + 1) - (m - 1) * m / 2);
+}
+__host__ __device__ inline int sh_index(int L, int n, int m, int part) {
+    if (m == 0) return n;
+    return sh_offset_m(L, m) + 2 * (n - m) + part;
+}
+__host__ __device__ inline int sh_count(int L) { return (L + 1) * (L + 1); }
+
+// Channels per close-pair source expansion.
+constexpr int kVelChannels = 10;   // grad Pa (3), grad Pb (3), Pc (1), grad Pd (3)
+constexpr int kTracChannels = 26;  // hess Pa (6), grad Pb (3), hess Pb (6), Pc (1), grad Pc (3), hess Pd (6), Pe (1)
+
+struct FarTune {
+    int threads;  // threads per CTA (multiple of 32)
+    int tpt;      // targets per thread (1, 2 or 4)
+    int split;    // source-range splits (partial sums reduced afterwards)
+    int tile;     // sources staged per tile
+};
+
+struct Profile {
+    bool on = false;
+    double ms[8] = {0};
+    long long launches[8] = {0};
+    long long pairs_far = 0;
+};
+enum Stage { ST_FAR = 0, ST_NEAR = 1, ST_SELF = 2, ST_COMPL = 3, ST_BLAS = 4, ST_OTHER = 5 };
+
+}  // namespace sbie
+
+struct sbie_ctx {
+    int n = 0, p = 0, nlat = 0, nlon = 0, npn = 0;
+    long long N = 0;
+    sbie_opts opts{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+
+    // host geometry
+    std::vector<double> h_c, h_a;
+    std::vector<int> h_near_ptr, h_near_idx;
+    long long n_near = 0;
+
+    // device geometry
+    double* d_c = nullptr;       // [n][3]
+    double* d_a = nullptr;       // [n]
+    double* d_x = nullptr;       // [N][4]  position (x, y, z, weight)
+    float4* d_xhi = nullptr;     // [N] float hi of position, .w = weight
+    float4* d_xlo = nullptr;     // [N] float lo of position
+    float4* d_nrm = nullptr;     // [N] outward normal (float)
+    double* d_nrm64 = nullptr;   // [N][4] outward normal (double)
+    int* d_sph = nullptr;        // [N] sphere index of each node
+    int* d_near_ptr = nullptr;   // [n+1] CSR of close pairs by target sphere
+    int* d_near_idx = nullptr;
+    double* d_tab = nullptr;
+    sbie::TabLayout tl{};
+
+    // scratch (owned)
+    double* d_coef = nullptr;    // [n][3][p+1][p+1][2]  VSH coefficients of the last analysed density
+    double* d_chan = nullptr;    // [n][sh_count(p+2)][kTracChannels]  close-pair expansions
+    float* d_chanf = nullptr;    // float copy
+    double* d_mom = nullptr;     // [n][6] moments int psi, int (y - c) x psi
+    double* d_part = nullptr;    // far-field partials [split][N][3] (double)
+    size_t part_cap = 0;
+    double4* d_src64 = nullptr;  // [N] density x weight (double)
+    float4* d_srcf = nullptr;    // [N] density x weight (float)
+    double* d_in = nullptr;      // [N][3] host-staged inputs
+    double* d_out = nullptr;     // [N][3]
+    double* d_tmp = nullptr;     // [N][3]
+    double* d_tmp2 = nullptr;    // [N][3]
+    double* d_small = nullptr;   // [n][3] x 4 per-sphere small arrays
+    double* d_red = nullptr;     // reduction scratch
+    double* h_red = nullptr;     // pinned host mirror of reduction results
+    // Krylov space
+    double* d_V = nullptr;       // [restart+1][3N]
+    double* d_xsol = nullptr;    // [3N]
+    double* d_rhs = nullptr;     // [3N]
+    double* d_res = nullptr;     // [3N]
+    int krylov_m = 0;
+
+    sbie::FarTune tune64{}, tune32{};
+    sbie::Profile prof;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[8];
+    int prof_used[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace sbie {
+
+// --- kernels launchers (each returns cudaError_t of the launch) ---
+// self.cu
+cudaError_t launch_self(sbie_ctx* c, Kern op, const double* dens, double* out, bool accumulate, bool write_coef);
+cudaError_t launch_analysis_only(sbie_ctx* c, const double* dens);
+// far.cu
+cudaError_t launch_pack(sbie_ctx* c, const double* dens, bool f32);
+cudaError_t launch_far(sbie_ctx* c, Kern op, bool f32, double* out);
+long long far_pairs(const sbie_ctx* c);
+// near.cu
+cudaError_t launch_near(sbie_ctx* c, Kern op, bool f32, double* out);
+// compl.cu
+cudaError_t launch_moments(sbie_ctx* c, const double* dens);
+cudaError_t launch_completion(sbie_ctx* c, bool f32, double* out);
+cudaError_t launch_finalize(sbie_ctx* c, int op, const double* dens, double* out);
+cudaError_t launch_rho(sbie_ctx* c, const double* F, const double* T, double* rho);
+cudaError_t launch_rigid_projection(sbie_ctx* c, const double* u, double* vel, double* omega);
+cudaError_t launch_resistance_rhs(sbie_ctx* c, const double* vel, const double* omega, const double* u0,
+                                  const double* G, double* b);
+cudaError_t launch_geometry(sbie_ctx* c);
+// blas.cu (FP64 vectors of length n)
+cudaError_t blas_dots(sbie_ctx* c, const double* V, int k, long long ld, const double* w, long long n, double* out_host);
+cudaError_t blas_gemv_sub(sbie_ctx* c, const double* V, int k, long long ld, const double* h_dev, double* w, long long n);
+cudaError_t blas_axpy(sbie_ctx* c, double a, const double* x, double* y, long long n);
+cudaError_t blas_scale_copy(sbie_ctx* c, double a, const double* x, double* y, long long n);
+cudaError_t blas_lincomb(sbie_ctx* c, double a, const double* x, double b, const double* y, double* out, long long n);
+cudaError_t blas_gemv_add(sbie_ctx* c, const double* V, int k, long long ld, const double* y_dev, double* x, long long n);
+
+}  // namespace sbie

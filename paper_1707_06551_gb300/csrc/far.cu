@@ -1,0 +1,371 @@
+// Far field: the smooth quadrature of Eq. 4.4 applied to the Stokeslet
+// (Eq. 2.19), the double layer (Eq. 2.21, sign of Theorem 2) or the traction of
+// the single layer (Eq. 2.22) over every source node of every sphere that is
+// well separated from the target sphere (Eq. 4.5).  This is the dense all-pairs
+// Nystrom sum; the paper hands it to an FMM.
+//
+// Design: one CTA owns the nodes of one target sphere (split into `chunks` if
+// the sphere has more nodes than the CTA has target slots).  Source nodes are
+// staged through shared memory in tiles; while staging, a source whose sphere
+// is the target sphere or one of its close partners gets zero weight (a
+// per-CTA bitmask over spheres), so the inner pair loop carries no mask.  The
+// source range can be split over gridDim.y CTAs whose partial sums are added
+// in a fixed order by far_reduce (deterministic).
+//
+// FP32 variant: positions are held as float hi + lo pairs and staged relative
+// to the target sphere's centre, so the difference x - y keeps relative FP32
+// accuracy; each tile's FP32 partial sum is added to the running total with
+// Neumaier's compensated summation.
+#include <algorithm>
+
+#include "common.h"
+
+namespace sbie {
+
+struct FarArgs {
+    int n, npn, chunks, tile;
+    long long N, split_len;
+    const float4* __restrict__ xhi;
+    const float4* __restrict__ xlo;
+    const float4* __restrict__ nrm;
+    const float4* __restrict__ srcf;
+    const double4* __restrict__ x64;
+    const double4* __restrict__ nrm64;
+    const double4* __restrict__ src64;
+    const double* __restrict__ c;
+    const int* __restrict__ sph;
+    const int* __restrict__ near_ptr;
+    const int* __restrict__ near_idx;
+    double* __restrict__ part;  // [split][N][3]
+};
+
+__device__ __forceinline__ void build_flags(const FarArgs& a, int sphere, unsigned* flags) {
+    const int nw = (a.n + 31) >> 5;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) flags[i] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) atomicOr(&flags[sphere >> 5], 1u << (sphere & 31));
+    for (int e = a.near_ptr[sphere] + threadIdx.x; e < a.near_ptr[sphere + 1]; e += blockDim.x) {
+        int k = a.near_idx[e];
+        atomicOr(&flags[k >> 5], 1u << (k & 31));
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void neumaier(float& sum, float& comp, float v) {
+    float t = sum + v;
+    if (fabsf(sum) >= fabsf(v))
+        comp += (sum - t) + v;
+    else
+        comp += (v - t) + sum;
+    sum = t;
+}
+
+template <int OP, int TPT>
+__global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
+    constexpr int NV = (OP == (int)Kern::D) ? 3 : 2;
+    const int sphere = blockIdx.x / a.chunks, chunk = blockIdx.x - sphere * a.chunks;
+    const int split = blockIdx.y;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    extern __shared__ float4 smem4[];
+    float4* s_pos = smem4;
+    float4* s_den = smem4 + a.tile;
+    float4* s_nrm = smem4 + 2 * a.tile;
+    unsigned* flags = reinterpret_cast<unsigned*>(smem4 + NV * a.tile);
+    build_flags(a, sphere, flags);
+
+    const double cx = a.c[3 * sphere], cy = a.c[3 * sphere + 1], cz = a.c[3 * sphere + 2];
+    const float chx = (float)cx, chy = (float)cy, chz = (float)cz;
+    const float clx = (float)(cx - (double)chx), cly = (float)(cy - (double)chy), clz = (float)(cz - (double)chz);
+
+    float tx[TPT], ty[TPT], tz[TPT], tnx[TPT], tny[TPT], tnz[TPT];
+    long long tnode[TPT];
+    bool tval[TPT];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        int q = chunk * (bd * TPT) + t * bd + tid;
+        tval[t] = q < a.npn;
+        long long node = (long long)sphere * a.npn + (tval[t] ? q : a.npn - 1);
+        tnode[t] = node;
+        float4 h = a.xhi[node], l = a.xlo[node];
+        tx[t] = (h.x - chx) + (l.x - clx);
+        ty[t] = (h.y - chy) + (l.y - cly);
+        tz[t] = (h.z - chz) + (l.z - clz);
+        if (OP == (int)Kern::K) {
+            float4 nn = a.nrm[node];
+            tnx[t] = nn.x; tny[t] = nn.y; tnz[t] = nn.z;
+        } else {
+            tnx[t] = tny[t] = tnz[t] = 0.f;
+        }
+    }
+    float sum[TPT][3], cmp[TPT][3];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sum[t][d] = cmp[t][d] = 0.f;
+
+    const long long b0 = (long long)split * a.split_len;
+    const long long b1 = min(a.N, b0 + a.split_len);
+    for (long long base = b0; base < b1; base += a.tile) {
+        __syncthreads();
+        for (int j = tid; j < a.tile; j += bd) {
+            long long s = base + j;
+            float4 P = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 0.f);
+            float4 F = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 Nn = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (s < b1) {
+                int k = a.sph[s];
+                if (!((flags[k >> 5] >> (k & 31)) & 1u)) {
+                    float4 h = a.xhi[s], l = a.xlo[s];
+                    P = make_float4((h.x - chx) + (l.x - clx), (h.y - chy) + (l.y - cly), (h.z - chz) + (l.z - clz), 0.f);
+                    F = a.srcf[s];
+                    if (OP == (int)Kern::D) Nn = a.nrm[s];
+                }
+            }
+            s_pos[j] = P;
+            s_den[j] = F;
+            if (OP == (int)Kern::D) s_nrm[j] = Nn;
+        }
+        __syncthreads();
+        float acc[TPT][3];
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < a.tile; ++j) {
+            const float4 P = s_pos[j];
+            const float4 F = s_den[j];
+            float4 Nn;
+            if (OP == (int)Kern::D) Nn = s_nrm[j];
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                float dx = tx[t] - P.x, dy = ty[t] - P.y, dz = tz[t] - P.z;
+                float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                float ri = rsqrtf(r2);
+                float ri2 = ri * ri;
+                float rf = fmaf(dz, F.z, fmaf(dy, F.y, dx * F.x));
+                if (OP == (int)Kern::S) {
+                    float s3 = rf * ri * ri2;
+                    acc[t][0] = fmaf(dx, s3, fmaf(F.x, ri, acc[t][0]));
+                    acc[t][1] = fmaf(dy, s3, fmaf(F.y, ri, acc[t][1]));
+                    acc[t][2] = fmaf(dz, s3, fmaf(F.z, ri, acc[t][2]));
+                } else {
+                    float rn;
+                    if (OP == (int)Kern::D)
+                        rn = fmaf(dz, Nn.z, fmaf(dy, Nn.y, dx * Nn.x));
+                    else
+                        rn = fmaf(dz, tnz[t], fmaf(dy, tny[t], dx * tnx[t]));
+                    float s5 = (rf * rn) * (ri2 * ri2) * ri;
+                    acc[t][0] = fmaf(dx, s5, acc[t][0]);
+                    acc[t][1] = fmaf(dy, s5, acc[t][1]);
+                    acc[t][2] = fmaf(dz, s5, acc[t][2]);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < TPT; ++t)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) neumaier(sum[t][d], cmp[t][d], acc[t][d]);
+    }
+    double* out = a.part + (size_t)split * a.N * 3;
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        if (!tval[t]) continue;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) out[tnode[t] * 3 + d] = (double)sum[t][d] + (double)cmp[t][d];
+    }
+}
+
+template <int OP, int TPT>
+__global__ void __launch_bounds__(256) far_f64_kernel(FarArgs a) {
+    constexpr int NV = (OP == (int)Kern::D) ? 3 : 2;
+    const int sphere = blockIdx.x / a.chunks, chunk = blockIdx.x - sphere * a.chunks;
+    const int split = blockIdx.y;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    extern __shared__ double4 smem8[];
+    double4* s_pos = smem8;
+    double4* s_den = smem8 + a.tile;
+    double4* s_nrm = smem8 + 2 * a.tile;
+    unsigned* flags = reinterpret_cast<unsigned*>(smem8 + NV * a.tile);
+    build_flags(a, sphere, flags);
+
+    double tx[TPT], ty[TPT], tz[TPT], tnx[TPT], tny[TPT], tnz[TPT];
+    long long tnode[TPT];
+    bool tval[TPT];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        int q = chunk * (bd * TPT) + t * bd + tid;
+        tval[t] = q < a.npn;
+        long long node = (long long)sphere * a.npn + (tval[t] ? q : a.npn - 1);
+        tnode[t] = node;
+        double4 x = a.x64[node];
+        tx[t] = x.x; ty[t] = x.y; tz[t] = x.z;
+        if (OP == (int)Kern::K) {
+            double4 nn = a.nrm64[node];
+            tnx[t] = nn.x; tny[t] = nn.y; tnz[t] = nn.z;
+        } else {
+            tnx[t] = tny[t] = tnz[t] = 0.0;
+        }
+    }
+    double acc[TPT][3];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = 0.0;
+    const double far_off = 1.0e6;
+    const long long b0 = (long long)split * a.split_len;
+    const long long b1 = min(a.N, b0 + a.split_len);
+    for (long long base = b0; base < b1; base += a.tile) {
+        __syncthreads();
+        for (int j = tid; j < a.tile; j += bd) {
+            long long s = base + j;
+            double4 P = make_double4(tx[0] + far_off, ty[0] + far_off, tz[0] + far_off, 0.0);
+            double4 F = make_double4(0, 0, 0, 0), Nn = make_double4(0, 0, 0, 0);
+            if (s < b1) {
+                int k = a.sph[s];
+                if (!((flags[k >> 5] >> (k & 31)) & 1u)) {
+                    P = a.x64[s];
+                    F = a.src64[s];
+                    if (OP == (int)Kern::D) Nn = a.nrm64[s];
+                }
+            }
+            s_pos[j] = P;
+            s_den[j] = F;
+            if (OP == (int)Kern::D) s_nrm[j] = Nn;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int j = 0; j < a.tile; ++j) {
+            const double4 P = s_pos[j];
+            const double4 F = s_den[j];
+            double4 Nn;
+            if (OP == (int)Kern::D) Nn = s_nrm[j];
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                double dx = tx[t] - P.x, dy = ty[t] - P.y, dz = tz[t] - P.z;
+                double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+                double ri = rsqrt(r2);
+                double ri2 = ri * ri;
+                double rf = fma(dz, F.z, fma(dy, F.y, dx * F.x));
+                if (OP == (int)Kern::S) {
+                    double s3 = rf * ri * ri2;
+                    acc[t][0] = fma(dx, s3, fma(F.x, ri, acc[t][0]));
+                    acc[t][1] = fma(dy, s3, fma(F.y, ri, acc[t][1]));
+                    acc[t][2] = fma(dz, s3, fma(F.z, ri, acc[t][2]));
+                } else {
+                    double rn;
+                    if (OP == (int)Kern::D)
+                        rn = fma(dz, Nn.z, fma(dy, Nn.y, dx * Nn.x));
+                    else
+                        rn = fma(dz, tnz[t], fma(dy, tny[t], dx * tnx[t]));
+                    double s5 = (rf * rn) * (ri2 * ri2) * ri;
+                    acc[t][0] = fma(dx, s5, acc[t][0]);
+                    acc[t][1] = fma(dy, s5, acc[t][1]);
+                    acc[t][2] = fma(dz, s5, acc[t][2]);
+                }
+            }
+        }
+    }
+    double* out = a.part + (size_t)split * a.N * 3;
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        if (!tval[t]) continue;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) out[tnode[t] * 3 + d] = acc[t][d];
+    }
+}
+
+__global__ void far_reduce(const double* __restrict__ part, int split, long long n3, double scale,
+                           double* __restrict__ out) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    double s = 0.0;
+    for (int k = 0; k < split; ++k) s += part[(size_t)k * n3 + i];
+    out[i] = scale * s;
+}
+
+__global__ void pack_kernel(const double* __restrict__ dens, const double* __restrict__ x64, long long N,
+                            float4* __restrict__ srcf, double4* __restrict__ src64) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double w = x64[4 * i + 3];
+    double fx = dens[3 * i] * w, fy = dens[3 * i + 1] * w, fz = dens[3 * i + 2] * w;
+    if (srcf) srcf[i] = make_float4((float)fx, (float)fy, (float)fz, 0.f);
+    if (src64) src64[i] = make_double4(fx, fy, fz, 0.0);
+}
+
+cudaError_t launch_pack(sbie_ctx* c, const double* dens, bool f32) {
+    int th = 256;
+    long long blocks = (c->N + th - 1) / th;
+    pack_kernel<<<(unsigned)blocks, th, 0, c->stream>>>(dens, c->d_x, c->N, f32 ? c->d_srcf : nullptr,
+                                                        f32 ? nullptr : c->d_src64);
+    return cudaGetLastError();
+}
+
+long long far_pairs(const sbie_ctx* c) {
+    long long tot = 0;
+    for (int i = 0; i < c->n; ++i) {
+        long long excl = 1 + (c->h_near_ptr[i + 1] - c->h_near_ptr[i]);
+        tot += (long long)c->npn * (c->N - excl * c->npn);
+    }
+    return tot;
+}
+
+template <int OP, int TPT>
+static cudaError_t launch_far_t(sbie_ctx* c, const FarTune& tu, bool f32, const FarArgs& a) {
+    dim3 grid(c->n * a.chunks, tu.split);
+    int nv = (OP == (int)Kern::D) ? 3 : 2;
+    size_t words = ((c->n + 31) / 32) * sizeof(unsigned);
+    if (f32) {
+        size_t sm = (size_t)nv * tu.tile * sizeof(float4) + words;
+        if (sm > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(far_f32_kernel<OP, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+        }
+        far_f32_kernel<OP, TPT><<<grid, tu.threads, sm, c->stream>>>(a);
+    } else {
+        size_t sm = (size_t)nv * tu.tile * sizeof(double4) + words;
+        if (sm > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(far_f64_kernel<OP, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+        }
+        far_f64_kernel<OP, TPT><<<grid, tu.threads, sm, c->stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <int OP>
+static cudaError_t launch_far_op(sbie_ctx* c, const FarTune& tu, bool f32, const FarArgs& a) {
+    switch (tu.tpt) {
+        case 1: return launch_far_t<OP, 1>(c, tu, f32, a);
+        case 2: return launch_far_t<OP, 2>(c, tu, f32, a);
+        default: return launch_far_t<OP, 4>(c, tu, f32, a);
+    }
+}
+
+cudaError_t launch_far(sbie_ctx* c, Kern op, bool f32, double* out) {
+    const FarTune& tu = f32 ? c->tune32 : c->tune64;
+    FarArgs a;
+    a.n = c->n;
+    a.npn = c->npn;
+    a.N = c->N;
+    a.tile = tu.tile;
+    a.chunks = (c->npn + tu.threads * tu.tpt - 1) / (tu.threads * tu.tpt);
+    long long per = (c->N + tu.split - 1) / tu.split;
+    a.split_len = ((per + tu.tile - 1) / tu.tile) * tu.tile;
+    a.xhi = c->d_xhi; a.xlo = c->d_xlo; a.nrm = c->d_nrm; a.srcf = c->d_srcf;
+    a.x64 = reinterpret_cast<const double4*>(c->d_x);
+    a.nrm64 = reinterpret_cast<const double4*>(c->d_nrm64);
+    a.src64 = c->d_src64;
+    a.c = c->d_c; a.sph = c->d_sph; a.near_ptr = c->d_near_ptr; a.near_idx = c->d_near_idx;
+    a.part = c->d_part;
+    cudaError_t e;
+    switch (op) {
+        case Kern::S: e = launch_far_op<(int)Kern::S>(c, tu, f32, a); break;
+        case Kern::D: e = launch_far_op<(int)Kern::D>(c, tu, f32, a); break;
+        default: e = launch_far_op<(int)Kern::K>(c, tu, f32, a); break;
+    }
+    if (e != cudaSuccess) return e;
+    double scale = (op == Kern::S) ? 1.0 / (8.0 * kPi) : (op == Kern::D ? 3.0 / (4.0 * kPi) : -3.0 / (4.0 * kPi));
+    long long n3 = c->N * 3;
+    far_reduce<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(c->d_part, tu.split, n3, scale, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sbie

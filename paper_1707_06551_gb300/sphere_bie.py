@@ -1,0 +1,238 @@
+"""ctypes binding of include/sphere_bie.h (argument marshalling only).
+
+Every function has the C name and forwards to libsphere_bie.so; arrays are
+numpy float64 (host memory, opts.mem_kind = 0) or torch float64 CUDA tensors
+(device memory, opts.mem_kind = 1), passed as raw pointers.  If the library
+has not been built this module raises; there is no other implementation to
+fall back to.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsphere_bie.so")
+
+SBIE_OK, SBIE_ERR_ARG, SBIE_ERR_OVERLAP, SBIE_ERR_CUDA, SBIE_ERR_OOM = 0, 1, 2, 3, 4
+SBIE_ERR_NOT_CONVERGED, SBIE_ERR_TIMEOUT, SBIE_ERR_NUMERIC = 5, 6, 7
+STATUS_NAMES = {0: "SBIE_OK", 1: "SBIE_ERR_ARG", 2: "SBIE_ERR_OVERLAP", 3: "SBIE_ERR_CUDA", 4: "SBIE_ERR_OOM",
+                5: "SBIE_ERR_NOT_CONVERGED", 6: "SBIE_ERR_TIMEOUT", 7: "SBIE_ERR_NUMERIC"}
+SBIE_FP64, SBIE_MIXED = 0, 1
+SBIE_OP_S, SBIE_OP_D, SBIE_OP_K, SBIE_OP_MOBILITY, SBIE_OP_RESISTANCE = 0, 1, 2, 3, 4
+OPS = {"S": 0, "D": 1, "K": 2, "mobility": 3, "resistance": 4}
+STAGES = ("far", "near", "self", "completion", "arnoldi", "other")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("eta", ctypes.c_double), ("prec", ctypes.c_int), ("tol", ctypes.c_double),
+                ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("use_learned_precond", ctypes.c_int),
+                ("mlp_weights_path", ctypes.c_char_p), ("mem_kind", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("rel_residual_true", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
+                ("t_solve_ms", ctypes.c_double), ("n_near_pairs", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_longlong * 6), ("far_pairs", ctypes.c_longlong)]
+
+
+class SphereBIEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.sphere_bie_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        L.sphere_bie_create.argtypes = [ctypes.c_int, _P, _P, ctypes.POINTER(Opts), ctypes.POINTER(_P)]
+        L.sphere_bie_num_nodes.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong)]
+        L.sphere_bie_nodes.argtypes = [_P, _P, _P, _P]
+        L.sphere_bie_apply_operator.argtypes = [_P, ctypes.c_int, _P, _P]
+        L.sphere_bie_solve_mobility.argtypes = [_P, _P, _P, _P, _P, ctypes.POINTER(SolveInfo)]
+        L.sphere_bie_solve_resistance.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(SolveInfo)]
+        L.sphere_bie_destroy.argtypes = [_P]
+        L.sphere_bie_last_error.argtypes = [_P]
+        L.sphere_bie_last_error.restype = ctypes.c_char_p
+        L.sphere_bie_profile.argtypes = [_P, ctypes.c_int]
+        L.sphere_bie_profile_read.argtypes = [_P, ctypes.POINTER(Profile)]
+        for f in ("sphere_bie_default_opts", "sphere_bie_create", "sphere_bie_num_nodes", "sphere_bie_nodes",
+                  "sphere_bie_apply_operator", "sphere_bie_solve_mobility", "sphere_bie_solve_resistance",
+                  "sphere_bie_destroy", "sphere_bie_profile", "sphere_bie_profile_read"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a, nullable=False):
+    """Raw pointer of a C-contiguous float64 numpy array or torch tensor."""
+    if a is None:
+        if nullable:
+            return None
+        raise ValueError("array required")
+    if hasattr(a, "data_ptr"):  # torch tensor
+        if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+            raise ValueError("torch tensors must be contiguous float64")
+        return ctypes.c_void_p(a.data_ptr())
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+        raise ValueError("numpy arrays must be C-contiguous float64")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _check(ctx, status, allow=()):
+    if status != SBIE_OK and status not in allow:
+        msg = lib().sphere_bie_last_error(ctx).decode()
+        raise SphereBIEError(status, msg)
+    return status
+
+
+def sphere_bie_default_opts():
+    o = Opts()
+    _check(None, lib().sphere_bie_default_opts(ctypes.byref(o)))
+    return o
+
+
+def make_opts(p, eta=1.0, prec=SBIE_FP64, tol=1e-8, restart=60, max_iter=600, mem_kind=0, stream=None):
+    o = sphere_bie_default_opts()
+    o.p, o.eta, o.prec, o.tol, o.restart, o.max_iter, o.mem_kind = p, eta, prec, tol, restart, max_iter, mem_kind
+    o.stream = stream
+    return o
+
+
+def sphere_bie_create(centres, radii, opts):
+    c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+    a = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
+    if len(c) != len(a):
+        raise ValueError("centres and radii disagree")
+    h = _P()
+    _check(None, lib().sphere_bie_create(len(a), _ptr(c), _ptr(a), ctypes.byref(opts), ctypes.byref(h)))
+    return h
+
+
+def sphere_bie_num_nodes(ctx):
+    n = ctypes.c_longlong()
+    _check(ctx, lib().sphere_bie_num_nodes(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def sphere_bie_nodes(ctx):
+    N = sphere_bie_num_nodes(ctx)
+    x = np.zeros((N, 3))
+    nr = np.zeros((N, 3))
+    w = np.zeros(N)
+    _check(ctx, lib().sphere_bie_nodes(ctx, _ptr(x), _ptr(nr), _ptr(w)))
+    return x, nr, w
+
+
+def sphere_bie_apply_operator(ctx, op, density, out):
+    op = OPS[op] if isinstance(op, str) else int(op)
+    _check(ctx, lib().sphere_bie_apply_operator(ctx, op, _ptr(density), _ptr(out)))
+    return out
+
+
+def sphere_bie_solve_mobility(ctx, forces, torques, vel, omega):
+    info = SolveInfo()
+    st = _check(ctx, lib().sphere_bie_solve_mobility(ctx, _ptr(forces), _ptr(torques), _ptr(vel), _ptr(omega),
+                                                     ctypes.byref(info)), allow=(SBIE_ERR_NOT_CONVERGED,))
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+def sphere_bie_solve_resistance(ctx, vel, omega, bg_u0, bg_grad, forces, torques):
+    info = SolveInfo()
+    u0 = None if bg_u0 is None else np.ascontiguousarray(bg_u0, dtype=np.float64).reshape(3)
+    G = None if bg_grad is None else np.ascontiguousarray(bg_grad, dtype=np.float64).reshape(3, 3)
+    st = _check(ctx, lib().sphere_bie_solve_resistance(ctx, _ptr(vel), _ptr(omega), _ptr(u0, True), _ptr(G, True),
+                                                       _ptr(forces), _ptr(torques), ctypes.byref(info)),
+                allow=(SBIE_ERR_NOT_CONVERGED,))
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+def sphere_bie_destroy(ctx):
+    if ctx:
+        _check(None, lib().sphere_bie_destroy(ctx))
+
+
+def sphere_bie_last_error(ctx=None):
+    return lib().sphere_bie_last_error(ctx).decode()
+
+
+def sphere_bie_profile(ctx, enable):
+    _check(ctx, lib().sphere_bie_profile(ctx, int(enable)))
+
+
+def sphere_bie_profile_read(ctx):
+    p = Profile()
+    _check(ctx, lib().sphere_bie_profile_read(ctx, ctypes.byref(p)))
+    return {"ms": dict(zip(STAGES, list(p.ms))), "launches": dict(zip(STAGES, list(p.launches))),
+            "far_pairs": p.far_pairs}
+
+
+class SphereBIE:
+    """Owning wrapper around a context (host memory interface)."""
+
+    def __init__(self, centres, radii, p, eta=1.0, prec=SBIE_FP64, tol=1e-8, restart=60, max_iter=600):
+        self.opts = make_opts(p, eta, prec, tol, restart, max_iter, 0)
+        self.ctx = sphere_bie_create(centres, radii, self.opts)
+        self.n = len(np.asarray(radii).reshape(-1))
+        self.N = sphere_bie_num_nodes(self.ctx)
+
+    def apply(self, op, density):
+        d = np.ascontiguousarray(density, dtype=np.float64).reshape(-1, 3)
+        out = np.zeros_like(d)
+        return sphere_bie_apply_operator(self.ctx, op, d, out)
+
+    def mobility(self, F, T):
+        F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1, 3)
+        T = np.ascontiguousarray(T, dtype=np.float64).reshape(-1, 3)
+        v = np.zeros_like(F)
+        w = np.zeros_like(T)
+        info = sphere_bie_solve_mobility(self.ctx, F, T, v, w)
+        return v, w, info
+
+    def resistance(self, v, w, u0=None, G=None):
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1, 3)
+        F = np.zeros_like(v)
+        T = np.zeros_like(w)
+        info = sphere_bie_solve_resistance(self.ctx, v, w, u0, G, F, T)
+        return F, T, info
+
+    def nodes(self):
+        return sphere_bie_nodes(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            sphere_bie_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

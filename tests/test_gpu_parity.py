@@ -1,0 +1,182 @@
+"""Parity of the CUDA path (through the C interface) with the FP64 oracle.
+
+Tolerances (normwise: max |gpu - oracle| / max |oracle| over all nodes):
+  * SBIE_FP64 operator applies: 1e-10 (the FP64 bound the method is held to);
+  * SBIE_MIXED operator applies: 2e-5 -- FP32 far field and close-pair
+    evaluation with compensated accumulation, FP64 everywhere else;
+  * solves: outputs (forces, torques, velocities) within 1e-8 relative in FP64
+    and 1e-6 in mixed precision, with the true FP64 residual <= tol.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import operators as ops
+from oracle import solve as osolve
+from paper_1707_06551_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+OPS = ["S", "D", "K", "mobility", "resistance"]
+TOL64 = 1e-10
+TOL32 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def sb():
+    from paper_1707_06551_gb300 import build_lib
+    build_lib.build()
+    from paper_1707_06551_gb300 import sphere_bie
+    return sphere_bie
+
+
+def _err(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+GEOMS = {
+    # several tiles and a ragged tail; close pairs present
+    "mono_p4": dict(n=6, p=4, seed=1, radius_range=(1.0, 1.0)),
+    "poly_p6": dict(n=9, p=6, seed=5, radius_range=(0.5, 1.5)),
+    "tiny_p1": dict(n=3, p=1, seed=2, radius_range=(1.0, 1.0)),
+    "p9_ragged": dict(n=5, p=9, seed=7, radius_range=(0.8, 1.2)),
+}
+
+
+def _geom(name):
+    k = GEOMS[name]
+    w = wl.small_suspension(k["n"], k["p"], k["seed"], radius_range=k["radius_range"])
+    return w["centres"], w["radii"], w["p"]
+
+
+@pytest.mark.parametrize("geom", list(GEOMS))
+@pytest.mark.parametrize("op", OPS)
+def test_apply_fp64_matches_oracle(sb, geom, op):
+    c, a, p = _geom(geom)
+    g = ops.Geometry(c, a, p)
+    dens = np.random.default_rng(3).normal(size=(g.N, 3))
+    ref = ops.apply(g, op, dens)
+    with sb.SphereBIE(c, a, p) as s:
+        out = s.apply(op, dens)
+    assert _err(out, ref) < TOL64
+
+
+@pytest.mark.parametrize("geom", ["mono_p4", "poly_p6"])
+@pytest.mark.parametrize("op", OPS)
+def test_apply_mixed_within_bound(sb, geom, op):
+    c, a, p = _geom(geom)
+    g = ops.Geometry(c, a, p)
+    dens = np.random.default_rng(4).normal(size=(g.N, 3))
+    ref = ops.apply(g, op, dens)
+    with sb.SphereBIE(c, a, p, prec=sb.SBIE_MIXED) as s:
+        out = s.apply(op, dens)
+    assert _err(out, ref) < TOL32
+
+
+@pytest.mark.parametrize("eta", [0.0, 10.0])
+@pytest.mark.parametrize("op", ["S", "D", "K"])
+def test_all_far_and_all_near(sb, eta, op):
+    c, a, p = _geom("mono_p4")
+    g = ops.Geometry(c, a, p, eta=eta)
+    assert g.n_near_pairs() == (0 if eta == 0 else g.n * (g.n - 1))
+    dens = np.random.default_rng(5).normal(size=(g.N, 3))
+    ref = ops.apply(g, op, dens)
+    with sb.SphereBIE(c, a, p, eta=eta) as s:
+        out = s.apply(op, dens)
+    assert _err(out, ref) < TOL64
+
+
+def test_single_sphere_operator(sb):
+    g = ops.Geometry([[0.3, 0.1, -0.2]], [1.3], 5)
+    dens = np.random.default_rng(6).normal(size=(g.N, 3))
+    with sb.SphereBIE(g.c, g.a, 5) as s:
+        for op in OPS:
+            assert _err(s.apply(op, dens), ops.apply(g, op, dens)) < TOL64
+
+
+@pytest.mark.parametrize("a", [0.5, 2.0])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_single_sphere_closed_forms(sb, a, prec):
+    """Drag 6 pi a U and torque 8 pi a^3 Omega (resistance) and their inverse (mobility)."""
+    U = np.array([[1.0, 0.5, -0.3]])
+    W = np.array([[0.2, -0.7, 0.4]])
+    with sb.SphereBIE([[0.3, -0.2, 0.1]], [a], 6, prec=prec, tol=1e-12) as s:
+        F, T, info = s.resistance(U, W)
+        np.testing.assert_allclose(F, 6 * math.pi * a * U, rtol=1e-9)
+        np.testing.assert_allclose(T, 8 * math.pi * a ** 3 * W, rtol=1e-9)
+        v, w, info = s.mobility(6 * math.pi * a * U, 8 * math.pi * a ** 3 * W)
+        np.testing.assert_allclose(v, U, rtol=1e-9)
+        np.testing.assert_allclose(w, W, rtol=1e-9)
+
+
+@pytest.mark.parametrize("prec,tolF", [(0, 1e-8), (1, 1e-6)])
+def test_resistance_solve_matches_oracle(sb, prec, tolF):
+    c, a, p = _geom("poly_p6")
+    g = ops.Geometry(c, a, p)
+    rng = np.random.default_rng(9)
+    v = rng.normal(size=(g.n, 3))
+    w = rng.normal(size=(g.n, 3))
+    u0 = rng.normal(size=3)
+    G = rng.normal(size=(3, 3))
+    Fr, Tr, _ = osolve.solve_resistance(g, v, w, u0, G, tol=1e-12)
+    with sb.SphereBIE(c, a, p, prec=prec, tol=1e-11) as s:
+        F, T, info = s.resistance(v, w, u0, G)
+    assert info["status"] == 0 and info["rel_residual_true"] <= 1e-11
+    assert _err(F, Fr) < tolF and _err(T, Tr) < tolF
+
+
+@pytest.mark.parametrize("prec,tolV", [(0, 1e-8), (1, 1e-6)])
+def test_mobility_8_solve_matches_oracle(sb, prec, tolV):
+    w8 = wl.mobility_8()
+    g = ops.Geometry(w8["centres"], w8["radii"], w8["p"])
+    vr, wr, _ = osolve.solve_mobility(g, w8["forces"], w8["torques"], tol=1e-12)
+    with sb.SphereBIE(w8["centres"], w8["radii"], w8["p"], prec=prec, tol=1e-11) as s:
+        v, w, info = s.mobility(w8["forces"], w8["torques"])
+    assert info["status"] == 0 and info["rel_residual_true"] <= 1e-11
+    assert _err(v, vr) < tolV and _err(w, wr) < tolV
+
+
+def test_resistance_256_sampled_parity(sb):
+    """Full-size resistance workload (256 spheres, p = 10): GPU applies in both
+    precisions against the oracle on sampled target spheres (one of them with
+    close partners), plus a mixed-precision solve meeting the 1e-8 residual."""
+    w = wl.resistance_256()
+    g = ops.Geometry(w["centres"], w["radii"], w["p"])
+    near_counts = [len(x) for x in g.near]
+    sample = [0, int(np.argmax(near_counts)), 200]
+    rows = np.concatenate([np.arange(g.sl(i).start, g.sl(i).stop) for i in sample])
+    dens = np.random.default_rng(11).normal(size=(g.N, 3))
+    ref = ops.apply_at(g, "resistance", dens, sample)[rows]
+    for prec, tol in ((0, TOL64), (1, TOL32)):
+        with sb.SphereBIE(w["centres"], w["radii"], w["p"], prec=prec, tol=w["tol"]) as s:
+            out = s.apply("resistance", dens)[rows]
+            assert _err(out, ref) < tol
+            if prec == 1:
+                F, T, info = s.resistance(w["vel"], w["omega"], w["u0"], w["G"])
+                assert info["status"] == 0 and info["rel_residual_true"] <= w["tol"]
+
+
+def test_not_converged_reports_and_fills(sb):
+    c, a, p = _geom("mono_p4")
+    with sb.SphereBIE(c, a, p, tol=1e-14, max_iter=2) as s:
+        F, T, info = s.resistance(np.ones((len(a), 3)), np.zeros((len(a), 3)))
+    assert info["status"] == sb.SBIE_ERR_NOT_CONVERGED
+    assert info["iters"] == 2 and np.all(np.isfinite(F)) and np.any(F != 0)
+
+
+def test_device_pointer_interface_matches_host(sb):
+    import torch
+    c, a, p = _geom("mono_p4")
+    dens = np.random.default_rng(12).normal(size=(len(a) * (p + 1) * (2 * p + 2), 3))
+    with sb.SphereBIE(c, a, p) as s:
+        ref = s.apply("K", dens)
+    o = sb.make_opts(p, mem_kind=1)
+    ctx = sb.sphere_bie_create(c, a, o)
+    try:
+        d_in = torch.tensor(dens, device="cuda", dtype=torch.float64)
+        d_out = torch.zeros_like(d_in)
+        sb.sphere_bie_apply_operator(ctx, "K", d_in, d_out)
+        assert _err(d_out.cpu().numpy(), ref) < 1e-14
+    finally:
+        sb.sphere_bie_destroy(ctx)

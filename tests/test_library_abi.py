@@ -1,0 +1,91 @@
+"""The C-ABI library builds, loads and exports every function the header
+declares; host-side argument checks run without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1707_06551_gb300 import build_lib
+    build_lib.build()
+    from paper_1707_06551_gb300 import sphere_bie
+    return sphere_bie
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(sphere_bie_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_header_declares_the_interface():
+    names = declared_functions()
+    for f in ("sphere_bie_create", "sphere_bie_apply_operator", "sphere_bie_solve_mobility",
+              "sphere_bie_solve_resistance", "sphere_bie_destroy"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    L = lib.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_default_opts(lib):
+    o = lib.sphere_bie_default_opts()
+    assert (o.p, o.eta, o.prec, o.tol, o.restart, o.max_iter, o.mem_kind) == (8, 1.0, 0, 1e-8, 60, 600, 0)
+
+
+@pytest.mark.parametrize("case,status", [
+    ("overlap", 2), ("p0", 1), ("p25", 1), ("radius", 1), ("nan", 1), ("learned", 1), ("tol", 1), ("empty", 1),
+])
+def test_create_rejects_bad_input_before_any_device_work(lib, case, status):
+    c = np.array([[0.0, 0, 0], [3.0, 0, 0]])
+    a = np.array([1.0, 1.0])
+    o = lib.make_opts(4)
+    if case == "overlap":
+        c[1, 0] = 1.5
+    elif case == "p0":
+        o.p = 0
+    elif case == "p25":
+        o.p = 25
+    elif case == "radius":
+        a[1] = 0.0
+    elif case == "nan":
+        c[0, 1] = np.nan
+    elif case == "learned":
+        o.use_learned_precond = 1
+    elif case == "tol":
+        o.tol = 0.0
+    h = ctypes.c_void_p()
+    n = 0 if case == "empty" else 2
+    st = lib.lib().sphere_bie_create(n, lib._ptr(c), lib._ptr(a), ctypes.byref(o), ctypes.byref(h))
+    assert st == status
+    assert not h.value
+    assert len(lib.sphere_bie_last_error(None)) > 0
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lib.SphereBIEError) as e:
+        lib.sphere_bie_create(np.zeros((1, 3)), np.ones(1), lib.make_opts(3))
+    assert e.value.status == lib.SBIE_ERR_CUDA
+
+
+def test_binding_rejects_wrong_dtypes(lib):
+    with pytest.raises(ValueError):
+        lib._ptr(np.zeros(3, dtype=np.float32))
+    with pytest.raises(ValueError):
+        lib._ptr(np.zeros((3, 3))[:, 0])

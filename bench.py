@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark: GMRES time-to-solve at a 1e-8 relative residual for the
+resistance workload of 256 unit spheres at volume fraction 0.10 (20% pushed to
+gaps 0.05-0.2), VSH order p = 10, in a background shear, mixed precision (FP32
+far field and close-pair evaluation, FP64 residuals), plus the far-field pair
+rate in FP32 and FP64.
+
+One step = one complete solve: right-hand side, GMRES with FP64 iterative
+refinement, forces and torques, with the geometry resident on the device.
+Under torchrun every rank solves its own replica (the solve does not shard);
+the time reported is the maximum over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line on rank 0.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GMRES time-to-solve at 1e-8 rel. residual; far-field pair-interactions/s vs FP64"
+WORKLOAD = "resistance_256"
+FLOP_PER_PAIR = {"S": 28, "D": 30, "K": 30}   # algorithmic flops per (target, source) pair
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+# ncu DRAM traffic (read + write bytes per launch) of the FP32 far-field pair
+# kernel on this workload, keyed by the hash of the far-field source it was
+# measured on; reported only while that source is unchanged.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def far_source_hash():
+    with open(os.path.join(ROOT, "paper_1707_06551_gb300", "csrc", "far.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons, sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.mark = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [p for (t, p) in self.rows if t0 <= t <= t1] or [p for (_, p) in self.rows]
+        if not rows:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[1]) for p in rows if num(p[1]) is not None]
+        mx = [num(p[2]) for p in rows if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in rows for i in range(4) if p[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peak_fp32_tflops(sm_count, mhz):
+    return sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def cpu_baseline(n_sample=8):
+    """Time the oracle as it stands on this host on a bounded sample of the
+    workload: the resistance operator on n_sample target spheres (self, far
+    and close-pair terms) plus the completion flow on all nodes, extrapolated
+    to one full apply; the solve estimate multiplies by the number of applies
+    the FP64 GMRES solve of this workload needs."""
+    code = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from oracle import operators as ops
+from paper_1707_06551_gb300 import workloads as wl
+w = wl.resistance_256()
+g = ops.Geometry(w["centres"], w["radii"], w["p"])
+dens = np.random.default_rng(0).normal(size=(g.N, 3))
+k = int(sys.argv[2])
+targets = list(range(0, g.n, g.n // k))[:k]
+t0 = time.perf_counter(); ops.layer(g, "D", dens, targets); t1 = time.perf_counter()
+ops.completion_N(g, dens); t2 = time.perf_counter()
+print(json.dumps({"t_layer": t1 - t0, "t_compl": t2 - t1, "k": k, "n": g.n}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code, ROOT, str(n_sample)], capture_output=True, text=True, env=env,
+                       timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-500:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    full_apply = d["t_layer"] * d["n"] / d["k"] + d["t_compl"]
+    return {"apply_s": full_apply, "sample_s": d["t_layer"] + d["t_compl"], "k": d["k"], "n": d["n"]}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    t_applies = []
+    for _ in range(max(1, args.warmup) + args.steps):
+        t_applies.append(cpu_baseline())
+    good = [t for t in t_applies[max(1, args.warmup):] if "apply_s" in t]
+    if not good:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle sample failed: " + str(t_applies[-1])}))
+        return
+    applies = REF_FP64_APPLIES
+    per_solve = statistics.mean(t["apply_s"] for t in good) * applies
+    sample = (f"resistance operator (self, far, close pairs) on {good[0]['k']} of {good[0]['n']} target spheres "
+              f"plus the completion flow on all nodes, extrapolated to one apply, x {applies} applies "
+              f"(FP64 GMRES apply count of this workload at tol 1e-8)")
+    line = {"impl": "reference", "metric": METRIC, "value": per_solve, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_spheres": 256, "p": 10, "nodes": 61952},
+            "cpu_baseline": {"value": per_solve, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": per_solve, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# FP64 GMRES applies (iterations + restart residuals + final residual) for
+# resistance_256 at tol 1e-8 on the GPU path; used to scale the oracle's
+# per-apply time to a solve.
+REF_FP64_APPLIES = 84
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1707_06551_gb300 import build_lib
+    if local == 0:
+        build_lib.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1707_06551_gb300 import sphere_bie as sb
+    from paper_1707_06551_gb300 import workloads as wl
+
+    w = wl.resistance_256()
+    n, p = len(w["radii"]), w["p"]
+    prec = sb.SBIE_MIXED if args.prec == "mixed" else sb.SBIE_FP64
+    stream = torch.cuda.Stream()
+    opts = sb.make_opts(p, prec=prec, tol=w["tol"], mem_kind=1, stream=stream.cuda_stream)
+    t_c0 = time.perf_counter()
+    ctx = sb.sphere_bie_create(w["centres"], w["radii"], opts)
+    t_create = time.perf_counter() - t_c0
+    dev = torch.device("cuda", local)
+    vel = torch.tensor(w["vel"], dtype=torch.float64, device=dev)
+    om = torch.tensor(w["omega"], dtype=torch.float64, device=dev)
+    F = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    T = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
+
+    def step():
+        return sb.sphere_bie_solve_resistance(ctx, vel, om, w["u0"], w["G"], F, T)
+
+    infos = []
+    for _ in range(args.warmup):
+        infos.append(step())
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = vis.split(",")[local] if vis and vis.split(",")[0].strip().isdigit() else str(local)
+    sampler = ClockSampler(smi_index)
+    sampler.start()
+    time.sleep(0.5)
+    sb.sphere_bie_profile(ctx, 1)
+    times = []
+    t_wall0 = time.time()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        info = step()
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        infos.append(info)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    prof = sb.sphere_bie_profile_read(ctx)
+    sb.sphere_bie_profile(ctx, 0)
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    t_step = statistics.mean(times)
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    last = infos[-1]
+
+    # far-field kernel roofline (FP32 pair kernel, the hot loop of the solve)
+    l32 = prof["launches"]["far_kernel_f32"]
+    ms32 = prof["ms"]["far_kernel_f32"]
+    pairs32 = prof["far_pairs_f32"]
+    l64 = prof["launches"]["far_kernel_f64"]
+    ms64 = prof["ms"]["far_kernel_f64"]
+    pairs64 = prof["far_pairs_f64"]
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = peak_fp32_tflops(sm_count, clk_max)
+    roof = None
+    if l32 > 0 and ms32 > 0:
+        flop_launch = pairs32 / l32 * FLOP_PER_PAIR["D"]
+        achieved = flop_launch / (ms32 / l32 * 1e-3) / 1e12
+        traffic = NCU_TRAFFIC.get(far_source_hash())
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "far_f32_kernel<D>",
+                "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clk_max:.0f} MHz",
+                "flop_per_pair": FLOP_PER_PAIR["D"], "pairs_per_launch": pairs32 // l32,
+                "ms_per_launch": ms32 / l32}
+    far = {"pairs_per_s_fp32": pairs32 / (ms32 * 1e-3) if ms32 > 0 else None,
+           "pairs_per_s_fp64": pairs64 / (ms64 * 1e-3) if ms64 > 0 else None,
+           "fp64_launches_per_solve": l64 / args.steps, "fp32_launches_per_solve": l32 / args.steps}
+    stage_ms = {k: v / args.steps for k, v in prof["ms"].items()}
+
+    # plain FP64 path on the same workload (comparison; outside the timed region)
+    fp64 = None
+    if not args.no_fp64_compare and prec == sb.SBIE_MIXED:
+        o64 = sb.make_opts(p, prec=sb.SBIE_FP64, tol=w["tol"], mem_kind=1, stream=stream.cuda_stream)
+        c64 = sb.sphere_bie_create(w["centres"], w["radii"], o64)
+        F64 = torch.zeros_like(F)
+        T64 = torch.zeros_like(T)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        i64 = sb.sphere_bie_solve_resistance(c64, vel, om, w["u0"], w["G"], F64, T64)
+        torch.cuda.synchronize()
+        fp64 = {"time_to_solve_s": time.perf_counter() - t0, "iters": i64["iters"],
+                "rel_residual_true": i64["rel_residual_true"],
+                "force_rel_diff_vs_mixed": float((F64 - F).abs().max() / F64.abs().max())}
+        sb.sphere_bie_destroy(c64)
+
+    # end to end through the public API with host buffers: create (geometry
+    # upload, tables, close-pair lists), solve, read forces/torques, destroy
+    e2e_times = []
+    hF = np.zeros((n, 3))
+    hT = np.zeros((n, 3))
+    for _ in range(args.e2e_steps):
+        oh = sb.make_opts(p, prec=prec, tol=w["tol"], mem_kind=0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ch = sb.sphere_bie_create(w["centres"], w["radii"], oh)
+        sb.sphere_bie_solve_resistance(ch, w["vel"], w["omega"], w["u0"], w["G"], hF, hT)
+        sb.sphere_bie_destroy(ch)
+        e2e_times.append(time.perf_counter() - t0)
+    h2d = 8 * (w["centres"].size + w["radii"].size + w["vel"].size + w["omega"].size + 3 + 9)
+    d2h = 8 * (hF.size + hT.size)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline()
+        if "apply_s" in cb:
+            applies = (fp64["iters"] + 2) if fp64 else REF_FP64_APPLIES
+            cpu = {"value": cb["apply_s"] * applies, "unit": "s", "cores": 1, "kind": "oracle",
+                   "sample": (f"resistance operator on {cb['k']} of {cb['n']} target spheres + completion flow on all "
+                              f"nodes ({cb['sample_s']:.1f} s of CPU), extrapolated to one apply ({cb['apply_s']:.1f} s)"
+                              f" x {applies} FP64 GMRES applies")}
+        else:
+            cpu = {"error": cb.get("error")}
+
+    launches_per_step = prof["kernel_launches"] / args.steps
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == sb.SBIE_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_spheres": n, "p": p, "nodes": n * (p + 1) * (2 * p + 2),
+                       "precision": args.prec, "tol": w["tol"], "close_pairs": last["n_near_pairs"],
+                       "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{world}"},
+            "solve": {"iters": last["iters"], "refinements": last["refinements"],
+                      "rel_residual_true": last["rel_residual_true"], "status": last["status"],
+                      "create_s": t_create},
+            "roofline": roof, "far_field": far, "stage_ms_per_step": stage_ms, "fp64_path": fp64,
+            "clocks": clocks, "gpu_launches": int(prof["kernel_launches"]),
+            "gpu_launches_per_step": launches_per_step,
+            "e2e": ({"value": statistics.mean(e2e_times), "unit": "s", "h2d_bytes_per_step": h2d,
+                     "d2h_bytes_per_step": d2h, "includes": "create + solve + destroy, host buffers"}
+                    if e2e_times else None),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    sb.sphere_bie_destroy(ctx)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -131,17 +131,20 @@ sbie_status sphere_bie_solve_resistance(sbie_ctx* ctx, const double* vel, const 
                                         const double* bg_u0, const double* bg_grad,
                                         double* forces, double* torques, sbie_solve_info* info);
 
-/* Stage timing.  Stages: 0 far field (Eq. 4.4 sum, including the density
- * pack and the split reduction), 1 close pairs (Sec. 4.1), 2 self term
- * (analysis, signature, synthesis), 3 completion / rigid-mode terms and
- * 1/2 I, 4 Arnoldi vector work, 5 other.  ms[s] is the total device time
- * between CUDA events recorded on the context stream around each launch of
- * that stage; launches[s] counts them.  far_pairs counts the (target node,
- * source node) kernel evaluations of the far-field launches. */
+/* Stage timing.  Stages: 0 far field (density pack, pair kernel and split
+ * reduction), 1 close pairs (Sec. 4.1), 2 self term (analysis, signature,
+ * synthesis), 3 completion / rigid-mode terms and 1/2 I, 4 Arnoldi vector
+ * work, 5 other, 6 the FP32 far-field pair kernel alone, 7 the FP64 far-field
+ * pair kernel alone.  ms[s] is the total device time between CUDA events
+ * recorded on the context stream around each launch of that stage;
+ * launches[s] counts them.  far_pairs_f32 / _f64 count the (target node,
+ * source node) kernel evaluations of the far-field launches in each
+ * precision; kernel_launches counts every CUDA kernel the context launched. */
 typedef struct {
-    double ms[6];
-    long long launches[6];
-    long long far_pairs;
+    double ms[8];
+    long long launches[8];
+    long long far_pairs_f32, far_pairs_f64;
+    long long kernel_launches;
 } sbie_profile;
 
 /* enable != 0 starts recording (and resets the counters); 0 stops. */

@@ -60,28 +60,6 @@ void free_all(sbie_ctx* c) {
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
-// ---- profiling: CUDA events around each stage launch on the context stream
-struct StageScope {
-    sbie_ctx* c;
-    int stage;
-    int idx = -1;
-    StageScope(sbie_ctx* cc, int st) : c(cc), stage(st) {
-        if (!c->prof.on) return;
-        auto& v = c->prof_events[stage];
-        idx = c->prof_used[stage]++;
-        if (idx >= (int)v.size()) {
-            cudaEvent_t a, b;
-            cudaEventCreate(&a);
-            cudaEventCreate(&b);
-            v.push_back({a, b});
-        }
-        cudaEventRecord(v[idx].first, c->stream);
-    }
-    ~StageScope() {
-        if (idx >= 0) cudaEventRecord(c->prof_events[stage][idx].second, c->stream);
-    }
-};
-
 void choose_tuning(sbie_ctx* c) {
     // targets per thread / threads per CTA: the combination that wastes the
     // fewest target slots per sphere; then enough source splits to give every
@@ -140,7 +118,7 @@ sbie_status apply_dev(sbie_ctx* c, int op, bool f32, const double* in, double* o
         StageScope s(c, ST_FAR);
         CK(launch_pack(c, in, f32));
         CK(launch_far(c, k, f32, out));
-        if (c->prof.on) c->prof.pairs_far += far_pairs(c);
+        if (c->prof.on) (f32 ? c->prof.pairs_f32 : c->prof.pairs_f64) += far_pairs(c);
     }
     {
         StageScope s(c, ST_SELF);
@@ -636,7 +614,8 @@ sbie_status sphere_bie_profile(sbie_ctx* c, int enable) {
         c->prof.launches[s] = 0;
         c->prof_used[s] = 0;
     }
-    c->prof.pairs_far = 0;
+    c->prof.pairs_f32 = c->prof.pairs_f64 = 0;
+    c->prof.kernels0 = c->n_launch;
     return SBIE_OK;
 }
 
@@ -653,11 +632,13 @@ sbie_status sphere_bie_profile_read(sbie_ctx* c, sbie_profile* out) {
         c->prof_used[s] = 0;
     }
     std::memset(out, 0, sizeof(*out));
-    for (int s = 0; s < 6; ++s) {
+    for (int s = 0; s < 8; ++s) {
         out->ms[s] = c->prof.ms[s];
         out->launches[s] = c->prof.launches[s];
     }
-    out->far_pairs = c->prof.pairs_far;
+    out->far_pairs_f32 = c->prof.pairs_f32;
+    out->far_pairs_f64 = c->prof.pairs_f64;
+    out->kernel_launches = c->n_launch - c->prof.kernels0;
     return SBIE_OK;
 }
 

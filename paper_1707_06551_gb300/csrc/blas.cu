@@ -67,8 +67,8 @@ static unsigned grid_for(long long n) {
 
 cudaError_t blas_dots(sbie_ctx* c, const double* V, int k, long long ld, const double* w, long long n, double* out_host) {
     dim3 grid(kDotBlocks, k);
-    dots_partial<<<grid, 256, 0, c->stream>>>(V, k, ld, w, n, c->d_red);
-    dots_final<<<k, 256, 0, c->stream>>>(c->d_red, kDotBlocks, c->d_red + (size_t)kDotBlocks * 256);
+    dots_partial<<<grid, 256, 0, c->stream>>>(V, k, ld, w, n, c->d_red); ++c->n_launch;
+    dots_final<<<k, 256, 0, c->stream>>>(c->d_red, kDotBlocks, c->d_red + (size_t)kDotBlocks * 256); ++c->n_launch;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (out_host) {
@@ -83,17 +83,17 @@ cudaError_t blas_dots(sbie_ctx* c, const double* V, int k, long long ld, const d
 }
 
 cudaError_t blas_gemv_sub(sbie_ctx* c, const double* V, int k, long long ld, const double* h_dev, double* w, long long n) {
-    gemv_kernel<<<grid_for(n), 256, 0, c->stream>>>(V, k, ld, h_dev, -1.0, w, n);
+    gemv_kernel<<<grid_for(n), 256, 0, c->stream>>>(V, k, ld, h_dev, -1.0, w, n); ++c->n_launch;
     return cudaGetLastError();
 }
 
 cudaError_t blas_gemv_add(sbie_ctx* c, const double* V, int k, long long ld, const double* y_dev, double* x, long long n) {
-    gemv_kernel<<<grid_for(n), 256, 0, c->stream>>>(V, k, ld, y_dev, 1.0, x, n);
+    gemv_kernel<<<grid_for(n), 256, 0, c->stream>>>(V, k, ld, y_dev, 1.0, x, n); ++c->n_launch;
     return cudaGetLastError();
 }
 
 cudaError_t blas_lincomb(sbie_ctx* c, double a, const double* x, double b, const double* y, double* out, long long n) {
-    lincomb_kernel<<<grid_for(n), 256, 0, c->stream>>>(a, x, b, y, out, n);
+    lincomb_kernel<<<grid_for(n), 256, 0, c->stream>>>(a, x, b, y, out, n); ++c->n_launch;
     return cudaGetLastError();
 }
 

@@ -61,9 +61,13 @@ struct Profile {
     bool on = false;
     double ms[8] = {0};
     long long launches[8] = {0};
-    long long pairs_far = 0;
+    long long pairs_f32 = 0, pairs_f64 = 0;
+    long long kernels0 = 0;  // kernel-launch counter at the last reset
 };
-enum Stage { ST_FAR = 0, ST_NEAR = 1, ST_SELF = 2, ST_COMPL = 3, ST_BLAS = 4, ST_OTHER = 5 };
+enum Stage {
+    ST_FAR = 0, ST_NEAR = 1, ST_SELF = 2, ST_COMPL = 3, ST_BLAS = 4, ST_OTHER = 5,
+    ST_FARK32 = 6, ST_FARK64 = 7  // the far-field pair kernel alone
+};
 
 }  // namespace sbie
 
@@ -123,10 +127,33 @@ struct sbie_ctx {
     sbie::Profile prof;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[8];
     int prof_used[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long n_launch = 0;  // kernels launched by this context
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 namespace sbie {
+
+// CUDA events around one stage launch on the context stream (profiling on).
+struct StageScope {
+    sbie_ctx* c;
+    int stage;
+    int idx = -1;
+    StageScope(sbie_ctx* cc, int st) : c(cc), stage(st) {
+        if (!c->prof.on) return;
+        auto& v = c->prof_events[stage];
+        idx = c->prof_used[stage]++;
+        if (idx >= (int)v.size()) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            v.push_back({a, b});
+        }
+        cudaEventRecord(v[idx].first, c->stream);
+    }
+    ~StageScope() {
+        if (idx >= 0) cudaEventRecord(c->prof_events[stage][idx].second, c->stream);
+    }
+};
 
 // --- kernels launchers (each returns cudaError_t of the launch) ---
 // self.cu

@@ -184,30 +184,32 @@ __global__ void geometry_kernel(const double* __restrict__ tab, TabLayout tl, co
 static unsigned nblk(long long n, int th) { return (unsigned)((n + th - 1) / th); }
 
 cudaError_t launch_moments(sbie_ctx* c, const double* dens) {
-    sphere_reduce_kernel<<<c->n, 256, 0, c->stream>>>(dens, c->d_x, c->d_c, c->d_a, c->npn, 0, c->d_mom, nullptr);
+    sphere_reduce_kernel<<<c->n, 256, 0, c->stream>>>(dens, c->d_x, c->d_c, c->d_a, c->npn, 0, c->d_mom, nullptr); ++c->n_launch;
     return cudaGetLastError();
 }
 
 cudaError_t launch_completion(sbie_ctx* c, bool f32, double* out) {
-    if (f32)
+    if (f32) {
         completion_kernel<float><<<nblk(c->N, 128), 128, 0, c->stream>>>(c->d_x, c->d_c, c->d_mom, c->n, c->N, out);
-    else
+    } else {
         completion_kernel<double><<<nblk(c->N, 128), 128, 0, c->stream>>>(c->d_x, c->d_c, c->d_mom, c->n, c->N, out);
+    }
+    ++c->n_launch;
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(sbie_ctx* c, int op, const double* dens, double* out) {
-    finalize_kernel<<<nblk(c->N, 256), 256, 0, c->stream>>>(op, dens, c->d_x, c->d_c, c->d_mom, c->npn, c->N, out);
+    finalize_kernel<<<nblk(c->N, 256), 256, 0, c->stream>>>(op, dens, c->d_x, c->d_c, c->d_mom, c->npn, c->N, out); ++c->n_launch;
     return cudaGetLastError();
 }
 
 cudaError_t launch_rho(sbie_ctx* c, const double* F, const double* T, double* rho) {
-    rho_kernel<<<nblk(c->N, 256), 256, 0, c->stream>>>(F, T, c->d_x, c->d_c, c->d_a, c->npn, c->N, rho);
+    rho_kernel<<<nblk(c->N, 256), 256, 0, c->stream>>>(F, T, c->d_x, c->d_c, c->d_a, c->npn, c->N, rho); ++c->n_launch;
     return cudaGetLastError();
 }
 
 cudaError_t launch_rigid_projection(sbie_ctx* c, const double* u, double* vel, double* omega) {
-    sphere_reduce_kernel<<<c->n, 256, 0, c->stream>>>(u, c->d_x, c->d_c, c->d_a, c->npn, 1, vel, omega);
+    sphere_reduce_kernel<<<c->n, 256, 0, c->stream>>>(u, c->d_x, c->d_c, c->d_a, c->npn, 1, vel, omega); ++c->n_launch;
     return cudaGetLastError();
 }
 
@@ -217,13 +219,13 @@ cudaError_t launch_resistance_rhs(sbie_ctx* c, const double* vel, const double* 
     const double* U = u0 ? u0 : z;
     const double* g = G ? G : g0;
     res_rhs_kernel<<<nblk(c->N, 256), 256, 0, c->stream>>>(vel, omega, U[0], U[1], U[2], g[0], g[1], g[2], g[3], g[4],
-                                                           g[5], g[6], g[7], g[8], c->d_x, c->d_c, c->npn, c->N, b);
+                                                           g[5], g[6], g[7], g[8], c->d_x, c->d_c, c->npn, c->N, b); ++c->n_launch;
     return cudaGetLastError();
 }
 
 cudaError_t launch_geometry(sbie_ctx* c) {
     geometry_kernel<<<nblk(c->N, 256), 256, 0, c->stream>>>(c->d_tab, c->tl, c->d_c, c->d_a, c->n, c->d_x, c->d_xhi,
-                                                            c->d_xlo, c->d_nrm, c->d_nrm64, c->d_sph);
+                                                            c->d_xlo, c->d_nrm, c->d_nrm64, c->d_sph); ++c->n_launch;
     return cudaGetLastError();
 }
 

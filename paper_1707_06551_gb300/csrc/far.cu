@@ -294,7 +294,7 @@ cudaError_t launch_pack(sbie_ctx* c, const double* dens, bool f32) {
     int th = 256;
     long long blocks = (c->N + th - 1) / th;
     pack_kernel<<<(unsigned)blocks, th, 0, c->stream>>>(dens, c->d_x, c->N, f32 ? c->d_srcf : nullptr,
-                                                        f32 ? nullptr : c->d_src64);
+                                                        f32 ? nullptr : c->d_src64); ++c->n_launch;
     return cudaGetLastError();
 }
 
@@ -318,14 +318,14 @@ static cudaError_t launch_far_t(sbie_ctx* c, const FarTune& tu, bool f32, const 
             cudaError_t e = cudaFuncSetAttribute(far_f32_kernel<OP, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
         }
-        far_f32_kernel<OP, TPT><<<grid, tu.threads, sm, c->stream>>>(a);
+        far_f32_kernel<OP, TPT><<<grid, tu.threads, sm, c->stream>>>(a); ++c->n_launch;
     } else {
         size_t sm = (size_t)nv * tu.tile * sizeof(double4) + words;
         if (sm > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(far_f64_kernel<OP, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
         }
-        far_f64_kernel<OP, TPT><<<grid, tu.threads, sm, c->stream>>>(a);
+        far_f64_kernel<OP, TPT><<<grid, tu.threads, sm, c->stream>>>(a); ++c->n_launch;
     }
     return cudaGetLastError();
 }
@@ -356,15 +356,18 @@ cudaError_t launch_far(sbie_ctx* c, Kern op, bool f32, double* out) {
     a.c = c->d_c; a.sph = c->d_sph; a.near_ptr = c->d_near_ptr; a.near_idx = c->d_near_idx;
     a.part = c->d_part;
     cudaError_t e;
-    switch (op) {
-        case Kern::S: e = launch_far_op<(int)Kern::S>(c, tu, f32, a); break;
-        case Kern::D: e = launch_far_op<(int)Kern::D>(c, tu, f32, a); break;
-        default: e = launch_far_op<(int)Kern::K>(c, tu, f32, a); break;
+    {
+        StageScope st(c, f32 ? ST_FARK32 : ST_FARK64);
+        switch (op) {
+            case Kern::S: e = launch_far_op<(int)Kern::S>(c, tu, f32, a); break;
+            case Kern::D: e = launch_far_op<(int)Kern::D>(c, tu, f32, a); break;
+            default: e = launch_far_op<(int)Kern::K>(c, tu, f32, a); break;
+        }
     }
     if (e != cudaSuccess) return e;
     double scale = (op == Kern::S) ? 1.0 / (8.0 * kPi) : (op == Kern::D ? 3.0 / (4.0 * kPi) : -3.0 / (4.0 * kPi));
     long long n3 = c->N * 3;
-    far_reduce<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(c->d_part, tu.split, n3, scale, out);
+    far_reduce<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(c->d_part, tu.split, n3, scale, out); ++c->n_launch;
     return cudaGetLastError();
 }
 

@@ -328,7 +328,7 @@ static cudaError_t run_eval(sbie_ctx* c, const NearArgs& A) {
     size_t sm = sizeof(T) * ((size_t)K * NCHS + 2 * K);
     cudaError_t e = cudaFuncSetAttribute(near_eval_kernel<T, NCH, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    near_eval_kernel<T, NCH, KIND><<<c->n * A.chunks, 128, sm, c->stream>>>(A);
+    near_eval_kernel<T, NCH, KIND><<<c->n * A.chunks, 128, sm, c->stream>>>(A); ++c->n_launch;
     return cudaGetLastError();
 }
 
@@ -348,7 +348,7 @@ cudaError_t launch_near(sbie_ctx* c, Kern op, bool f32, double* out) {
     size_t sm = sizeof(double) * (size_t)(5 * K + 12 * K + K);
     cudaError_t e = cudaFuncSetAttribute(near_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    near_prep_kernel<<<c->n, 256, sm, c->stream>>>(A, kind);
+    near_prep_kernel<<<c->n, 256, sm, c->stream>>>(A, kind); ++c->n_launch;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (f32) {

@@ -222,7 +222,7 @@ static cudaError_t run_self(sbie_ctx* c, int op, const double* dens, double* out
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    self_kernel<<<c->n, 256, sm, c->stream>>>(A);
+    self_kernel<<<c->n, 256, sm, c->stream>>>(A); ++c->n_launch;
     return cudaGetLastError();
 }
 

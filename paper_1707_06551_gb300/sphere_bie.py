@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "SBIE_OK", 1: "SBIE_ERR_ARG", 2: "SBIE_ERR_OVERLAP", 3: "SBIE
 SBIE_FP64, SBIE_MIXED = 0, 1
 SBIE_OP_S, SBIE_OP_D, SBIE_OP_K, SBIE_OP_MOBILITY, SBIE_OP_RESISTANCE = 0, 1, 2, 3, 4
 OPS = {"S": 0, "D": 1, "K": 2, "mobility": 3, "resistance": 4}
-STAGES = ("far", "near", "self", "completion", "arnoldi", "other")
+STAGES = ("far", "near", "self", "completion", "arnoldi", "other", "far_kernel_f32", "far_kernel_f64")
 
 
 class Opts(ctypes.Structure):
@@ -40,7 +40,9 @@ class SolveInfo(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_longlong * 6), ("far_pairs", ctypes.c_longlong)]
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_longlong * 8),
+                ("far_pairs_f32", ctypes.c_longlong), ("far_pairs_f64", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong)]
 
 
 class SphereBIEError(RuntimeError):
@@ -184,7 +186,8 @@ def sphere_bie_profile_read(ctx):
     p = Profile()
     _check(ctx, lib().sphere_bie_profile_read(ctx, ctypes.byref(p)))
     return {"ms": dict(zip(STAGES, list(p.ms))), "launches": dict(zip(STAGES, list(p.launches))),
-            "far_pairs": p.far_pairs}
+            "far_pairs_f32": p.far_pairs_f32, "far_pairs_f64": p.far_pairs_f64,
+            "kernel_launches": p.kernel_launches}
 
 
 class SphereBIE:

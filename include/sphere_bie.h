@@ -152,6 +152,29 @@ sbie_status sphere_bie_profile(sbie_ctx* ctx, int enable);
 /* Synchronises the context stream and returns the totals since the last reset. */
 sbie_status sphere_bie_profile_read(sbie_ctx* ctx, sbie_profile* out);
 
+/* Raw layer operator without any device allocation.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc (a memory
+ * manager owns the device, allocation is banned inside their hot loop, or
+ * they are building a CUDA graph around the call).
+ * Computes out = sum_k S_k, D_k or K_k (op = SBIE_OP_S, _D or _K) in FP64 at
+ * every node: the self term by the Theorem 2 signatures and every other pair
+ * by the smooth quadrature of Eq. 4.4 -- i.e. sphere_bie_apply_operator with
+ * eta = 0 (no close-pair correction).  centres [n][3], radii [n], density and
+ * out [N][3] (N = n_spheres (p+1)(2p+2)) are DEVICE pointers on the current
+ * device; work runs on `stream` (a cudaStream_t or NULL) and the call returns
+ * when out is complete.
+ * Limits: 1 <= n_spheres <= 4096, 1 <= p <= 24, N <= 65536; larger sizes
+ * return SBIE_ERR_ARG with a message.  All intermediates live in one static
+ * 20 MiB __device__ array that every GPU loading this library holds until
+ * exit; no cudaMalloc, cudaFree or allocating library routine is called.  The
+ * first call on a device looks up that array's address (and uploads the
+ * Legendre tables for its p), so make it before any stream capture.  Every
+ * call shares the array, which keeps the last call's contents: calls whose
+ * work overlaps on the GPU (different streams or host threads) race. */
+sbie_status sphere_bie_apply_layer_noalloc(sbie_op op, int n_spheres, int p, const double* centres,
+                                           const double* radii, const double* density, double* out,
+                                           void* stream);
+
 /* Frees every device buffer and the context.  NULL is accepted. */
 sbie_status sphere_bie_destroy(sbie_ctx* ctx);
 

@@ -14,6 +14,8 @@ using namespace sbie;
 
 static std::string g_last_error = "no error";
 
+void sbie::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 #define CK(expr)                                                            \
     do {                                                                    \
         cudaError_t e__ = (expr);                                           \

@@ -155,6 +155,9 @@ struct StageScope {
     }
 };
 
+// Message returned by sphere_bie_last_error(NULL).
+void set_last_error(const std::string& msg);
+
 // --- kernels launchers (each returns cudaError_t of the launch) ---
 // self.cu
 cudaError_t launch_self(sbie_ctx* c, Kern op, const double* dens, double* out, bool accumulate, bool write_coef);

@@ -74,9 +74,11 @@ def lib():
         L.sphere_bie_last_error.restype = ctypes.c_char_p
         L.sphere_bie_profile.argtypes = [_P, ctypes.c_int]
         L.sphere_bie_profile_read.argtypes = [_P, ctypes.POINTER(Profile)]
+        L.sphere_bie_apply_layer_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]
         for f in ("sphere_bie_default_opts", "sphere_bie_create", "sphere_bie_num_nodes", "sphere_bie_nodes",
                   "sphere_bie_apply_operator", "sphere_bie_solve_mobility", "sphere_bie_solve_resistance",
-                  "sphere_bie_destroy", "sphere_bie_profile", "sphere_bie_profile_read"):
+                  "sphere_bie_destroy", "sphere_bie_profile", "sphere_bie_profile_read",
+                  "sphere_bie_apply_layer_noalloc"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -167,6 +169,14 @@ def sphere_bie_solve_resistance(ctx, vel, omega, bg_u0, bg_grad, forces, torques
     d = info.as_dict()
     d["status"] = st
     return d
+
+
+def sphere_bie_apply_layer_noalloc(op, n_spheres, p, centres, radii, density, out, stream=None):
+    """Device tensors only; see the header for limits and the shared scratch."""
+    op = OPS[op] if isinstance(op, str) else int(op)
+    _check(None, lib().sphere_bie_apply_layer_noalloc(op, int(n_spheres), int(p), _ptr(centres), _ptr(radii),
+                                                      _ptr(density), _ptr(out), stream))
+    return out
 
 
 def sphere_bie_destroy(ctx):

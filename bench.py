@@ -206,6 +206,9 @@ def main():
     t_c0 = time.perf_counter()
     ctx = sb.sphere_bie_create(w["centres"], w["radii"], opts)
     t_create = time.perf_counter() - t_c0
+    t_c0 = time.perf_counter()
+    tuning = sb.sphere_bie_autotune(ctx, "resistance") if prec == sb.SBIE_MIXED else None
+    t_tune = time.perf_counter() - t_c0
     dev = torch.device("cuda", local)
     vel = torch.tensor(w["vel"], dtype=torch.float64, device=dev)
     om = torch.tensor(w["omega"], dtype=torch.float64, device=dev)
@@ -335,7 +338,7 @@ def main():
                        "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{world}"},
             "solve": {"iters": last["iters"], "refinements": last["refinements"],
                       "rel_residual_true": last["rel_residual_true"], "status": last["status"],
-                      "create_s": t_create},
+                      "create_s": t_create, "autotune_s": t_tune, "far_tiling": tuning},
             "roofline": roof, "far_field": far, "stage_ms_per_step": stage_ms, "fp64_path": fp64,
             "clocks": clocks, "gpu_launches": int(prof["kernel_launches"]),
             "gpu_launches_per_step": launches_per_step,

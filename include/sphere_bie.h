@@ -147,6 +147,23 @@ typedef struct {
     long long kernel_launches;
 } sbie_profile;
 
+/* Tiling of the FP32 far-field pair kernel (Sec. 4.1 smooth quadrature). */
+typedef struct {
+    int threads;             /* threads per CTA                                   */
+    int targets_per_thread;  /* target nodes per thread (held in FP32 pairs)      */
+    int split;               /* source-range splits (partial sums added in order) */
+    int tile;                /* sources staged in shared memory per tile          */
+    double ms;               /* measured time of one launch with this tiling      */
+    int candidates;          /* tilings timed                                     */
+} sbie_far_tuning;
+
+/* Autotuner: times every admissible tiling of the FP32 far-field kernel used by
+ * `op` (SBIE_OP_S, _D or _K; _MOBILITY tunes K, _RESISTANCE tunes D) on this
+ * context's geometry with CUDA events, keeps the fastest for this context and
+ * caches it for later contexts of the same (n_spheres, p, SM count) in this
+ * process.  chosen may be NULL.  Takes about 100 launches of the kernel. */
+sbie_status sphere_bie_autotune(sbie_ctx* ctx, sbie_op op, sbie_far_tuning* chosen);
+
 /* enable != 0 starts recording (and resets the counters); 0 stops. */
 sbie_status sphere_bie_profile(sbie_ctx* ctx, int enable);
 /* Synchronises the context stream and returns the totals since the last reset. */

@@ -6,7 +6,10 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "common.h"
 
@@ -62,21 +65,25 @@ void free_all(sbie_ctx* c) {
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
+// Far-field tilings found by sphere_bie_autotune, by (n, p, SM count, op, f32).
+std::map<std::tuple<int, int, int, int, int>, FarTune> g_tune_cache;
+std::mutex g_tune_mu;
+
 void choose_tuning(sbie_ctx* c) {
-    // targets per thread / threads per CTA: the combination that wastes the
-    // fewest target slots per sphere; then enough source splits to give every
-    // SM several CTAs.
+    // Default tiling: targets per thread / threads per CTA with the fewest idle
+    // target slots per sphere, then enough source splits for several CTAs per SM.
     auto pick = [&](bool f32) {
-        FarTune best{128, 1, 1, 256};
+        FarTune best{128, f32 ? 2 : 1, 1, 256};
         double best_waste = 1e30;
         const int tpts[3] = {1, 2, 4};
         for (int tpt : tpts) {
+            if (f32 && tpt == 1) continue;  // the FP32 kernel holds targets in pairs
             for (int th = 64; th <= 256; th += 32) {
                 int slots = th * tpt;
                 int chunks = (c->npn + slots - 1) / slots;
                 double waste = (double)(chunks * slots - c->npn) / c->npn;
-                // prefer 2 targets per thread in FP32 (source reuse), 1 in FP64 (registers)
                 double pref = f32 ? (tpt == 2 ? 0.0 : 0.03) : (tpt == 1 ? 0.0 : 0.05);
+                pref += th == 128 ? 0.0 : 0.001;
                 double score = waste + pref;
                 if (score < best_waste - 1e-12) {
                     best_waste = score;
@@ -86,22 +93,35 @@ void choose_tuning(sbie_ctx* c) {
         }
         int chunks = (c->npn + best.threads * best.tpt - 1) / (best.threads * best.tpt);
         long long ctas = (long long)c->n * chunks;
-        long long want = (long long)c->sm_count * (f32 ? 8 : 4);
+        long long want = (long long)c->sm_count * (f32 ? 12 : 4);
         int split = (int)std::min<long long>(32, std::max<long long>(1, (want + ctas - 1) / ctas));
         long long per = (c->N + split - 1) / split;
-        if (per < best.tile) split = std::max<long long>(1, c->N / best.tile);
+        if (per < best.tile) split = (int)std::max<long long>(1, c->N / best.tile);
         best.split = split;
         return best;
     };
-    c->tune32 = pick(true);
-    c->tune64 = pick(false);
+    FarTune t32 = pick(true), t64 = pick(false);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (int op = 0; op < 3; ++op) {
+        c->tune32[op] = t32;
+        c->tune64[op] = t64;
+        auto it = g_tune_cache.find(std::make_tuple(c->n, c->p, c->sm_count, op, 1));
+        if (it != g_tune_cache.end()) c->tune32[op] = it->second;
+    }
 }
 
-sbie_status ensure_part(sbie_ctx* c) {
-    size_t need = (size_t)std::max(c->tune32.split, c->tune64.split) * c->N * 3;
+int max_split(const sbie_ctx* c) {
+    int s = 1;
+    for (int op = 0; op < 3; ++op) s = std::max(s, std::max(c->tune32[op].split, c->tune64[op].split));
+    return s;
+}
+
+sbie_status ensure_part(sbie_ctx* c, int split_needed = 0) {
+    size_t need = (size_t)std::max(max_split(c), split_needed) * c->N * 3;
     if (need <= c->part_cap) return SBIE_OK;
     if (c->d_part) cudaFree(c->d_part);
     c->d_part = nullptr;
+    c->part_cap = 0;
     if (dmalloc(&c->d_part, need) != cudaSuccess) return fail(c, SBIE_ERR_OOM, "far-field partials");
     c->part_cap = need;
     return SBIE_OK;
@@ -605,6 +625,65 @@ sbie_status sphere_bie_destroy(sbie_ctx* c) {
 
 const char* sphere_bie_last_error(const sbie_ctx* c) {
     return c ? c->err.c_str() : g_last_error.c_str();
+}
+
+sbie_status sphere_bie_autotune(sbie_ctx* c, sbie_op op, sbie_far_tuning* chosen) {
+    if (!c) return SBIE_ERR_ARG;
+    if (op < SBIE_OP_S || op > SBIE_OP_RESISTANCE) return fail(c, SBIE_ERR_ARG, "bad operator");
+    const Kern k = kern_of(op);
+    const int split_max = 16;
+    CKS(ensure_part(c, split_max));
+    CK(cudaMemsetAsync(c->d_srcf, 0, sizeof(float4) * c->N, c->stream));
+    struct Cand { FarTune t; float ms; };
+    std::vector<Cand> cands;
+    const int tpts[2] = {2, 4}, ths[5] = {64, 96, 128, 192, 256}, splits[8] = {1, 2, 3, 4, 6, 8, 12, 16};
+    const int tiles[2] = {128, 256};
+    for (int tpt : tpts)
+        for (int th : ths) {
+            int slots = th * tpt;
+            int chunks = (c->npn + slots - 1) / slots;
+            double waste = (double)(chunks * slots - c->npn) / c->npn;
+            if (waste > 0.30) continue;
+            for (int sp : splits) {
+                long long ctas = (long long)c->n * chunks * sp;
+                if (ctas < c->sm_count && sp != splits[0]) continue;
+                if (ctas > 64LL * c->sm_count) continue;
+                for (int tile : tiles) {
+                    if ((c->N + sp - 1) / sp < tile) continue;
+                    cands.push_back(Cand{FarTune{th, tpt, sp, tile}, 0.f});
+                }
+            }
+        }
+    if (cands.empty()) cands.push_back(Cand{c->tune32[(int)k], 0.f});
+    float dummy;
+    CK(time_far(c, k, true, cands[0].t, &dummy));  // warm-up
+    for (auto& cd : cands) CK(time_far(c, k, true, cd.t, &cd.ms));
+    std::sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
+    const size_t top = std::min<size_t>(6, cands.size());
+    for (size_t i = 0; i < top; ++i) {
+        float best = cands[i].ms;
+        for (int r = 0; r < 3; ++r) {
+            float ms;
+            CK(time_far(c, k, true, cands[i].t, &ms));
+            best = std::min(best, ms);
+        }
+        cands[i].ms = best;
+    }
+    std::sort(cands.begin(), cands.begin() + top, [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
+    c->tune32[(int)k] = cands[0].t;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[std::make_tuple(c->n, c->p, c->sm_count, (int)k, 1)] = cands[0].t;
+    }
+    if (chosen) {
+        chosen->threads = cands[0].t.threads;
+        chosen->targets_per_thread = cands[0].t.tpt;
+        chosen->split = cands[0].t.split;
+        chosen->tile = cands[0].t.tile;
+        chosen->ms = cands[0].ms;
+        chosen->candidates = (int)cands.size();
+    }
+    return SBIE_OK;
 }
 
 sbie_status sphere_bie_profile(sbie_ctx* c, int enable) {

@@ -123,7 +123,7 @@ struct sbie_ctx {
     double* d_res = nullptr;     // [3N]
     int krylov_m = 0;
 
-    sbie::FarTune tune64{}, tune32{};
+    sbie::FarTune tune64[3]{}, tune32[3]{};  // per far-field kernel (S, D, K)
     sbie::Profile prof;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[8];
     int prof_used[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -165,6 +165,8 @@ cudaError_t launch_analysis_only(sbie_ctx* c, const double* dens);
 // far.cu
 cudaError_t launch_pack(sbie_ctx* c, const double* dens, bool f32);
 cudaError_t launch_far(sbie_ctx* c, Kern op, bool f32, double* out);
+// Times one launch of the far-field pair kernel with tiling `tu` (no reduce); *ms = event time.
+cudaError_t time_far(sbie_ctx* c, Kern op, bool f32, const FarTune& tu, float* ms);
 long long far_pairs(const sbie_ctx* c);
 // near.cu
 cudaError_t launch_near(sbie_ctx* c, Kern op, bool f32, double* out);

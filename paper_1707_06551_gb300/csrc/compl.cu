@@ -59,39 +59,45 @@ __global__ void sphere_reduce_kernel(const double* __restrict__ dens, const doub
     }
 }
 
+// FP64: direct.  FP32: target and centre positions are split into float hi +
+// lo parts so that x - c keeps relative FP32 accuracy (as in the far field).
 template <typename T>
 __global__ void completion_kernel(const double* __restrict__ x64, const double* __restrict__ c,
                                   const double* __restrict__ mom, int n, long long N, double* __restrict__ out) {
     // out[i] += sum_k G(x_i - c_k) M0_k + M1_k x (x_i - c_k) / (8 pi |x_i - c_k|^3)
     constexpr int TILE = 128;
-    __shared__ double sc[TILE][3];
-    __shared__ double sm[TILE][6];
+    __shared__ T sc[TILE][6];   // centre hi (3), lo (3)
+    __shared__ T sm[TILE][6];
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < N;
     const long long ii = valid ? i : 0;
     const double X = x64[4 * ii], Y = x64[4 * ii + 1], Z = x64[4 * ii + 2];
+    const T xh = (T)X, yh = (T)Y, zh = (T)Z;
+    const T xl = (T)(X - (double)xh), yl = (T)(Y - (double)yh), zl = (T)(Z - (double)zh);
     T ux = 0, uy = 0, uz = 0;
     for (int b = 0; b < n; b += TILE) {
         __syncthreads();
         for (int j = threadIdx.x; j < TILE; j += blockDim.x) {
             int k = b + j;
-            if (k < n) {
-                for (int d = 0; d < 3; ++d) sc[j][d] = c[3 * k + d];
-                for (int d = 0; d < 6; ++d) sm[j][d] = mom[6 * k + d];
-            } else {
-                sc[j][0] = X + 1.0e6; sc[j][1] = Y + 1.0e6; sc[j][2] = Z + 1.0e6;
-                for (int d = 0; d < 6; ++d) sm[j][d] = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                double cd = (k < n) ? c[3 * k + d] : 0.0;
+                T h = (T)cd;
+                sc[j][d] = h;
+                sc[j][3 + d] = (T)(cd - (double)h);
             }
+            for (int d = 0; d < 6; ++d) sm[j][d] = (k < n) ? (T)mom[6 * k + d] : (T)0;
         }
         __syncthreads();
         int cnt = min(TILE, n - b);
         for (int j = 0; j < cnt; ++j) {
-            T dx = (T)(X - sc[j][0]), dy = (T)(Y - sc[j][1]), dz = (T)(Z - sc[j][2]);
+            T dx = (xh - sc[j][0]) + (xl - sc[j][3]);
+            T dy = (yh - sc[j][1]) + (yl - sc[j][4]);
+            T dz = (zh - sc[j][2]) + (zl - sc[j][5]);
             T r2 = dx * dx + dy * dy + dz * dz;
             T ri = (T)1 / sqrt(r2);
             T ri3 = ri * ri * ri;
-            T fx = (T)sm[j][0], fy = (T)sm[j][1], fz = (T)sm[j][2];
-            T tx = (T)sm[j][3], ty = (T)sm[j][4], tz = (T)sm[j][5];
+            T fx = sm[j][0], fy = sm[j][1], fz = sm[j][2];
+            T tx = sm[j][3], ty = sm[j][4], tz = sm[j][5];
             T rf = dx * fx + dy * fy + dz * fz;
             // Stokeslet f / r + r (r.f) / r^3 and rotlet (t x r) / r^3, common factor 1/(8 pi)
             ux += fx * ri + dx * rf * ri3 + (ty * dz - tz * dy) * ri3;

@@ -60,16 +60,26 @@ __device__ __forceinline__ void neumaier(float& sum, float& comp, float v) {
     sum = t;
 }
 
-template <int OP, int TPT>
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// FP32 pair kernel on packed FP32x2 arithmetic: every thread owns 2 * NP
+// targets held in float2 pairs, so one __ffma2_rn evaluates two (target,
+// source) pairs.  Each staged source is stored pre-duplicated in shared memory
+// ({-x, -x, -y, -y}, {-z, -z, fx, fx}, {fy, fy, fz, fz} and, for D, the source
+// normal {nx, nx, ny, ny}, {nz, nz, 0, 0}), so every packed operand comes from
+// one 128-bit shared-memory broadcast.
+template <int OP, int NP>
 __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
-    constexpr int NV = (OP == (int)Kern::D) ? 3 : 2;
+    constexpr int NV = (OP == (int)Kern::D) ? 5 : 3;  // float4 per staged source
+    constexpr int TPT = 2 * NP;
     const int sphere = blockIdx.x / a.chunks, chunk = blockIdx.x - sphere * a.chunks;
     const int split = blockIdx.y;
     const int tid = threadIdx.x, bd = blockDim.x;
     extern __shared__ float4 smem4[];
-    float4* s_pos = smem4;
-    float4* s_den = smem4 + a.tile;
-    float4* s_nrm = smem4 + 2 * a.tile;
     unsigned* flags = reinterpret_cast<unsigned*>(smem4 + NV * a.tile);
     build_flags(a, sphere, flags);
 
@@ -77,7 +87,7 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
     const float chx = (float)cx, chy = (float)cy, chz = (float)cz;
     const float clx = (float)(cx - (double)chx), cly = (float)(cy - (double)chy), clz = (float)(cz - (double)chz);
 
-    float tx[TPT], ty[TPT], tz[TPT], tnx[TPT], tny[TPT], tnz[TPT];
+    float2 tx[NP], ty[NP], tz[NP], tnx[NP], tny[NP], tnz[NP];
     long long tnode[TPT];
     bool tval[TPT];
 #pragma unroll
@@ -87,14 +97,15 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
         long long node = (long long)sphere * a.npn + (tval[t] ? q : a.npn - 1);
         tnode[t] = node;
         float4 h = a.xhi[node], l = a.xlo[node];
-        tx[t] = (h.x - chx) + (l.x - clx);
-        ty[t] = (h.y - chy) + (l.y - cly);
-        tz[t] = (h.z - chz) + (l.z - clz);
-        if (OP == (int)Kern::K) {
-            float4 nn = a.nrm[node];
-            tnx[t] = nn.x; tny[t] = nn.y; tnz[t] = nn.z;
+        float px = (h.x - chx) + (l.x - clx), py = (h.y - chy) + (l.y - cly), pz = (h.z - chz) + (l.z - clz);
+        float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (OP == (int)Kern::K) nn = a.nrm[node];
+        if (t & 1) {
+            tx[t >> 1].y = px; ty[t >> 1].y = py; tz[t >> 1].y = pz;
+            tnx[t >> 1].y = nn.x; tny[t >> 1].y = nn.y; tnz[t >> 1].y = nn.z;
         } else {
-            tnx[t] = tny[t] = tnz[t] = 0.f;
+            tx[t >> 1].x = px; ty[t >> 1].x = py; tz[t >> 1].x = pz;
+            tnx[t >> 1].x = nn.x; tny[t >> 1].x = nn.y; tnz[t >> 1].x = nn.z;
         }
     }
     float sum[TPT][3], cmp[TPT][3];
@@ -109,61 +120,90 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
         __syncthreads();
         for (int j = tid; j < a.tile; j += bd) {
             long long s = base + j;
-            float4 P = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 0.f);
-            float4 F = make_float4(0.f, 0.f, 0.f, 0.f);
-            float4 Nn = make_float4(0.f, 0.f, 0.f, 0.f);
+            float px = -1.0e4f, py = -1.0e4f, pz = -1.0e4f, fx = 0.f, fy = 0.f, fz = 0.f;
+            float nx = 0.f, ny = 0.f, nz = 0.f;
             if (s < b1) {
                 int k = a.sph[s];
                 if (!((flags[k >> 5] >> (k & 31)) & 1u)) {
                     float4 h = a.xhi[s], l = a.xlo[s];
-                    P = make_float4((h.x - chx) + (l.x - clx), (h.y - chy) + (l.y - cly), (h.z - chz) + (l.z - clz), 0.f);
-                    F = a.srcf[s];
-                    if (OP == (int)Kern::D) Nn = a.nrm[s];
+                    px = -((h.x - chx) + (l.x - clx));
+                    py = -((h.y - chy) + (l.y - cly));
+                    pz = -((h.z - chz) + (l.z - clz));
+                    float4 F = a.srcf[s];
+                    fx = F.x; fy = F.y; fz = F.z;
+                    if (OP == (int)Kern::D) {
+                        float4 nn = a.nrm[s];
+                        nx = nn.x; ny = nn.y; nz = nn.z;
+                    }
                 }
             }
-            s_pos[j] = P;
-            s_den[j] = F;
-            if (OP == (int)Kern::D) s_nrm[j] = Nn;
+            float4* dst = smem4 + (size_t)j * NV;
+            dst[0] = make_float4(px, px, py, py);
+            dst[1] = make_float4(pz, pz, fx, fx);
+            dst[2] = make_float4(fy, fy, fz, fz);
+            if (OP == (int)Kern::D) {
+                dst[3] = make_float4(nx, nx, ny, ny);
+                dst[4] = make_float4(nz, nz, 0.f, 0.f);
+            }
         }
         __syncthreads();
-        float acc[TPT][3];
+        float2 acc[NP][3];
 #pragma unroll
-        for (int t = 0; t < TPT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = 0.f;
-#pragma unroll 4
+        for (int t = 0; t < NP; ++t) acc[t][0] = acc[t][1] = acc[t][2] = make_float2(0.f, 0.f);
+#pragma unroll 2
         for (int j = 0; j < a.tile; ++j) {
-            const float4 P = s_pos[j];
-            const float4 F = s_den[j];
-            float4 Nn;
-            if (OP == (int)Kern::D) Nn = s_nrm[j];
+            const float4* src = smem4 + (size_t)j * NV;
+            const float4 v0 = src[0], v1 = src[1], v2 = src[2];
+            const float2 mx = make_float2(v0.x, v0.y), my = make_float2(v0.z, v0.w), mz = make_float2(v1.x, v1.y);
+            const float2 fx = make_float2(v1.z, v1.w), fy = make_float2(v2.x, v2.y), fz = make_float2(v2.z, v2.w);
+            float2 nx, ny, nz;
+            if (OP == (int)Kern::D) {
+                const float4 v3 = src[3], v4 = src[4];
+                nx = make_float2(v3.x, v3.y);
+                ny = make_float2(v3.z, v3.w);
+                nz = make_float2(v4.x, v4.y);
+            }
 #pragma unroll
-            for (int t = 0; t < TPT; ++t) {
-                float dx = tx[t] - P.x, dy = ty[t] - P.y, dz = tz[t] - P.z;
-                float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                float ri = rsqrtf(r2);
-                float ri2 = ri * ri;
-                float rf = fmaf(dz, F.z, fmaf(dy, F.y, dx * F.x));
+            for (int t = 0; t < NP; ++t) {
+                const float2 dx = __fadd2_rn(tx[t], mx), dy = __fadd2_rn(ty[t], my), dz = __fadd2_rn(tz[t], mz);
+                float2 r2 = __fmul2_rn(dx, dx);
+                r2 = __ffma2_rn(dy, dy, r2);
+                r2 = __ffma2_rn(dz, dz, r2);
+                float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                const float2 ri2 = __fmul2_rn(ri, ri);
+                float2 rf = __fmul2_rn(dx, fx);
+                rf = __ffma2_rn(dy, fy, rf);
+                rf = __ffma2_rn(dz, fz, rf);
                 if (OP == (int)Kern::S) {
-                    float s3 = rf * ri * ri2;
-                    acc[t][0] = fmaf(dx, s3, fmaf(F.x, ri, acc[t][0]));
-                    acc[t][1] = fmaf(dy, s3, fmaf(F.y, ri, acc[t][1]));
-                    acc[t][2] = fmaf(dz, s3, fmaf(F.z, ri, acc[t][2]));
+                    const float2 s3 = __fmul2_rn(__fmul2_rn(rf, ri), ri2);
+                    acc[t][0] = __ffma2_rn(dx, s3, __ffma2_rn(fx, ri, acc[t][0]));
+                    acc[t][1] = __ffma2_rn(dy, s3, __ffma2_rn(fy, ri, acc[t][1]));
+                    acc[t][2] = __ffma2_rn(dz, s3, __ffma2_rn(fz, ri, acc[t][2]));
                 } else {
-                    float rn;
-                    if (OP == (int)Kern::D)
-                        rn = fmaf(dz, Nn.z, fmaf(dy, Nn.y, dx * Nn.x));
-                    else
-                        rn = fmaf(dz, tnz[t], fmaf(dy, tny[t], dx * tnx[t]));
-                    float s5 = (rf * rn) * (ri2 * ri2) * ri;
-                    acc[t][0] = fmaf(dx, s5, acc[t][0]);
-                    acc[t][1] = fmaf(dy, s5, acc[t][1]);
-                    acc[t][2] = fmaf(dz, s5, acc[t][2]);
+                    float2 rn;
+                    if (OP == (int)Kern::D) {
+                        rn = __fmul2_rn(dx, nx);
+                        rn = __ffma2_rn(dy, ny, rn);
+                        rn = __ffma2_rn(dz, nz, rn);
+                    } else {
+                        rn = __fmul2_rn(dx, tnx[t]);
+                        rn = __ffma2_rn(dy, tny[t], rn);
+                        rn = __ffma2_rn(dz, tnz[t], rn);
+                    }
+                    const float2 s5 = __fmul2_rn(__fmul2_rn(rf, rn), __fmul2_rn(__fmul2_rn(ri2, ri2), ri));
+                    acc[t][0] = __ffma2_rn(dx, s5, acc[t][0]);
+                    acc[t][1] = __ffma2_rn(dy, s5, acc[t][1]);
+                    acc[t][2] = __ffma2_rn(dz, s5, acc[t][2]);
                 }
             }
         }
 #pragma unroll
-        for (int t = 0; t < TPT; ++t)
+        for (int t = 0; t < NP; ++t)
 #pragma unroll
-            for (int d = 0; d < 3; ++d) neumaier(sum[t][d], cmp[t][d], acc[t][d]);
+            for (int d = 0; d < 3; ++d) {
+                neumaier(sum[2 * t][d], cmp[2 * t][d], acc[t][d].x);
+                neumaier(sum[2 * t + 1][d], cmp[2 * t + 1][d], acc[t][d].y);
+            }
     }
     double* out = a.part + (size_t)split * a.N * 3;
 #pragma unroll
@@ -313,12 +353,13 @@ static cudaError_t launch_far_t(sbie_ctx* c, const FarTune& tu, bool f32, const 
     int nv = (OP == (int)Kern::D) ? 3 : 2;
     size_t words = ((c->n + 31) / 32) * sizeof(unsigned);
     if (f32) {
-        size_t sm = (size_t)nv * tu.tile * sizeof(float4) + words;
+        const int nv32 = (OP == (int)Kern::D) ? 5 : 3;
+        size_t sm = (size_t)nv32 * tu.tile * sizeof(float4) + words;
         if (sm > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(far_f32_kernel<OP, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaError_t e = cudaFuncSetAttribute(far_f32_kernel<OP, (TPT + 1) / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
         }
-        far_f32_kernel<OP, TPT><<<grid, tu.threads, sm, c->stream>>>(a); ++c->n_launch;
+        far_f32_kernel<OP, (TPT + 1) / 2><<<grid, tu.threads, sm, c->stream>>>(a); ++c->n_launch;
     } else {
         size_t sm = (size_t)nv * tu.tile * sizeof(double4) + words;
         if (sm > 48 * 1024) {
@@ -339,8 +380,7 @@ static cudaError_t launch_far_op(sbie_ctx* c, const FarTune& tu, bool f32, const
     }
 }
 
-cudaError_t launch_far(sbie_ctx* c, Kern op, bool f32, double* out) {
-    const FarTune& tu = f32 ? c->tune32 : c->tune64;
+static FarArgs make_args(sbie_ctx* c, const FarTune& tu) {
     FarArgs a;
     a.n = c->n;
     a.npn = c->npn;
@@ -355,20 +395,46 @@ cudaError_t launch_far(sbie_ctx* c, Kern op, bool f32, double* out) {
     a.src64 = c->d_src64;
     a.c = c->d_c; a.sph = c->d_sph; a.near_ptr = c->d_near_ptr; a.near_idx = c->d_near_idx;
     a.part = c->d_part;
+    return a;
+}
+
+static cudaError_t launch_pair_kernel(sbie_ctx* c, Kern op, bool f32, const FarTune& tu) {
+    FarArgs a = make_args(c, tu);
+    switch (op) {
+        case Kern::S: return launch_far_op<(int)Kern::S>(c, tu, f32, a);
+        case Kern::D: return launch_far_op<(int)Kern::D>(c, tu, f32, a);
+        default: return launch_far_op<(int)Kern::K>(c, tu, f32, a);
+    }
+}
+
+cudaError_t launch_far(sbie_ctx* c, Kern op, bool f32, double* out) {
+    const FarTune& tu = f32 ? c->tune32[(int)op] : c->tune64[(int)op];
     cudaError_t e;
     {
         StageScope st(c, f32 ? ST_FARK32 : ST_FARK64);
-        switch (op) {
-            case Kern::S: e = launch_far_op<(int)Kern::S>(c, tu, f32, a); break;
-            case Kern::D: e = launch_far_op<(int)Kern::D>(c, tu, f32, a); break;
-            default: e = launch_far_op<(int)Kern::K>(c, tu, f32, a); break;
-        }
+        e = launch_pair_kernel(c, op, f32, tu);
     }
     if (e != cudaSuccess) return e;
     double scale = (op == Kern::S) ? 1.0 / (8.0 * kPi) : (op == Kern::D ? 3.0 / (4.0 * kPi) : -3.0 / (4.0 * kPi));
     long long n3 = c->N * 3;
     far_reduce<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(c->d_part, tu.split, n3, scale, out); ++c->n_launch;
     return cudaGetLastError();
+}
+
+cudaError_t time_far(sbie_ctx* c, Kern op, bool f32, const FarTune& tu, float* ms) {
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
+    e = cudaEventRecord(e0, c->stream);
+    if (e == cudaSuccess) e = launch_pair_kernel(c, op, f32, tu);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
 }
 
 }  // namespace sbie

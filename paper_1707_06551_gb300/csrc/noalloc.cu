@@ -148,7 +148,7 @@ extern "C" sbie_status sphere_bie_apply_layer_noalloc(sbie_op op, int n_spheres,
         int chunks = (int)((npn + th - 1) / th);
         long long ctas = (long long)n_spheres * chunks;
         int split = (int)std::min<long long>(kNoallocSplit, std::max<long long>(1, (4LL * sms + ctas - 1) / ctas));
-        c.tune64 = FarTune{th, 1, split, 128};
+        for (int op = 0; op < 3; ++op) c.tune64[op] = FarTune{th, 1, split, 128};
     }
     const Kern k = op == SBIE_OP_S ? Kern::S : (op == SBIE_OP_D ? Kern::D : Kern::K);
 

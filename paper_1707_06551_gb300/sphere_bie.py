@@ -45,6 +45,11 @@ class Profile(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong)]
 
 
+class FarTuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("targets_per_thread", ctypes.c_int), ("split", ctypes.c_int),
+                ("tile", ctypes.c_int), ("ms", ctypes.c_double), ("candidates", ctypes.c_int)]
+
+
 class SphereBIEError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -74,11 +79,12 @@ def lib():
         L.sphere_bie_last_error.restype = ctypes.c_char_p
         L.sphere_bie_profile.argtypes = [_P, ctypes.c_int]
         L.sphere_bie_profile_read.argtypes = [_P, ctypes.POINTER(Profile)]
+        L.sphere_bie_autotune.argtypes = [_P, ctypes.c_int, ctypes.POINTER(FarTuning)]
         L.sphere_bie_apply_layer_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]
         for f in ("sphere_bie_default_opts", "sphere_bie_create", "sphere_bie_num_nodes", "sphere_bie_nodes",
                   "sphere_bie_apply_operator", "sphere_bie_solve_mobility", "sphere_bie_solve_resistance",
                   "sphere_bie_destroy", "sphere_bie_profile", "sphere_bie_profile_read",
-                  "sphere_bie_apply_layer_noalloc"):
+                  "sphere_bie_apply_layer_noalloc", "sphere_bie_autotune"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -186,6 +192,13 @@ def sphere_bie_destroy(ctx):
 
 def sphere_bie_last_error(ctx=None):
     return lib().sphere_bie_last_error(ctx).decode()
+
+
+def sphere_bie_autotune(ctx, op):
+    op = OPS[op] if isinstance(op, str) else int(op)
+    t = FarTuning()
+    _check(ctx, lib().sphere_bie_autotune(ctx, op, ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in t._fields_}
 
 
 def sphere_bie_profile(ctx, enable):

@@ -298,6 +298,21 @@ def main():
                 "rel_residual_true": i64["rel_residual_true"],
                 "force_rel_diff_vs_mixed": float((F64 - F).abs().max() / F64.abs().max())}
         sb.sphere_bie_destroy(c64)
+        # FP64-accurate path with the double-float far field
+        odf = sb.make_opts(p, prec=sb.SBIE_FP64_DF, tol=w["tol"], mem_kind=1, stream=stream.cuda_stream)
+        cdf = sb.sphere_bie_create(w["centres"], w["radii"], odf)
+        sb.sphere_bie_autotune(cdf, "resistance")
+        Fdf = torch.zeros_like(F)
+        Tdf = torch.zeros_like(T)
+        sb.sphere_bie_solve_resistance(cdf, vel, om, w["u0"], w["G"], Fdf, Tdf)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        idf = sb.sphere_bie_solve_resistance(cdf, vel, om, w["u0"], w["G"], Fdf, Tdf)
+        torch.cuda.synchronize()
+        fp64["df_path"] = {"time_to_solve_s": time.perf_counter() - t0, "iters": idf["iters"],
+                           "rel_residual_true": idf["rel_residual_true"],
+                           "force_rel_diff_vs_fp64": float((Fdf - F64).abs().max() / F64.abs().max())}
+        sb.sphere_bie_destroy(cdf)
 
     # end to end through the public API with host buffers: create (geometry
     # upload, tables, close-pair lists), solve, read forces/torques, destroy

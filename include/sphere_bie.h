@@ -47,10 +47,14 @@ typedef enum {
 } sbie_status;
 
 typedef enum {
-    SBIE_FP64 = 0,  /* every kernel in FP64                                          */
-    SBIE_MIXED = 1  /* far field and near-field evaluation in FP32 with compensated
-                       accumulation; tables, coefficients, Arnoldi and the
-                       outer residual in FP64 (iterative refinement)               */
+    SBIE_FP64 = 0,    /* every kernel in native FP64                                  */
+    SBIE_MIXED = 1,   /* GMRES on an operator whose far field and close-pair
+                         evaluation run in FP32 (compensated accumulation), inside
+                         iterative refinement on the FP64-accurate operator of
+                         SBIE_FP64_DF; tables, coefficients and Arnoldi in FP64      */
+    SBIE_FP64_DF = 2  /* FP64-accurate operator whose far-field pair arithmetic is
+                         double-float (a value = sum of two FP32 numbers, about 48
+                         significant bits; ~1e-13 relative); everything else FP64   */
 } sbie_precision;
 
 typedef enum {
@@ -157,11 +161,14 @@ typedef struct {
     int candidates;          /* tilings timed                                     */
 } sbie_far_tuning;
 
-/* Autotuner: times every admissible tiling of the FP32 far-field kernel used by
- * `op` (SBIE_OP_S, _D or _K; _MOBILITY tunes K, _RESISTANCE tunes D) on this
- * context's geometry with CUDA events, keeps the fastest for this context and
- * caches it for later contexts of the same (n_spheres, p, SM count) in this
- * process.  chosen may be NULL.  Takes about 100 launches of the kernel. */
+/* Autotuner: times every admissible tiling of the far-field kernels used by
+ * `op` (SBIE_OP_S, _D or _K; _MOBILITY tunes K, _RESISTANCE tunes D) in the
+ * context's precision -- the FP32 kernel (SBIE_MIXED) and the double-float
+ * kernel (SBIE_MIXED, SBIE_FP64_DF) -- on this context's geometry with CUDA
+ * events, keeps the fastest for this context and caches it for later contexts
+ * of the same (n_spheres, p, SM count) in this process.  chosen, if not NULL,
+ * points to two records: [0] FP32 kernel, [1] double-float kernel (zeroed when
+ * not tuned).  SBIE_FP64 contexts keep their default tiling. */
 sbie_status sphere_bie_autotune(sbie_ctx* ctx, sbie_op op, sbie_far_tuning* chosen);
 
 /* enable != 0 starts recording (and resets the counters); 0 stops. */

@@ -101,18 +101,37 @@ void choose_tuning(sbie_ctx* c) {
         return best;
     };
     FarTune t32 = pick(true), t64 = pick(false);
+    // double-float kernel: one target per thread, FP32-ALU bound like the FP32 kernel
+    FarTune tdf{128, 1, 1, 128};
+    {
+        double best = 1e30;
+        for (int th = 64; th <= 256; th += 64) {
+            int chunks = (c->npn + th - 1) / th;
+            double waste = (double)(chunks * th - c->npn) / c->npn + (th == 128 ? 0.0 : 0.001);
+            if (waste < best - 1e-12) { best = waste; tdf.threads = th; }
+        }
+        int chunks = (c->npn + tdf.threads - 1) / tdf.threads;
+        long long ctas = (long long)c->n * chunks;
+        long long want = (long long)c->sm_count * 8;
+        tdf.split = (int)std::min<long long>(16, std::max<long long>(1, (want + ctas - 1) / ctas));
+        if ((c->N + tdf.split - 1) / tdf.split < tdf.tile) tdf.split = (int)std::max<long long>(1, c->N / tdf.tile);
+    }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (int op = 0; op < 3; ++op) {
         c->tune32[op] = t32;
         c->tune64[op] = t64;
-        auto it = g_tune_cache.find(std::make_tuple(c->n, c->p, c->sm_count, op, 1));
+        c->tunedf[op] = tdf;
+        auto it = g_tune_cache.find(std::make_tuple(c->n, c->p, c->sm_count, op, (int)kModeF32));
         if (it != g_tune_cache.end()) c->tune32[op] = it->second;
+        it = g_tune_cache.find(std::make_tuple(c->n, c->p, c->sm_count, op, (int)kModeDF));
+        if (it != g_tune_cache.end()) c->tunedf[op] = it->second;
     }
 }
 
 int max_split(const sbie_ctx* c) {
     int s = 1;
-    for (int op = 0; op < 3; ++op) s = std::max(s, std::max(c->tune32[op].split, c->tune64[op].split));
+    for (int op = 0; op < 3; ++op)
+        s = std::max(s, std::max(c->tune32[op].split, std::max(c->tune64[op].split, c->tunedf[op].split)));
     return s;
 }
 
@@ -127,19 +146,25 @@ sbie_status ensure_part(sbie_ctx* c, int split_needed = 0) {
     return SBIE_OK;
 }
 
+// Arithmetic of the FP64-accurate operator of a context: native FP64 for
+// SBIE_FP64, the double-float far field otherwise.
+int hi_mode(const sbie_ctx* c) { return c->opts.prec == SBIE_FP64 ? kModeF64 : kModeDF; }
+
 Kern kern_of(int op) {
     if (op == SBIE_OP_S) return Kern::S;
     if (op == SBIE_OP_D || op == SBIE_OP_RESISTANCE) return Kern::D;
     return Kern::K;
 }
 
-// out = A in, all device memory, on c->stream.
-sbie_status apply_dev(sbie_ctx* c, int op, bool f32, const double* in, double* out) {
+// out = A in, all device memory, on c->stream, in arithmetic `mode`
+// (kModeF64, kModeF32 or kModeDF).
+sbie_status apply_dev(sbie_ctx* c, int op, int mode, const double* in, double* out) {
     const Kern k = kern_of(op);
+    const bool f32 = mode == kModeF32;
     {
         StageScope s(c, ST_FAR);
-        CK(launch_pack(c, in, f32));
-        CK(launch_far(c, k, f32, out));
+        CK(launch_pack(c, in, mode));
+        CK(launch_far(c, k, mode, out));
         if (c->prof.on) (f32 ? c->prof.pairs_f32 : c->prof.pairs_f64) += far_pairs(c);
     }
     {
@@ -291,12 +316,13 @@ sbie_status gmres(sbie_ctx* c, const std::function<sbie_status(const double*, do
 // FP64 operator, corrections by GMRES on the mixed-precision operator.
 sbie_status solve_op(sbie_ctx* c, int op, const double* b, double* x, sbie_solve_info* info) {
     const long long n3 = c->N * 3;
-    auto A64 = [&](const double* in, double* out) { return apply_dev(c, op, false, in, out); };
-    auto A32 = [&](const double* in, double* out) { return apply_dev(c, op, true, in, out); };
+    // FP64-accurate operator: native FP64, or the far field in double-float
+    auto A64 = [&](const double* in, double* out) { return apply_dev(c, op, hi_mode(c), in, out); };
+    auto A32 = [&](const double* in, double* out) { return apply_dev(c, op, kModeF32, in, out); };
     const double tol = c->opts.tol;
     GmresOut go;
     sbie_solve_info inf{};
-    if (c->opts.prec == SBIE_FP64) {
+    if (c->opts.prec != SBIE_MIXED) {
         CKS(gmres(c, A64, b, x, tol, c->opts.restart, c->opts.max_iter, go));
         inf.iters = go.iters;
         inf.restarts = go.restarts;
@@ -371,7 +397,8 @@ sbie_status sphere_bie_create(int n, const double* centres, const double* radii,
     if (n < 1 || !centres || !radii || !opts) return fail(nullptr, SBIE_ERR_ARG, "need n >= 1 and non-NULL arrays");
     if (opts->p < 1 || opts->p > kMaxP) return fail(nullptr, SBIE_ERR_ARG, "p must be in [1, 24]");
     if (!(opts->eta >= 0.0) || !std::isfinite(opts->eta)) return fail(nullptr, SBIE_ERR_ARG, "eta must be >= 0");
-    if (opts->prec != SBIE_FP64 && opts->prec != SBIE_MIXED) return fail(nullptr, SBIE_ERR_ARG, "bad precision");
+    if (opts->prec != SBIE_FP64 && opts->prec != SBIE_MIXED && opts->prec != SBIE_FP64_DF)
+        return fail(nullptr, SBIE_ERR_ARG, "bad precision");
     if (opts->mem_kind != 0 && opts->mem_kind != 1) return fail(nullptr, SBIE_ERR_ARG, "mem_kind must be 0 or 1");
     if (opts->use_learned_precond != 0) return fail(nullptr, SBIE_ERR_ARG, "learned preconditioner not available");
     if (!(opts->tol > 0.0) || opts->restart < 1 || opts->max_iter < 0)
@@ -514,14 +541,14 @@ sbie_status sphere_bie_apply_operator(sbie_ctx* c, sbie_op op, const double* den
     if (!density || !out) return fail(c, SBIE_ERR_ARG, "NULL density or out");
     if (op < SBIE_OP_S || op > SBIE_OP_RESISTANCE) return fail(c, SBIE_ERR_ARG, "bad operator");
     if (density == out) return fail(c, SBIE_ERR_ARG, "density and out must not alias");
-    const bool f32 = c->opts.prec == SBIE_MIXED;
+    const int mode = c->opts.prec == SBIE_MIXED ? kModeF32 : hi_mode(c);
     const size_t bytes = sizeof(double) * 3 * (size_t)c->N;
     if (c->opts.mem_kind == 0) {
         CK(cudaMemcpyAsync(c->d_in, density, bytes, cudaMemcpyHostToDevice, c->stream));
-        CKS(apply_dev(c, op, f32, c->d_in, c->d_out));
+        CKS(apply_dev(c, op, mode, c->d_in, c->d_out));
         CK(cudaMemcpyAsync(out, c->d_out, bytes, cudaMemcpyDeviceToHost, c->stream));
     } else {
-        CKS(apply_dev(c, op, f32, density, out));
+        CKS(apply_dev(c, op, mode, density, out));
     }
     CK(cudaStreamSynchronize(c->stream));
     return SBIE_OK;
@@ -550,7 +577,7 @@ sbie_status sphere_bie_solve_mobility(sbie_ctx* c, const double* forces, const d
     double* mu = c->d_xsol;
     CK(launch_rho(c, F, T, rho));
     // b = -(1/2 I + K) rho
-    CKS(apply_dev(c, SBIE_OP_K, false, rho, b));
+    CKS(apply_dev(c, SBIE_OP_K, hi_mode(c), rho, b));
     CK(blas_lincomb(c, -0.5, rho, -1.0, b, b, n3));
     // keep rho: solve_op uses d_tmp in mixed mode, so copy it aside
     double* rho_keep = c->d_in;
@@ -560,7 +587,7 @@ sbie_status sphere_bie_solve_mobility(sbie_ctx* c, const double* forces, const d
     if (st != SBIE_OK && st != SBIE_ERR_NOT_CONVERGED) return st;
     // u = S[mu + rho] on every sphere; rigid projection
     CK(blas_lincomb(c, 1.0, mu, 1.0, rho_keep, c->d_tmp2, n3));
-    CKS(apply_dev(c, SBIE_OP_S, false, c->d_tmp2, c->d_out));
+    CKS(apply_dev(c, SBIE_OP_S, hi_mode(c), c->d_tmp2, c->d_out));
     double* V = c->opts.mem_kind == 0 ? dv : vel;
     double* W = c->opts.mem_kind == 0 ? dw : omega;
     CK(launch_rigid_projection(c, c->d_out, V, W));
@@ -627,53 +654,66 @@ const char* sphere_bie_last_error(const sbie_ctx* c) {
     return c ? c->err.c_str() : g_last_error.c_str();
 }
 
-sbie_status sphere_bie_autotune(sbie_ctx* c, sbie_op op, sbie_far_tuning* chosen) {
-    if (!c) return SBIE_ERR_ARG;
-    if (op < SBIE_OP_S || op > SBIE_OP_RESISTANCE) return fail(c, SBIE_ERR_ARG, "bad operator");
-    const Kern k = kern_of(op);
-    const int split_max = 16;
-    CKS(ensure_part(c, split_max));
-    CK(cudaMemsetAsync(c->d_srcf, 0, sizeof(float4) * c->N, c->stream));
+}  // extern "C"
+
+namespace {
+
+// Times every admissible tiling of one far-field kernel; keeps the fastest.
+sbie_status tune_one(sbie_ctx* c, Kern k, int mode, sbie_far_tuning* chosen) {
     struct Cand { FarTune t; float ms; };
     std::vector<Cand> cands;
-    const int tpts[2] = {2, 4}, ths[5] = {64, 96, 128, 192, 256}, splits[8] = {1, 2, 3, 4, 6, 8, 12, 16};
-    const int tiles[2] = {128, 256};
-    for (int tpt : tpts)
-        for (int th : ths) {
+    const bool f32 = mode == kModeF32;
+    const int tpts32[2] = {2, 4}, tpts1[1] = {1};
+    const int* tpts = f32 ? tpts32 : tpts1;
+    const int ntpt = f32 ? 2 : 1;
+    const int ths32[5] = {64, 96, 128, 192, 256}, thsdf[3] = {64, 128, 256};
+    const int* ths = f32 ? ths32 : thsdf;
+    const int nth = f32 ? 5 : 3;
+    const int splits32[8] = {1, 2, 3, 4, 6, 8, 12, 16}, splitsdf[4] = {1, 2, 4, 8};
+    const int* splits = f32 ? splits32 : splitsdf;
+    const int nsp = f32 ? 8 : 4;
+    const int tiles32[2] = {128, 256}, tilesdf[1] = {128};
+    const int* tiles = f32 ? tiles32 : tilesdf;
+    const int nti = f32 ? 2 : 1;
+    for (int a = 0; a < ntpt; ++a)
+        for (int b = 0; b < nth; ++b) {
+            const int tpt = tpts[a], th = ths[b];
             int slots = th * tpt;
             int chunks = (c->npn + slots - 1) / slots;
             double waste = (double)(chunks * slots - c->npn) / c->npn;
             if (waste > 0.30) continue;
-            for (int sp : splits) {
+            for (int s = 0; s < nsp; ++s) {
+                const int sp = splits[s];
                 long long ctas = (long long)c->n * chunks * sp;
-                if (ctas < c->sm_count && sp != splits[0]) continue;
+                if (ctas < c->sm_count && s != 0) continue;
                 if (ctas > 64LL * c->sm_count) continue;
-                for (int tile : tiles) {
-                    if ((c->N + sp - 1) / sp < tile) continue;
-                    cands.push_back(Cand{FarTune{th, tpt, sp, tile}, 0.f});
+                for (int t = 0; t < nti; ++t) {
+                    if ((c->N + sp - 1) / sp < tiles[t]) continue;
+                    cands.push_back(Cand{FarTune{th, tpt, sp, tiles[t]}, 0.f});
                 }
             }
         }
-    if (cands.empty()) cands.push_back(Cand{c->tune32[(int)k], 0.f});
+    FarTune* slot = f32 ? &c->tune32[(int)k] : &c->tunedf[(int)k];
+    if (cands.empty()) cands.push_back(Cand{*slot, 0.f});
     float dummy;
-    CK(time_far(c, k, true, cands[0].t, &dummy));  // warm-up
-    for (auto& cd : cands) CK(time_far(c, k, true, cd.t, &cd.ms));
+    CK(time_far(c, k, mode, cands[0].t, &dummy));  // warm-up
+    for (auto& cd : cands) CK(time_far(c, k, mode, cd.t, &cd.ms));
     std::sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
-    const size_t top = std::min<size_t>(6, cands.size());
+    const size_t top = std::min<size_t>(f32 ? 6 : 3, cands.size());
     for (size_t i = 0; i < top; ++i) {
         float best = cands[i].ms;
-        for (int r = 0; r < 3; ++r) {
+        for (int r = 0; r < 2; ++r) {
             float ms;
-            CK(time_far(c, k, true, cands[i].t, &ms));
+            CK(time_far(c, k, mode, cands[i].t, &ms));
             best = std::min(best, ms);
         }
         cands[i].ms = best;
     }
     std::sort(cands.begin(), cands.begin() + top, [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
-    c->tune32[(int)k] = cands[0].t;
+    *slot = cands[0].t;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[std::make_tuple(c->n, c->p, c->sm_count, (int)k, 1)] = cands[0].t;
+        g_tune_cache[std::make_tuple(c->n, c->p, c->sm_count, (int)k, mode)] = cands[0].t;
     }
     if (chosen) {
         chosen->threads = cands[0].t.threads;
@@ -683,6 +723,23 @@ sbie_status sphere_bie_autotune(sbie_ctx* c, sbie_op op, sbie_far_tuning* chosen
         chosen->ms = cands[0].ms;
         chosen->candidates = (int)cands.size();
     }
+    return SBIE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sbie_status sphere_bie_autotune(sbie_ctx* c, sbie_op op, sbie_far_tuning* chosen) {
+    if (!c) return SBIE_ERR_ARG;
+    if (op < SBIE_OP_S || op > SBIE_OP_RESISTANCE) return fail(c, SBIE_ERR_ARG, "bad operator");
+    const Kern k = kern_of(op);
+    CKS(ensure_part(c, 16));
+    CK(cudaMemsetAsync(c->d_srcf, 0, sizeof(float4) * c->N, c->stream));
+    CK(cudaMemsetAsync(c->d_src64, 0, sizeof(double4) * c->N, c->stream));
+    if (chosen) std::memset(chosen, 0, 2 * sizeof(*chosen));
+    if (c->opts.prec == SBIE_MIXED) CKS(tune_one(c, k, kModeF32, chosen));
+    if (c->opts.prec != SBIE_FP64) CKS(tune_one(c, k, kModeDF, chosen ? chosen + 1 : nullptr));
     return SBIE_OK;
 }
 

@@ -16,6 +16,10 @@ constexpr int kMaxP = 24;
 
 enum class Kern { S = 0, D = 1, K = 2 };
 
+// Arithmetic of one operator apply: FP64 everywhere; FP32 far field and
+// close-pair evaluation; FP64 with the far field in double-float arithmetic.
+constexpr int kModeF64 = 0, kModeF32 = 1, kModeDF = 2;
+
 // Offsets into the packed FP64 table of one order p (device copy in Ctx::tab).
 struct TabLayout {
     int p, nlat, nlon, npn;
@@ -123,7 +127,7 @@ struct sbie_ctx {
     double* d_res = nullptr;     // [3N]
     int krylov_m = 0;
 
-    sbie::FarTune tune64[3]{}, tune32[3]{};  // per far-field kernel (S, D, K)
+    sbie::FarTune tune64[3]{}, tune32[3]{}, tunedf[3]{};  // per far-field kernel (S, D, K)
     sbie::Profile prof;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[8];
     int prof_used[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -163,10 +167,10 @@ void set_last_error(const std::string& msg);
 cudaError_t launch_self(sbie_ctx* c, Kern op, const double* dens, double* out, bool accumulate, bool write_coef);
 cudaError_t launch_analysis_only(sbie_ctx* c, const double* dens);
 // far.cu
-cudaError_t launch_pack(sbie_ctx* c, const double* dens, bool f32);
-cudaError_t launch_far(sbie_ctx* c, Kern op, bool f32, double* out);
+cudaError_t launch_pack(sbie_ctx* c, const double* dens, int mode);
+cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out);
 // Times one launch of the far-field pair kernel with tiling `tu` (no reduce); *ms = event time.
-cudaError_t time_far(sbie_ctx* c, Kern op, bool f32, const FarTune& tu, float* ms);
+cudaError_t time_far(sbie_ctx* c, Kern op, int mode, const FarTune& tu, float* ms);
 long long far_pairs(const sbie_ctx* c);
 // near.cu
 cudaError_t launch_near(sbie_ctx* c, Kern op, bool f32, double* out);

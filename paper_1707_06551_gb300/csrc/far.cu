@@ -214,6 +214,160 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
     }
 }
 
+// ---- double-float ("df") arithmetic: a value is the unevaluated sum hi + lo of
+// two floats.  Building blocks: Knuth's TwoSum, Dekker's Fast2Sum and the
+// FMA-based exact product; about 48 significant bits.
+struct df {
+    float h, l;
+};
+__device__ __forceinline__ df df_split(double x) {
+    float h = (float)x;
+    return df{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = a + b;
+    return df{s, b - (s - a)};
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    return df{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ df df_sub(df x, df y) {  // x - y
+    df s = two_sum(x.h, -y.h);
+    s.l += x.l - y.l;
+    return fast_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+    df s = two_sum(x.h, y.h);
+    s.l += x.l + y.l;
+    return fast_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ df df_mul(df x, df y) {
+    float p = x.h * y.h;
+    float e = fmaf(x.h, y.h, -p);
+    e = fmaf(x.h, y.l, e);
+    e = fmaf(x.l, y.h, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_sqr(df x) {
+    float p = x.h * x.h;
+    float e = fmaf(x.h, x.h, -p);
+    e = fmaf(2.f * x.h, x.l, e);
+    return fast_two_sum(p, e);
+}
+// 1/sqrt(x) for x > 0: hardware estimate y0, then one Newton step carried in
+// df with its second-order term: y = y0 (1 - t/2 + 3 t^2 / 8), t = x y0^2 - 1.
+__device__ __forceinline__ df df_rsqrt(df x) {
+    float y0 = rsqrt_approx(x.h);
+    float q = y0 * y0;
+    float ql = fmaf(y0, y0, -q);
+    float h = x.h * q;
+    float e = fmaf(x.h, q, -h);
+    e = fmaf(x.h, ql, e);
+    e = fmaf(x.l, q, e);
+    float t = (h - 1.0f) + e;
+    float corr = y0 * t * fmaf(0.375f, t, -0.5f);
+    return fast_two_sum(y0, corr);
+}
+
+// Far field with every pair evaluated in df arithmetic (about 1e-13 relative
+// per pair), sums within a tile in df and across tiles in FP64.  Sources are
+// staged relative to the target sphere's centre, computed in FP64 and split.
+template <int OP>
+__global__ void __launch_bounds__(256) far_df_kernel(FarArgs a) {
+    constexpr int NV = (OP == (int)Kern::D) ? 5 : 3;  // float4 per staged source: pos(6) dens(6) [nrm(6)]
+    const int sphere = blockIdx.x / a.chunks, chunk = blockIdx.x - sphere * a.chunks;
+    const int split = blockIdx.y;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    extern __shared__ float4 smem4[];
+    unsigned* flags = reinterpret_cast<unsigned*>(smem4 + NV * a.tile);
+    build_flags(a, sphere, flags);
+    const double cx = a.c[3 * sphere], cy = a.c[3 * sphere + 1], cz = a.c[3 * sphere + 2];
+    const int q = chunk * bd + tid;
+    const bool tval = q < a.npn;
+    const long long tnode = (long long)sphere * a.npn + (tval ? q : a.npn - 1);
+    const double4 X = a.x64[tnode];
+    const df tx = df_split(X.x - cx), ty = df_split(X.y - cy), tz = df_split(X.z - cz);
+    df tnx{0.f, 0.f}, tny{0.f, 0.f}, tnz{0.f, 0.f};
+    if (OP == (int)Kern::K) {
+        const double4 nn = a.nrm64[tnode];
+        tnx = df_split(nn.x); tny = df_split(nn.y); tnz = df_split(nn.z);
+    }
+    double sum[3] = {0.0, 0.0, 0.0};
+    const long long b0 = (long long)split * a.split_len;
+    const long long b1 = min(a.N, b0 + a.split_len);
+    for (long long base = b0; base < b1; base += a.tile) {
+        __syncthreads();
+        for (int j = tid; j < a.tile; j += bd) {
+            long long s = base + j;
+            double px = 1.0e4, py = 1.0e4, pz = 1.0e4, fx = 0, fy = 0, fz = 0, nx = 0, ny = 0, nz = 0;
+            if (s < b1) {
+                int k = a.sph[s];
+                if (!((flags[k >> 5] >> (k & 31)) & 1u)) {
+                    const double4 P = a.x64[s];
+                    px = P.x - cx; py = P.y - cy; pz = P.z - cz;
+                    const double4 F = a.src64[s];
+                    fx = F.x; fy = F.y; fz = F.z;
+                    if (OP == (int)Kern::D) {
+                        const double4 nn = a.nrm64[s];
+                        nx = nn.x; ny = nn.y; nz = nn.z;
+                    }
+                }
+            }
+            const df qx = df_split(px), qy = df_split(py), qz = df_split(pz);
+            const df gx = df_split(fx), gy = df_split(fy), gz = df_split(fz);
+            float4* dst = smem4 + (size_t)j * NV;
+            dst[0] = make_float4(qx.h, qx.l, qy.h, qy.l);
+            dst[1] = make_float4(qz.h, qz.l, gx.h, gx.l);
+            dst[2] = make_float4(gy.h, gy.l, gz.h, gz.l);
+            if (OP == (int)Kern::D) {
+                const df mx = df_split(nx), my = df_split(ny), mz = df_split(nz);
+                dst[3] = make_float4(mx.h, mx.l, my.h, my.l);
+                dst[4] = make_float4(mz.h, mz.l, 0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        df acc0{0.f, 0.f}, acc1{0.f, 0.f}, acc2{0.f, 0.f};
+#pragma unroll 2
+        for (int j = 0; j < a.tile; ++j) {
+            const float4* src = smem4 + (size_t)j * NV;
+            const float4 v0 = src[0], v1 = src[1], v2 = src[2];
+            const df dx = df_sub(tx, df{v0.x, v0.y}), dy = df_sub(ty, df{v0.z, v0.w}), dz = df_sub(tz, df{v1.x, v1.y});
+            const df fx{v1.z, v1.w}, fy{v2.x, v2.y}, fz{v2.z, v2.w};
+            const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+            const df ri = df_rsqrt(r2);
+            const df ri2 = df_sqr(ri);
+            const df rf = df_add(df_add(df_mul(dx, fx), df_mul(dy, fy)), df_mul(dz, fz));
+            if (OP == (int)Kern::S) {
+                const df s3 = df_mul(df_mul(rf, ri), ri2);
+                acc0 = df_add(acc0, df_add(df_mul(fx, ri), df_mul(dx, s3)));
+                acc1 = df_add(acc1, df_add(df_mul(fy, ri), df_mul(dy, s3)));
+                acc2 = df_add(acc2, df_add(df_mul(fz, ri), df_mul(dz, s3)));
+            } else {
+                df rn;
+                if (OP == (int)Kern::D) {
+                    const float4 v3 = src[3], v4 = src[4];
+                    rn = df_add(df_add(df_mul(dx, df{v3.x, v3.y}), df_mul(dy, df{v3.z, v3.w})), df_mul(dz, df{v4.x, v4.y}));
+                } else {
+                    rn = df_add(df_add(df_mul(dx, tnx), df_mul(dy, tny)), df_mul(dz, tnz));
+                }
+                const df s5 = df_mul(df_mul(rf, rn), df_mul(df_sqr(ri2), ri));
+                acc0 = df_add(acc0, df_mul(dx, s5));
+                acc1 = df_add(acc1, df_mul(dy, s5));
+                acc2 = df_add(acc2, df_mul(dz, s5));
+            }
+        }
+        sum[0] += (double)acc0.h + (double)acc0.l;
+        sum[1] += (double)acc1.h + (double)acc1.l;
+        sum[2] += (double)acc2.h + (double)acc2.l;
+    }
+    if (tval) {
+        double* out = a.part + (size_t)split * a.N * 3;
+        for (int d = 0; d < 3; ++d) out[tnode * 3 + d] = sum[d];
+    }
+}
+
 template <int OP, int TPT>
 __global__ void __launch_bounds__(256) far_f64_kernel(FarArgs a) {
     constexpr int NV = (OP == (int)Kern::D) ? 3 : 2;
@@ -330,9 +484,10 @@ __global__ void pack_kernel(const double* __restrict__ dens, const double* __res
     if (src64) src64[i] = make_double4(fx, fy, fz, 0.0);
 }
 
-cudaError_t launch_pack(sbie_ctx* c, const double* dens, bool f32) {
+cudaError_t launch_pack(sbie_ctx* c, const double* dens, int mode) {
     int th = 256;
     long long blocks = (c->N + th - 1) / th;
+    const bool f32 = mode == kModeF32;
     pack_kernel<<<(unsigned)blocks, th, 0, c->stream>>>(dens, c->d_x, c->N, f32 ? c->d_srcf : nullptr,
                                                         f32 ? nullptr : c->d_src64); ++c->n_launch;
     return cudaGetLastError();
@@ -345,6 +500,19 @@ long long far_pairs(const sbie_ctx* c) {
         tot += (long long)c->npn * (c->N - excl * c->npn);
     }
     return tot;
+}
+
+template <int OP>
+static cudaError_t launch_far_df(sbie_ctx* c, const FarTune& tu, const FarArgs& a) {
+    dim3 grid(c->n * a.chunks, tu.split);
+    const int nv = (OP == (int)Kern::D) ? 5 : 3;
+    size_t sm = (size_t)nv * tu.tile * sizeof(float4) + ((c->n + 31) / 32) * sizeof(unsigned);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(far_df_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    far_df_kernel<OP><<<grid, tu.threads, sm, c->stream>>>(a); ++c->n_launch;
+    return cudaGetLastError();
 }
 
 template <int OP, int TPT>
@@ -398,8 +566,16 @@ static FarArgs make_args(sbie_ctx* c, const FarTune& tu) {
     return a;
 }
 
-static cudaError_t launch_pair_kernel(sbie_ctx* c, Kern op, bool f32, const FarTune& tu) {
+static cudaError_t launch_pair_kernel(sbie_ctx* c, Kern op, int mode, const FarTune& tu) {
     FarArgs a = make_args(c, tu);
+    if (mode == kModeDF) {
+        switch (op) {
+            case Kern::S: return launch_far_df<(int)Kern::S>(c, tu, a);
+            case Kern::D: return launch_far_df<(int)Kern::D>(c, tu, a);
+            default: return launch_far_df<(int)Kern::K>(c, tu, a);
+        }
+    }
+    const bool f32 = mode == kModeF32;
     switch (op) {
         case Kern::S: return launch_far_op<(int)Kern::S>(c, tu, f32, a);
         case Kern::D: return launch_far_op<(int)Kern::D>(c, tu, f32, a);
@@ -407,12 +583,12 @@ static cudaError_t launch_pair_kernel(sbie_ctx* c, Kern op, bool f32, const FarT
     }
 }
 
-cudaError_t launch_far(sbie_ctx* c, Kern op, bool f32, double* out) {
-    const FarTune& tu = f32 ? c->tune32[(int)op] : c->tune64[(int)op];
+cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out) {
+    const FarTune& tu = mode == kModeF32 ? c->tune32[(int)op] : (mode == kModeDF ? c->tunedf[(int)op] : c->tune64[(int)op]);
     cudaError_t e;
     {
-        StageScope st(c, f32 ? ST_FARK32 : ST_FARK64);
-        e = launch_pair_kernel(c, op, f32, tu);
+        StageScope st(c, mode == kModeF32 ? ST_FARK32 : ST_FARK64);
+        e = launch_pair_kernel(c, op, mode, tu);
     }
     if (e != cudaSuccess) return e;
     double scale = (op == Kern::S) ? 1.0 / (8.0 * kPi) : (op == Kern::D ? 3.0 / (4.0 * kPi) : -3.0 / (4.0 * kPi));
@@ -421,14 +597,14 @@ cudaError_t launch_far(sbie_ctx* c, Kern op, bool f32, double* out) {
     return cudaGetLastError();
 }
 
-cudaError_t time_far(sbie_ctx* c, Kern op, bool f32, const FarTune& tu, float* ms) {
+cudaError_t time_far(sbie_ctx* c, Kern op, int mode, const FarTune& tu, float* ms) {
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e != cudaSuccess) return e;
     e = cudaEventCreate(&e1);
     if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
     e = cudaEventRecord(e0, c->stream);
-    if (e == cudaSuccess) e = launch_pair_kernel(c, op, f32, tu);
+    if (e == cudaSuccess) e = launch_pair_kernel(c, op, mode, tu);
     if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);

@@ -168,8 +168,8 @@ extern "C" sbie_status sphere_bie_apply_layer_noalloc(sbie_op op, int n_spheres,
     // start empty; every other slot is fully rewritten below before it is read.
     e = cudaMemsetAsync(c.d_near_ptr, 0, sizeof(int) * (n_spheres + 1), c.stream);
     if (e == cudaSuccess) e = launch_geometry(&c);
-    if (e == cudaSuccess) e = launch_pack(&c, density, false);
-    if (e == cudaSuccess) e = launch_far(&c, k, false, out);
+    if (e == cudaSuccess) e = launch_pack(&c, density, kModeF64);
+    if (e == cudaSuccess) e = launch_far(&c, k, kModeF64, out);
     if (e == cudaSuccess) e = launch_self(&c, k, density, out, true, false);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) {

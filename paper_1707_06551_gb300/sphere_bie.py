@@ -18,7 +18,7 @@ SBIE_OK, SBIE_ERR_ARG, SBIE_ERR_OVERLAP, SBIE_ERR_CUDA, SBIE_ERR_OOM = 0, 1, 2, 
 SBIE_ERR_NOT_CONVERGED, SBIE_ERR_TIMEOUT, SBIE_ERR_NUMERIC = 5, 6, 7
 STATUS_NAMES = {0: "SBIE_OK", 1: "SBIE_ERR_ARG", 2: "SBIE_ERR_OVERLAP", 3: "SBIE_ERR_CUDA", 4: "SBIE_ERR_OOM",
                 5: "SBIE_ERR_NOT_CONVERGED", 6: "SBIE_ERR_TIMEOUT", 7: "SBIE_ERR_NUMERIC"}
-SBIE_FP64, SBIE_MIXED = 0, 1
+SBIE_FP64, SBIE_MIXED, SBIE_FP64_DF = 0, 1, 2
 SBIE_OP_S, SBIE_OP_D, SBIE_OP_K, SBIE_OP_MOBILITY, SBIE_OP_RESISTANCE = 0, 1, 2, 3, 4
 OPS = {"S": 0, "D": 1, "K": 2, "mobility": 3, "resistance": 4}
 STAGES = ("far", "near", "self", "completion", "arnoldi", "other", "far_kernel_f32", "far_kernel_f64")
@@ -196,9 +196,9 @@ def sphere_bie_last_error(ctx=None):
 
 def sphere_bie_autotune(ctx, op):
     op = OPS[op] if isinstance(op, str) else int(op)
-    t = FarTuning()
-    _check(ctx, lib().sphere_bie_autotune(ctx, op, ctypes.byref(t)))
-    return {k: getattr(t, k) for k, _ in t._fields_}
+    t = (FarTuning * 2)()
+    _check(ctx, lib().sphere_bie_autotune(ctx, op, t))
+    return {name: {k: getattr(t[i], k) for k, _ in FarTuning._fields_} for i, name in enumerate(("fp32", "df"))}
 
 
 def sphere_bie_profile(ctx, enable):

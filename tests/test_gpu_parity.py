@@ -50,14 +50,16 @@ def _geom(name):
     return w["centres"], w["radii"], w["p"]
 
 
+@pytest.mark.parametrize("prec", [0, 2])
 @pytest.mark.parametrize("geom", list(GEOMS))
 @pytest.mark.parametrize("op", OPS)
-def test_apply_fp64_matches_oracle(sb, geom, op):
+def test_apply_fp64_matches_oracle(sb, geom, op, prec):
+    """SBIE_FP64 (native) and SBIE_FP64_DF (double-float far field) applies."""
     c, a, p = _geom(geom)
     g = ops.Geometry(c, a, p)
     dens = np.random.default_rng(3).normal(size=(g.N, 3))
     ref = ops.apply(g, op, dens)
-    with sb.SphereBIE(c, a, p) as s:
+    with sb.SphereBIE(c, a, p, prec=prec) as s:
         out = s.apply(op, dens)
     assert _err(out, ref) < TOL64
 
@@ -96,7 +98,7 @@ def test_single_sphere_operator(sb):
 
 
 @pytest.mark.parametrize("a", [0.5, 2.0])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_single_sphere_closed_forms(sb, a, prec):
     """Drag 6 pi a U and torque 8 pi a^3 Omega (resistance) and their inverse (mobility)."""
     U = np.array([[1.0, 0.5, -0.3]])
@@ -110,7 +112,7 @@ def test_single_sphere_closed_forms(sb, a, prec):
         np.testing.assert_allclose(w, W, rtol=1e-9)
 
 
-@pytest.mark.parametrize("prec,tolF", [(0, 1e-8), (1, 1e-6)])
+@pytest.mark.parametrize("prec,tolF", [(0, 1e-8), (1, 1e-6), (2, 1e-8)])
 def test_resistance_solve_matches_oracle(sb, prec, tolF):
     c, a, p = _geom("poly_p6")
     g = ops.Geometry(c, a, p)
@@ -126,7 +128,7 @@ def test_resistance_solve_matches_oracle(sb, prec, tolF):
     assert _err(F, Fr) < tolF and _err(T, Tr) < tolF
 
 
-@pytest.mark.parametrize("prec,tolV", [(0, 1e-8), (1, 1e-6)])
+@pytest.mark.parametrize("prec,tolV", [(0, 1e-8), (1, 1e-6), (2, 1e-8)])
 def test_mobility_8_solve_matches_oracle(sb, prec, tolV):
     w8 = wl.mobility_8()
     g = ops.Geometry(w8["centres"], w8["radii"], w8["p"])
@@ -148,7 +150,7 @@ def test_resistance_256_sampled_parity(sb):
     rows = np.concatenate([np.arange(g.sl(i).start, g.sl(i).stop) for i in sample])
     dens = np.random.default_rng(11).normal(size=(g.N, 3))
     ref = ops.apply_at(g, "resistance", dens, sample)[rows]
-    for prec, tol in ((0, TOL64), (1, TOL32)):
+    for prec, tol in ((0, TOL64), (2, TOL64), (1, TOL32)):
         with sb.SphereBIE(w["centres"], w["radii"], w["p"], prec=prec, tol=w["tol"]) as s:
             out = s.apply("resistance", dens)[rows]
             assert _err(out, ref) < tol
@@ -163,6 +165,30 @@ def test_not_converged_reports_and_fills(sb):
         F, T, info = s.resistance(np.ones((len(a), 3)), np.zeros((len(a), 3)))
     assert info["status"] == sb.SBIE_ERR_NOT_CONVERGED
     assert info["iters"] == 2 and np.all(np.isfinite(F)) and np.any(F != 0)
+
+
+@pytest.mark.parametrize("op", ["S", "D", "K"])
+def test_df_far_field_is_fp64_accurate(sb, op):
+    """The double-float far field agrees with native FP64 far below the 1e-10
+    parity bound (all pairs far, so the far field is the whole off-self sum)."""
+    c, a, p = _geom("poly_p6")
+    dens = np.random.default_rng(13).normal(size=(len(a) * (p + 1) * (2 * p + 2), 3))
+    with sb.SphereBIE(c, a, p, eta=0.0, prec=0) as s:
+        ref = s.apply(op, dens)
+    with sb.SphereBIE(c, a, p, eta=0.0, prec=2) as s:
+        got = s.apply(op, dens)
+    assert _err(got, ref) < 1e-12
+
+
+def test_autotune_keeps_results(sb):
+    c, a, p = _geom("p9_ragged")
+    dens = np.random.default_rng(14).normal(size=(len(a) * (p + 1) * (2 * p + 2), 3))
+    with sb.SphereBIE(c, a, p, prec=1) as s:
+        before = s.apply("D", dens)
+        tun = sb.sphere_bie_autotune(s.ctx, "resistance")
+        assert tun["fp32"]["candidates"] > 0 and tun["df"]["candidates"] > 0
+        after = s.apply("D", dens)
+    assert _err(after, before) < 1e-5
 
 
 def test_device_pointer_interface_matches_host(sb):

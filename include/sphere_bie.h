@@ -99,7 +99,20 @@ sbie_status sphere_bie_default_opts(sbie_opts* opts);
 sbie_status sphere_bie_create(int n_spheres, const double* centres, const double* radii,
                               const sbie_opts* opts, sbie_ctx** out);
 
-/* Number of quadrature nodes N = n_spheres (p+1)(2p+2). */
+/* A batch of independent problems (suspensions) in one context: problem q has
+ * n_spheres[q] spheres and VSH order p_per_problem[q] (opts->p is ignored);
+ * centres [sum n][3] and radii [sum n] are the problems' arrays concatenated
+ * in problem order (host memory).  Nodes, densities and per-sphere arrays of
+ * every later call are likewise concatenated in problem order.  Close pairs
+ * (Eq. 4.5) and the far field (Eq. 4.4) never couple different problems, and
+ * a solve runs one GMRES per problem (each to opts->tol) with one operator
+ * launch sequence per distinct p serving all problems of that order.
+ * sphere_bie_create is this call with one problem. */
+sbie_status sphere_bie_create_batch(int n_problems, const int* n_spheres, const int* p_per_problem,
+                                    const double* centres, const double* radii, const sbie_opts* opts,
+                                    sbie_ctx** out);
+
+/* Number of quadrature nodes N = sum over spheres of (p+1)(2p+2). */
 sbie_status sphere_bie_num_nodes(const sbie_ctx* ctx, long long* n_nodes);
 
 /* Host copies of node positions, outward normals ([N][3] each) and smooth
@@ -113,6 +126,9 @@ sbie_status sphere_bie_nodes(const sbie_ctx* ctx, double* xyz, double* normals, 
  * density, out: [N][3]; host or device per opts.mem_kind; must not alias.
  * Precision per opts.prec. */
 sbie_status sphere_bie_apply_operator(sbie_ctx* ctx, sbie_op op, const double* density, double* out);
+
+/* For a batch the solve outputs are per problem, concatenated; info reports
+ * the total inner iterations and the worst true residual over problems. */
 
 /* Mobility problem (Problem 2, Eqs. 5.5-5.8): given force F_k and torque T_k
  * on each sphere ([n][3] each), solve (1/2 I + K + L) mu = -(1/2 I + K) rho

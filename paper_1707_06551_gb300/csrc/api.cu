@@ -48,10 +48,15 @@ cudaError_t dmalloc(T** p, size_t count) {
 }
 
 void free_all(sbie_ctx* c) {
+    for (sbie_ctx* q : c->parts) {
+        free_all(q);
+        delete q;
+    }
+    c->parts.clear();
     void* ptrs[] = {c->d_c, c->d_a, c->d_x, c->d_xhi, c->d_xlo, c->d_nrm, c->d_nrm64, c->d_sph, c->d_near_ptr,
                     c->d_near_idx, c->d_tab, c->d_coef, c->d_chan, c->d_chanf, c->d_mom, c->d_part, c->d_src64,
                     c->d_srcf, c->d_in, c->d_out, c->d_tmp, c->d_tmp2, c->d_small, c->d_red, c->d_V, c->d_xsol,
-                    c->d_rhs, c->d_res};
+                    c->d_rhs, c->d_res, c->d_prob_sph, c->d_sph_prob, c->d_node_prob, c->d_seg3, c->d_H, c->d_pvec};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -184,185 +189,297 @@ sbie_status apply_dev(sbie_ctx* c, int op, int mode, const double* in, double* o
     return SBIE_OK;
 }
 
-double nrm2(sbie_ctx* c, const double* v, long long n, sbie_status* st) {
-    double r = 0.0;
-    cudaError_t e = blas_dots(c, v, 1, n, v, n, &r);
-    if (e != cudaSuccess) {
-        c->err = std::string("norm: ") + cudaGetErrorString(e);
-        *st = SBIE_ERR_CUDA;
-        return 0.0;
+// ---- system view: the parts (one per VSH order) and the problem segments of
+// a context's vector.  A single-order context is its own only part.
+struct Sys {
+    sbie_ctx* top;
+    std::vector<sbie_ctx*> parts;
+    std::vector<long long> off3;
+    long long n3;
+    int P;
+};
+
+Sys sys_of(sbie_ctx* c) {
+    Sys s;
+    s.top = c;
+    if (c->is_batch) {
+        s.parts = c->parts;
+        s.off3 = c->part_off3;
+    } else {
+        s.parts = {c};
+        s.off3 = {0};
     }
-    *st = SBIE_OK;
-    return std::sqrt(r);
+    s.n3 = c->N * 3;
+    s.P = (int)c->seg3.size() - 1;
+    return s;
 }
 
-sbie_status ensure_krylov(sbie_ctx* c, int m) {
-    if (c->d_V && c->krylov_m >= m) return SBIE_OK;
-    if (c->d_V) cudaFree(c->d_V);
-    c->d_V = nullptr;
-    if (dmalloc(&c->d_V, (size_t)(m + 1) * c->N * 3) != cudaSuccess) return fail(c, SBIE_ERR_OOM, "Krylov basis");
-    c->krylov_m = m;
+sbie_status apply_sys(const Sys& S, int op, int mode, const double* in, double* out) {
+    for (size_t i = 0; i < S.parts.size(); ++i) {
+        sbie_status st = apply_dev(S.parts[i], op, mode, in + S.off3[i], out + S.off3[i]);
+        if (st != SBIE_OK) {
+            if (S.parts[i] != S.top) S.top->err = S.parts[i]->err;
+            return st;
+        }
+    }
+    return SBIE_OK;
+}
+
+sbie_status ensure_krylov(sbie_ctx* c, int m, int P) {
+    const int B = seg_blocks(c->N * 3, P);
+    if (!c->d_V || c->krylov_m < m) {
+        if (c->d_V) cudaFree(c->d_V);
+        c->d_V = nullptr;
+        c->krylov_m = 0;
+        if (dmalloc(&c->d_V, (size_t)(m + 1) * c->N * 3) != cudaSuccess) return fail(c, SBIE_ERR_OOM, "Krylov basis");
+        c->krylov_m = m;
+    }
+    const size_t red = (size_t)(m + 1) * P * B + 64;
+    if (red > c->red_cap) {
+        if (c->d_red) cudaFree(c->d_red);
+        c->d_red = nullptr;
+        c->red_cap = 0;
+        if (dmalloc(&c->d_red, red) != cudaSuccess) return fail(c, SBIE_ERR_OOM, "reduction scratch");
+        c->red_cap = red;
+    }
+    const size_t small = (size_t)(m + 1) * P + 64;
+    if (2 * small > c->hred_cap) {
+        if (c->h_red) cudaFreeHost(c->h_red);
+        if (c->d_H) cudaFree(c->d_H);
+        if (c->d_pvec) cudaFree(c->d_pvec);
+        c->h_red = nullptr;
+        c->d_H = c->d_pvec = nullptr;
+        c->hred_cap = 0;
+        if (cudaMallocHost(reinterpret_cast<void**>(&c->h_red), sizeof(double) * 2 * small) != cudaSuccess ||
+            dmalloc(&c->d_H, small) != cudaSuccess || dmalloc(&c->d_pvec, small) != cudaSuccess)
+            return fail(c, SBIE_ERR_OOM, "small solver buffers");
+        c->hred_cap = 2 * small;
+    }
+    return SBIE_OK;
+}
+
+// Per-problem 2-norms of v (all problems of the system).
+sbie_status seg_norms(const Sys& S, const double* v, std::vector<double>& out) {
+    sbie_ctx* c = S.top;
+    if (!c->d_pvec || !c->h_red || !c->d_red || c->hred_cap < 2 * (size_t)S.P)
+        return fail(c, SBIE_ERR_ARG, "internal: solver buffers not allocated");
+    CK(seg_dots(c, v, 1, S.n3, v, S.n3, c->d_seg3, S.P, c->d_pvec));
+    CK(cudaMemcpyAsync(c->h_red, c->d_pvec, sizeof(double) * S.P, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    out.resize(S.P);
+    for (int p = 0; p < S.P; ++p) out[p] = std::sqrt(std::max(0.0, c->h_red[p]));
+    return SBIE_OK;
+}
+
+// Stage a per-problem (or [k][P]) host array into the device matrix d_H.
+sbie_status stage_H(sbie_ctx* c, const double* host, size_t count) {
+    if (!c->h_red || !c->d_H || 2 * count > c->hred_cap) return fail(c, SBIE_ERR_ARG, "internal: staging overflow");
+    double* st = c->h_red + c->hred_cap / 2;
+    std::memcpy(st, host, sizeof(double) * count);
+    CK(cudaMemcpyAsync(c->d_H, st, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
     return SBIE_OK;
 }
 
 struct GmresOut {
     int iters = 0, restarts = 0;
-    double rel = 0.0;  // residual of the final iterate, recomputed with A
-    bool converged = false;
+    std::vector<double> rel;  // per problem, residual of the final iterate recomputed with A
 };
 
-// Restarted GMRES with classical Gram-Schmidt applied twice, x0 = 0.
-// A(in, out) applies the operator to device vectors.  The residual at every
-// restart (and at the end) is recomputed as b - A x.
-sbie_status gmres(sbie_ctx* c, const std::function<sbie_status(const double*, double*)>& A, const double* b,
-                  double* x, double tol, int restart, int max_iter, GmresOut& go) {
-    const long long n3 = c->N * 3;
+using AFn = std::function<sbie_status(const double*, double*)>;
+
+// Restarted GMRES, one Krylov space per problem (classical Gram-Schmidt
+// applied twice), x0 = 0.  Problem p runs while want[p] and its relative
+// residual exceeds tol[p]; the residual is recomputed as b - A x at every
+// restart.  A problem that has converged keeps zero Krylov vectors.
+sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const std::vector<double>& tol,
+                  const std::vector<char>& want, int restart, int max_iter, GmresOut& go) {
+    sbie_ctx* c = S.top;
+    const long long n3 = S.n3;
+    const int P = S.P;
     restart = std::max(1, std::min(restart, 250));
-    CKS(ensure_krylov(c, restart));
-    sbie_status st;
-    const double nb = nrm2(c, b, n3, &st);
-    CKS(st);
+    CKS(ensure_krylov(c, restart, P));
+    const int m = restart;
+    std::vector<double> nb, beta, hk1;
+    CKS(seg_norms(S, b, nb));
     CK(cudaMemsetAsync(x, 0, sizeof(double) * n3, c->stream));
     go = GmresOut();
-    if (!(nb > 0.0)) {
-        if (!std::isfinite(nb)) return fail(c, SBIE_ERR_NUMERIC, "right-hand side is not finite");
-        go.converged = true;
-        return SBIE_OK;
-    }
+    go.rel.assign(P, 0.0);
+    for (int p = 0; p < P; ++p)
+        if (!std::isfinite(nb[p])) return fail(c, SBIE_ERR_NUMERIC, "right-hand side is not finite");
+    std::vector<char> active(P, 0);
+    for (int p = 0; p < P; ++p) active[p] = want[p] && nb[p] > 0.0 && 1.0 > tol[p];
     double* r = c->d_res;
     CK(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->stream));
-    double beta = nb;
-    std::vector<double> H((restart + 1) * restart), cs(restart), sn(restart), g(restart + 1), h(restart + 1),
-        h2(restart + 1), y(restart);
-    double* d_h = c->d_red + 2 * 296 * 256;  // scratch for small device vectors (after dot partials)
+    beta = nb;
+    std::vector<double> H((size_t)P * (m + 1) * m), cs((size_t)P * m), sn((size_t)P * m), g((size_t)P * (m + 1));
+    std::vector<double> hcol((size_t)(m + 1) * P), h2((size_t)(m + 1) * P), stage((size_t)(m + 1) * P), y(m);
+    std::vector<int> kd(P);
+    std::vector<char> live(P);
     int total = 0;
-    while (true) {
-        if (beta / nb <= tol) {
-            go.converged = true;
-            break;
-        }
-        if (total >= max_iter) break;
-        const int m = std::min(restart, max_iter - total);
+    auto any = [](const std::vector<char>& v) {
+        for (char q : v)
+            if (q) return true;
+        return false;
+    };
+    while (any(active) && total < max_iter) {
+        const int mm = std::min(m, max_iter - total);
         double* V = c->d_V;
-        CK(blas_scale_copy(c, 1.0 / beta, r, V, n3));
+        for (int p = 0; p < P; ++p) stage[p] = active[p] ? 1.0 / beta[p] : 0.0;
+        CKS(stage_H(c, stage.data(), P));
+        CK(seg_scale(c, r, c->d_H, c->d_node_prob, V, n3));
         std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        int kd = 0;
-        bool breakdown = false;
-        for (int k = 0; k < m; ++k) {
+        for (int p = 0; p < P; ++p) {
+            g[(size_t)p * (m + 1)] = active[p] ? beta[p] : 0.0;
+            kd[p] = 0;
+            live[p] = active[p];
+        }
+        for (int k = 0; k < mm && any(live); ++k) {
             double* w = V + (size_t)(k + 1) * n3;
             CKS(A(V + (size_t)k * n3, w));
             {
-                StageScope s(c, ST_BLAS);
-                CK(blas_dots(c, V, k + 1, n3, w, n3, h.data()));
-                std::memcpy(c->h_red + 256, h.data(), sizeof(double) * (k + 1));
-                CK(cudaMemcpyAsync(d_h, c->h_red + 256, sizeof(double) * (k + 1), cudaMemcpyHostToDevice, c->stream));
-                CK(blas_gemv_sub(c, V, k + 1, n3, d_h, w, n3));
-                CK(blas_dots(c, V, k + 1, n3, w, n3, h2.data()));
-                std::memcpy(c->h_red + 256, h2.data(), sizeof(double) * (k + 1));
-                CK(cudaMemcpyAsync(d_h, c->h_red + 256, sizeof(double) * (k + 1), cudaMemcpyHostToDevice, c->stream));
-                CK(blas_gemv_sub(c, V, k + 1, n3, d_h, w, n3));
+                StageScope sc(c, ST_BLAS);
+                for (int pass = 0; pass < 2; ++pass) {
+                    double* dst = pass == 0 ? hcol.data() : h2.data();
+                    CK(seg_dots(c, V, k + 1, n3, w, n3, c->d_seg3, P, c->d_pvec));
+                    CK(cudaMemcpyAsync(c->h_red, c->d_pvec, sizeof(double) * (k + 1) * P, cudaMemcpyDeviceToHost,
+                                       c->stream));
+                    CK(cudaStreamSynchronize(c->stream));
+                    for (int j = 0; j <= k; ++j)
+                        for (int p = 0; p < P; ++p) {
+                            double v = live[p] ? c->h_red[(size_t)j * P + p] : 0.0;
+                            dst[(size_t)j * P + p] = v;
+                            stage[(size_t)j * P + p] = v;
+                        }
+                    CKS(stage_H(c, stage.data(), (size_t)(k + 1) * P));
+                    CK(seg_gemv(c, V, k + 1, n3, c->d_H, P, -1.0, c->d_node_prob, w, n3));
+                }
             }
-            for (int j = 0; j <= k; ++j) h[j] += h2[j];
-            double hk1 = nrm2(c, w, n3, &st);
-            CKS(st);
-            if (!std::isfinite(hk1)) return fail(c, SBIE_ERR_NUMERIC, "NaN/Inf in the Krylov basis");
-            if (hk1 > 0.0) CK(blas_scale_copy(c, 1.0 / hk1, w, w, n3));
-            for (int j = 0; j < k; ++j) {
-                double a0 = h[j], a1 = h[j + 1];
-                h[j] = cs[j] * a0 + sn[j] * a1;
-                h[j + 1] = -sn[j] * a0 + cs[j] * a1;
+            CKS(seg_norms(S, w, hk1));
+            for (int p = 0; p < P; ++p) {
+                if (live[p] && !std::isfinite(hk1[p])) return fail(c, SBIE_ERR_NUMERIC, "NaN/Inf in the Krylov basis");
+                stage[p] = (live[p] && hk1[p] > 0.0) ? 1.0 / hk1[p] : 0.0;
             }
-            double den = std::hypot(h[k], hk1);
-            cs[k] = den > 0 ? h[k] / den : 1.0;
-            sn[k] = den > 0 ? hk1 / den : 0.0;
-            h[k] = den;
-            for (int j = 0; j <= k; ++j) H[j * restart + k] = h[j];
-            g[k + 1] = -sn[k] * g[k];
-            g[k] = cs[k] * g[k];
+            CKS(stage_H(c, stage.data(), P));
+            CK(seg_scale(c, w, c->d_H, c->d_node_prob, w, n3));
+            for (int p = 0; p < P; ++p) {
+                if (!live[p]) continue;
+                double* Hp = H.data() + (size_t)p * (m + 1) * m;
+                double* csp = cs.data() + (size_t)p * m;
+                double* snp = sn.data() + (size_t)p * m;
+                double* gp = g.data() + (size_t)p * (m + 1);
+                std::vector<double> h(k + 2);
+                for (int j = 0; j <= k; ++j) h[j] = hcol[(size_t)j * P + p] + h2[(size_t)j * P + p];
+                for (int j = 0; j < k; ++j) {
+                    double a0 = h[j], a1 = h[j + 1];
+                    h[j] = csp[j] * a0 + snp[j] * a1;
+                    h[j + 1] = -snp[j] * a0 + csp[j] * a1;
+                }
+                double den = std::hypot(h[k], hk1[p]);
+                csp[k] = den > 0 ? h[k] / den : 1.0;
+                snp[k] = den > 0 ? hk1[p] / den : 0.0;
+                h[k] = den;
+                for (int j = 0; j <= k; ++j) Hp[(size_t)j * m + k] = h[j];
+                gp[k + 1] = -snp[k] * gp[k];
+                gp[k] = csp[k] * gp[k];
+                kd[p] = k + 1;
+                if (std::fabs(gp[k + 1]) / nb[p] <= tol[p] || hk1[p] == 0.0) live[p] = 0;
+            }
             ++total;
-            kd = k + 1;
-            if (std::fabs(g[k + 1]) / nb <= tol) break;
-            if (hk1 == 0.0) {
-                breakdown = true;
-                break;
+        }
+        // x += V y per problem
+        int kmax = 0;
+        std::fill(stage.begin(), stage.end(), 0.0);
+        for (int p = 0; p < P; ++p) {
+            const int kk = kd[p];
+            kmax = std::max(kmax, kk);
+            const double* Hp = H.data() + (size_t)p * (m + 1) * m;
+            const double* gp = g.data() + (size_t)p * (m + 1);
+            for (int i = kk - 1; i >= 0; --i) {
+                double s = gp[i];
+                for (int j = i + 1; j < kk; ++j) s -= Hp[(size_t)i * m + j] * y[j];
+                y[i] = s / Hp[(size_t)i * m + i];
             }
+            for (int j = 0; j < kk; ++j) stage[(size_t)j * P + p] = y[j];
         }
-        // back substitution for y, then x += V y
-        for (int i = kd - 1; i >= 0; --i) {
-            double s = g[i];
-            for (int j = i + 1; j < kd; ++j) s -= H[i * restart + j] * y[j];
-            y[i] = s / H[i * restart + i];
-        }
-        std::memcpy(c->h_red + 256, y.data(), sizeof(double) * kd);
-        CK(cudaMemcpyAsync(d_h, c->h_red + 256, sizeof(double) * kd, cudaMemcpyHostToDevice, c->stream));
-        CK(blas_gemv_add(c, V, kd, n3, d_h, x, n3));
+        if (kmax == 0) break;
+        CKS(stage_H(c, stage.data(), (size_t)kmax * P));
+        CK(seg_gemv(c, V, kmax, n3, c->d_H, P, 1.0, c->d_node_prob, x, n3));
         CKS(A(x, r));
         CK(blas_lincomb(c, 1.0, b, -1.0, r, r, n3));
-        beta = nrm2(c, r, n3, &st);
-        CKS(st);
-        if (!std::isfinite(beta)) return fail(c, SBIE_ERR_NUMERIC, "NaN/Inf residual");
+        CKS(seg_norms(S, r, beta));
+        for (int p = 0; p < P; ++p) {
+            if (!std::isfinite(beta[p])) return fail(c, SBIE_ERR_NUMERIC, "NaN/Inf residual");
+            active[p] = want[p] && nb[p] > 0.0 && beta[p] / nb[p] > tol[p];
+        }
         ++go.restarts;
-        if (breakdown && beta / nb > tol) break;
     }
     go.iters = total;
-    go.rel = beta / nb;
-    go.converged = go.rel <= tol;
+    for (int p = 0; p < P; ++p) go.rel[p] = nb[p] > 0.0 ? beta[p] / nb[p] : 0.0;
     return SBIE_OK;
 }
 
-// Solve A x = b to the FP64 residual tolerance.  SBIE_FP64: GMRES on the FP64
-// operator.  SBIE_MIXED: iterative refinement -- the residual b - A x with the
-// FP64 operator, corrections by GMRES on the mixed-precision operator.
-sbie_status solve_op(sbie_ctx* c, int op, const double* b, double* x, sbie_solve_info* info) {
-    const long long n3 = c->N * 3;
-    // FP64-accurate operator: native FP64, or the far field in double-float
-    auto A64 = [&](const double* in, double* out) { return apply_dev(c, op, hi_mode(c), in, out); };
-    auto A32 = [&](const double* in, double* out) { return apply_dev(c, op, kModeF32, in, out); };
+// Solve A x = b to the FP64-accurate residual tolerance, every problem of the
+// system at once.  SBIE_FP64 / SBIE_FP64_DF: GMRES on the FP64-accurate
+// operator.  SBIE_MIXED: iterative refinement -- residuals b - A x with the
+// FP64-accurate operator, corrections by GMRES on the FP32 operator.
+sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_solve_info* info) {
+    sbie_ctx* c = S.top;
+    const long long n3 = S.n3;
+    const int P = S.P;
+    const int hm = hi_mode(c);
+    AFn A64 = [&](const double* in, double* out) { return apply_sys(S, op, hm, in, out); };
+    AFn A32 = [&](const double* in, double* out) { return apply_sys(S, op, kModeF32, in, out); };
     const double tol = c->opts.tol;
     GmresOut go;
     sbie_solve_info inf{};
+    std::vector<double> rel(P, 0.0);
+    // reduction and staging buffers must exist before the first norm
+    CKS(ensure_krylov(c, std::max(1, std::min(c->opts.restart, 250)), P));
     if (c->opts.prec != SBIE_MIXED) {
-        CKS(gmres(c, A64, b, x, tol, c->opts.restart, c->opts.max_iter, go));
+        CKS(gmres(S, A64, b, x, std::vector<double>(P, tol), std::vector<char>(P, 1), c->opts.restart,
+                  c->opts.max_iter, go));
         inf.iters = go.iters;
         inf.restarts = go.restarts;
-        inf.rel_residual_true = go.rel;
+        rel = go.rel;
     } else {
-        sbie_status st;
-        const double nb = nrm2(c, b, n3, &st);
-        CKS(st);
+        std::vector<double> nb;
+        CKS(seg_norms(S, b, nb));
         CK(cudaMemsetAsync(x, 0, sizeof(double) * n3, c->stream));
-        double* r = c->d_rhs == b ? c->d_tmp2 : c->d_rhs;
+        double* r = c->d_tmp2;
+        double* d = c->d_tmp;
         CK(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->stream));
-        double rel = nb > 0 ? 1.0 : 0.0;
+        for (int p = 0; p < P; ++p) rel[p] = nb[p] > 0 ? 1.0 : 0.0;
         int iters = 0, outers = 0;
-        double* d = c->d_xsol == x ? c->d_tmp : c->d_xsol;
-        while (rel > tol && iters < c->opts.max_iter && outers < 20) {
-            const double inner_tol = std::min(1e-3, std::max(1e-5, 0.5 * tol / rel));
-            CKS(gmres(c, A32, r, d, inner_tol, c->opts.restart, c->opts.max_iter - iters, go));
+        auto worst = [&]() { return *std::max_element(rel.begin(), rel.end()); };
+        while (worst() > tol && iters < c->opts.max_iter && outers < 20) {
+            std::vector<double> itol(P);
+            std::vector<char> want(P);
+            for (int p = 0; p < P; ++p) {
+                want[p] = rel[p] > tol;
+                itol[p] = std::min(1e-3, std::max(1e-5, 0.5 * tol / std::max(rel[p], 1e-300)));
+            }
+            CKS(gmres(S, A32, r, d, itol, want, c->opts.restart, c->opts.max_iter - iters, go));
             iters += go.iters;
             CK(blas_axpy(c, 1.0, d, x, n3));
             CKS(A64(x, r));
             CK(blas_lincomb(c, 1.0, b, -1.0, r, r, n3));
-            double rn = nrm2(c, r, n3, &st);
-            CKS(st);
-            if (!std::isfinite(rn)) return fail(c, SBIE_ERR_NUMERIC, "NaN/Inf residual");
+            std::vector<double> rn;
+            CKS(seg_norms(S, r, rn));
+            for (int p = 0; p < P; ++p) {
+                if (!std::isfinite(rn[p])) return fail(c, SBIE_ERR_NUMERIC, "NaN/Inf residual");
+                rel[p] = nb[p] > 0 ? rn[p] / nb[p] : 0.0;
+            }
             ++outers;
-            rel = rn / nb;
             if (go.iters == 0) break;
         }
         inf.iters = iters;
         inf.refinements = outers;
-        inf.rel_residual_true = rel;
     }
-    inf.n_near_pairs = c->n_near;
-    if (info) {
-        info->iters = inf.iters;
-        info->restarts = inf.restarts;
-        info->refinements = inf.refinements;
-        info->rel_residual_true = inf.rel_residual_true;
-        info->n_near_pairs = inf.n_near_pairs;
-    }
+    inf.rel_residual_true = *std::max_element(rel.begin(), rel.end());
+    long long nn = 0;
+    for (sbie_ctx* q : S.parts) nn += q->n_near;
+    inf.n_near_pairs = nn;
+    if (info) *info = inf;
     return inf.rel_residual_true <= tol ? SBIE_OK : SBIE_ERR_NOT_CONVERGED;
 }
 
@@ -372,29 +489,7 @@ bool finite_all(const double* v, size_t n) {
     return true;
 }
 
-}  // namespace
-
-extern "C" {
-
-sbie_status sphere_bie_default_opts(sbie_opts* o) {
-    if (!o) return SBIE_ERR_ARG;
-    std::memset(o, 0, sizeof(*o));
-    o->p = 8;
-    o->eta = 1.0;
-    o->prec = SBIE_FP64;
-    o->tol = 1e-8;
-    o->restart = 60;
-    o->max_iter = 600;
-    o->mem_kind = 0;
-    o->stream = nullptr;
-    return SBIE_OK;
-}
-
-sbie_status sphere_bie_create(int n, const double* centres, const double* radii, const sbie_opts* opts,
-                              sbie_ctx** out) {
-    if (!out) return fail(nullptr, SBIE_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    if (n < 1 || !centres || !radii || !opts) return fail(nullptr, SBIE_ERR_ARG, "need n >= 1 and non-NULL arrays");
+sbie_status check_opts(const sbie_opts* opts) {
     if (opts->p < 1 || opts->p > kMaxP) return fail(nullptr, SBIE_ERR_ARG, "p must be in [1, 24]");
     if (!(opts->eta >= 0.0) || !std::isfinite(opts->eta)) return fail(nullptr, SBIE_ERR_ARG, "eta must be >= 0");
     if (opts->prec != SBIE_FP64 && opts->prec != SBIE_MIXED && opts->prec != SBIE_FP64_DF)
@@ -403,27 +498,34 @@ sbie_status sphere_bie_create(int n, const double* centres, const double* radii,
     if (opts->use_learned_precond != 0) return fail(nullptr, SBIE_ERR_ARG, "learned preconditioner not available");
     if (!(opts->tol > 0.0) || opts->restart < 1 || opts->max_iter < 0)
         return fail(nullptr, SBIE_ERR_ARG, "need tol > 0, restart >= 1, max_iter >= 0");
-    if (!finite_all(centres, (size_t)n * 3) || !finite_all(radii, n))
-        return fail(nullptr, SBIE_ERR_ARG, "non-finite centre or radius");
-    for (int i = 0; i < n; ++i)
-        if (!(radii[i] > 0.0)) return fail(nullptr, SBIE_ERR_ARG, "radii must be positive");
+    return SBIE_OK;
+}
 
+// One context for spheres of one VSH order p = o.p, holding the independent
+// problems prob_sph[q] .. prob_sph[q+1]-1.  Close pairs never cross problems.
+sbie_status create_part(const sbie_opts& o, int n, const double* centres, const double* radii,
+                        const std::vector<int>& prob_sph, cudaStream_t stream, sbie_ctx** out) {
     sbie_ctx* c = new (std::nothrow) sbie_ctx();
     if (!c) return fail(nullptr, SBIE_ERR_OOM, "host allocation");
-    c->opts = *opts;
+    c->opts = o;
     c->n = n;
-    c->p = opts->p;
+    c->p = o.p;
     c->nlat = c->p + 1;
     c->nlon = 2 * c->p + 2;
     c->npn = c->nlat * c->nlon;
     c->N = (long long)n * c->npn;
     c->h_c.assign(centres, centres + 3 * (size_t)n);
     c->h_a.assign(radii, radii + n);
-
-    // close pairs (negation of Eq. 4.5) and overlap check
+    c->n_prob = (int)prob_sph.size() - 1;
+    c->h_prob_sph = prob_sph;
+    std::vector<int> sph_prob(n);
+    for (int q = 0; q < c->n_prob; ++q)
+        for (int i = prob_sph[q]; i < prob_sph[q + 1]; ++i) sph_prob[i] = q;
+    // close pairs (negation of Eq. 4.5) and overlap check, within each problem
     c->h_near_ptr.assign(n + 1, 0);
     for (int i = 0; i < n; ++i) {
-        for (int k = 0; k < n; ++k) {
+        const int q = sph_prob[i];
+        for (int k = prob_sph[q]; k < prob_sph[q + 1]; ++k) {
             if (k == i) continue;
             double dx = centres[3 * i] - centres[3 * k], dy = centres[3 * i + 1] - centres[3 * k + 1],
                    dz = centres[3 * i + 2] - centres[3 * k + 2];
@@ -433,11 +535,15 @@ sbie_status sphere_bie_create(int n, const double* centres, const double* radii,
                 delete c;
                 return SBIE_ERR_OVERLAP;
             }
-            if (gap < opts->eta * 2.0 * std::max(radii[i], radii[k])) c->h_near_idx.push_back(k);
+            if (gap < o.eta * 2.0 * std::max(radii[i], radii[k])) c->h_near_idx.push_back(k);
         }
         c->h_near_ptr[i + 1] = (int)c->h_near_idx.size();
     }
     c->n_near = (long long)c->h_near_idx.size();
+    c->seg3.resize(c->n_prob + 1);
+    for (int q = 0; q <= c->n_prob; ++q) c->seg3[q] = (long long)prob_sph[q] * c->npn * 3;
+    std::vector<int> node_prob((size_t)c->N);
+    for (long long i = 0; i < c->N; ++i) node_prob[i] = sph_prob[i / c->npn];
 
     auto bail = [&](sbie_status s, const std::string& m) {
         g_last_error = m;
@@ -451,8 +557,8 @@ sbie_status sphere_bie_create(int n, const double* centres, const double* radii,
     e = cudaGetDeviceProperties(&prop, c->device);
     if (e != cudaSuccess) return bail(SBIE_ERR_CUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
     c->sm_count = prop.multiProcessorCount;
-    if (opts->stream) {
-        c->stream = (cudaStream_t)opts->stream;
+    if (stream || o.stream) {
+        c->stream = stream ? stream : (cudaStream_t)o.stream;
     } else {
         e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return bail(SBIE_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
@@ -475,6 +581,10 @@ sbie_status sphere_bie_create(int n, const double* centres, const double* radii,
     ok &= dmalloc(&c->d_sph, (size_t)N) == cudaSuccess;
     ok &= dmalloc(&c->d_near_ptr, (size_t)n + 1) == cudaSuccess;
     ok &= dmalloc(&c->d_near_idx, (size_t)std::max<long long>(1, c->n_near)) == cudaSuccess;
+    ok &= dmalloc(&c->d_prob_sph, (size_t)c->n_prob + 1) == cudaSuccess;
+    ok &= dmalloc(&c->d_sph_prob, (size_t)n) == cudaSuccess;
+    ok &= dmalloc(&c->d_node_prob, (size_t)N) == cudaSuccess;
+    ok &= dmalloc(&c->d_seg3, (size_t)c->n_prob + 1) == cudaSuccess;
     ok &= dmalloc(&c->d_tab, (size_t)c->tl.total) == cudaSuccess;
     ok &= dmalloc(&c->d_coef, (size_t)n * 3 * P1 * P1 * 2) == cudaSuccess;
     if (c->n_near > 0) {
@@ -484,16 +594,9 @@ sbie_status sphere_bie_create(int n, const double* centres, const double* radii,
     ok &= dmalloc(&c->d_mom, 6 * (size_t)n) == cudaSuccess;
     ok &= dmalloc(&c->d_src64, (size_t)N) == cudaSuccess;
     ok &= dmalloc(&c->d_srcf, (size_t)N) == cudaSuccess;
-    ok &= dmalloc(&c->d_in, 3 * (size_t)N) == cudaSuccess;
-    ok &= dmalloc(&c->d_out, 3 * (size_t)N) == cudaSuccess;
-    ok &= dmalloc(&c->d_tmp, 3 * (size_t)N) == cudaSuccess;
-    ok &= dmalloc(&c->d_tmp2, 3 * (size_t)N) == cudaSuccess;
-    ok &= dmalloc(&c->d_xsol, 3 * (size_t)N) == cudaSuccess;
-    ok &= dmalloc(&c->d_rhs, 3 * (size_t)N) == cudaSuccess;
-    ok &= dmalloc(&c->d_res, 3 * (size_t)N) == cudaSuccess;
+    for (double** p : {&c->d_in, &c->d_out, &c->d_tmp, &c->d_tmp2, &c->d_xsol, &c->d_rhs, &c->d_res})
+        ok &= dmalloc(p, 3 * (size_t)N) == cudaSuccess;
     ok &= dmalloc(&c->d_small, 3 * (size_t)n * 6 + 32) == cudaSuccess;
-    ok &= dmalloc(&c->d_red, (size_t)4 * 296 * 256) == cudaSuccess;
-    ok &= cudaMallocHost(reinterpret_cast<void**>(&c->h_red), sizeof(double) * 1024) == cudaSuccess;
     if (!ok) return bail(SBIE_ERR_OOM, "device allocation failed");
     choose_tuning(c);
     {
@@ -505,12 +608,223 @@ sbie_status sphere_bie_create(int n, const double* centres, const double* radii,
     if (e == cudaSuccess) e = cudaMemcpy(c->d_near_ptr, c->h_near_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && c->n_near > 0)
         e = cudaMemcpy(c->d_near_idx, c->h_near_idx.data(), sizeof(int) * c->n_near, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_prob_sph, prob_sph.data(), sizeof(int) * (c->n_prob + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_sph_prob, sph_prob.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_node_prob, node_prob.data(), sizeof(int) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_seg3, c->seg3.data(), sizeof(long long) * c->seg3.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_tab, htab.data(), sizeof(double) * htab.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = launch_geometry(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bail(SBIE_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
     c->err = "no error";
     *out = c;
+    return SBIE_OK;
+}
+
+// Copy a user array (host or device per opts.mem_kind) into internal order on
+// the device: per node (3 doubles each) if nodal, else per sphere.
+sbie_status to_internal(sbie_ctx* c, const double* user, double* dev, bool nodal) {
+    const cudaMemcpyKind kind = c->opts.mem_kind == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (!c->is_batch) {
+        const size_t cnt = nodal ? (size_t)c->N : (size_t)c->n;
+        if (user != dev) CK(cudaMemcpyAsync(dev, user, sizeof(double) * 3 * cnt, kind, c->stream));
+        return SBIE_OK;
+    }
+    long long sph_base[64] = {0};
+    for (size_t s = 1; s < c->parts.size() && s < 64; ++s) sph_base[s] = sph_base[s - 1] + c->parts[s - 1]->n;
+    for (int q = 0; q < c->n_prob; ++q) {
+        const int s = c->prob_part[q];
+        sbie_ctx* part = c->parts[s];
+        const long long isph = sph_base[s] + part->h_prob_sph[c->prob_local[q]];
+        long long ioff, uoff, cnt;
+        if (nodal) {
+            ioff = c->part_off3[s] / 3 + (long long)part->h_prob_sph[c->prob_local[q]] * part->npn;
+            uoff = c->prob_user_node[q];
+            cnt = c->prob_user_node[q + 1] - uoff;
+        } else {
+            ioff = isph;
+            uoff = c->prob_user_sph[q];
+            cnt = c->prob_user_sph[q + 1] - uoff;
+        }
+        CK(cudaMemcpyAsync(dev + 3 * ioff, user + 3 * uoff, sizeof(double) * 3 * cnt, kind, c->stream));
+    }
+    return SBIE_OK;
+}
+
+sbie_status to_user(sbie_ctx* c, const double* dev, double* user, bool nodal) {
+    const cudaMemcpyKind kind = c->opts.mem_kind == 0 ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (!c->is_batch) {
+        const size_t cnt = nodal ? (size_t)c->N : (size_t)c->n;
+        if (user != dev) CK(cudaMemcpyAsync(user, dev, sizeof(double) * 3 * cnt, kind, c->stream));
+        return SBIE_OK;
+    }
+    long long sph_base[64] = {0};
+    for (size_t s = 1; s < c->parts.size() && s < 64; ++s) sph_base[s] = sph_base[s - 1] + c->parts[s - 1]->n;
+    for (int q = 0; q < c->n_prob; ++q) {
+        const int s = c->prob_part[q];
+        sbie_ctx* part = c->parts[s];
+        long long ioff, uoff, cnt;
+        if (nodal) {
+            ioff = c->part_off3[s] / 3 + (long long)part->h_prob_sph[c->prob_local[q]] * part->npn;
+            uoff = c->prob_user_node[q];
+            cnt = c->prob_user_node[q + 1] - uoff;
+        } else {
+            ioff = sph_base[s] + part->h_prob_sph[c->prob_local[q]];
+            uoff = c->prob_user_sph[q];
+            cnt = c->prob_user_sph[q + 1] - uoff;
+        }
+        CK(cudaMemcpyAsync(user + 3 * uoff, dev + 3 * ioff, sizeof(double) * 3 * cnt, kind, c->stream));
+    }
+    return SBIE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sbie_status sphere_bie_default_opts(sbie_opts* o) {
+    if (!o) return SBIE_ERR_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->p = 8;
+    o->eta = 1.0;
+    o->prec = SBIE_FP64;
+    o->tol = 1e-8;
+    o->restart = 60;
+    o->max_iter = 600;
+    o->mem_kind = 0;
+    o->stream = nullptr;
+    return SBIE_OK;
+}
+
+sbie_status sphere_bie_create(int n, const double* centres, const double* radii, const sbie_opts* opts,
+                              sbie_ctx** out) {
+    int one = n;
+    return sphere_bie_create_batch(1, &one, opts ? &opts->p : nullptr, centres, radii, opts, out);
+}
+
+sbie_status sphere_bie_create_batch(int n_problems, const int* n_spheres, const int* p_per_problem,
+                                    const double* centres, const double* radii, const sbie_opts* opts, sbie_ctx** out) {
+    if (!out) return fail(nullptr, SBIE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_problems < 1 || !n_spheres || !p_per_problem || !centres || !radii || !opts)
+        return fail(nullptr, SBIE_ERR_ARG, "need n_problems >= 1 and non-NULL arrays");
+    CKS(check_opts(opts));
+    long long ntot = 0;
+    for (int q = 0; q < n_problems; ++q) {
+        if (n_spheres[q] < 1) return fail(nullptr, SBIE_ERR_ARG, "every problem needs n >= 1 spheres");
+        if (p_per_problem[q] < 1 || p_per_problem[q] > kMaxP) return fail(nullptr, SBIE_ERR_ARG, "p must be in [1, 24]");
+        ntot += n_spheres[q];
+    }
+    if (ntot > (1LL << 30)) return fail(nullptr, SBIE_ERR_ARG, "too many spheres");
+    if (!finite_all(centres, (size_t)ntot * 3) || !finite_all(radii, ntot))
+        return fail(nullptr, SBIE_ERR_ARG, "non-finite centre or radius");
+    for (long long i = 0; i < ntot; ++i)
+        if (!(radii[i] > 0.0)) return fail(nullptr, SBIE_ERR_ARG, "radii must be positive");
+    std::vector<long long> usph(n_problems + 1, 0), unode(n_problems + 1, 0);
+    for (int q = 0; q < n_problems; ++q) {
+        usph[q + 1] = usph[q] + n_spheres[q];
+        unode[q + 1] = unode[q] + (long long)n_spheres[q] * (p_per_problem[q] + 1) * (2 * p_per_problem[q] + 2);
+    }
+    // overlap check for every problem before any device work
+    for (int q = 0; q < n_problems; ++q)
+        for (long long i = usph[q]; i < usph[q + 1]; ++i)
+            for (long long k = i + 1; k < usph[q + 1]; ++k) {
+                double dx = centres[3 * i] - centres[3 * k], dy = centres[3 * i + 1] - centres[3 * k + 1],
+                       dz = centres[3 * i + 2] - centres[3 * k + 2];
+                if (std::sqrt(dx * dx + dy * dy + dz * dz) - radii[i] - radii[k] <= 0.0)
+                    return fail(nullptr, SBIE_ERR_OVERLAP,
+                                "problem " + std::to_string(q) + ": spheres " + std::to_string(i - usph[q]) + " and " +
+                                    std::to_string(k - usph[q]) + " overlap or touch");
+            }
+    // group problems by VSH order
+    std::vector<int> orders(p_per_problem, p_per_problem + n_problems);
+    std::sort(orders.begin(), orders.end());
+    orders.erase(std::unique(orders.begin(), orders.end()), orders.end());
+    if (orders.size() == 1) {
+        std::vector<int> prob_sph(n_problems + 1);
+        for (int q = 0; q <= n_problems; ++q) prob_sph[q] = (int)usph[q];
+        sbie_opts o = *opts;
+        o.p = orders[0];
+        sbie_ctx* c = nullptr;
+        CKS(create_part(o, (int)ntot, centres, radii, prob_sph, nullptr, &c));
+        *out = c;
+        return SBIE_OK;
+    }
+    sbie_ctx* top = new (std::nothrow) sbie_ctx();
+    if (!top) return fail(nullptr, SBIE_ERR_OOM, "host allocation");
+    top->opts = *opts;
+    top->is_batch = true;
+    auto bail = [&](sbie_status s, const std::string& m) {
+        g_last_error = m;
+        free_all(top);
+        delete top;
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&top->device);
+    if (e != cudaSuccess) return bail(SBIE_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (opts->stream) {
+        top->stream = (cudaStream_t)opts->stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&top->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(SBIE_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+        top->own_stream = true;
+    }
+    top->prob_part.assign(n_problems, 0);
+    top->prob_local.assign(n_problems, 0);
+    top->prob_user_node = unode;
+    top->prob_user_sph = usph;
+    long long off3 = 0;
+    std::vector<int> node_prob;
+    top->seg3.assign(1, 0);
+    int pbase = 0;
+    for (size_t s = 0; s < orders.size(); ++s) {
+        std::vector<double> cc, aa;
+        std::vector<int> prob_sph(1, 0);
+        int local = 0;
+        for (int q = 0; q < n_problems; ++q) {
+            if (p_per_problem[q] != orders[s]) continue;
+            cc.insert(cc.end(), centres + 3 * usph[q], centres + 3 * usph[q + 1]);
+            aa.insert(aa.end(), radii + usph[q], radii + usph[q + 1]);
+            prob_sph.push_back(prob_sph.back() + n_spheres[q]);
+            top->prob_part[q] = (int)s;
+            top->prob_local[q] = local++;
+        }
+        sbie_opts o = *opts;
+        o.p = orders[s];
+        o.stream = top->stream;
+        sbie_ctx* part = nullptr;
+        sbie_status st = create_part(o, (int)aa.size(), cc.data(), aa.data(), prob_sph, top->stream, &part);
+        if (st != SBIE_OK) return bail(st, g_last_error);
+        top->parts.push_back(part);
+        top->part_off3.push_back(off3);
+        for (size_t k = 1; k < part->seg3.size(); ++k) top->seg3.push_back(off3 + part->seg3[k]);
+        for (int k = 0; k < part->n_prob; ++k)
+            node_prob.insert(node_prob.end(), (size_t)(part->h_prob_sph[k + 1] - part->h_prob_sph[k]) * part->npn,
+                             pbase + k);
+        pbase += part->n_prob;
+        off3 += part->N * 3;
+        top->n += part->n;
+        top->n_near += part->n_near;
+    }
+    top->N = off3 / 3;
+    top->n_prob = n_problems;
+    top->sm_count = top->parts[0]->sm_count;
+    const long long N = top->N;
+    bool ok = true;
+    for (double** p : {&top->d_in, &top->d_out, &top->d_tmp, &top->d_tmp2, &top->d_xsol, &top->d_rhs, &top->d_res})
+        ok &= dmalloc(p, 3 * (size_t)N) == cudaSuccess;
+    ok &= dmalloc(&top->d_small, 3 * (size_t)top->n * 6 + 32) == cudaSuccess;
+    ok &= dmalloc(&top->d_node_prob, (size_t)N) == cudaSuccess;
+    ok &= dmalloc(&top->d_seg3, top->seg3.size()) == cudaSuccess;
+    if (!ok) return bail(SBIE_ERR_OOM, "device allocation failed");
+    e = cudaMemcpy(top->d_node_prob, node_prob.data(), sizeof(int) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(top->d_seg3, top->seg3.data(), sizeof(long long) * top->seg3.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(SBIE_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
+    top->err = "no error";
+    *out = top;
     return SBIE_OK;
 }
 
@@ -523,16 +837,41 @@ sbie_status sphere_bie_num_nodes(const sbie_ctx* c, long long* n_nodes) {
 sbie_status sphere_bie_nodes(const sbie_ctx* cc, double* xyz, double* normals, double* weights) {
     sbie_ctx* c = const_cast<sbie_ctx*>(cc);
     if (!c) return SBIE_ERR_ARG;
-    std::vector<double> x4(4 * (size_t)c->N), n4(4 * (size_t)c->N);
-    CK(cudaMemcpy(x4.data(), c->d_x, sizeof(double) * x4.size(), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(n4.data(), c->d_nrm64, sizeof(double) * n4.size(), cudaMemcpyDeviceToHost));
-    for (long long i = 0; i < c->N; ++i) {
-        for (int d = 0; d < 3; ++d) {
-            if (xyz) xyz[3 * i + d] = x4[4 * i + d];
-            if (normals) normals[3 * i + d] = n4[4 * i + d];
+    Sys S = sys_of(c);
+    std::vector<double> x4, n4, ix((size_t)c->N * 3), inr((size_t)c->N * 3), iw((size_t)c->N);
+    for (size_t s = 0; s < S.parts.size(); ++s) {
+        sbie_ctx* q = S.parts[s];
+        x4.resize(4 * (size_t)q->N);
+        n4.resize(4 * (size_t)q->N);
+        CK(cudaMemcpy(x4.data(), q->d_x, sizeof(double) * x4.size(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(n4.data(), q->d_nrm64, sizeof(double) * n4.size(), cudaMemcpyDeviceToHost));
+        const long long o = S.off3[s] / 3;
+        for (long long i = 0; i < q->N; ++i) {
+            for (int d = 0; d < 3; ++d) {
+                ix[3 * (o + i) + d] = x4[4 * i + d];
+                inr[3 * (o + i) + d] = n4[4 * i + d];
+            }
+            iw[o + i] = x4[4 * i + 3];
         }
-        if (weights) weights[i] = x4[4 * i + 3];
     }
+    // internal -> user order (identity unless the batch holds several VSH orders)
+    auto put = [&](double* dst, const std::vector<double>& src, int width) {
+        if (!dst) return;
+        if (!c->is_batch) {
+            std::memcpy(dst, src.data(), sizeof(double) * src.size());
+            return;
+        }
+        for (int q = 0; q < c->n_prob; ++q) {
+            sbie_ctx* part = c->parts[c->prob_part[q]];
+            long long inode = c->part_off3[c->prob_part[q]] / 3 +
+                              (long long)part->h_prob_sph[c->prob_local[q]] * part->npn;
+            long long cnt = c->prob_user_node[q + 1] - c->prob_user_node[q];
+            std::memcpy(dst + width * c->prob_user_node[q], src.data() + width * inode, sizeof(double) * width * cnt);
+        }
+    };
+    put(xyz, ix, 3);
+    put(normals, inr, 3);
+    put(weights, iw, 1);
     return SBIE_OK;
 }
 
@@ -542,13 +881,14 @@ sbie_status sphere_bie_apply_operator(sbie_ctx* c, sbie_op op, const double* den
     if (op < SBIE_OP_S || op > SBIE_OP_RESISTANCE) return fail(c, SBIE_ERR_ARG, "bad operator");
     if (density == out) return fail(c, SBIE_ERR_ARG, "density and out must not alias");
     const int mode = c->opts.prec == SBIE_MIXED ? kModeF32 : hi_mode(c);
-    const size_t bytes = sizeof(double) * 3 * (size_t)c->N;
-    if (c->opts.mem_kind == 0) {
-        CK(cudaMemcpyAsync(c->d_in, density, bytes, cudaMemcpyHostToDevice, c->stream));
-        CKS(apply_dev(c, op, mode, c->d_in, c->d_out));
-        CK(cudaMemcpyAsync(out, c->d_out, bytes, cudaMemcpyDeviceToHost, c->stream));
+    Sys S = sys_of(c);
+    const bool direct = c->opts.mem_kind == 1 && !c->is_batch;
+    if (direct) {
+        CKS(apply_sys(S, op, mode, density, out));
     } else {
-        CKS(apply_dev(c, op, mode, density, out));
+        CKS(to_internal(c, density, c->d_in, true));
+        CKS(apply_sys(S, op, mode, c->d_in, c->d_out));
+        CKS(to_user(c, c->d_out, out, true));
     }
     CK(cudaStreamSynchronize(c->stream));
     return SBIE_OK;
@@ -559,42 +899,38 @@ sbie_status sphere_bie_solve_mobility(sbie_ctx* c, const double* forces, const d
     if (!c) return SBIE_ERR_ARG;
     if (!forces || !torques || !vel || !omega) return fail(c, SBIE_ERR_ARG, "NULL argument");
     auto t0 = std::chrono::steady_clock::now();
-    const size_t sb = sizeof(double) * 3 * c->n;
-    const long long n3 = c->N * 3;
+    Sys S = sys_of(c);
+    const long long n3 = S.n3;
     double* dF = c->d_small;
     double* dT = dF + 3 * c->n;
     double* dv = dT + 3 * c->n;
     double* dw = dv + 3 * c->n;
-    const double *F = forces, *T = torques;
-    if (c->opts.mem_kind == 0) {
-        CK(cudaMemcpyAsync(dF, forces, sb, cudaMemcpyHostToDevice, c->stream));
-        CK(cudaMemcpyAsync(dT, torques, sb, cudaMemcpyHostToDevice, c->stream));
-        F = dF;
-        T = dT;
-    }
-    double* rho = c->d_tmp;
+    CKS(to_internal(c, forces, dF, false));
+    CKS(to_internal(c, torques, dT, false));
+    double* rho = c->d_in;
     double* b = c->d_rhs;
     double* mu = c->d_xsol;
-    CK(launch_rho(c, F, T, rho));
+    long long sph_off = 0;
+    for (size_t s = 0; s < S.parts.size(); ++s) {
+        CK(launch_rho(S.parts[s], dF + 3 * sph_off, dT + 3 * sph_off, rho + S.off3[s]));
+        sph_off += S.parts[s]->n;
+    }
     // b = -(1/2 I + K) rho
-    CKS(apply_dev(c, SBIE_OP_K, hi_mode(c), rho, b));
+    CKS(apply_sys(S, SBIE_OP_K, hi_mode(c), rho, b));
     CK(blas_lincomb(c, -0.5, rho, -1.0, b, b, n3));
-    // keep rho: solve_op uses d_tmp in mixed mode, so copy it aside
-    double* rho_keep = c->d_in;
-    CK(cudaMemcpyAsync(rho_keep, rho, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->stream));
     sbie_solve_info inf{};
-    sbie_status st = solve_op(c, SBIE_OP_MOBILITY, b, mu, &inf);
+    sbie_status st = solve_sys(S, SBIE_OP_MOBILITY, b, mu, &inf);
     if (st != SBIE_OK && st != SBIE_ERR_NOT_CONVERGED) return st;
     // u = S[mu + rho] on every sphere; rigid projection
-    CK(blas_lincomb(c, 1.0, mu, 1.0, rho_keep, c->d_tmp2, n3));
-    CKS(apply_dev(c, SBIE_OP_S, hi_mode(c), c->d_tmp2, c->d_out));
-    double* V = c->opts.mem_kind == 0 ? dv : vel;
-    double* W = c->opts.mem_kind == 0 ? dw : omega;
-    CK(launch_rigid_projection(c, c->d_out, V, W));
-    if (c->opts.mem_kind == 0) {
-        CK(cudaMemcpyAsync(vel, dv, sb, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaMemcpyAsync(omega, dw, sb, cudaMemcpyDeviceToHost, c->stream));
+    CK(blas_lincomb(c, 1.0, mu, 1.0, rho, c->d_tmp2, n3));
+    CKS(apply_sys(S, SBIE_OP_S, hi_mode(c), c->d_tmp2, c->d_out));
+    sph_off = 0;
+    for (size_t s = 0; s < S.parts.size(); ++s) {
+        CK(launch_rigid_projection(S.parts[s], c->d_out + S.off3[s], dv + 3 * sph_off, dw + 3 * sph_off));
+        sph_off += S.parts[s]->n;
     }
+    CKS(to_user(c, dv, vel, false));
+    CKS(to_user(c, dw, omega, false));
     CK(cudaStreamSynchronize(c->stream));
     inf.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = inf;
@@ -605,37 +941,39 @@ sbie_status sphere_bie_solve_resistance(sbie_ctx* c, const double* vel, const do
                                         const double* bg_grad, double* forces, double* torques, sbie_solve_info* info) {
     if (!c) return SBIE_ERR_ARG;
     if (!vel || !omega || !forces || !torques) return fail(c, SBIE_ERR_ARG, "NULL argument");
-    auto t0 = std::chrono::steady_clock::now();
-    const size_t sb = sizeof(double) * 3 * c->n;
-    double* dv = c->d_small;
-    double* dw = dv + 3 * c->n;
-    const double *V = vel, *W = omega;
-    if (c->opts.mem_kind == 0) {
-        CK(cudaMemcpyAsync(dv, vel, sb, cudaMemcpyHostToDevice, c->stream));
-        CK(cudaMemcpyAsync(dw, omega, sb, cudaMemcpyHostToDevice, c->stream));
-        V = dv;
-        W = dw;
-    }
     if (bg_u0 && !finite_all(bg_u0, 3)) return fail(c, SBIE_ERR_ARG, "non-finite u0");
     if (bg_grad && !finite_all(bg_grad, 9)) return fail(c, SBIE_ERR_ARG, "non-finite velocity gradient");
+    auto t0 = std::chrono::steady_clock::now();
+    Sys S = sys_of(c);
+    double* dv = c->d_small;
+    double* dw = dv + 3 * c->n;
+    double* dF = dw + 3 * c->n;
+    double* dT = dF + 3 * c->n;
+    CKS(to_internal(c, vel, dv, false));
+    CKS(to_internal(c, omega, dw, false));
     double* b = c->d_rhs;
     double* psi = c->d_xsol;
-    CK(launch_resistance_rhs(c, V, W, bg_u0, bg_grad, b));
-    sbie_solve_info inf{};
-    sbie_status st = solve_op(c, SBIE_OP_RESISTANCE, b, psi, &inf);
-    if (st != SBIE_OK && st != SBIE_ERR_NOT_CONVERGED) return st;
-    CK(launch_moments(c, psi));
-    // forces / torques from the moments [n][6]
-    double* dF = c->d_small + 6 * c->n;
-    double* dT = dF + 3 * c->n;
-    CK(cudaMemcpy2DAsync(c->opts.mem_kind == 0 ? dF : forces, sizeof(double) * 3, c->d_mom, sizeof(double) * 6,
-                         sizeof(double) * 3, c->n, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpy2DAsync(c->opts.mem_kind == 0 ? dT : torques, sizeof(double) * 3, c->d_mom + 3, sizeof(double) * 6,
-                         sizeof(double) * 3, c->n, cudaMemcpyDeviceToDevice, c->stream));
-    if (c->opts.mem_kind == 0) {
-        CK(cudaMemcpyAsync(forces, dF, sb, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaMemcpyAsync(torques, dT, sb, cudaMemcpyDeviceToHost, c->stream));
+    long long sph_off = 0;
+    for (size_t s = 0; s < S.parts.size(); ++s) {
+        CK(launch_resistance_rhs(S.parts[s], dv + 3 * sph_off, dw + 3 * sph_off, bg_u0, bg_grad, b + S.off3[s]));
+        sph_off += S.parts[s]->n;
     }
+    sbie_solve_info inf{};
+    sbie_status st = solve_sys(S, SBIE_OP_RESISTANCE, b, psi, &inf);
+    if (st != SBIE_OK && st != SBIE_ERR_NOT_CONVERGED) return st;
+    sph_off = 0;
+    for (size_t s = 0; s < S.parts.size(); ++s) {
+        sbie_ctx* q = S.parts[s];
+        CK(launch_moments(q, psi + S.off3[s]));
+        // forces / torques from the moments [n][6]
+        CK(cudaMemcpy2DAsync(dF + 3 * sph_off, sizeof(double) * 3, q->d_mom, sizeof(double) * 6, sizeof(double) * 3,
+                             q->n, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpy2DAsync(dT + 3 * sph_off, sizeof(double) * 3, q->d_mom + 3, sizeof(double) * 6, sizeof(double) * 3,
+                             q->n, cudaMemcpyDeviceToDevice, c->stream));
+        sph_off += q->n;
+    }
+    CKS(to_user(c, dF, forces, false));
+    CKS(to_user(c, dT, torques, false));
     CK(cudaStreamSynchronize(c->stream));
     inf.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = inf;
@@ -734,49 +1072,70 @@ sbie_status sphere_bie_autotune(sbie_ctx* c, sbie_op op, sbie_far_tuning* chosen
     if (!c) return SBIE_ERR_ARG;
     if (op < SBIE_OP_S || op > SBIE_OP_RESISTANCE) return fail(c, SBIE_ERR_ARG, "bad operator");
     const Kern k = kern_of(op);
-    CKS(ensure_part(c, 16));
-    CK(cudaMemsetAsync(c->d_srcf, 0, sizeof(float4) * c->N, c->stream));
-    CK(cudaMemsetAsync(c->d_src64, 0, sizeof(double4) * c->N, c->stream));
     if (chosen) std::memset(chosen, 0, 2 * sizeof(*chosen));
-    if (c->opts.prec == SBIE_MIXED) CKS(tune_one(c, k, kModeF32, chosen));
-    if (c->opts.prec != SBIE_FP64) CKS(tune_one(c, k, kModeDF, chosen ? chosen + 1 : nullptr));
+    Sys S = sys_of(c);
+    for (sbie_ctx* q : S.parts) {
+        sbie_status st = SBIE_OK;
+        {
+            sbie_ctx* cc = q;
+            std::swap(c, cc);
+            CKS(ensure_part(c, 16));
+            CK(cudaMemsetAsync(c->d_srcf, 0, sizeof(float4) * c->N, c->stream));
+            CK(cudaMemsetAsync(c->d_src64, 0, sizeof(double4) * c->N, c->stream));
+            if (c->opts.prec == SBIE_MIXED) st = tune_one(c, k, kModeF32, chosen);
+            if (st == SBIE_OK && c->opts.prec != SBIE_FP64) st = tune_one(c, k, kModeDF, chosen ? chosen + 1 : nullptr);
+            std::swap(c, cc);
+        }
+        if (st != SBIE_OK) {
+            if (q != c) c->err = q->err;
+            return st;
+        }
+    }
     return SBIE_OK;
 }
 
 sbie_status sphere_bie_profile(sbie_ctx* c, int enable) {
     if (!c) return SBIE_ERR_ARG;
     CK(cudaStreamSynchronize(c->stream));
-    c->prof.on = enable != 0;
-    for (int s = 0; s < 8; ++s) {
-        c->prof.ms[s] = 0;
-        c->prof.launches[s] = 0;
-        c->prof_used[s] = 0;
+    Sys S = sys_of(c);
+    std::vector<sbie_ctx*> all = S.parts;
+    if (c->is_batch) all.push_back(c);
+    for (sbie_ctx* q : all) {
+        q->prof.on = enable != 0;
+        for (int s = 0; s < 8; ++s) {
+            q->prof.ms[s] = 0;
+            q->prof.launches[s] = 0;
+            q->prof_used[s] = 0;
+        }
+        q->prof.pairs_f32 = q->prof.pairs_f64 = 0;
+        q->prof.kernels0 = q->n_launch;
     }
-    c->prof.pairs_f32 = c->prof.pairs_f64 = 0;
-    c->prof.kernels0 = c->n_launch;
     return SBIE_OK;
 }
 
 sbie_status sphere_bie_profile_read(sbie_ctx* c, sbie_profile* out) {
     if (!c || !out) return SBIE_ERR_ARG;
     CK(cudaStreamSynchronize(c->stream));
-    for (int s = 0; s < 8; ++s) {
-        for (int i = 0; i < c->prof_used[s]; ++i) {
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, c->prof_events[s][i].first, c->prof_events[s][i].second));
-            c->prof.ms[s] += ms;
-            c->prof.launches[s] += 1;
-        }
-        c->prof_used[s] = 0;
-    }
     std::memset(out, 0, sizeof(*out));
-    for (int s = 0; s < 8; ++s) {
-        out->ms[s] = c->prof.ms[s];
-        out->launches[s] = c->prof.launches[s];
+    Sys S = sys_of(c);
+    std::vector<sbie_ctx*> all = S.parts;
+    if (c->is_batch) all.push_back(c);
+    for (sbie_ctx* q : all) {
+        for (int s = 0; s < 8; ++s) {
+            for (int i = 0; i < q->prof_used[s]; ++i) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, q->prof_events[s][i].first, q->prof_events[s][i].second));
+                q->prof.ms[s] += ms;
+                q->prof.launches[s] += 1;
+            }
+            q->prof_used[s] = 0;
+            out->ms[s] += q->prof.ms[s];
+            out->launches[s] += q->prof.launches[s];
+        }
+        out->far_pairs_f32 += q->prof.pairs_f32;
+        out->far_pairs_f64 += q->prof.pairs_f64;
+        out->kernel_launches += q->n_launch - q->prof.kernels0;
     }
-    out->far_pairs_f32 = c->prof.pairs_f32;
-    out->far_pairs_f64 = c->prof.pairs_f64;
-    out->kernel_launches = c->n_launch - c->prof.kernels0;
     return SBIE_OK;
 }
 

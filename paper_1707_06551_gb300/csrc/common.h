@@ -85,6 +85,26 @@ struct sbie_ctx {
     int sm_count = 0;
     std::string err;
 
+    // problems held by this context (a batch of independent suspensions with
+    // one VSH order): spheres h_prob_sph[q] .. h_prob_sph[q+1]-1 form problem q
+    int n_prob = 1;
+    std::vector<int> h_prob_sph;
+    int* d_prob_sph = nullptr;   // [n_prob+1]
+    int* d_sph_prob = nullptr;   // [n] problem of each sphere
+
+    // a batch of problems with several VSH orders: one part per distinct p
+    bool is_batch = false;
+    std::vector<sbie_ctx*> parts;
+    std::vector<long long> part_off3;   // offset of each part in the batch vector (doubles)
+    std::vector<int> prob_part, prob_local;  // user problem -> (part, problem within part)
+    std::vector<long long> prob_user_node, prob_user_sph;  // user offsets (nodes, spheres)
+    std::vector<long long> seg3;        // problem segments of the internal vector (doubles), internal order
+    int* d_node_prob = nullptr;         // internal node -> internal problem index
+    long long* d_seg3 = nullptr;        // device copy of seg3
+    double* d_H = nullptr;              // [restart+1][n_prob_total] small device matrix
+    double* d_pvec = nullptr;           // [n_prob_total] per-problem scalars
+    size_t red_cap = 0, hred_cap = 0;
+
     // host geometry
     std::vector<double> h_c, h_a;
     std::vector<int> h_near_ptr, h_near_idx;
@@ -190,5 +210,13 @@ cudaError_t blas_axpy(sbie_ctx* c, double a, const double* x, double* y, long lo
 cudaError_t blas_scale_copy(sbie_ctx* c, double a, const double* x, double* y, long long n);
 cudaError_t blas_lincomb(sbie_ctx* c, double a, const double* x, double b, const double* y, double* out, long long n);
 cudaError_t blas_gemv_add(sbie_ctx* c, const double* V, int k, long long ld, const double* y_dev, double* x, long long n);
+// segmented (one segment per independent problem; see blas.cu)
+int seg_blocks(long long n3, int P);
+cudaError_t seg_dots(sbie_ctx* c, const double* V, int k, long long ld, const double* w, long long n3,
+                     const long long* d_seg, int P, double* d_out);
+cudaError_t seg_gemv(sbie_ctx* c, const double* V, int k, long long ld, const double* d_H, int P, double sign,
+                     const int* d_node_prob, double* w, long long n3);
+cudaError_t seg_scale(sbie_ctx* c, const double* x, const double* d_scale, const int* d_node_prob, double* y,
+                      long long n3);
 
 }  // namespace sbie

@@ -63,33 +63,47 @@ __global__ void sphere_reduce_kernel(const double* __restrict__ dens, const doub
 // lo parts so that x - c keeps relative FP32 accuracy (as in the far field).
 template <typename T>
 __global__ void completion_kernel(const double* __restrict__ x64, const double* __restrict__ c,
-                                  const double* __restrict__ mom, int n, long long N, double* __restrict__ out) {
-    // out[i] += sum_k G(x_i - c_k) M0_k + M1_k x (x_i - c_k) / (8 pi |x_i - c_k|^3)
+                                  const double* __restrict__ mom, const int* __restrict__ sph,
+                                  const int* __restrict__ sph_prob, const int* __restrict__ prob_sph, long long N,
+                                  double* __restrict__ out) {
+    // out[i] += sum over spheres k of i's problem of
+    //           G(x_i - c_k) M0_k + M1_k x (x_i - c_k) / (8 pi |x_i - c_k|^3)
     constexpr int TILE = 128;
     __shared__ T sc[TILE][6];   // centre hi (3), lo (3)
     __shared__ T sm[TILE][6];
+    __shared__ int range[2];
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < N;
     const long long ii = valid ? i : 0;
+    const int pr = sph_prob[sph[ii]];
+    const int k0 = prob_sph[pr], k1 = prob_sph[pr + 1];
+    if (threadIdx.x == 0) {
+        long long last = min(N - 1, (long long)blockIdx.x * blockDim.x + blockDim.x - 1);
+        range[0] = k0;
+        range[1] = prob_sph[sph_prob[sph[last]] + 1];
+    }
+    __syncthreads();
+    const int kb = range[0], ke = range[1];
     const double X = x64[4 * ii], Y = x64[4 * ii + 1], Z = x64[4 * ii + 2];
     const T xh = (T)X, yh = (T)Y, zh = (T)Z;
     const T xl = (T)(X - (double)xh), yl = (T)(Y - (double)yh), zl = (T)(Z - (double)zh);
     T ux = 0, uy = 0, uz = 0;
-    for (int b = 0; b < n; b += TILE) {
+    for (int b = kb; b < ke; b += TILE) {
         __syncthreads();
         for (int j = threadIdx.x; j < TILE; j += blockDim.x) {
             int k = b + j;
             for (int d = 0; d < 3; ++d) {
-                double cd = (k < n) ? c[3 * k + d] : 0.0;
+                double cd = (k < ke) ? c[3 * k + d] : 0.0;
                 T h = (T)cd;
                 sc[j][d] = h;
                 sc[j][3 + d] = (T)(cd - (double)h);
             }
-            for (int d = 0; d < 6; ++d) sm[j][d] = (k < n) ? (T)mom[6 * k + d] : (T)0;
+            for (int d = 0; d < 6; ++d) sm[j][d] = (k < ke) ? (T)mom[6 * k + d] : (T)0;
         }
         __syncthreads();
-        int cnt = min(TILE, n - b);
+        int cnt = min(TILE, ke - b);
         for (int j = 0; j < cnt; ++j) {
+            if (b + j < k0 || b + j >= k1) continue;
             T dx = (xh - sc[j][0]) + (xl - sc[j][3]);
             T dy = (yh - sc[j][1]) + (yl - sc[j][4]);
             T dz = (zh - sc[j][2]) + (zl - sc[j][5]);
@@ -196,9 +210,11 @@ cudaError_t launch_moments(sbie_ctx* c, const double* dens) {
 
 cudaError_t launch_completion(sbie_ctx* c, bool f32, double* out) {
     if (f32) {
-        completion_kernel<float><<<nblk(c->N, 128), 128, 0, c->stream>>>(c->d_x, c->d_c, c->d_mom, c->n, c->N, out);
+        completion_kernel<float><<<nblk(c->N, 128), 128, 0, c->stream>>>(c->d_x, c->d_c, c->d_mom, c->d_sph,
+                                                                          c->d_sph_prob, c->d_prob_sph, c->N, out);
     } else {
-        completion_kernel<double><<<nblk(c->N, 128), 128, 0, c->stream>>>(c->d_x, c->d_c, c->d_mom, c->n, c->N, out);
+        completion_kernel<double><<<nblk(c->N, 128), 128, 0, c->stream>>>(c->d_x, c->d_c, c->d_mom, c->d_sph,
+                                                                           c->d_sph_prob, c->d_prob_sph, c->N, out);
     }
     ++c->n_launch;
     return cudaGetLastError();

@@ -36,8 +36,21 @@ struct FarArgs {
     const int* __restrict__ sph;
     const int* __restrict__ near_ptr;
     const int* __restrict__ near_idx;
+    const int* __restrict__ sph_prob;  // problem of each sphere
+    const int* __restrict__ prob_sph;  // first sphere of each problem (+ end)
     double* __restrict__ part;  // [split][N][3]
 };
+
+// Source nodes of split `split` for a target sphere: its problem's nodes cut
+// into gridDim.y tile-aligned pieces.
+__device__ __forceinline__ void source_range(const FarArgs& a, int sphere, int split, long long& b0, long long& b1) {
+    const int pr = a.sph_prob[sphere];
+    const long long beg = (long long)a.prob_sph[pr] * a.npn, end = (long long)a.prob_sph[pr + 1] * a.npn;
+    long long len = (end - beg + gridDim.y - 1) / gridDim.y;
+    len = ((len + a.tile - 1) / a.tile) * a.tile;
+    b0 = beg + (long long)split * len;
+    b1 = min(end, b0 + len);
+}
 
 __device__ __forceinline__ void build_flags(const FarArgs& a, int sphere, unsigned* flags) {
     const int nw = (a.n + 31) >> 5;
@@ -114,8 +127,8 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) sum[t][d] = cmp[t][d] = 0.f;
 
-    const long long b0 = (long long)split * a.split_len;
-    const long long b1 = min(a.N, b0 + a.split_len);
+    long long b0, b1;
+    source_range(a, sphere, split, b0, b1);
     for (long long base = b0; base < b1; base += a.tile) {
         __syncthreads();
         for (int j = tid; j < a.tile; j += bd) {
@@ -295,8 +308,8 @@ __global__ void __launch_bounds__(256) far_df_kernel(FarArgs a) {
         tnx = df_split(nn.x); tny = df_split(nn.y); tnz = df_split(nn.z);
     }
     double sum[3] = {0.0, 0.0, 0.0};
-    const long long b0 = (long long)split * a.split_len;
-    const long long b1 = min(a.N, b0 + a.split_len);
+    long long b0, b1;
+    source_range(a, sphere, split, b0, b1);
     for (long long base = b0; base < b1; base += a.tile) {
         __syncthreads();
         for (int j = tid; j < a.tile; j += bd) {
@@ -403,8 +416,8 @@ __global__ void __launch_bounds__(256) far_f64_kernel(FarArgs a) {
 #pragma unroll
     for (int t = 0; t < TPT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = 0.0;
     const double far_off = 1.0e6;
-    const long long b0 = (long long)split * a.split_len;
-    const long long b1 = min(a.N, b0 + a.split_len);
+    long long b0, b1;
+    source_range(a, sphere, split, b0, b1);
     for (long long base = b0; base < b1; base += a.tile) {
         __syncthreads();
         for (int j = tid; j < a.tile; j += bd) {
@@ -495,9 +508,12 @@ cudaError_t launch_pack(sbie_ctx* c, const double* dens, int mode) {
 
 long long far_pairs(const sbie_ctx* c) {
     long long tot = 0;
-    for (int i = 0; i < c->n; ++i) {
-        long long excl = 1 + (c->h_near_ptr[i + 1] - c->h_near_ptr[i]);
-        tot += (long long)c->npn * (c->N - excl * c->npn);
+    for (int pr = 0; pr < c->n_prob; ++pr) {
+        const long long nodes = (long long)(c->h_prob_sph[pr + 1] - c->h_prob_sph[pr]) * c->npn;
+        for (int i = c->h_prob_sph[pr]; i < c->h_prob_sph[pr + 1]; ++i) {
+            long long excl = 1 + (c->h_near_ptr[i + 1] - c->h_near_ptr[i]);
+            tot += (long long)c->npn * (nodes - excl * c->npn);
+        }
     }
     return tot;
 }
@@ -562,6 +578,7 @@ static FarArgs make_args(sbie_ctx* c, const FarTune& tu) {
     a.nrm64 = reinterpret_cast<const double4*>(c->d_nrm64);
     a.src64 = c->d_src64;
     a.c = c->d_c; a.sph = c->d_sph; a.near_ptr = c->d_near_ptr; a.near_idx = c->d_near_idx;
+    a.sph_prob = c->d_sph_prob; a.prob_sph = c->d_prob_sph;
     a.part = c->d_part;
     return a;
 }

@@ -26,7 +26,7 @@ constexpr int kMaxDevices = 128;
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Slots {
-    size_t tab, x64, xhi, xlo, nrm, nrm64, sph, near_ptr, near_idx, src64, part, end;
+    size_t tab, x64, xhi, xlo, nrm, nrm64, sph, near_ptr, near_idx, sph_prob, prob_sph, src64, part, end;
 };
 
 Slots slots() {
@@ -41,6 +41,8 @@ Slots slots() {
     s.sph = o;      o = align256(o + sizeof(int) * kNoallocMaxNodes);
     s.near_ptr = o; o = align256(o + sizeof(int) * (kNoallocMaxSpheres + 1));
     s.near_idx = o; o = align256(o + sizeof(int));
+    s.sph_prob = o; o = align256(o + sizeof(int) * kNoallocMaxSpheres);
+    s.prob_sph = o; o = align256(o + sizeof(int) * 2);
     s.src64 = o;    o = align256(o + sizeof(double) * 4 * kNoallocMaxNodes);
     s.part = o;     o = align256(o + sizeof(double) * 3 * kNoallocSplit * kNoallocMaxNodes);
     s.end = o;
@@ -140,6 +142,9 @@ extern "C" sbie_status sphere_bie_apply_layer_noalloc(sbie_op op, int n_spheres,
     c.d_sph = reinterpret_cast<int*>(base + sl.sph);
     c.d_near_ptr = reinterpret_cast<int*>(base + sl.near_ptr);
     c.d_near_idx = reinterpret_cast<int*>(base + sl.near_idx);
+    c.d_sph_prob = reinterpret_cast<int*>(base + sl.sph_prob);
+    c.d_prob_sph = reinterpret_cast<int*>(base + sl.prob_sph);
+    c.n_prob = 1;
     c.d_src64 = reinterpret_cast<double4*>(base + sl.src64);
     c.d_part = reinterpret_cast<double*>(base + sl.part);
     c.n_near = 0;
@@ -165,8 +170,13 @@ extern "C" sbie_status sphere_bie_apply_layer_noalloc(sbie_op op, int n_spheres,
         g_tab_p[dev] = p;
     }
     // The scratch keeps the previous call's contents: the close-pair list must
-    // start empty; every other slot is fully rewritten below before it is read.
+    // start empty and every sphere belongs to the one problem [0, n_spheres);
+    // every other slot is fully rewritten below before it is read.
+    const int one_problem[2] = {0, n_spheres};
     e = cudaMemsetAsync(c.d_near_ptr, 0, sizeof(int) * (n_spheres + 1), c.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.d_sph_prob, 0, sizeof(int) * n_spheres, c.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c.d_prob_sph, one_problem, sizeof(one_problem), cudaMemcpyHostToDevice, c.stream);
     if (e == cudaSuccess) e = launch_geometry(&c);
     if (e == cudaSuccess) e = launch_pack(&c, density, kModeF64);
     if (e == cudaSuccess) e = launch_far(&c, k, kModeF64, out);

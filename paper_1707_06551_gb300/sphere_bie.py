@@ -69,6 +69,7 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         L.sphere_bie_default_opts.argtypes = [ctypes.POINTER(Opts)]
         L.sphere_bie_create.argtypes = [ctypes.c_int, _P, _P, ctypes.POINTER(Opts), ctypes.POINTER(_P)]
+        L.sphere_bie_create_batch.argtypes = [ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(Opts), ctypes.POINTER(_P)]
         L.sphere_bie_num_nodes.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong)]
         L.sphere_bie_nodes.argtypes = [_P, _P, _P, _P]
         L.sphere_bie_apply_operator.argtypes = [_P, ctypes.c_int, _P, _P]
@@ -81,7 +82,8 @@ def lib():
         L.sphere_bie_profile_read.argtypes = [_P, ctypes.POINTER(Profile)]
         L.sphere_bie_autotune.argtypes = [_P, ctypes.c_int, ctypes.POINTER(FarTuning)]
         L.sphere_bie_apply_layer_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]
-        for f in ("sphere_bie_default_opts", "sphere_bie_create", "sphere_bie_num_nodes", "sphere_bie_nodes",
+        for f in ("sphere_bie_default_opts", "sphere_bie_create", "sphere_bie_create_batch", "sphere_bie_num_nodes",
+                  "sphere_bie_nodes",
                   "sphere_bie_apply_operator", "sphere_bie_solve_mobility", "sphere_bie_solve_resistance",
                   "sphere_bie_destroy", "sphere_bie_profile", "sphere_bie_profile_read",
                   "sphere_bie_apply_layer_noalloc", "sphere_bie_autotune"):
@@ -132,6 +134,18 @@ def sphere_bie_create(centres, radii, opts):
         raise ValueError("centres and radii disagree")
     h = _P()
     _check(None, lib().sphere_bie_create(len(a), _ptr(c), _ptr(a), ctypes.byref(opts), ctypes.byref(h)))
+    return h
+
+
+def sphere_bie_create_batch(centres_list, radii_list, p_list, opts):
+    """One context for independent problems; arrays are concatenated in problem order."""
+    n = np.ascontiguousarray([len(np.asarray(r).reshape(-1)) for r in radii_list], dtype=np.int32)
+    p = np.ascontiguousarray(p_list, dtype=np.int32)
+    c = np.ascontiguousarray(np.concatenate([np.asarray(x, float).reshape(-1, 3) for x in centres_list]))
+    a = np.ascontiguousarray(np.concatenate([np.asarray(x, float).reshape(-1) for x in radii_list]))
+    h = _P()
+    _check(None, lib().sphere_bie_create_batch(len(n), ctypes.c_void_p(n.ctypes.data), ctypes.c_void_p(p.ctypes.data),
+                                               _ptr(c), _ptr(a), ctypes.byref(opts), ctypes.byref(h)))
     return h
 
 
@@ -214,12 +228,19 @@ def sphere_bie_profile_read(ctx):
 
 
 class SphereBIE:
-    """Owning wrapper around a context (host memory interface)."""
+    """Owning wrapper around a context (host memory interface).  With
+    `batch=[(centres, radii, p), ...]` it holds a batch of problems."""
 
-    def __init__(self, centres, radii, p, eta=1.0, prec=SBIE_FP64, tol=1e-8, restart=60, max_iter=600):
-        self.opts = make_opts(p, eta, prec, tol, restart, max_iter, 0)
-        self.ctx = sphere_bie_create(centres, radii, self.opts)
-        self.n = len(np.asarray(radii).reshape(-1))
+    def __init__(self, centres=None, radii=None, p=None, eta=1.0, prec=SBIE_FP64, tol=1e-8, restart=60, max_iter=600,
+                 batch=None):
+        self.opts = make_opts(p if p is not None else batch[0][2], eta, prec, tol, restart, max_iter, 0)
+        if batch is None:
+            self.ctx = sphere_bie_create(centres, radii, self.opts)
+            self.n = len(np.asarray(radii).reshape(-1))
+        else:
+            self.ctx = sphere_bie_create_batch([x[0] for x in batch], [x[1] for x in batch], [x[2] for x in batch],
+                                               self.opts)
+            self.n = sum(len(np.asarray(x[1]).reshape(-1)) for x in batch)
         self.N = sphere_bie_num_nodes(self.ctx)
 
     def apply(self, op, density):

@@ -89,3 +89,22 @@ def test_binding_rejects_wrong_dtypes(lib):
         lib._ptr(np.zeros(3, dtype=np.float32))
     with pytest.raises(ValueError):
         lib._ptr(np.zeros((3, 3))[:, 0])
+
+
+def test_create_batch_rejects_bad_input(lib):
+    c = np.array([[0.0, 0, 0], [3.0, 0, 0], [10.0, 0, 0]])
+    a = np.ones(3)
+    o = lib.make_opts(4)
+    h = ctypes.c_void_p()
+    for ns, ps, status in (([2, 1], [4, 30], 1), ([2, 0], [4, 4], 1), ([0, 3], [4, 4], 1)):
+        n = np.array(ns, dtype=np.int32)
+        p = np.array(ps, dtype=np.int32)
+        st = lib.lib().sphere_bie_create_batch(2, ctypes.c_void_p(n.ctypes.data), ctypes.c_void_p(p.ctypes.data),
+                                               lib._ptr(c), lib._ptr(a), ctypes.byref(o), ctypes.byref(h))
+        assert st == status
+    c[1, 0] = 1.5  # overlap inside problem 0
+    n = np.array([2, 1], dtype=np.int32)
+    p = np.array([4, 6], dtype=np.int32)
+    st = lib.lib().sphere_bie_create_batch(2, ctypes.c_void_p(n.ctypes.data), ctypes.c_void_p(p.ctypes.data),
+                                           lib._ptr(c), lib._ptr(a), ctypes.byref(o), ctypes.byref(h))
+    assert st == 2

@@ -73,8 +73,8 @@ typedef struct {
     double tol;             /* GMRES stop: ||b - A x||_2 / ||b||_2 <= tol (nodal l2)            */
     int restart;            /* GMRES restart length                                            */
     int max_iter;           /* total GMRES iterations allowed                                  */
-    int use_learned_precond;/* reserved; must be 0                                             */
-    const char* mlp_weights_path; /* reserved; may be NULL                                     */
+    int use_learned_precond;/* 0 none; 1 pair network (mlp_weights_path); 2 exact pair blocks */
+    const char* mlp_weights_path; /* pair-network file written by sphere_bie_train_pair_network */
     int mem_kind;           /* 0 host pointers, 1 device pointers                              */
     void* stream;           /* cudaStream_t for mem_kind = 1, or NULL                          */
 } sbie_opts;
@@ -214,6 +214,58 @@ sbie_status sphere_bie_profile_read(sbie_ctx* ctx, sbie_profile* out);
 sbie_status sphere_bie_apply_layer_noalloc(sbie_op op, int n_spheres, int p, const double* centres,
                                            const double* radii, const double* density, double* out,
                                            void* stream);
+
+/* ---- learned pair preconditioner ------------------------------------------
+ * With opts.use_learned_precond = 1 (network read from opts.mlp_weights_path)
+ * or 2 (exact blocks), create builds a right preconditioner for GMRES:
+ *   M^{-1} r = H r + Z C^{-1} Z^+ r,
+ * Z^+ the VSH analysis restricted to degree <= 4 (73 real coefficients per
+ * sphere), H the exact inverse of each sphere's own operator above degree 4
+ * (1/D+ of Theorem 2, and 2 on the non-band-limited remainder), C^{-1} an
+ * additive Schwarz inverse over close pairs of the low-mode pair systems
+ * [[L_i, B_ik], [B_ki, L_k]] (L probed exactly; B probed exactly, or for 1
+ * predicted by the pair network in the pair frame and rotated).  The operator
+ * and the true residual are unchanged: the preconditioner changes the
+ * iteration count, not the answer.  Built for the resistance operator. */
+
+typedef struct {
+    int n_samples;         /* two-sphere configurations generated (>= 16)          */
+    int p;                 /* VSH order of the probed grid (4..24)                 */
+    double gap_min, gap_max; /* surface gaps, log-uniform                          */
+    double radius;         /* both radii                                           */
+    int epochs, batch;
+    double lr;             /* Adam learning rate                                   */
+    unsigned long long seed;
+    double val_frac;       /* held-out fraction for the validation error           */
+} sbie_pair_train_opts;
+
+typedef struct {
+    double train_loss;     /* mean squared error of the last epoch (standardised)   */
+    double val_rel_err;    /* mean relative Frobenius error of held-out blocks      */
+    double t_data_s, t_train_s;
+    int n_train, n_val;
+} sbie_pair_train_info;
+
+/* Generates exact pair-frame low-mode blocks of two-sphere configurations
+ * (probing the close-pair path of the operator on the GPU), trains the pair
+ * network on them with the library's own kernels, and writes it to path. */
+sbie_status sphere_bie_train_pair_network(const sbie_pair_train_opts* opts, const char* path,
+                                          sbie_pair_train_info* info);
+
+/* Exact pair-frame blocks: source of radius a_src at the origin, target of
+ * radius a_tgt at (0, 0, dist[q]); blocks: host [n][73][73] (target row,
+ * source column) of the resistance operator, grid order p. */
+sbie_status sphere_bie_pair_blocks(int n, const double* dist, const double* a_src, const double* a_tgt, int p,
+                                   double* blocks);
+
+/* Number of network parameters (FP32, layer by layer: W1 (5x128), b1, ...). */
+sbie_status sphere_bie_pair_network_size(long long* n_params);
+
+/* Loss (mean squared error over all outputs) and its gradient for raw
+ * network inputs X [n][5] and targets Y [n][5329] (host), with the weights
+ * rounded to BF16 as in training. */
+sbie_status sphere_bie_pair_network_gradients(const float* params, int n, const float* X, const float* Y,
+                                              float* grads, double* loss);
 
 /* Frees every device buffer and the context.  NULL is accepted. */
 sbie_status sphere_bie_destroy(sbie_ctx* ctx);

@@ -7,11 +7,15 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <utility>
 #include <mutex>
 #include <new>
 #include <tuple>
+#include <fstream>
+#include <random>
 
 #include "common.h"
+#include "mlp.h"
 
 using namespace sbie;
 
@@ -47,6 +51,20 @@ cudaError_t dmalloc(T** p, size_t count) {
     return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * std::max<size_t>(count, 1));
 }
 
+// Host <-> device copies ordered on a (non-blocking) stream.  A plain
+// cudaMemcpy runs on the legacy default stream, which is not ordered with
+// non-blocking streams, so every copy of a context goes through these.
+template <typename T>
+cudaError_t h2d(cudaStream_t s, T* dst, const T* src, size_t count) {
+    return cudaMemcpyAsync(dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, s);
+}
+
+template <typename T>
+cudaError_t d2h(cudaStream_t s, T* dst, const T* src, size_t count) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, sizeof(T) * count, cudaMemcpyDeviceToHost, s);
+    return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+}
+
 void free_all(sbie_ctx* c) {
     for (sbie_ctx* q : c->parts) {
         free_all(q);
@@ -56,7 +74,9 @@ void free_all(sbie_ctx* c) {
     void* ptrs[] = {c->d_c, c->d_a, c->d_x, c->d_xhi, c->d_xlo, c->d_nrm, c->d_nrm64, c->d_sph, c->d_near_ptr,
                     c->d_near_idx, c->d_tab, c->d_coef, c->d_chan, c->d_chanf, c->d_mom, c->d_part, c->d_src64,
                     c->d_srcf, c->d_in, c->d_out, c->d_tmp, c->d_tmp2, c->d_small, c->d_red, c->d_V, c->d_xsol,
-                    c->d_rhs, c->d_res, c->d_prob_sph, c->d_sph_prob, c->d_node_prob, c->d_seg3, c->d_H, c->d_pvec};
+                    c->d_rhs, c->d_res, c->d_prob_sph, c->d_sph_prob, c->d_node_prob, c->d_seg3, c->d_H, c->d_pvec,
+                    c->d_ZS, c->d_ZA, c->d_modes, c->d_near_pair, c->d_pinv, c->d_sinv, c->d_low, c->d_lowe,
+                    c->d_pz};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -292,7 +312,7 @@ using AFn = std::function<sbie_status(const double*, double*)>;
 // residual exceeds tol[p]; the residual is recomputed as b - A x at every
 // restart.  A problem that has converged keeps zero Krylov vectors.
 sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const std::vector<double>& tol,
-                  const std::vector<char>& want, int restart, int max_iter, GmresOut& go) {
+                  const std::vector<char>& want, int restart, int max_iter, GmresOut& go, const AFn* M = nullptr) {
     sbie_ctx* c = S.top;
     const long long n3 = S.n3;
     const int P = S.P;
@@ -335,7 +355,12 @@ sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const 
         }
         for (int k = 0; k < mm && any(live); ++k) {
             double* w = V + (size_t)(k + 1) * n3;
-            CKS(A(V + (size_t)k * n3, w));
+            if (M) {  // right preconditioning: Arnoldi on A M^{-1}
+                CKS((*M)(V + (size_t)k * n3, c->d_pz));
+                CKS(A(c->d_pz, w));
+            } else {
+                CKS(A(V + (size_t)k * n3, w));
+            }
             {
                 StageScope sc(c, ST_BLAS);
                 for (int pass = 0; pass < 2; ++pass) {
@@ -403,7 +428,15 @@ sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const 
         }
         if (kmax == 0) break;
         CKS(stage_H(c, stage.data(), (size_t)kmax * P));
-        CK(seg_gemv(c, V, kmax, n3, c->d_H, P, 1.0, c->d_node_prob, x, n3));
+        if (M) {  // x += M^{-1} (V y)
+            double* t = c->d_pz + n3;
+            CK(cudaMemsetAsync(t, 0, sizeof(double) * n3, c->stream));
+            CK(seg_gemv(c, V, kmax, n3, c->d_H, P, 1.0, c->d_node_prob, t, n3));
+            CKS((*M)(t, c->d_pz));
+            CK(blas_axpy(c, 1.0, c->d_pz, x, n3));
+        } else {
+            CK(seg_gemv(c, V, kmax, n3, c->d_H, P, 1.0, c->d_node_prob, x, n3));
+        }
         CKS(A(x, r));
         CK(blas_lincomb(c, 1.0, b, -1.0, r, r, n3));
         CKS(seg_norms(S, r, beta));
@@ -429,6 +462,25 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
     const int hm = hi_mode(c);
     AFn A64 = [&](const double* in, double* out) { return apply_sys(S, op, hm, in, out); };
     AFn A32 = [&](const double* in, double* out) { return apply_sys(S, op, kModeF32, in, out); };
+    bool prec = false;
+    for (sbie_ctx* q : S.parts) prec |= q->prec_kind > 0;
+    AFn Mf = [&](const double* in, double* out) {
+        for (size_t i = 0; i < S.parts.size(); ++i) {
+            sbie_ctx* q = S.parts[i];
+            if (q->prec_kind > 0) {
+                cudaError_t e = precond_apply(q, in + S.off3[i], out + S.off3[i]);
+                if (e != cudaSuccess) return fail(c, SBIE_ERR_CUDA, std::string("preconditioner: ") + cudaGetErrorString(e));
+            } else {
+                cudaError_t e = cudaMemcpyAsync(out + S.off3[i], in + S.off3[i], sizeof(double) * q->N * 3,
+                                                cudaMemcpyDeviceToDevice, c->stream);
+                if (e != cudaSuccess) return fail(c, SBIE_ERR_CUDA, cudaGetErrorString(e));
+            }
+        }
+        return SBIE_OK;
+    };
+    const AFn* M = prec ? &Mf : nullptr;
+    if (prec && !c->d_pz && dmalloc(&c->d_pz, 2 * (size_t)n3) != cudaSuccess)
+        return fail(c, SBIE_ERR_OOM, "preconditioner buffers");
     const double tol = c->opts.tol;
     GmresOut go;
     sbie_solve_info inf{};
@@ -437,7 +489,7 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
     CKS(ensure_krylov(c, std::max(1, std::min(c->opts.restart, 250)), P));
     if (c->opts.prec != SBIE_MIXED) {
         CKS(gmres(S, A64, b, x, std::vector<double>(P, tol), std::vector<char>(P, 1), c->opts.restart,
-                  c->opts.max_iter, go));
+                  c->opts.max_iter, go, M));
         inf.iters = go.iters;
         inf.restarts = go.restarts;
         rel = go.rel;
@@ -458,7 +510,7 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
                 want[p] = rel[p] > tol;
                 itol[p] = std::min(1e-3, std::max(1e-5, 0.5 * tol / std::max(rel[p], 1e-300)));
             }
-            CKS(gmres(S, A32, r, d, itol, want, c->opts.restart, c->opts.max_iter - iters, go));
+            CKS(gmres(S, A32, r, d, itol, want, c->opts.restart, c->opts.max_iter - iters, go, M));
             iters += go.iters;
             CK(blas_axpy(c, 1.0, d, x, n3));
             CKS(A64(x, r));
@@ -495,7 +547,10 @@ sbie_status check_opts(const sbie_opts* opts) {
     if (opts->prec != SBIE_FP64 && opts->prec != SBIE_MIXED && opts->prec != SBIE_FP64_DF)
         return fail(nullptr, SBIE_ERR_ARG, "bad precision");
     if (opts->mem_kind != 0 && opts->mem_kind != 1) return fail(nullptr, SBIE_ERR_ARG, "mem_kind must be 0 or 1");
-    if (opts->use_learned_precond != 0) return fail(nullptr, SBIE_ERR_ARG, "learned preconditioner not available");
+    if (opts->use_learned_precond < 0 || opts->use_learned_precond > 2)
+        return fail(nullptr, SBIE_ERR_ARG, "use_learned_precond must be 0, 1 or 2");
+    if (opts->use_learned_precond == 1 && !opts->mlp_weights_path)
+        return fail(nullptr, SBIE_ERR_ARG, "the learned preconditioner needs mlp_weights_path");
     if (!(opts->tol > 0.0) || opts->restart < 1 || opts->max_iter < 0)
         return fail(nullptr, SBIE_ERR_ARG, "need tol > 0, restart >= 1, max_iter >= 0");
     return SBIE_OK;
@@ -603,18 +658,18 @@ sbie_status create_part(const sbie_opts& o, int n, const double* centres, const 
         sbie_status s = ensure_part(c);
         if (s != SBIE_OK) return bail(s, c->err);
     }
-    e = cudaMemcpy(c->d_c, centres, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->d_a, radii, sizeof(double) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->d_near_ptr, c->h_near_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+    e = h2d(c->stream, c->d_c, centres, 3 * (size_t)n);
+    if (e == cudaSuccess) e = h2d(c->stream, c->d_a, radii, (size_t)n);
+    if (e == cudaSuccess) e = h2d(c->stream, c->d_near_ptr, c->h_near_ptr.data(), (size_t)n + 1);
     if (e == cudaSuccess && c->n_near > 0)
-        e = cudaMemcpy(c->d_near_idx, c->h_near_idx.data(), sizeof(int) * c->n_near, cudaMemcpyHostToDevice);
+        e = h2d(c->stream, c->d_near_idx, c->h_near_idx.data(), (size_t)c->n_near);
     if (e == cudaSuccess)
-        e = cudaMemcpy(c->d_prob_sph, prob_sph.data(), sizeof(int) * (c->n_prob + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->d_sph_prob, sph_prob.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->d_node_prob, node_prob.data(), sizeof(int) * N, cudaMemcpyHostToDevice);
+        e = h2d(c->stream, c->d_prob_sph, prob_sph.data(), (size_t)c->n_prob + 1);
+    if (e == cudaSuccess) e = h2d(c->stream, c->d_sph_prob, sph_prob.data(), (size_t)n);
+    if (e == cudaSuccess) e = h2d(c->stream, c->d_node_prob, node_prob.data(), (size_t)N);
     if (e == cudaSuccess)
-        e = cudaMemcpy(c->d_seg3, c->seg3.data(), sizeof(long long) * c->seg3.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->d_tab, htab.data(), sizeof(double) * htab.size(), cudaMemcpyHostToDevice);
+        e = h2d(c->stream, c->d_seg3, c->seg3.data(), c->seg3.size());
+    if (e == cudaSuccess) e = h2d(c->stream, c->d_tab, htab.data(), htab.size());
     if (e == cudaSuccess) e = launch_geometry(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bail(SBIE_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
@@ -680,6 +735,353 @@ sbie_status to_user(sbie_ctx* c, const double* dev, double* user, bool nodal) {
     return SBIE_OK;
 }
 
+// ---- pair preconditioner and pair network (kernels in precond.cu, mlp.cu)
+
+struct PairNet {
+    std::vector<float> params;          // FP32 weights (mlp_layout)
+    float in_mean[kMlpIn], in_std[kMlpIn];
+    std::vector<float> out_mean, out_std;
+    int p_train = 0;
+};
+const char kNetMagic[9] = "SBIEPN01";
+
+sbie_status net_save(const char* path, const PairNet& net) {
+    std::ofstream f(path, std::ios::binary);
+    if (!f) return fail(nullptr, SBIE_ERR_ARG, std::string("cannot write ") + path);
+    int hdr[6] = {kPrecL, kMlpIn, kMlpHidden, kMlpOut, net.p_train, (int)net.params.size()};
+    f.write(kNetMagic, 8);
+    f.write(reinterpret_cast<const char*>(hdr), sizeof(hdr));
+    f.write(reinterpret_cast<const char*>(net.in_mean), sizeof(net.in_mean));
+    f.write(reinterpret_cast<const char*>(net.in_std), sizeof(net.in_std));
+    f.write(reinterpret_cast<const char*>(net.out_mean.data()), sizeof(float) * kMlpOut);
+    f.write(reinterpret_cast<const char*>(net.out_std.data()), sizeof(float) * kMlpOut);
+    f.write(reinterpret_cast<const char*>(net.params.data()), sizeof(float) * net.params.size());
+    return f ? SBIE_OK : fail(nullptr, SBIE_ERR_ARG, "write failed");
+}
+
+sbie_status net_load(const char* path, PairNet& net) {
+    std::ifstream f(path, std::ios::binary);
+    if (!f) return fail(nullptr, SBIE_ERR_ARG, std::string("cannot read ") + path);
+    char magic[8];
+    int hdr[6];
+    f.read(magic, 8);
+    f.read(reinterpret_cast<char*>(hdr), sizeof(hdr));
+    MlpLayout L = mlp_layout();
+    if (!f || std::memcmp(magic, kNetMagic, 8) != 0 || hdr[0] != kPrecL || hdr[1] != kMlpIn || hdr[2] != kMlpHidden ||
+        hdr[3] != kMlpOut || hdr[5] != (int)L.total)
+        return fail(nullptr, SBIE_ERR_ARG, std::string("not a pair-network file: ") + path);
+    net.p_train = hdr[4];
+    net.out_mean.resize(kMlpOut);
+    net.out_std.resize(kMlpOut);
+    net.params.resize(L.total);
+    f.read(reinterpret_cast<char*>(net.in_mean), sizeof(net.in_mean));
+    f.read(reinterpret_cast<char*>(net.in_std), sizeof(net.in_std));
+    f.read(reinterpret_cast<char*>(net.out_mean.data()), sizeof(float) * kMlpOut);
+    f.read(reinterpret_cast<char*>(net.out_std.data()), sizeof(float) * kMlpOut);
+    f.read(reinterpret_cast<char*>(net.params.data()), sizeof(float) * L.total);
+    return f ? SBIE_OK : fail(nullptr, SBIE_ERR_ARG, std::string("truncated pair-network file: ") + path);
+}
+
+// Exact low-mode blocks by probing context `c` (problems of sph_per_prob
+// spheres): for each side s < nsides the 73 low modes are placed on local
+// sphere s of every problem and the resistance operator applied in FP64; the
+// low-mode analysis of every sphere's response fills
+// out[s][sphere][row][mode] (host).
+sbie_status probe_blocks(sbie_ctx* c, int sph_per_prob, int nsides, std::vector<double>& out) {
+    std::vector<double> ZS, ZA;
+    lowmode_tables(c->p, ZS, ZA);
+    double *dZS = nullptr, *dZA = nullptr, *dB = nullptr;
+    const size_t per = (size_t)c->n * kLowModes * kLowModes;
+    sbie_status st = SBIE_OK;
+    if (dmalloc(&dZS, ZS.size()) != cudaSuccess || dmalloc(&dZA, ZA.size()) != cudaSuccess ||
+        dmalloc(&dB, per * nsides) != cudaSuccess) {
+        st = fail(c, SBIE_ERR_OOM, "probe buffers");
+    }
+    cudaError_t e = cudaSuccess;
+    if (st == SBIE_OK) {
+        e = h2d(c->stream, dZS, ZS.data(), ZS.size());
+        if (e == cudaSuccess) e = h2d(c->stream, dZA, ZA.data(), ZA.size());
+        for (int s = 0; s < nsides && e == cudaSuccess && st == SBIE_OK; ++s)
+            for (int b = 0; b < kLowModes && e == cudaSuccess && st == SBIE_OK; ++b) {
+                e = launch_probe_density(c, sph_per_prob, s, b, dZS, c->d_in);
+                if (e == cudaSuccess) st = apply_dev(c, SBIE_OP_RESISTANCE, kModeF64, c->d_in, c->d_out);
+                if (st == SBIE_OK && e == cudaSuccess) e = launch_probe_analysis(c, dZA, c->d_out, b, dB + s * per);
+            }
+        if (e == cudaSuccess && st == SBIE_OK) {
+            out.resize(per * nsides);
+            e = d2h(c->stream, out.data(), dB, out.size());
+        }
+        if (e != cudaSuccess) st = fail(c, SBIE_ERR_CUDA, std::string("probe: ") + cudaGetErrorString(e));
+    }
+    for (double* p : {dZS, dZA, dB})
+        if (p) cudaFree(p);
+    return st;
+}
+
+sbie_status create_part(const sbie_opts& o, int n, const double* centres, const double* radii,
+                        const std::vector<int>& prob_sph, cudaStream_t stream, sbie_ctx** out);
+
+// Exact aligned blocks: source sphere (radius a_s) at the origin, target
+// (radius a_t) at (0, 0, d); out [n][73][73] (target <- source).
+sbie_status aligned_blocks(int n, const double* d, const double* a_s, const double* a_t, int p, double eta,
+                           std::vector<double>& out) {
+    std::vector<double> cc((size_t)n * 6, 0.0), aa((size_t)n * 2);
+    std::vector<int> ps(n + 1);
+    for (int q = 0; q < n; ++q) {
+        cc[6 * q + 5] = d[q];
+        aa[2 * q] = a_s[q];
+        aa[2 * q + 1] = a_t[q];
+        ps[q] = 2 * q;
+    }
+    ps[n] = 2 * n;
+    sbie_opts o;
+    sphere_bie_default_opts(&o);
+    o.p = p;
+    o.eta = eta;
+    sbie_ctx* pc = nullptr;
+    CKS(create_part(o, 2 * n, cc.data(), aa.data(), ps, nullptr, &pc));
+    std::vector<double> B;
+    sbie_status st = probe_blocks(pc, 2, 1, B);
+    if (st == SBIE_OK) {
+        out.resize((size_t)n * kLowModes * kLowModes);
+        const size_t blk = (size_t)kLowModes * kLowModes;
+        for (int q = 0; q < n; ++q) std::memcpy(out.data() + q * blk, B.data() + (2 * q + 1) * blk, sizeof(double) * blk);
+    } else {
+        g_last_error = pc->err;
+    }
+    free_all(pc);
+    delete pc;
+    return st;
+}
+
+// y = Rinv * B * R for 73 x 73 matrices (R, Rinv sparse block diagonal).
+void rotate_block(const std::vector<double>& Rinv, const double* B, const std::vector<double>& R, double* out) {
+    const int n = kLowModes;
+    std::vector<double> T((size_t)n * n, 0.0);
+    // T = B R
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j) {
+            const double r = R[(size_t)k * n + j];
+            if (r == 0.0) continue;
+            for (int i = 0; i < n; ++i) T[(size_t)i * n + j] += B[(size_t)i * n + k] * r;
+        }
+    std::fill(out, out + (size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            const double r = Rinv[(size_t)i * n + k];
+            if (r == 0.0) continue;
+            for (int j = 0; j < n; ++j) out[(size_t)i * n + j] += r * T[(size_t)k * n + j];
+        }
+}
+
+void pair_frame(const double* cs, const double* ct, double Q[9], double* dist) {
+    double u[3] = {ct[0] - cs[0], ct[1] - cs[1], ct[2] - cs[2]};
+    double d = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    for (double& v : u) v /= d;
+    int ax = 0;
+    for (int a = 1; a < 3; ++a)
+        if (std::fabs(u[a]) < std::fabs(u[ax])) ax = a;
+    double e1[3] = {0, 0, 0};
+    e1[ax] = 1.0;
+    double dot = e1[0] * u[0] + e1[1] * u[1] + e1[2] * u[2];
+    for (int a = 0; a < 3; ++a) e1[a] -= dot * u[a];
+    double nn = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (double& v : e1) v /= nn;
+    double e2[3] = {u[1] * e1[2] - u[2] * e1[1], u[2] * e1[0] - u[0] * e1[2], u[0] * e1[1] - u[1] * e1[0]};
+    for (int a = 0; a < 3; ++a) {
+        Q[3 * a + 0] = e1[a];
+        Q[3 * a + 1] = e2[a];
+        Q[3 * a + 2] = u[a];
+    }
+    *dist = d;
+}
+
+// Network blocks (pair frame, de-standardised) for inputs (0, 0, d, a_s, a_t).
+sbie_status net_blocks(const PairNet& net, const std::vector<float>& X5, std::vector<double>& out) {
+    const int n = (int)(X5.size() / kMlpIn);
+    MlpLayout L = mlp_layout();
+    float *dw = nullptr, *dX = nullptr, *dY = nullptr;
+    __nv_bfloat16* dwb = nullptr;
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(nullptr, SBIE_ERR_CUDA, "stream");
+    std::vector<float> Xs(X5.size());
+    for (int q = 0; q < n; ++q)
+        for (int j = 0; j < kMlpIn; ++j) Xs[q * kMlpIn + j] = (X5[q * kMlpIn + j] - net.in_mean[j]) / net.in_std[j];
+    cudaError_t e = cudaMalloc(&dw, sizeof(float) * L.total);
+    if (e == cudaSuccess) e = cudaMalloc(&dwb, sizeof(__nv_bfloat16) * L.total);
+    if (e == cudaSuccess) e = cudaMalloc(&dX, sizeof(float) * Xs.size());
+    if (e == cudaSuccess) e = cudaMalloc(&dY, sizeof(float) * (size_t)n * kMlpOut);
+    if (e == cudaSuccess) e = h2d(s, dw, net.params.data(), (size_t)L.total);
+    if (e == cudaSuccess) e = h2d(s, dX, Xs.data(), Xs.size());
+    if (e == cudaSuccess) e = mlp_to_bf16(s, dw, dwb);
+    if (e == cudaSuccess) e = mlp_forward_dev(s, dw, dwb, n, dX, dY);
+    std::vector<float> Y;
+    if (e == cudaSuccess) {
+        Y.resize((size_t)n * kMlpOut);
+        e = d2h(s, Y.data(), dY, Y.size());
+    }
+    for (void* p : {(void*)dw, (void*)dwb, (void*)dX, (void*)dY})
+        if (p) cudaFree(p);
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess) return fail(nullptr, SBIE_ERR_CUDA, std::string("network: ") + cudaGetErrorString(e));
+    out.resize(Y.size());
+    for (size_t i = 0; i < Y.size(); ++i)
+        out[i] = (double)Y[i] * net.out_std[i % kMlpOut] + net.out_mean[i % kMlpOut];
+    return SBIE_OK;
+}
+
+sbie_status precond_setup(sbie_ctx* c, int kind, const PairNet* net);
+
+// Pair preconditioner for every part when the options ask for one.
+sbie_status setup_preconditioner(const std::vector<sbie_ctx*>& parts, const sbie_opts& o) {
+    if (o.use_learned_precond == 0) return SBIE_OK;
+    PairNet net;
+    if (o.use_learned_precond == 1) CKS(net_load(o.mlp_weights_path, net));
+    for (sbie_ctx* q : parts) {
+        sbie_status st = precond_setup(q, o.use_learned_precond, &net);
+        if (st != SBIE_OK) {
+            if (q->err.empty() || q->err == "no error") q->err = g_last_error;
+            return st;
+        }
+    }
+    return SBIE_OK;
+}
+
+// Builds the pair preconditioner of one part (kind 1: network, 2: exact).
+sbie_status precond_setup(sbie_ctx* c, int kind, const PairNet* net) {
+    auto t0 = std::chrono::steady_clock::now();
+    const int n = c->n, NM = kLowModes;
+    const size_t blk = (size_t)NM * NM;
+    std::vector<double> ZS, ZA;
+    lowmode_tables(c->p, ZS, ZA);
+    std::vector<int4> modes = low_mode_table();
+    // undirected close pairs
+    std::map<std::pair<int, int>, int> pid;
+    std::vector<std::pair<int, int>> pairs;
+    std::vector<int> near_pair(std::max<long long>(1, c->n_near));
+    for (int i = 0; i < n; ++i)
+        for (int e = c->h_near_ptr[i]; e < c->h_near_ptr[i + 1]; ++e) {
+            const int k = c->h_near_idx[e];
+            auto key = std::make_pair(std::min(i, k), std::max(i, k));
+            auto it = pid.find(key);
+            if (it == pid.end()) {
+                it = pid.emplace(key, (int)pairs.size()).first;
+                pairs.push_back(key);
+            }
+            near_pair[e] = it->second;
+        }
+    const int np = (int)pairs.size();
+    // own blocks L_i: single-sphere problems
+    sbie_opts o = c->opts;
+    o.use_learned_precond = 0;
+    o.stream = nullptr;
+    std::vector<int> ps1(n + 1);
+    for (int q = 0; q <= n; ++q) ps1[q] = q;
+    sbie_ctx* sc = nullptr;
+    CKS(create_part(o, n, c->h_c.data(), c->h_a.data(), ps1, c->stream, &sc));
+    std::vector<double> Lam;
+    sbie_status st = probe_blocks(sc, 1, 1, Lam);
+    if (st != SBIE_OK) c->err = sc->err;
+    free_all(sc);
+    delete sc;
+    CKS(st);
+    // pair blocks B_ab (target a <- source b) and B_ba
+    std::vector<double> Bab((size_t)np * blk), Bba((size_t)np * blk);
+    if (kind == 2 && np > 0) {
+        std::vector<double> cc((size_t)np * 6), aa((size_t)np * 2);
+        std::vector<int> ps(np + 1);
+        for (int q = 0; q < np; ++q) {
+            for (int d = 0; d < 3; ++d) {
+                cc[6 * q + d] = c->h_c[3 * pairs[q].first + d];
+                cc[6 * q + 3 + d] = c->h_c[3 * pairs[q].second + d];
+            }
+            aa[2 * q] = c->h_a[pairs[q].first];
+            aa[2 * q + 1] = c->h_a[pairs[q].second];
+            ps[q] = 2 * q;
+        }
+        ps[np] = 2 * np;
+        sbie_ctx* pc = nullptr;
+        CKS(create_part(o, 2 * np, cc.data(), aa.data(), ps, c->stream, &pc));
+        std::vector<double> PB;
+        st = probe_blocks(pc, 2, 2, PB);
+        if (st != SBIE_OK) c->err = pc->err;
+        const size_t per = (size_t)2 * np * blk;
+        if (st == SBIE_OK)
+            for (int q = 0; q < np; ++q) {
+                std::memcpy(Bba.data() + q * blk, PB.data() + 0 * per + (2 * q + 1) * blk, sizeof(double) * blk);
+                std::memcpy(Bab.data() + q * blk, PB.data() + 1 * per + (2 * q + 0) * blk, sizeof(double) * blk);
+            }
+        free_all(pc);
+        delete pc;
+        CKS(st);
+    } else if (kind == 1 && np > 0) {
+        std::vector<float> X((size_t)2 * np * kMlpIn, 0.f);
+        std::vector<double> Qs((size_t)2 * np * 9);
+        for (int q = 0; q < np; ++q) {
+            const int a = pairs[q].first, b = pairs[q].second;
+            double d;
+            pair_frame(&c->h_c[3 * a], &c->h_c[3 * b], &Qs[(2 * q) * 9], &d);      // a -> b
+            pair_frame(&c->h_c[3 * b], &c->h_c[3 * a], &Qs[(2 * q + 1) * 9], &d);  // b -> a
+            float* x0 = &X[(2 * q) * kMlpIn];
+            x0[2] = (float)d; x0[3] = (float)c->h_a[a]; x0[4] = (float)c->h_a[b];
+            float* x1 = &X[(2 * q + 1) * kMlpIn];
+            x1[2] = (float)d; x1[3] = (float)c->h_a[b]; x1[4] = (float)c->h_a[a];
+        }
+        std::vector<double> Bp;
+        CKS(net_blocks(*net, X, Bp));
+        std::vector<double> R, Ri;
+        for (int q = 0; q < np; ++q)
+            for (int dir = 0; dir < 2; ++dir) {
+                const double* Q = &Qs[(2 * q + dir) * 9];
+                double Qt[9];
+                for (int r = 0; r < 3; ++r)
+                    for (int s = 0; s < 3; ++s) Qt[3 * r + s] = Q[3 * s + r];
+                lowmode_rotation(Q, R);
+                lowmode_rotation(Qt, Ri);
+                rotate_block(Ri, Bp.data() + (2 * q + dir) * blk, R, (dir == 0 ? Bba : Bab).data() + q * blk);
+            }
+    }
+    // pair systems [[L_a, B_ab], [B_ba, L_b]] and own blocks, inverted in FP32
+    std::vector<float> A((size_t)std::max(1, np) * 4 * blk), S((size_t)n * blk);
+    for (int q = 0; q < np; ++q) {
+        const int a = pairs[q].first, b = pairs[q].second;
+        float* M = A.data() + q * 4 * blk;
+        for (int r = 0; r < NM; ++r)
+            for (int s = 0; s < NM; ++s) {
+                M[r * 2 * NM + s] = (float)Lam[a * blk + r * NM + s];
+                M[r * 2 * NM + NM + s] = (float)Bab[q * blk + r * NM + s];
+                M[(NM + r) * 2 * NM + s] = (float)Bba[q * blk + r * NM + s];
+                M[(NM + r) * 2 * NM + NM + s] = (float)Lam[b * blk + r * NM + s];
+            }
+    }
+    for (size_t i = 0; i < S.size(); ++i) S[i] = (float)Lam[i];
+    bool ok = dmalloc(&c->d_ZS, ZS.size()) == cudaSuccess && dmalloc(&c->d_ZA, ZA.size()) == cudaSuccess &&
+              dmalloc(&c->d_modes, modes.size()) == cudaSuccess && dmalloc(&c->d_near_pair, near_pair.size()) == cudaSuccess &&
+              dmalloc(&c->d_pinv, A.size()) == cudaSuccess && dmalloc(&c->d_sinv, S.size()) == cudaSuccess &&
+              dmalloc(&c->d_low, (size_t)n * NM) == cudaSuccess && dmalloc(&c->d_lowe, (size_t)n * NM) == cudaSuccess;
+    if (!ok) return fail(c, SBIE_ERR_OOM, "preconditioner buffers");
+    int* d_bad = nullptr;
+    CK(cudaMalloc(&d_bad, sizeof(int)));
+    CK(cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
+    CK(h2d(c->stream, c->d_ZS, ZS.data(), ZS.size()));
+    CK(h2d(c->stream, c->d_ZA, ZA.data(), ZA.size()));
+    CK(h2d(c->stream, c->d_modes, modes.data(), modes.size()));
+    CK(h2d(c->stream, c->d_near_pair, near_pair.data(), near_pair.size()));
+    CK(h2d(c->stream, c->d_pinv, A.data(), A.size()));
+    CK(h2d(c->stream, c->d_sinv, S.data(), S.size()));
+    CK(launch_gauss_jordan(c->stream, 2 * NM, np, c->d_pinv, d_bad));
+    CK(launch_gauss_jordan(c->stream, NM, n, c->d_sinv, d_bad));
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(d_bad);
+    if (bad) return fail(c, SBIE_ERR_NUMERIC, "singular pair system in the preconditioner");
+    c->n_pairs = np;
+    c->prec_kind = kind;
+    c->t_prec_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return SBIE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -715,6 +1117,8 @@ sbie_status sphere_bie_create_batch(int n_problems, const int* n_spheres, const 
     for (int q = 0; q < n_problems; ++q) {
         if (n_spheres[q] < 1) return fail(nullptr, SBIE_ERR_ARG, "every problem needs n >= 1 spheres");
         if (p_per_problem[q] < 1 || p_per_problem[q] > kMaxP) return fail(nullptr, SBIE_ERR_ARG, "p must be in [1, 24]");
+        if (opts->use_learned_precond > 0 && p_per_problem[q] < kPrecL)
+            return fail(nullptr, SBIE_ERR_ARG, "the pair preconditioner needs p >= 4");
         ntot += n_spheres[q];
     }
     if (ntot > (1LL << 30)) return fail(nullptr, SBIE_ERR_ARG, "too many spheres");
@@ -749,6 +1153,13 @@ sbie_status sphere_bie_create_batch(int n_problems, const int* n_spheres, const 
         o.p = orders[0];
         sbie_ctx* c = nullptr;
         CKS(create_part(o, (int)ntot, centres, radii, prob_sph, nullptr, &c));
+        sbie_status ps = setup_preconditioner({c}, *opts);
+        if (ps != SBIE_OK) {
+            g_last_error = c->err;
+            free_all(c);
+            delete c;
+            return ps;
+        }
         *out = c;
         return SBIE_OK;
     }
@@ -819,10 +1230,19 @@ sbie_status sphere_bie_create_batch(int n_problems, const int* n_spheres, const 
     ok &= dmalloc(&top->d_node_prob, (size_t)N) == cudaSuccess;
     ok &= dmalloc(&top->d_seg3, top->seg3.size()) == cudaSuccess;
     if (!ok) return bail(SBIE_ERR_OOM, "device allocation failed");
-    e = cudaMemcpy(top->d_node_prob, node_prob.data(), sizeof(int) * N, cudaMemcpyHostToDevice);
+    e = h2d(top->stream, top->d_node_prob, node_prob.data(), (size_t)N);
     if (e == cudaSuccess)
-        e = cudaMemcpy(top->d_seg3, top->seg3.data(), sizeof(long long) * top->seg3.size(), cudaMemcpyHostToDevice);
+        e = h2d(top->stream, top->d_seg3, top->seg3.data(), top->seg3.size());
     if (e != cudaSuccess) return bail(SBIE_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
+    {
+        sbie_status ps = setup_preconditioner(top->parts, *opts);
+        if (ps != SBIE_OK) {
+            std::string m = g_last_error;
+            for (sbie_ctx* q : top->parts)
+                if (q->err != "no error") m = q->err;
+            return bail(ps, m);
+        }
+    }
     top->err = "no error";
     *out = top;
     return SBIE_OK;
@@ -843,8 +1263,8 @@ sbie_status sphere_bie_nodes(const sbie_ctx* cc, double* xyz, double* normals, d
         sbie_ctx* q = S.parts[s];
         x4.resize(4 * (size_t)q->N);
         n4.resize(4 * (size_t)q->N);
-        CK(cudaMemcpy(x4.data(), q->d_x, sizeof(double) * x4.size(), cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(n4.data(), q->d_nrm64, sizeof(double) * n4.size(), cudaMemcpyDeviceToHost));
+        CK(d2h(q->stream, x4.data(), q->d_x, x4.size()));
+        CK(d2h(q->stream, n4.data(), q->d_nrm64, n4.size()));
         const long long o = S.off3[s] / 3;
         for (long long i = 0; i < q->N; ++i) {
             for (int d = 0; d < 3; ++d) {
@@ -1135,6 +1555,140 @@ sbie_status sphere_bie_profile_read(sbie_ctx* c, sbie_profile* out) {
         out->far_pairs_f32 += q->prof.pairs_f32;
         out->far_pairs_f64 += q->prof.pairs_f64;
         out->kernel_launches += q->n_launch - q->prof.kernels0;
+    }
+    return SBIE_OK;
+}
+
+sbie_status sphere_bie_pair_network_size(long long* n_params) {
+    if (!n_params) return SBIE_ERR_ARG;
+    *n_params = mlp_layout().total;
+    return SBIE_OK;
+}
+
+sbie_status sphere_bie_pair_blocks(int n, const double* dist, const double* a_src, const double* a_tgt, int p,
+                                   double* blocks) {
+    if (n < 1 || !dist || !a_src || !a_tgt || !blocks || p < kPrecL || p > kMaxP)
+        return fail(nullptr, SBIE_ERR_ARG, "pair_blocks: bad arguments");
+    for (int q = 0; q < n; ++q)
+        if (!(dist[q] > a_src[q] + a_tgt[q]) || !(a_src[q] > 0) || !(a_tgt[q] > 0))
+            return fail(nullptr, SBIE_ERR_ARG, "pair_blocks: spheres must be disjoint with positive radii");
+    std::vector<double> out;
+    CKS(aligned_blocks(n, dist, a_src, a_tgt, p, 1e9, out));
+    std::memcpy(blocks, out.data(), sizeof(double) * out.size());
+    return SBIE_OK;
+}
+
+sbie_status sphere_bie_pair_network_gradients(const float* params, int n, const float* X, const float* Y,
+                                              float* grads, double* loss) {
+    if (!params || !X || !Y || !grads || !loss || n < 1) return fail(nullptr, SBIE_ERR_ARG, "bad arguments");
+    cudaError_t e = mlp_gradients(params, n, X, Y, grads, loss);
+    if (e != cudaSuccess) return fail(nullptr, SBIE_ERR_CUDA, std::string("network gradients: ") + cudaGetErrorString(e));
+    return SBIE_OK;
+}
+
+sbie_status sphere_bie_train_pair_network(const sbie_pair_train_opts* o, const char* path, sbie_pair_train_info* info) {
+    if (!o || !path || o->n_samples < 16 || o->p < kPrecL || o->p > kMaxP || !(o->gap_min > 0) ||
+        !(o->gap_max >= o->gap_min) || !(o->radius > 0) || o->epochs < 1 || o->batch < 1 || !(o->val_frac >= 0) ||
+        !(o->val_frac < 0.9))
+        return fail(nullptr, SBIE_ERR_ARG, "train_pair_network: bad options");
+    auto t0 = std::chrono::steady_clock::now();
+    const int n = o->n_samples;
+    std::mt19937_64 rng(o->seed);
+    std::uniform_real_distribution<double> U(std::log(o->gap_min), std::log(o->gap_max));
+    std::vector<double> d(n), as(n, o->radius), at(n, o->radius);
+    for (int q = 0; q < n; ++q) d[q] = 2.0 * o->radius + std::exp(U(rng));
+    std::vector<double> blocks((size_t)n * kMlpOut);
+    const int chunk = 4096;
+    for (int q0 = 0; q0 < n; q0 += chunk) {
+        const int m = std::min(chunk, n - q0);
+        std::vector<double> out;
+        CKS(aligned_blocks(m, d.data() + q0, as.data() + q0, at.data() + q0, o->p, 1e9, out));
+        std::memcpy(blocks.data() + (size_t)q0 * kMlpOut, out.data(), sizeof(double) * out.size());
+    }
+    auto t1 = std::chrono::steady_clock::now();
+    PairNet net;
+    net.p_train = o->p;
+    std::vector<float> X((size_t)n * kMlpIn, 0.f);
+    for (int q = 0; q < n; ++q) {
+        X[q * kMlpIn + 2] = (float)d[q];
+        X[q * kMlpIn + 3] = (float)as[q];
+        X[q * kMlpIn + 4] = (float)at[q];
+    }
+    for (int j = 0; j < kMlpIn; ++j) {
+        double s = 0, s2 = 0;
+        for (int q = 0; q < n; ++q) {
+            s += X[q * kMlpIn + j];
+            s2 += (double)X[q * kMlpIn + j] * X[q * kMlpIn + j];
+        }
+        const double mu = s / n, var = std::max(0.0, s2 / n - mu * mu);
+        net.in_mean[j] = (float)mu;
+        net.in_std[j] = var > 1e-20 ? (float)std::sqrt(var) : 1.f;
+    }
+    net.out_mean.assign(kMlpOut, 0.f);
+    net.out_std.assign(kMlpOut, 1.f);
+    double smax = 0.0;
+    std::vector<double> sd(kMlpOut);
+    for (int k = 0; k < kMlpOut; ++k) {
+        double s = 0, s2 = 0;
+        for (int q = 0; q < n; ++q) {
+            const double v = blocks[(size_t)q * kMlpOut + k];
+            s += v;
+            s2 += v * v;
+        }
+        const double mu = s / n;
+        sd[k] = std::sqrt(std::max(0.0, s2 / n - mu * mu));
+        net.out_mean[k] = (float)mu;
+        smax = std::max(smax, sd[k]);
+    }
+    // Entries that do not vary over the samples (most of the block: in the
+    // pair frame only modes of equal order m couple) get std 0, so that the
+    // prediction is their mean exactly and the network's error there is not
+    // added to the block; their standardised target is 0.
+    for (int k = 0; k < kMlpOut; ++k) net.out_std[k] = sd[k] > 1e-6 * smax ? (float)sd[k] : 0.f;
+    std::vector<float> Xs(X.size()), Ys((size_t)n * kMlpOut);
+    for (int q = 0; q < n; ++q) {
+        for (int j = 0; j < kMlpIn; ++j) Xs[q * kMlpIn + j] = (X[q * kMlpIn + j] - net.in_mean[j]) / net.in_std[j];
+        for (int k = 0; k < kMlpOut; ++k)
+            Ys[(size_t)q * kMlpOut + k] =
+                net.out_std[k] > 0.f
+                    ? (float)((blocks[(size_t)q * kMlpOut + k] - net.out_mean[k]) / net.out_std[k])
+                    : 0.f;
+    }
+    const int nval = (int)(o->val_frac * n), ntr = n - nval;
+    mlp_init(o->seed + 1, net.params);
+    MlpTrainOpts to;
+    to.epochs = o->epochs;
+    to.batch = o->batch;
+    to.lr = o->lr;
+    to.seed = o->seed + 2;
+    std::vector<double> hist;
+    cudaError_t e = mlp_train(to, ntr, Xs.data(), Ys.data(), net.params.data(), hist);
+    if (e != cudaSuccess) return fail(nullptr, SBIE_ERR_CUDA, std::string("training: ") + cudaGetErrorString(e));
+    auto t2 = std::chrono::steady_clock::now();
+    double val = 0.0;
+    if (nval > 0) {
+        std::vector<float> Xv(X.begin() + (size_t)ntr * kMlpIn, X.end());
+        std::vector<double> P;
+        CKS(net_blocks(net, Xv, P));
+        for (int q = 0; q < nval; ++q) {
+            double num = 0, den = 0;
+            for (int k = 0; k < kMlpOut; ++k) {
+                const double t = blocks[(size_t)(ntr + q) * kMlpOut + k], y = P[(size_t)q * kMlpOut + k];
+                num += (y - t) * (y - t);
+                den += t * t;
+            }
+            val += std::sqrt(num / den);
+        }
+        val /= nval;
+    }
+    CKS(net_save(path, net));
+    if (info) {
+        info->train_loss = hist.empty() ? 0.0 : hist.back();
+        info->val_rel_err = val;
+        info->t_data_s = std::chrono::duration<double>(t1 - t0).count();
+        info->t_train_s = std::chrono::duration<double>(t2 - t1).count();
+        info->n_train = ntr;
+        info->n_val = nval;
     }
     return SBIE_OK;
 }

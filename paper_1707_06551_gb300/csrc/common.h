@@ -105,6 +105,20 @@ struct sbie_ctx {
     double* d_pvec = nullptr;           // [n_prob_total] per-problem scalars
     size_t red_cap = 0, hred_cap = 0;
 
+    // pair preconditioner (precond.cu): 0 none, 1 learned pair network, 2 exact blocks
+    int prec_kind = 0;
+    double* d_ZS = nullptr;        // [npn][3][73] low-mode synthesis
+    double* d_ZA = nullptr;        // [73][npn][3] low-mode analysis
+    int4* d_modes = nullptr;       // [73] (type, n, m, part)
+    int* d_near_pair = nullptr;    // [n_near] undirected pair of each directed close pair
+    int n_pairs = 0;
+    float* d_pinv = nullptr;       // [n_pairs][146][146] inverses of the pair systems
+    float* d_sinv = nullptr;       // [n][73][73] inverses of the spheres' own low-mode blocks
+    double* d_low = nullptr;       // [n][73]
+    double* d_lowe = nullptr;      // [n][73]
+    double* d_pz = nullptr;        // preconditioned vector (system level)
+    double t_prec_setup_ms = 0.0;
+
     // host geometry
     std::vector<double> h_c, h_a;
     std::vector<int> h_near_ptr, h_near_idx;
@@ -186,6 +200,15 @@ void set_last_error(const std::string& msg);
 // self.cu
 cudaError_t launch_self(sbie_ctx* c, Kern op, const double* dens, double* out, bool accumulate, bool write_coef);
 cudaError_t launch_analysis_only(sbie_ctx* c, const double* dens);
+cudaError_t launch_self_precond(sbie_ctx* c, const double* v, double* out);
+// precond.cu
+void lowmode_tables(int p, std::vector<double>& ZS, std::vector<double>& ZA);
+void lowmode_rotation(const double Q[9], std::vector<double>& R);
+std::vector<int4> low_mode_table();
+cudaError_t launch_gauss_jordan(cudaStream_t s, int n, int count, float* mats, int* d_bad);
+cudaError_t launch_probe_density(sbie_ctx* c, int sph_per_prob, int side, int beta, const double* ZS, double* dens);
+cudaError_t launch_probe_analysis(sbie_ctx* c, const double* ZA, const double* u, int beta, double* blocks);
+cudaError_t precond_apply(sbie_ctx* c, const double* v, double* out);
 // far.cu
 cudaError_t launch_pack(sbie_ctx* c, const double* dens, int mode);
 cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out);

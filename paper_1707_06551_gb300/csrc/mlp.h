@@ -1,0 +1,37 @@
+// Internal declarations of the pair network (mlp.cu) and the learned
+// preconditioner (precond.cu).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <vector>
+
+namespace sbie {
+
+constexpr int kPrecL = 4;                                  // low modes: VSH degree <= 4
+constexpr int kLowModes = 3 * (kPrecL + 1) * (kPrecL + 1) - 2;  // 73 real coefficients per sphere
+constexpr int kMlpIn = 5, kMlpHidden = 128, kMlpOut = kLowModes * kLowModes;
+
+struct MlpLayout {
+    int din[4], dout[4];
+    long long w[4], b[4];  // offsets of the (din x dout) weights and (dout) biases
+    long long total;
+};
+MlpLayout mlp_layout();
+
+struct MlpTrainOpts {
+    int epochs = 40;
+    int batch = 256;
+    double lr = 2e-3;
+    unsigned long long seed = 7;
+};
+
+void mlp_init(unsigned long long seed, std::vector<float>& params);
+cudaError_t mlp_train(const MlpTrainOpts& o, int n, const float* h_X, const float* h_T, float* h_params,
+                      std::vector<double>& history);
+cudaError_t mlp_gradients(const float* h_params, int n, const float* h_X, const float* h_T, float* h_grad,
+                          double* loss);
+cudaError_t mlp_to_bf16(cudaStream_t s, const float* w, __nv_bfloat16* wb);
+cudaError_t mlp_forward_dev(cudaStream_t s, const float* w, const __nv_bfloat16* wb, int n, const float* X, float* Y);
+
+}  // namespace sbie

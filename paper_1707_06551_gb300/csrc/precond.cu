@@ -1,0 +1,415 @@
+// Two-body (pair) preconditioner for GMRES on the resistance operator
+// 1/2 I + D + N (Eq. 5.19).
+//
+//   M^{-1} r = H r + Z C^{-1} Z^+ r
+//
+// Z^+ is the VSH analysis (Sec. 2.1) restricted to degree <= 4 ("low modes",
+// 73 real coefficients per sphere) and Z the matching synthesis.  H inverts
+// each sphere's own operator above degree 4 (the exterior eigenvalues D+ of
+// Theorem 2) and the non-band-limited remainder (1/2 I -> x2), and vanishes on
+// the low modes.  C^{-1} is an additive Schwarz approximation of the low-mode
+// operator over close pairs: for each close pair (i, k) the 146 x 146 system
+// [[L_i, B_ik], [B_ki, L_k]] is inverted once, and sphere i averages the
+// answers of its pairs (an isolated sphere uses L_i^{-1}).  L_i is the
+// sphere's own low-mode block and B_ik the low-mode block of the pair
+// coupling (close-pair expansion + completion flow), either probed exactly
+// (the operator applied to each low mode on a two-sphere problem) or
+// predicted by the pair network in the pair frame and rotated.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.h"
+#include "mlp.h"
+
+namespace sbie {
+
+namespace {
+
+struct Mode {
+    int t, n, m, part;
+};
+
+std::vector<Mode> low_modes() {
+    std::vector<Mode> out;
+    for (int t = 0; t < 3; ++t)
+        for (int n = 0; n <= kPrecL; ++n) {
+            if (t > 0 && n == 0) continue;
+            for (int m = 0; m <= n; ++m) {
+                out.push_back(Mode{t, n, m, 0});
+                if (m >= 1) out.push_back(Mode{t, n, m, 1});
+            }
+        }
+    return out;
+}
+
+// Normalised Pbar_n^m(t) (no Condon-Shortley phase) for n <= nmax at one
+// point, by the normalised three-term recurrence; P[m * (nmax+1) + n].
+void pbar(int nmax, double t, double s, std::vector<double>& P) {
+    P.assign((nmax + 1) * (nmax + 1), 0.0);
+    double pmm = 1.0 / std::sqrt(4.0 * kPi);
+    for (int m = 0; m <= nmax; ++m) {
+        if (m > 0) pmm *= std::sqrt((2.0 * m + 1.0) / (2.0 * m)) * s;
+        P[m * (nmax + 1) + m] = pmm;
+        if (m + 1 <= nmax) P[m * (nmax + 1) + m + 1] = std::sqrt(2.0 * m + 3.0) * t * pmm;
+        for (int n = m + 2; n <= nmax; ++n) {
+            double a = std::sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
+            double b = std::sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
+            P[m * (nmax + 1) + n] = a * (t * P[m * (nmax + 1) + n - 1] - b * P[m * (nmax + 1) + n - 2]);
+        }
+    }
+}
+
+}  // namespace
+
+// Low-mode synthesis ZS [npn][3][73] and analysis ZA [73][npn][3] on the grid
+// of order p, from the Legendre tables (same quadrature as the self kernel).
+void lowmode_tables(int p, std::vector<double>& ZS, std::vector<double>& ZA) {
+    TabLayout tl = tab_layout(p);
+    std::vector<double> tab;
+    build_tables(p, tab);
+    const std::vector<Mode> modes = low_modes();
+    const int NM = (int)modes.size(), npn = tl.npn, P1 = p + 1;
+    ZS.assign((size_t)npn * 3 * NM, 0.0);
+    ZA.assign((size_t)NM * npn * 3, 0.0);
+    for (int j = 0; j < tl.nlat; ++j)
+        for (int k = 0; k < tl.nlon; ++k) {
+            const int q = j * tl.nlon + k;
+            const double ct = tab[tl.o_ct + j], st = tab[tl.o_st + j], cp = tab[tl.o_cph + k], sp = tab[tl.o_sph + k];
+            const double w = tab[tl.o_w + j];
+            const double er[3] = {st * cp, st * sp, ct}, et[3] = {ct * cp, ct * sp, -st}, ep[3] = {-sp, cp, 0.0};
+            for (int b = 0; b < NM; ++b) {
+                const Mode& md = modes[b];
+                const int n = md.n, m = md.m;
+                const int o = (m * P1 + n) * tl.nlat + j;
+                const double P = tab[tl.o_P + o], dP = tab[tl.o_dP + o], mS = tab[tl.o_mS + o];
+                // spherical components (r, theta, phi) of Z / e^{i m phi}: (real, imag) pairs
+                double zr[3][2];
+                if (md.t == 0) {  // V = G - (n+1) Y e_r
+                    zr[0][0] = -(n + 1.0) * P; zr[0][1] = 0.0;
+                    zr[1][0] = dP; zr[1][1] = 0.0;
+                    zr[2][0] = 0.0; zr[2][1] = mS;
+                } else if (md.t == 1) {  // W = G + n Y e_r
+                    zr[0][0] = n * P; zr[0][1] = 0.0;
+                    zr[1][0] = dP; zr[1][1] = 0.0;
+                    zr[2][0] = 0.0; zr[2][1] = mS;
+                } else {  // X = dY e_phi - (i m Y / sin) e_theta
+                    zr[0][0] = 0.0; zr[0][1] = 0.0;
+                    zr[1][0] = 0.0; zr[1][1] = -mS;
+                    zr[2][0] = dP; zr[2][1] = 0.0;
+                }
+                const double cm = tab[tl.o_cmk + m * tl.nlon + k], sm = tab[tl.o_smk + m * tl.nlon + k];
+                double re[3], im[3];  // Cartesian Re Z, Im Z
+                for (int c = 0; c < 3; ++c) {
+                    double sr = 0, si = 0;
+                    for (int a = 0; a < 3; ++a) {
+                        const double ea = a == 0 ? er[c] : (a == 1 ? et[c] : ep[c]);
+                        // (zr + i zi) (cm + i sm)
+                        sr += ea * (zr[a][0] * cm - zr[a][1] * sm);
+                        si += ea * (zr[a][0] * sm + zr[a][1] * cm);
+                    }
+                    re[c] = sr;
+                    im[c] = si;
+                }
+                double norm2 = md.t == 0 ? (n + 1.0) * (2.0 * n + 1.0) : (md.t == 1 ? n * (2.0 * n + 1.0) : n * (n + 1.0));
+                for (int c = 0; c < 3; ++c) {
+                    double syn, ana;
+                    if (md.part == 0) {
+                        syn = (m == 0 ? 1.0 : 2.0) * re[c];
+                        ana = w * re[c] / norm2;
+                    } else {
+                        syn = -2.0 * im[c];
+                        ana = -w * im[c] / norm2;
+                    }
+                    ZS[((size_t)q * 3 + c) * NM + b] = syn;
+                    ZA[((size_t)b * npn + q) * 3 + c] = ana;
+                }
+            }
+        }
+}
+
+// Real low-mode rotation R (73 x 73): coefficients of the field in the frame
+// whose axes are the columns of Q, a' = R a.  Block diagonal in (type, n) with
+// the scalar rotation of degree n, computed by resampling Y o Q on the grid of
+// order 4 (exact: Y o Q has degree n).
+void lowmode_rotation(const double Q[9], std::vector<double>& R) {
+    const int L = kPrecL, NM = kLowModes;
+    const int p = L;
+    TabLayout tl = tab_layout(p);
+    std::vector<double> tab;
+    build_tables(p, tab);
+    // scalar real basis values psi_(n, m, part)(y) at rotated nodes Q y'_j and
+    // at the nodes y'_j; coefficient index within degree n: m = 0 -> 0,
+    // m >= 1 -> 2m - 1 (re), 2m (im)
+    R.assign((size_t)NM * NM, 0.0);
+    std::vector<double> D[kPrecL + 1];
+    for (int n = 0; n <= L; ++n) D[n].assign((size_t)(2 * n + 1) * (2 * n + 1), 0.0);
+    std::vector<double> P;
+    for (int j = 0; j < tl.nlat; ++j)
+        for (int k = 0; k < tl.nlon; ++k) {
+            const double ct = tab[tl.o_ct + j], st = tab[tl.o_st + j], cp = tab[tl.o_cph + k], sp = tab[tl.o_sph + k];
+            const double w = tab[tl.o_w + j];
+            const double y[3] = {st * cp, st * sp, ct};
+            double x[3];
+            for (int a = 0; a < 3; ++a) x[a] = Q[3 * a + 0] * y[0] + Q[3 * a + 1] * y[1] + Q[3 * a + 2] * y[2];
+            const double rho = std::sqrt(x[0] * x[0] + x[1] * x[1]);
+            const double cpx = rho > 0 ? x[0] / rho : 1.0, spx = rho > 0 ? x[1] / rho : 0.0;
+            std::vector<double> Pn;
+            pbar(L, x[2], rho, P);
+            pbar(L, ct, st, Pn);
+            for (int n = 0; n <= L; ++n) {
+                const int d = 2 * n + 1;
+                // values of the real basis at x (rotated) and conjugate-projection weights at y
+                std::vector<double> vx(d), ry(d), iy(d);
+                for (int m = 0; m <= n; ++m) {
+                    const double cmx = std::cos(m * std::atan2(spx, cpx)), smx = std::sin(m * std::atan2(spx, cpx));
+                    const double Px = P[m * (L + 1) + n];
+                    const double cmy = std::cos(m * std::atan2(sp, cp)), smy = std::sin(m * std::atan2(sp, cp));
+                    const double Py = Pn[m * (L + 1) + n];
+                    if (m == 0) {
+                        vx[0] = Px;
+                        ry[0] = Py;
+                        iy[0] = 0.0;
+                    } else {
+                        vx[2 * m - 1] = 2.0 * Px * cmx;   // 2 Re Y
+                        vx[2 * m] = -2.0 * Px * smx;      // -2 Im Y
+                        ry[2 * m - 1] = Py * cmy;         // Re Y(y)
+                        iy[2 * m - 1] = Py * smy;         // Im Y(y)
+                    }
+                }
+                // coefficient of psi_nu: Re c_nm = sum w f Re Y, Im c_nm = -sum w f Im Y
+                for (int mu = 0; mu < d; ++mu) {
+                    const double f = vx[mu];
+                    for (int m = 0; m <= n; ++m) {
+                        if (m == 0) {
+                            D[n][0 * d + mu] += w * f * ry[0];
+                        } else {
+                            D[n][(2 * m - 1) * d + mu] += w * f * ry[2 * m - 1];
+                            D[n][(2 * m) * d + mu] += -w * f * iy[2 * m - 1];
+                        }
+                    }
+                }
+            }
+        }
+    // scatter into R: same D_n for V, W, X
+    const std::vector<Mode> modes = low_modes();
+    auto sub = [](const Mode& md) { return md.m == 0 ? 0 : (md.part == 0 ? 2 * md.m - 1 : 2 * md.m); };
+    for (int a = 0; a < NM; ++a)
+        for (int b = 0; b < NM; ++b) {
+            const Mode &ma = modes[a], &mb = modes[b];
+            if (ma.t != mb.t || ma.n != mb.n) continue;
+            const int d = 2 * ma.n + 1;
+            R[(size_t)a * NM + b] = D[ma.n][sub(ma) * d + sub(mb)];
+        }
+}
+
+namespace {
+
+// ---- device kernels --------------------------------------------------------
+
+// density of problem q: low mode `beta` on local sphere `side` (0 or 1), zero elsewhere
+__global__ void probe_density_kernel(int npn, int sph_per_prob, int side, int beta, const double* __restrict__ ZS,
+                                     long long N, double* __restrict__ dens) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const long long sphere = i / npn;
+    const int q = (int)(i - sphere * npn);
+    const bool on = (int)(sphere % sph_per_prob) == side;
+    for (int c = 0; c < 3; ++c) dens[3 * i + c] = on ? ZS[((size_t)q * 3 + c) * kLowModes + beta] : 0.0;
+}
+
+// column beta of the low-mode blocks: out[sphere][row][beta] = (ZA . u_sphere)[row]
+__global__ void probe_analysis_kernel(int npn, const double* __restrict__ ZA, const double* __restrict__ u, int beta,
+                                      double* __restrict__ blocks) {
+    const long long sphere = blockIdx.x;
+    const int row = threadIdx.x;
+    if (row >= kLowModes) return;
+    const double* us = u + (size_t)sphere * npn * 3;
+    const double* za = ZA + (size_t)row * npn * 3;
+    double s = 0.0;
+    for (int e = 0; e < npn * 3; ++e) s = fma(za[e], us[e], s);
+    blocks[((size_t)sphere * kLowModes + row) * kLowModes + beta] = s;
+}
+
+// In-place inverse of `count` n x n matrices (FP32, row-major, contiguous) by
+// Gauss-Jordan elimination with partial pivoting in shared memory.  A pivot
+// below 1e-30 sets *bad (the matrix is left unchanged in that case).
+__global__ void __launch_bounds__(256) gauss_jordan_kernel(int n, float* __restrict__ mats, int* __restrict__ bad) {
+    extern __shared__ float sm[];
+    const int W = 2 * n;
+    float* A = sm;          // [n][2n]
+    float* f = sm + n * W;  // [n] elimination multipliers of the current column
+    __shared__ int piv;
+    __shared__ float pval;
+    float* M = mats + (size_t)blockIdx.x * n * n;
+    for (int e = threadIdx.x; e < n * W; e += blockDim.x) {
+        int r = e / W, c = e - r * W;
+        A[e] = c < n ? M[r * n + c] : (c - n == r ? 1.f : 0.f);
+    }
+    __syncthreads();
+    bool ok = true;
+    for (int col = 0; col < n; ++col) {
+        if (threadIdx.x < 32) {
+            float best = -1.f;
+            int bi = col;
+            for (int r = col + threadIdx.x; r < n; r += 32) {
+                float v = fabsf(A[r * W + col]);
+                if (v > best) { best = v; bi = r; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                float ob = __shfl_down_sync(0xffffffffu, best, o);
+                int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ob > best) { best = ob; bi = oi; }
+            }
+            if (threadIdx.x == 0) {
+                piv = bi;
+                pval = A[bi * W + col];
+            }
+        }
+        __syncthreads();
+        if (fabsf(pval) < 1e-30f) {
+            ok = false;
+            break;
+        }
+        const int pr = piv;
+        if (pr != col)
+            for (int c = threadIdx.x; c < W; c += blockDim.x) {
+                float t = A[col * W + c];
+                A[col * W + c] = A[pr * W + c];
+                A[pr * W + c] = t;
+            }
+        __syncthreads();
+        const float inv = 1.f / A[col * W + col];
+        __syncthreads();
+        for (int c = threadIdx.x; c < W; c += blockDim.x) A[col * W + c] *= inv;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) f[r] = (r == col) ? 0.f : A[r * W + col];
+        __syncthreads();
+        for (int e = threadIdx.x; e < n * W; e += blockDim.x) {
+            int r = e / W, c = e - r * W;
+            A[e] -= f[r] * A[col * W + c];
+        }
+        __syncthreads();
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) atomicExch(bad, 1);
+        return;
+    }
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int r = e / n, c = e - r * n;
+        M[e] = A[r * W + n + c];
+    }
+}
+
+// low-mode real coefficients of every sphere from the VSH coefficients
+__global__ void gather_low_kernel(int n_sph, int P1, const double* __restrict__ coef, const int4* __restrict__ modes,
+                                  double* __restrict__ low) {
+    const int s = blockIdx.x;
+    const int b = threadIdx.x;
+    if (s >= n_sph || b >= kLowModes) return;
+    const int4 md = modes[b];  // t, n, m, part
+    const double* cg = coef + (size_t)s * 3 * P1 * P1 * 2;
+    const int o = md.y * P1 + md.z;  // coefficient layout [type][n][m] (re, im)
+    low[(size_t)s * kLowModes + b] = cg[2 * (md.x * P1 * P1 + o) + md.w];
+}
+
+// coarse correction e_i (see the header comment)
+__global__ void coarse_kernel(const int* __restrict__ near_ptr, const int* __restrict__ near_idx,
+                              const int* __restrict__ near_pair, const float* __restrict__ pinv,
+                              const float* __restrict__ sinv, const double* __restrict__ low, double* __restrict__ e) {
+    const int i = blockIdx.x;
+    const int r = threadIdx.x;
+    __shared__ double c2[2 * kLowModes];
+    const int e0 = near_ptr[i], e1 = near_ptr[i + 1];
+    const int deg = e1 - e0;
+    double acc = 0.0;
+    if (deg == 0) {
+        __syncthreads();
+        if (r < kLowModes) {
+            const float* Mi = sinv + (size_t)i * kLowModes * kLowModes + (size_t)r * kLowModes;
+            const double* ci = low + (size_t)i * kLowModes;
+            for (int c = 0; c < kLowModes; ++c) acc += (double)Mi[c] * ci[c];
+        }
+    }
+    for (int ee = e0; ee < e1; ++ee) {
+        const int k = near_idx[ee];
+        const int a = min(i, k), b = max(i, k);
+        __syncthreads();
+        for (int t = threadIdx.x; t < 2 * kLowModes; t += blockDim.x)
+            c2[t] = t < kLowModes ? low[(size_t)a * kLowModes + t] : low[(size_t)b * kLowModes + t - kLowModes];
+        __syncthreads();
+        if (r < kLowModes) {
+            const int row = (i == a ? 0 : kLowModes) + r;
+            const float* Mr = pinv + (size_t)near_pair[ee] * 4 * kLowModes * kLowModes + (size_t)row * 2 * kLowModes;
+            double s = 0.0;
+            for (int c = 0; c < 2 * kLowModes; ++c) s += (double)Mr[c] * c2[c];
+            acc += s / deg;
+        }
+    }
+    if (r < kLowModes) e[(size_t)i * kLowModes + r] = acc;
+}
+
+// out_sphere += ZS . e_sphere
+__global__ void synth_add_kernel(int npn, long long N, const double* __restrict__ ZS, const double* __restrict__ e,
+                                 double* __restrict__ out) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const long long s = i / npn;
+    const int q = (int)(i - s * npn);
+    const double* es = e + (size_t)s * kLowModes;
+    for (int c = 0; c < 3; ++c) {
+        const double* z = ZS + ((size_t)q * 3 + c) * kLowModes;
+        double v = 0.0;
+        for (int b = 0; b < kLowModes; ++b) v = fma(z[b], es[b], v);
+        out[3 * i + c] += v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_gauss_jordan(cudaStream_t s, int n, int count, float* mats, int* d_bad) {
+    if (count == 0) return cudaSuccess;
+    size_t sm = sizeof(float) * ((size_t)n * 2 * n + n);
+    cudaError_t e = cudaFuncSetAttribute(gauss_jordan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    gauss_jordan_kernel<<<count, 256, sm, s>>>(n, mats, d_bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe_density(sbie_ctx* c, int sph_per_prob, int side, int beta, const double* ZS, double* dens) {
+    probe_density_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->npn, sph_per_prob, side, beta, ZS,
+                                                                                 c->N, dens);
+    ++c->n_launch;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe_analysis(sbie_ctx* c, const double* ZA, const double* u, int beta, double* blocks) {
+    probe_analysis_kernel<<<c->n, 96, 0, c->stream>>>(c->npn, ZA, u, beta, blocks);
+    ++c->n_launch;
+    return cudaGetLastError();
+}
+
+std::vector<int4> low_mode_table() {
+    std::vector<int4> out;
+    for (const Mode& m : low_modes()) out.push_back(make_int4(m.t, m.n, m.m, m.part));
+    return out;
+}
+
+// M^{-1} v on one part (device vectors of that part): see the header comment.
+cudaError_t precond_apply(sbie_ctx* c, const double* v, double* out) {
+    const long long n3 = c->N * 3;
+    // H v: synthesis of (1/D+ above degree 4, 0 below) minus 2, plus 2 v; the
+    // self kernel also leaves the VSH coefficients of v in d_coef
+    cudaError_t e = launch_self_precond(c, v, out);
+    if (e == cudaSuccess) e = blas_lincomb(c, 2.0, v, 1.0, out, out, n3);
+    if (e != cudaSuccess) return e;
+    gather_low_kernel<<<c->n, 96, 0, c->stream>>>(c->n, c->p + 1, c->d_coef, c->d_modes, c->d_low);
+    ++c->n_launch;
+    coarse_kernel<<<c->n, 96, 0, c->stream>>>(c->d_near_ptr, c->d_near_idx, c->d_near_pair, c->d_pinv, c->d_sinv,
+                                              c->d_low, c->d_lowe);
+    ++c->n_launch;
+    synth_add_kernel<<<(unsigned)((c->N + 127) / 128), 128, 0, c->stream>>>(c->npn, c->N, c->d_ZS, c->d_lowe, out);
+    ++c->n_launch;
+    return cudaGetLastError();
+}
+
+}  // namespace sbie

@@ -23,8 +23,25 @@ struct SelfArgs {
     int accumulate;
 };
 
+// op 3: the high-mode part of the pair preconditioner: 1/D+ above degree 4
+// (the exterior eigenvalues of Theorem 2), 0 at or below, minus 2.
+constexpr int kOpPrecHigh = 3;
+
 __device__ __forceinline__ void signature(int op, int n, double a, double& lv, double& lw, double& lx) {
     double tn1 = 2.0 * n + 1.0;
+    if (op == kOpPrecHigh) {
+        if (n > 4) {
+            lv = (tn1 * (2.0 * n + 3.0)) / (2.0 * n * n + 4.0 * n + 3.0);
+            lw = (tn1 * (2.0 * n - 1.0)) / (2.0 * (n - 1.0) * (n + 1.0));
+            lx = tn1 / (n - 1.0);
+        } else {
+            lv = lw = lx = 0.0;
+        }
+        lv -= 2.0;
+        lw -= 2.0;
+        lx -= 2.0;
+        return;
+    }
     if (op == (int)Kern::S) {
         lv = n / (tn1 * (2.0 * n + 3.0));
         lw = (n + 1.0) / (tn1 * (2.0 * n - 1.0));
@@ -228,6 +245,10 @@ static cudaError_t run_self(sbie_ctx* c, int op, const double* dens, double* out
 
 cudaError_t launch_self(sbie_ctx* c, Kern op, const double* dens, double* out, bool accumulate, bool write_coef) {
     return run_self(c, (int)op, dens, out, accumulate, write_coef);
+}
+
+cudaError_t launch_self_precond(sbie_ctx* c, const double* v, double* out) {
+    return run_self(c, kOpPrecHigh, v, out, false, true);
 }
 
 cudaError_t launch_analysis_only(sbie_ctx* c, const double* dens) {

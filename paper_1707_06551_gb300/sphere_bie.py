@@ -50,6 +50,18 @@ class FarTuning(ctypes.Structure):
                 ("tile", ctypes.c_int), ("ms", ctypes.c_double), ("candidates", ctypes.c_int)]
 
 
+class PairTrainOpts(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_int), ("p", ctypes.c_int), ("gap_min", ctypes.c_double),
+                ("gap_max", ctypes.c_double), ("radius", ctypes.c_double), ("epochs", ctypes.c_int),
+                ("batch", ctypes.c_int), ("lr", ctypes.c_double), ("seed", ctypes.c_ulonglong),
+                ("val_frac", ctypes.c_double)]
+
+
+class PairTrainInfo(ctypes.Structure):
+    _fields_ = [("train_loss", ctypes.c_double), ("val_rel_err", ctypes.c_double), ("t_data_s", ctypes.c_double),
+                ("t_train_s", ctypes.c_double), ("n_train", ctypes.c_int), ("n_val", ctypes.c_int)]
+
+
 class SphereBIEError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -80,13 +92,19 @@ def lib():
         L.sphere_bie_last_error.restype = ctypes.c_char_p
         L.sphere_bie_profile.argtypes = [_P, ctypes.c_int]
         L.sphere_bie_profile_read.argtypes = [_P, ctypes.POINTER(Profile)]
+        L.sphere_bie_train_pair_network.argtypes = [ctypes.POINTER(PairTrainOpts), ctypes.c_char_p,
+                                                    ctypes.POINTER(PairTrainInfo)]
+        L.sphere_bie_pair_blocks.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]
+        L.sphere_bie_pair_network_size.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+        L.sphere_bie_pair_network_gradients.argtypes = [_P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]
         L.sphere_bie_autotune.argtypes = [_P, ctypes.c_int, ctypes.POINTER(FarTuning)]
         L.sphere_bie_apply_layer_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]
         for f in ("sphere_bie_default_opts", "sphere_bie_create", "sphere_bie_create_batch", "sphere_bie_num_nodes",
                   "sphere_bie_nodes",
                   "sphere_bie_apply_operator", "sphere_bie_solve_mobility", "sphere_bie_solve_resistance",
                   "sphere_bie_destroy", "sphere_bie_profile", "sphere_bie_profile_read",
-                  "sphere_bie_apply_layer_noalloc", "sphere_bie_autotune"):
+                  "sphere_bie_apply_layer_noalloc", "sphere_bie_autotune", "sphere_bie_train_pair_network",
+                  "sphere_bie_pair_blocks", "sphere_bie_pair_network_size", "sphere_bie_pair_network_gradients"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -215,6 +233,40 @@ def sphere_bie_autotune(ctx, op):
     return {name: {k: getattr(t[i], k) for k, _ in FarTuning._fields_} for i, name in enumerate(("fp32", "df"))}
 
 
+def sphere_bie_train_pair_network(path, n_samples=4096, p=10, gap_min=0.01, gap_max=0.5, radius=1.0, epochs=200,
+                                  batch=256, lr=2e-3, seed=7, val_frac=0.1):
+    o = PairTrainOpts(n_samples, p, gap_min, gap_max, radius, epochs, batch, lr, seed, val_frac)
+    info = PairTrainInfo()
+    _check(None, lib().sphere_bie_train_pair_network(ctypes.byref(o), str(path).encode(), ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def sphere_bie_pair_blocks(dist, a_src, a_tgt, p):
+    d = np.ascontiguousarray(dist, dtype=np.float64).reshape(-1)
+    s = np.ascontiguousarray(np.broadcast_to(a_src, d.shape), dtype=np.float64)
+    t = np.ascontiguousarray(np.broadcast_to(a_tgt, d.shape), dtype=np.float64)
+    out = np.zeros((len(d), 73, 73))
+    _check(None, lib().sphere_bie_pair_blocks(len(d), _ptr(d), _ptr(s), _ptr(t), int(p), _ptr(out)))
+    return out
+
+
+def sphere_bie_pair_network_size():
+    n = ctypes.c_longlong()
+    _check(None, lib().sphere_bie_pair_network_size(ctypes.byref(n)))
+    return n.value
+
+
+def sphere_bie_pair_network_gradients(params, X, Y):
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Y = np.ascontiguousarray(Y, dtype=np.float32)
+    g = np.zeros_like(params)
+    loss = ctypes.c_double()
+    fp = lambda a: ctypes.c_void_p(a.ctypes.data)
+    _check(None, lib().sphere_bie_pair_network_gradients(fp(params), len(X), fp(X), fp(Y), fp(g), ctypes.byref(loss)))
+    return loss.value, g
+
+
 def sphere_bie_profile(ctx, enable):
     _check(ctx, lib().sphere_bie_profile(ctx, int(enable)))
 
@@ -232,8 +284,11 @@ class SphereBIE:
     `batch=[(centres, radii, p), ...]` it holds a batch of problems."""
 
     def __init__(self, centres=None, radii=None, p=None, eta=1.0, prec=SBIE_FP64, tol=1e-8, restart=60, max_iter=600,
-                 batch=None):
+                 batch=None, precond=0, weights=None):
         self.opts = make_opts(p if p is not None else batch[0][2], eta, prec, tol, restart, max_iter, 0)
+        self.opts.use_learned_precond = precond
+        self._wpath = None if weights is None else str(weights).encode()
+        self.opts.mlp_weights_path = self._wpath
         if batch is None:
             self.ctx = sphere_bie_create(centres, radii, self.opts)
             self.n = len(np.asarray(radii).reshape(-1))

@@ -1,0 +1,99 @@
+"""Learned pair preconditioner: exact pair-frame blocks against the oracle,
+network gradients against the reference back-propagation, and preconditioned
+solves (exact blocks and trained network) that return the unpreconditioned
+answer in fewer GMRES iterations."""
+import numpy as np
+import pytest
+
+from oracle import pairblock as opb
+from paper_1707_06551_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sb():
+    from paper_1707_06551_gb300 import build_lib
+    build_lib.build()
+    from paper_1707_06551_gb300 import sphere_bie
+    return sphere_bie
+
+
+def _bf16(x):
+    b = np.asarray(x, np.float32).view(np.uint32)
+    # round to nearest even on the upper 16 bits
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+@pytest.mark.parametrize("d,a_s,a_t", [(2.1, 1.0, 1.0), (2.6, 1.0, 1.0), (2.05, 0.8, 1.2)])
+def test_pair_blocks_match_oracle(sb, d, a_s, a_t):
+    got = sb.sphere_bie_pair_blocks([d], a_s, a_t, 6)[0]
+    ref = opb.aligned_block(d, a_s, a_t, 6, 4)
+    assert np.max(np.abs(got - ref)) < 1e-9 * np.max(np.abs(ref))
+
+
+def test_network_gradients_match_reference(sb):
+    n_par = sb.sphere_bie_pair_network_size()
+    rng = np.random.default_rng(0)
+    sizes = [5, 128, 128, 128, 73 * 73]
+    flat = []
+    params = []
+    for i in range(4):
+        W = _bf16(rng.normal(size=(sizes[i], sizes[i + 1])) / np.sqrt(sizes[i]))
+        b = (rng.normal(size=sizes[i + 1]) * 0.1).astype(np.float32)
+        flat += [W.ravel(), b]
+        params += [W.astype(np.float64), b.astype(np.float64)]
+    flat = np.concatenate(flat)
+    assert flat.size == n_par
+    X = rng.normal(size=(6, 5)).astype(np.float32)
+    Y = rng.normal(size=(6, 73 * 73)).astype(np.float32)
+    loss, g = sb.sphere_bie_pair_network_gradients(flat, X, Y)
+    lref, gref = opb.mlp_loss_grad(params, X.astype(np.float64), Y.astype(np.float64))
+    assert abs(loss - lref) < 1e-5 * lref
+    off = 0
+    for k in range(8):
+        sz = gref[k].size
+        gk = g[off:off + sz]
+        off += sz
+        assert np.max(np.abs(gk - gref[k].ravel())) < 2e-4 * np.max(np.abs(gref[k])) + 1e-9, k
+
+
+def _suspension():
+    w = wl.small_suspension(16, 6, 11, push=0.5, gap_range=(0.05, 0.2))
+    return w["centres"], w["radii"], 6
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_exact_pair_preconditioner(sb, prec):
+    c, a, p = _suspension()
+    rng = np.random.default_rng(3)
+    v = rng.normal(size=(len(a), 3))
+    w = rng.normal(size=(len(a), 3))
+    with sb.SphereBIE(c, a, p, prec=prec, tol=1e-10) as s:
+        F0, T0, i0 = s.resistance(v, w)
+    with sb.SphereBIE(c, a, p, prec=prec, tol=1e-10, precond=2) as s:
+        F1, T1, i1 = s.resistance(v, w)
+    assert i0["status"] == 0 and i1["status"] == 0
+    assert np.max(np.abs(F1 - F0)) < 1e-7 * np.max(np.abs(F0))
+    assert i1["iters"] < 0.75 * i0["iters"], (i0["iters"], i1["iters"])
+
+
+def test_learned_pair_preconditioner(sb, tmp_path):
+    path = tmp_path / "pairnet.bin"
+    info = sb.sphere_bie_train_pair_network(path, n_samples=3000, p=6, epochs=200, seed=5)
+    assert info["val_rel_err"] < 0.01, info
+    c, a, p = _suspension()
+    rng = np.random.default_rng(4)
+    v = rng.normal(size=(len(a), 3))
+    w = rng.normal(size=(len(a), 3))
+    with sb.SphereBIE(c, a, p, tol=1e-10) as s:
+        F0, T0, i0 = s.resistance(v, w)
+    with sb.SphereBIE(c, a, p, tol=1e-10, precond=2) as s:
+        F2, T2, i2 = s.resistance(v, w)
+    with sb.SphereBIE(c, a, p, tol=1e-10, precond=1, weights=path) as s:
+        F1, T1, i1 = s.resistance(v, w)
+    assert i1["status"] == 0 and np.max(np.abs(F1 - F0)) < 1e-7 * np.max(np.abs(F0))
+    # the network's gain over the unpreconditioned method, and its distance from exact blocks
+    assert i1["iters"] < 0.8 * i0["iters"], (i0["iters"], i1["iters"], i2["iters"])
+    assert i1["iters"] <= i2["iters"] + 3, (i1["iters"], i2["iters"])

@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-precond", action="store_true")
+    ap.add_argument("--pair-samples", type=int, default=4096,
+                    help="two-sphere configurations the pair network is trained on")
     return ap.parse_args()
 
 
@@ -112,6 +115,55 @@ class ClockSampler:
 
 def peak_fp32_tflops(sm_count, mhz):
     return sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def precond_compare(sb, torch, w, prec, stream, vel, om, F_ref, base, samples):
+    """Resistance solve of the same workload with the pair preconditioner:
+    exact pair blocks, and blocks predicted by the pair network trained here
+    for the workload's close-pair gaps (training time reported apart)."""
+    import tempfile
+    p = w["p"]
+    out = {"none": {"iters": base["iters"], "refinements": base["refinements"]}}
+    gap_max = 2.0 * float(max(w["radii"]))  # close if gap < eta * 2 max(a), eta = 1
+    tmp = tempfile.mkdtemp()
+    path = os.path.join(tmp, "pairnet.bin")
+    tr = sb.sphere_bie_train_pair_network(path, n_samples=samples, p=p, gap_min=0.01, gap_max=gap_max,
+                                          radius=float(w["radii"][0]), epochs=200, seed=7)
+    out["network"] = {"samples": samples, "gap_range": [0.01, gap_max], "val_rel_err": tr["val_rel_err"],
+                      "train_loss": tr["train_loss"], "data_s": tr["t_data_s"], "train_s": tr["t_train_s"]}
+    wpath = path.encode()
+    for kind, name in ((2, "exact"), (1, "learned")):
+        o = sb.make_opts(p, prec=prec, tol=w["tol"], mem_kind=1, stream=stream.cuda_stream)
+        o.use_learned_precond = kind
+        o.mlp_weights_path = wpath if kind == 1 else None
+        t0 = time.perf_counter()
+        ctx = sb.sphere_bie_create(w["centres"], w["radii"], o)
+        t_create = time.perf_counter() - t0
+        if prec == sb.SBIE_MIXED:
+            sb.sphere_bie_autotune(ctx, "resistance")
+        F = torch.zeros_like(F_ref)
+        T = torch.zeros_like(F_ref)
+        sb.sphere_bie_solve_resistance(ctx, vel, om, w["u0"], w["G"], F, T)  # warm-up
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(2):
+            t0 = time.perf_counter()
+            info = sb.sphere_bie_solve_resistance(ctx, vel, om, w["u0"], w["G"], F, T)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        pi = sb.sphere_bie_precond_info(ctx)
+        out[name] = {"iters": info["iters"], "refinements": info["refinements"], "status": info["status"],
+                     "rel_residual_true": info["rel_residual_true"], "time_to_solve_s": min(ts),
+                     "create_s": t_create, "precond_setup_s": pi["setup_ms"] / 1e3, "pairs": pi["pairs"],
+                     "pairs_out_of_range": pi["dropped"],
+                     "force_rel_diff_vs_unpreconditioned": float((F - F_ref).abs().max() / F_ref.abs().max())}
+        sb.sphere_bie_destroy(ctx)
+    try:
+        os.remove(path)
+        os.rmdir(tmp)
+    except OSError:
+        pass
+    return out
 
 
 def cpu_baseline(n_sample=8):
@@ -314,6 +366,10 @@ def main():
                            "force_rel_diff_vs_fp64": float((Fdf - F64).abs().max() / F64.abs().max())}
         sb.sphere_bie_destroy(cdf)
 
+    pre = None
+    if not args.no_precond:
+        pre = precond_compare(sb, torch, w, prec, stream, vel, om, F, last, args.pair_samples)
+
     # end to end through the public API with host buffers: create (geometry
     # upload, tables, close-pair lists), solve, read forces/torques, destroy
     e2e_times = []
@@ -355,6 +411,7 @@ def main():
                       "rel_residual_true": last["rel_residual_true"], "status": last["status"],
                       "create_s": t_create, "autotune_s": t_tune, "far_tiling": tuning},
             "roofline": roof, "far_field": far, "stage_ms_per_step": stage_ms, "fp64_path": fp64,
+            "pair_preconditioner": pre,
             "clocks": clocks, "gpu_launches": int(prof["kernel_launches"]),
             "gpu_launches_per_step": launches_per_step,
             "e2e": ({"value": statistics.mean(e2e_times), "unit": "s", "h2d_bytes_per_step": h2d,

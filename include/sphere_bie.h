@@ -84,7 +84,8 @@ typedef struct {
     int restarts;
     int refinements;        /* outer FP64 residual corrections (SBIE_MIXED)                    */
     double rel_residual_true; /* ||b - A x|| / ||b|| recomputed with the FP64 operator        */
-    double t_setup_ms, t_solve_ms;
+    double t_setup_ms;      /* wall time of the context's create, preconditioner included      */
+    double t_solve_ms;      /* wall time of this solve call                                    */
     long long n_near_pairs; /* directed close pairs (i, k)                                     */
 } sbie_solve_info;
 
@@ -257,6 +258,12 @@ sbie_status sphere_bie_train_pair_network(const sbie_pair_train_opts* opts, cons
  * source column) of the resistance operator, grid order p. */
 sbie_status sphere_bie_pair_blocks(int n, const double* dist, const double* a_src, const double* a_tgt, int p,
                                    double* blocks);
+
+/* Pair preconditioner of a context: kind (0 none, 1 network, 2 exact),
+ * undirected pairs in the pair systems, close pairs left out because they lie
+ * outside the network's trained input range (kind 1), and the wall time of
+ * its setup inside create.  Any output pointer may be NULL. */
+sbie_status sphere_bie_precond_info(const sbie_ctx* ctx, int* kind, int* n_pairs, int* n_dropped, double* setup_ms);
 
 /* Number of network parameters (FP32, layer by layer: W1 (5x128), b1, ...). */
 sbie_status sphere_bie_pair_network_size(long long* n_params);

@@ -75,7 +75,7 @@ void free_all(sbie_ctx* c) {
                     c->d_near_idx, c->d_tab, c->d_coef, c->d_chan, c->d_chanf, c->d_mom, c->d_part, c->d_src64,
                     c->d_srcf, c->d_in, c->d_out, c->d_tmp, c->d_tmp2, c->d_small, c->d_red, c->d_V, c->d_xsol,
                     c->d_rhs, c->d_res, c->d_prob_sph, c->d_sph_prob, c->d_node_prob, c->d_seg3, c->d_H, c->d_pvec,
-                    c->d_ZS, c->d_ZA, c->d_modes, c->d_near_pair, c->d_pinv, c->d_sinv, c->d_low, c->d_lowe,
+                    c->d_ZS, c->d_ZA, c->d_modes, c->d_pp_ptr, c->d_pp_idx, c->d_pp_pair, c->d_pinv, c->d_sinv, c->d_low, c->d_lowe,
                     c->d_pz};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -740,10 +740,20 @@ sbie_status to_user(sbie_ctx* c, const double* dev, double* user, bool nodal) {
 struct PairNet {
     std::vector<float> params;          // FP32 weights (mlp_layout)
     float in_mean[kMlpIn], in_std[kMlpIn];
+    float in_min[kMlpIn], in_max[kMlpIn];  // range of the training inputs
     std::vector<float> out_mean, out_std;
     int p_train = 0;
+    // true when x lies inside the trained input range (a pair outside it is
+    // left out of the preconditioner rather than extrapolated)
+    bool covers(const float* x) const {
+        for (int j = 0; j < kMlpIn; ++j) {
+            const float slack = 1e-4f * (1.f + std::fabs(in_min[j]) + std::fabs(in_max[j]));
+            if (!(x[j] >= in_min[j] - slack && x[j] <= in_max[j] + slack)) return false;
+        }
+        return true;
+    }
 };
-const char kNetMagic[9] = "SBIEPN01";
+const char kNetMagic[9] = "SBIEPN02";
 
 sbie_status net_save(const char* path, const PairNet& net) {
     std::ofstream f(path, std::ios::binary);
@@ -753,6 +763,8 @@ sbie_status net_save(const char* path, const PairNet& net) {
     f.write(reinterpret_cast<const char*>(hdr), sizeof(hdr));
     f.write(reinterpret_cast<const char*>(net.in_mean), sizeof(net.in_mean));
     f.write(reinterpret_cast<const char*>(net.in_std), sizeof(net.in_std));
+    f.write(reinterpret_cast<const char*>(net.in_min), sizeof(net.in_min));
+    f.write(reinterpret_cast<const char*>(net.in_max), sizeof(net.in_max));
     f.write(reinterpret_cast<const char*>(net.out_mean.data()), sizeof(float) * kMlpOut);
     f.write(reinterpret_cast<const char*>(net.out_std.data()), sizeof(float) * kMlpOut);
     f.write(reinterpret_cast<const char*>(net.params.data()), sizeof(float) * net.params.size());
@@ -776,6 +788,8 @@ sbie_status net_load(const char* path, PairNet& net) {
     net.params.resize(L.total);
     f.read(reinterpret_cast<char*>(net.in_mean), sizeof(net.in_mean));
     f.read(reinterpret_cast<char*>(net.in_std), sizeof(net.in_std));
+    f.read(reinterpret_cast<char*>(net.in_min), sizeof(net.in_min));
+    f.read(reinterpret_cast<char*>(net.in_max), sizeof(net.in_max));
     f.read(reinterpret_cast<char*>(net.out_mean.data()), sizeof(float) * kMlpOut);
     f.read(reinterpret_cast<char*>(net.out_std.data()), sizeof(float) * kMlpOut);
     f.read(reinterpret_cast<char*>(net.params.data()), sizeof(float) * L.total);
@@ -955,22 +969,45 @@ sbie_status precond_setup(sbie_ctx* c, int kind, const PairNet* net) {
     std::vector<double> ZS, ZA;
     lowmode_tables(c->p, ZS, ZA);
     std::vector<int4> modes = low_mode_table();
-    // undirected close pairs
-    std::map<std::pair<int, int>, int> pid;
+    // undirected close pairs (the close-pair relation is symmetric)
     std::vector<std::pair<int, int>> pairs;
-    std::vector<int> near_pair(std::max<long long>(1, c->n_near));
     for (int i = 0; i < n; ++i)
-        for (int e = c->h_near_ptr[i]; e < c->h_near_ptr[i + 1]; ++e) {
-            const int k = c->h_near_idx[e];
-            auto key = std::make_pair(std::min(i, k), std::max(i, k));
-            auto it = pid.find(key);
-            if (it == pid.end()) {
-                it = pid.emplace(key, (int)pairs.size()).first;
-                pairs.push_back(key);
-            }
-            near_pair[e] = it->second;
+        for (int e = c->h_near_ptr[i]; e < c->h_near_ptr[i + 1]; ++e)
+            if (c->h_near_idx[e] > i) pairs.push_back({i, c->h_near_idx[e]});
+    // the network is used only inside the input range it was trained on; a
+    // pair outside it is left out of the pair systems (not extrapolated)
+    if (kind == 1) {
+        std::vector<std::pair<int, int>> kept;
+        for (const auto& pr : pairs) {
+            const double* ca = &c->h_c[3 * pr.first];
+            const double* cb = &c->h_c[3 * pr.second];
+            const float d = (float)std::sqrt((cb[0] - ca[0]) * (cb[0] - ca[0]) + (cb[1] - ca[1]) * (cb[1] - ca[1]) +
+                                             (cb[2] - ca[2]) * (cb[2] - ca[2]));
+            const float x0[kMlpIn] = {0.f, 0.f, d, (float)c->h_a[pr.first], (float)c->h_a[pr.second]};
+            const float x1[kMlpIn] = {0.f, 0.f, d, (float)c->h_a[pr.second], (float)c->h_a[pr.first]};
+            if (net->covers(x0) && net->covers(x1)) kept.push_back(pr);
         }
+        c->n_pairs_dropped = (int)(pairs.size() - kept.size());
+        pairs.swap(kept);
+    }
     const int np = (int)pairs.size();
+    // per-sphere lists of the preconditioner's pairs: partner and pair index
+    std::vector<int> pp_ptr(n + 1, 0), pp_idx(std::max(1, 2 * np)), pp_pair(std::max(1, 2 * np));
+    for (const auto& pr : pairs) {
+        ++pp_ptr[pr.first + 1];
+        ++pp_ptr[pr.second + 1];
+    }
+    for (int i = 0; i < n; ++i) pp_ptr[i + 1] += pp_ptr[i];
+    {
+        std::vector<int> cur(pp_ptr.begin(), pp_ptr.end() - 1);
+        for (int q = 0; q < np; ++q) {
+            const int a = pairs[q].first, b = pairs[q].second;
+            pp_idx[cur[a]] = b;
+            pp_pair[cur[a]++] = q;
+            pp_idx[cur[b]] = a;
+            pp_pair[cur[b]++] = q;
+        }
+    }
     // own blocks L_i: single-sphere problems
     sbie_opts o = c->opts;
     o.use_learned_precond = 0;
@@ -1056,7 +1093,8 @@ sbie_status precond_setup(sbie_ctx* c, int kind, const PairNet* net) {
     }
     for (size_t i = 0; i < S.size(); ++i) S[i] = (float)Lam[i];
     bool ok = dmalloc(&c->d_ZS, ZS.size()) == cudaSuccess && dmalloc(&c->d_ZA, ZA.size()) == cudaSuccess &&
-              dmalloc(&c->d_modes, modes.size()) == cudaSuccess && dmalloc(&c->d_near_pair, near_pair.size()) == cudaSuccess &&
+              dmalloc(&c->d_modes, modes.size()) == cudaSuccess && dmalloc(&c->d_pp_ptr, pp_ptr.size()) == cudaSuccess &&
+              dmalloc(&c->d_pp_idx, pp_idx.size()) == cudaSuccess && dmalloc(&c->d_pp_pair, pp_pair.size()) == cudaSuccess &&
               dmalloc(&c->d_pinv, A.size()) == cudaSuccess && dmalloc(&c->d_sinv, S.size()) == cudaSuccess &&
               dmalloc(&c->d_low, (size_t)n * NM) == cudaSuccess && dmalloc(&c->d_lowe, (size_t)n * NM) == cudaSuccess;
     if (!ok) return fail(c, SBIE_ERR_OOM, "preconditioner buffers");
@@ -1066,7 +1104,9 @@ sbie_status precond_setup(sbie_ctx* c, int kind, const PairNet* net) {
     CK(h2d(c->stream, c->d_ZS, ZS.data(), ZS.size()));
     CK(h2d(c->stream, c->d_ZA, ZA.data(), ZA.size()));
     CK(h2d(c->stream, c->d_modes, modes.data(), modes.size()));
-    CK(h2d(c->stream, c->d_near_pair, near_pair.data(), near_pair.size()));
+    CK(h2d(c->stream, c->d_pp_ptr, pp_ptr.data(), pp_ptr.size()));
+    CK(h2d(c->stream, c->d_pp_idx, pp_idx.data(), pp_idx.size()));
+    CK(h2d(c->stream, c->d_pp_pair, pp_pair.data(), pp_pair.size()));
     CK(h2d(c->stream, c->d_pinv, A.data(), A.size()));
     CK(h2d(c->stream, c->d_sinv, S.data(), S.size()));
     CK(launch_gauss_jordan(c->stream, 2 * NM, np, c->d_pinv, d_bad));
@@ -1113,6 +1153,10 @@ sbie_status sphere_bie_create_batch(int n_problems, const int* n_spheres, const 
     if (n_problems < 1 || !n_spheres || !p_per_problem || !centres || !radii || !opts)
         return fail(nullptr, SBIE_ERR_ARG, "need n_problems >= 1 and non-NULL arrays");
     CKS(check_opts(opts));
+    const auto t_create0 = std::chrono::steady_clock::now();
+    auto create_ms = [&]() {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_create0).count();
+    };
     long long ntot = 0;
     for (int q = 0; q < n_problems; ++q) {
         if (n_spheres[q] < 1) return fail(nullptr, SBIE_ERR_ARG, "every problem needs n >= 1 spheres");
@@ -1160,6 +1204,7 @@ sbie_status sphere_bie_create_batch(int n_problems, const int* n_spheres, const 
             delete c;
             return ps;
         }
+        c->t_create_ms = create_ms();
         *out = c;
         return SBIE_OK;
     }
@@ -1244,6 +1289,7 @@ sbie_status sphere_bie_create_batch(int n_problems, const int* n_spheres, const 
         }
     }
     top->err = "no error";
+    top->t_create_ms = create_ms();
     *out = top;
     return SBIE_OK;
 }
@@ -1353,6 +1399,7 @@ sbie_status sphere_bie_solve_mobility(sbie_ctx* c, const double* forces, const d
     CKS(to_user(c, dw, omega, false));
     CK(cudaStreamSynchronize(c->stream));
     inf.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    inf.t_setup_ms = c->t_create_ms;
     if (info) *info = inf;
     return st;
 }
@@ -1396,6 +1443,7 @@ sbie_status sphere_bie_solve_resistance(sbie_ctx* c, const double* vel, const do
     CKS(to_user(c, dT, torques, false));
     CK(cudaStreamSynchronize(c->stream));
     inf.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    inf.t_setup_ms = c->t_create_ms;
     if (info) *info = inf;
     return st;
 }
@@ -1559,6 +1607,23 @@ sbie_status sphere_bie_profile_read(sbie_ctx* c, sbie_profile* out) {
     return SBIE_OK;
 }
 
+sbie_status sphere_bie_precond_info(const sbie_ctx* c, int* kind, int* n_pairs, int* n_dropped, double* setup_ms) {
+    if (!c) return SBIE_ERR_ARG;
+    int k = 0, np = 0, nd = 0;
+    double ms = 0.0;
+    for (const sbie_ctx* q : c->is_batch ? c->parts : std::vector<sbie_ctx*>{const_cast<sbie_ctx*>(c)}) {
+        k = std::max(k, q->prec_kind);
+        np += q->n_pairs;
+        nd += q->n_pairs_dropped;
+        ms += q->t_prec_setup_ms;
+    }
+    if (kind) *kind = k;
+    if (n_pairs) *n_pairs = np;
+    if (n_dropped) *n_dropped = nd;
+    if (setup_ms) *setup_ms = ms;
+    return SBIE_OK;
+}
+
 sbie_status sphere_bie_pair_network_size(long long* n_params) {
     if (!n_params) return SBIE_ERR_ARG;
     *n_params = mlp_layout().total;
@@ -1621,6 +1686,11 @@ sbie_status sphere_bie_train_pair_network(const sbie_pair_train_opts* o, const c
             s2 += (double)X[q * kMlpIn + j] * X[q * kMlpIn + j];
         }
         const double mu = s / n, var = std::max(0.0, s2 / n - mu * mu);
+        net.in_min[j] = net.in_max[j] = X[j];
+        for (int q = 0; q < n; ++q) {
+            net.in_min[j] = std::min(net.in_min[j], X[q * kMlpIn + j]);
+            net.in_max[j] = std::max(net.in_max[j], X[q * kMlpIn + j]);
+        }
         net.in_mean[j] = (float)mu;
         net.in_std[j] = var > 1e-20 ? (float)std::sqrt(var) : 1.f;
     }

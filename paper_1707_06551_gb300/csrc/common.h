@@ -110,14 +110,18 @@ struct sbie_ctx {
     double* d_ZS = nullptr;        // [npn][3][73] low-mode synthesis
     double* d_ZA = nullptr;        // [73][npn][3] low-mode analysis
     int4* d_modes = nullptr;       // [73] (type, n, m, part)
-    int* d_near_pair = nullptr;    // [n_near] undirected pair of each directed close pair
+    int* d_pp_ptr = nullptr;       // [n+1] per-sphere lists of the preconditioner's pairs
+    int* d_pp_idx = nullptr;       // partner sphere
+    int* d_pp_pair = nullptr;      // pair index into d_pinv
     int n_pairs = 0;
+    int n_pairs_dropped = 0;       // close pairs outside the network's trained range
     float* d_pinv = nullptr;       // [n_pairs][146][146] inverses of the pair systems
     float* d_sinv = nullptr;       // [n][73][73] inverses of the spheres' own low-mode blocks
     double* d_low = nullptr;       // [n][73]
     double* d_lowe = nullptr;      // [n][73]
     double* d_pz = nullptr;        // preconditioned vector (system level)
     double t_prec_setup_ms = 0.0;
+    double t_create_ms = 0.0;      // wall time of create (grid, tables, close pairs, preconditioner)
 
     // host geometry
     std::vector<double> h_c, h_a;

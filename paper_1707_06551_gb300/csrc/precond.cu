@@ -313,13 +313,13 @@ __global__ void gather_low_kernel(int n_sph, int P1, const double* __restrict__ 
 }
 
 // coarse correction e_i (see the header comment)
-__global__ void coarse_kernel(const int* __restrict__ near_ptr, const int* __restrict__ near_idx,
-                              const int* __restrict__ near_pair, const float* __restrict__ pinv,
+__global__ void coarse_kernel(const int* __restrict__ pp_ptr, const int* __restrict__ pp_idx,
+                              const int* __restrict__ pp_pair, const float* __restrict__ pinv,
                               const float* __restrict__ sinv, const double* __restrict__ low, double* __restrict__ e) {
     const int i = blockIdx.x;
     const int r = threadIdx.x;
     __shared__ double c2[2 * kLowModes];
-    const int e0 = near_ptr[i], e1 = near_ptr[i + 1];
+    const int e0 = pp_ptr[i], e1 = pp_ptr[i + 1];
     const int deg = e1 - e0;
     double acc = 0.0;
     if (deg == 0) {
@@ -331,7 +331,7 @@ __global__ void coarse_kernel(const int* __restrict__ near_ptr, const int* __res
         }
     }
     for (int ee = e0; ee < e1; ++ee) {
-        const int k = near_idx[ee];
+        const int k = pp_idx[ee];
         const int a = min(i, k), b = max(i, k);
         __syncthreads();
         for (int t = threadIdx.x; t < 2 * kLowModes; t += blockDim.x)
@@ -339,7 +339,7 @@ __global__ void coarse_kernel(const int* __restrict__ near_ptr, const int* __res
         __syncthreads();
         if (r < kLowModes) {
             const int row = (i == a ? 0 : kLowModes) + r;
-            const float* Mr = pinv + (size_t)near_pair[ee] * 4 * kLowModes * kLowModes + (size_t)row * 2 * kLowModes;
+            const float* Mr = pinv + (size_t)pp_pair[ee] * 4 * kLowModes * kLowModes + (size_t)row * 2 * kLowModes;
             double s = 0.0;
             for (int c = 0; c < 2 * kLowModes; ++c) s += (double)Mr[c] * c2[c];
             acc += s / deg;
@@ -404,7 +404,7 @@ cudaError_t precond_apply(sbie_ctx* c, const double* v, double* out) {
     if (e != cudaSuccess) return e;
     gather_low_kernel<<<c->n, 96, 0, c->stream>>>(c->n, c->p + 1, c->d_coef, c->d_modes, c->d_low);
     ++c->n_launch;
-    coarse_kernel<<<c->n, 96, 0, c->stream>>>(c->d_near_ptr, c->d_near_idx, c->d_near_pair, c->d_pinv, c->d_sinv,
+    coarse_kernel<<<c->n, 96, 0, c->stream>>>(c->d_pp_ptr, c->d_pp_idx, c->d_pp_pair, c->d_pinv, c->d_sinv,
                                               c->d_low, c->d_lowe);
     ++c->n_launch;
     synth_add_kernel<<<(unsigned)((c->N + 127) / 128), 128, 0, c->stream>>>(c->npn, c->N, c->d_ZS, c->d_lowe, out);

@@ -96,6 +96,8 @@ def lib():
                                                     ctypes.POINTER(PairTrainInfo)]
         L.sphere_bie_pair_blocks.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]
         L.sphere_bie_pair_network_size.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+        L.sphere_bie_precond_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
         L.sphere_bie_pair_network_gradients.argtypes = [_P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]
         L.sphere_bie_autotune.argtypes = [_P, ctypes.c_int, ctypes.POINTER(FarTuning)]
         L.sphere_bie_apply_layer_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]
@@ -104,7 +106,8 @@ def lib():
                   "sphere_bie_apply_operator", "sphere_bie_solve_mobility", "sphere_bie_solve_resistance",
                   "sphere_bie_destroy", "sphere_bie_profile", "sphere_bie_profile_read",
                   "sphere_bie_apply_layer_noalloc", "sphere_bie_autotune", "sphere_bie_train_pair_network",
-                  "sphere_bie_pair_blocks", "sphere_bie_pair_network_size", "sphere_bie_pair_network_gradients"):
+                  "sphere_bie_pair_blocks", "sphere_bie_pair_network_size", "sphere_bie_pair_network_gradients",
+                  "sphere_bie_precond_info"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -248,6 +251,13 @@ def sphere_bie_pair_blocks(dist, a_src, a_tgt, p):
     out = np.zeros((len(d), 73, 73))
     _check(None, lib().sphere_bie_pair_blocks(len(d), _ptr(d), _ptr(s), _ptr(t), int(p), _ptr(out)))
     return out
+
+
+def sphere_bie_precond_info(ctx):
+    k, npairs, nd, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(ctx, lib().sphere_bie_precond_info(ctx, ctypes.byref(k), ctypes.byref(npairs), ctypes.byref(nd),
+                                              ctypes.byref(ms)))
+    return {"kind": k.value, "pairs": npairs.value, "dropped": nd.value, "setup_ms": ms.value}
 
 
 def sphere_bie_pair_network_size():

@@ -91,9 +91,14 @@ def test_learned_pair_preconditioner(sb, tmp_path):
         F0, T0, i0 = s.resistance(v, w)
     with sb.SphereBIE(c, a, p, tol=1e-10, precond=2) as s:
         F2, T2, i2 = s.resistance(v, w)
+        pi2 = sb.sphere_bie_precond_info(s.ctx)
     with sb.SphereBIE(c, a, p, tol=1e-10, precond=1, weights=path) as s:
         F1, T1, i1 = s.resistance(v, w)
+        pi1 = sb.sphere_bie_precond_info(s.ctx)
     assert i1["status"] == 0 and np.max(np.abs(F1 - F0)) < 1e-7 * np.max(np.abs(F0))
+    # pairs beyond the trained gap range (0.01 .. 0.5) are left out, not extrapolated
+    assert pi2["kind"] == 2 and pi1["kind"] == 1 and pi2["dropped"] == 0
+    assert pi1["pairs"] + pi1["dropped"] == pi2["pairs"] and pi1["pairs"] > 0
     # the network's gain over the unpreconditioned method, and its distance from exact blocks
     assert i1["iters"] < 0.8 * i0["iters"], (i0["iters"], i1["iters"], i2["iters"])
     assert i1["iters"] <= i2["iters"] + 3, (i1["iters"], i2["iters"])

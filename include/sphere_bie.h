@@ -77,6 +77,10 @@ typedef struct {
     const char* mlp_weights_path; /* pair-network file written by sphere_bie_train_pair_network */
     int mem_kind;           /* 0 host pointers, 1 device pointers                              */
     void* stream;           /* cudaStream_t for mem_kind = 1, or NULL                          */
+    int use_graphs;         /* 1: each GMRES restart cycle runs on the device as one CUDA
+                               graph launch (a WHILE node over the Arnoldi iteration, no host
+                               round trip per iteration); 0: the same device iteration stepped
+                               from the host.  Profiling (sphere_bie_profile) always steps.    */
 } sbie_opts;
 
 typedef struct {
@@ -87,10 +91,11 @@ typedef struct {
     double t_setup_ms;      /* wall time of the context's create, preconditioner included      */
     double t_solve_ms;      /* wall time of this solve call                                    */
     long long n_near_pairs; /* directed close pairs (i, k)                                     */
+    int graph_cycles;       /* restart cycles that ran as one CUDA graph launch each            */
 } sbie_solve_info;
 
 /* Fills *opts with defaults: p = 8, eta = 1, FP64, tol = 1e-8, restart = 60,
- * max_iter = 600, host memory, NULL stream. */
+ * max_iter = 600, host memory, NULL stream, graphs on. */
 sbie_status sphere_bie_default_opts(sbie_opts* opts);
 
 /* Builds the grid (Eq. 4.2), smooth weights (Eq. 4.4), close-pair lists

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <atomic>
 #include <map>
 #include <utility>
 #include <mutex>
@@ -65,7 +66,21 @@ cudaError_t d2h(cudaStream_t s, T* dst, const T* src, size_t count) {
     return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
 }
 
+// Captured restart cycles bake in device addresses and far-field tilings;
+// every reallocation or retuning advances this counter and a cycle graph
+// recorded under an older value is captured again before its next use.
+std::atomic<unsigned long long> g_graph_epoch{1};
+
+void drop_graphs(sbie_ctx* c) {
+    for (CycleGraph& g : c->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    c->graphs.clear();
+}
+
 void free_all(sbie_ctx* c) {
+    drop_graphs(c);
     for (sbie_ctx* q : c->parts) {
         free_all(q);
         delete q;
@@ -76,10 +91,12 @@ void free_all(sbie_ctx* c) {
                     c->d_srcf, c->d_in, c->d_out, c->d_tmp, c->d_tmp2, c->d_small, c->d_red, c->d_V, c->d_xsol,
                     c->d_rhs, c->d_res, c->d_prob_sph, c->d_sph_prob, c->d_node_prob, c->d_seg3, c->d_H, c->d_pvec,
                     c->d_ZS, c->d_ZA, c->d_modes, c->d_pp_ptr, c->d_pp_idx, c->d_pp_pair, c->d_pinv, c->d_sinv, c->d_low, c->d_lowe,
-                    c->d_pz};
+                    c->d_pz, c->d_ad, c->d_adi, c->d_vk};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
+    if (c->h_st) cudaFreeHost(c->h_st);
+    if (c->h_pack) cudaFreeHost(c->h_pack);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     for (auto& v : c->prof_events)
@@ -168,6 +185,7 @@ sbie_status ensure_part(sbie_ctx* c, int split_needed = 0) {
     c->part_cap = 0;
     if (dmalloc(&c->d_part, need) != cudaSuccess) return fail(c, SBIE_ERR_OOM, "far-field partials");
     c->part_cap = need;
+    ++g_graph_epoch;
     return SBIE_OK;
 }
 
@@ -247,12 +265,59 @@ sbie_status apply_sys(const Sys& S, int op, int mode, const double* in, double* 
 
 sbie_status ensure_krylov(sbie_ctx* c, int m, int P) {
     const int B = seg_blocks(c->N * 3, P);
+    const long long n3 = c->N * 3;
     if (!c->d_V || c->krylov_m < m) {
         if (c->d_V) cudaFree(c->d_V);
         c->d_V = nullptr;
         c->krylov_m = 0;
-        if (dmalloc(&c->d_V, (size_t)(m + 1) * c->N * 3) != cudaSuccess) return fail(c, SBIE_ERR_OOM, "Krylov basis");
+        if (dmalloc(&c->d_V, (size_t)(m + 1) * n3) != cudaSuccess) return fail(c, SBIE_ERR_OOM, "Krylov basis");
         c->krylov_m = m;
+        ++g_graph_epoch;
+    }
+    if (!c->d_ad || c->ad.m < m || c->ad.P < P) {
+        for (void* q : {(void*)c->d_ad, (void*)c->d_adi, (void*)c->d_vk})
+            if (q) cudaFree(q);
+        if (c->h_st) cudaFreeHost(c->h_st);
+        if (c->h_pack) cudaFreeHost(c->h_pack);
+        c->d_ad = nullptr;
+        c->d_adi = nullptr;
+        c->d_vk = nullptr;
+        c->h_st = nullptr;
+        c->h_pack = nullptr;
+        c->ad = ArnoldiDev();
+        const size_t Pm = (size_t)P * m, Pm1 = (size_t)P * (m + 1);
+        const size_t nd = 4 * (size_t)P + Pm1 * m + 2 * Pm + Pm1 + 2 * Pm1 + Pm + (4 * (size_t)P + 1) + n3;
+        if (dmalloc(&c->d_ad, nd) != cudaSuccess || dmalloc(&c->d_adi, 4 + 2 * (size_t)P) != cudaSuccess ||
+            dmalloc(&c->d_vk, (size_t)n3) != cudaSuccess ||
+            cudaMallocHost(reinterpret_cast<void**>(&c->h_st), sizeof(int) * 4) != cudaSuccess ||
+            cudaMallocHost(reinterpret_cast<void**>(&c->h_pack), sizeof(double) * (4 * (size_t)P + 1)) != cudaSuccess)
+            return fail(c, SBIE_ERR_OOM, "GMRES cycle state");
+        ArnoldiDev& A = c->ad;
+        A.m = m;
+        A.P = P;
+        double* d = c->d_ad;
+        auto take = [&](size_t k) {
+            double* r = d;
+            d += k;
+            return r;
+        };
+        A.nb = take(P);
+        A.tol = take(P);
+        A.nrm = take(P);
+        A.scale = take(P);
+        A.H = take(Pm1 * m);
+        A.cs = take(Pm);
+        A.sn = take(Pm);
+        A.g = take(Pm1);
+        A.h1 = take(Pm1);
+        A.h2 = take(Pm1);
+        A.y = take(Pm);
+        A.pack = take(4 * (size_t)P + 1);
+        A.w = take(n3);
+        A.st = c->d_adi;
+        A.live = c->d_adi + 4;
+        A.kd = c->d_adi + 4 + P;
+        ++g_graph_epoch;
     }
     const size_t red = (size_t)(m + 1) * P * B + 64;
     if (red > c->red_cap) {
@@ -301,25 +366,127 @@ sbie_status stage_H(sbie_ctx* c, const double* host, size_t count) {
 }
 
 struct GmresOut {
-    int iters = 0, restarts = 0;
+    int iters = 0, restarts = 0, graph_cycles = 0;
     std::vector<double> rel;  // per problem, residual of the final iterate recomputed with A
 };
 
 using AFn = std::function<sbie_status(const double*, double*)>;
 
+// Kernel-launch counters of every context a system touches (top and parts).
+std::vector<std::pair<sbie_ctx*, long long>> launch_counters(const Sys& S) {
+    std::vector<std::pair<sbie_ctx*, long long>> v;
+    v.push_back({S.top, S.top->n_launch});
+    for (sbie_ctx* q : S.parts)
+        if (q != S.top) v.push_back({q, q->n_launch});
+    return v;
+}
+
+// One Arnoldi iteration of the device-resident cycle (krylov.cu): w = A V_k
+// (A M^{-1} V_k with a right preconditioner), classical Gram-Schmidt twice,
+// Givens update and convergence test per problem, V_{k+1} = w / ||w||.
+sbie_status enqueue_iteration(const Sys& S, const AFn& A, const AFn* M, cudaGraphConditionalHandle cond,
+                              bool has_cond) {
+    sbie_ctx* c = S.top;
+    const ArnoldiDev& AD = c->ad;
+    CK(arnoldi_copy_k(c, AD, c->d_V, S.n3, c->d_vk));
+    if (M) {
+        CKS((*M)(c->d_vk, c->d_pz));
+        CKS(A(c->d_pz, AD.w));
+    } else {
+        CKS(A(c->d_vk, AD.w));
+    }
+    StageScope sc(c, ST_BLAS);
+    CK(arnoldi_orthogonalise(c, AD, c->d_V, S.n3, c->d_seg3, c->d_node_prob));
+    CK(arnoldi_step_end(c, AD, c->d_V, S.n3, c->d_node_prob, cond, has_cond));
+    return SBIE_OK;
+}
+
+// The restart cycle as a CUDA graph: one WHILE node whose body is one
+// iteration; the advance kernel sets the condition.  Captured once per
+// (operator, arithmetic, preconditioner) and reused while the device
+// addresses and far-field tilings it holds are unchanged.
+sbie_status cycle_graph(const Sys& S, const AFn& A, const AFn* M, int key, CycleGraph** out) {
+    sbie_ctx* c = S.top;
+    const unsigned long long ep = g_graph_epoch.load();
+    for (size_t i = 0; i < c->graphs.size();) {
+        CycleGraph& g = c->graphs[i];
+        if (g.key == key && g.epoch == ep) {
+            *out = &g;
+            return SBIE_OK;
+        }
+        if (g.key == key || g.epoch != ep) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.graph) cudaGraphDestroy(g.graph);
+            c->graphs.erase(c->graphs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+    CycleGraph g;
+    g.key = key;
+    g.epoch = ep;
+    CK(cudaGraphCreate(&g.graph, 0));
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g.graph, 1, cudaGraphCondAssignDefault);
+    // the parameter union has no default constructor: zeroed raw storage
+    alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(np_raw, 0, sizeof(np_raw));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_raw);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &np);
+    sbie_status st = SBIE_OK;
+    auto counters = launch_counters(S);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            st = enqueue_iteration(S, A, M, cond, true);
+            cudaGraph_t captured = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(c->stream, &captured);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    // the captured launches run once per iteration: count them when they do
+    g.body_launches = 0;
+    for (auto& pr : launch_counters(S)) g.body_launches += pr.second;
+    for (auto& pr : counters) {
+        g.body_launches -= pr.second;
+        pr.first->n_launch = pr.second;
+    }
+    if (st == SBIE_OK && e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+    if (st != SBIE_OK || e != cudaSuccess) {
+        cudaGraphDestroy(g.graph);
+        cudaGetLastError();
+        return fail(c, st != SBIE_OK ? st : SBIE_ERR_CUDA,
+                    std::string("cycle graph: ") + (e != cudaSuccess ? cudaGetErrorString(e) : c->err));
+    }
+    c->graphs.push_back(g);
+    *out = &c->graphs.back();
+    return SBIE_OK;
+}
+
 // Restarted GMRES, one Krylov space per problem (classical Gram-Schmidt
 // applied twice), x0 = 0.  Problem p runs while want[p] and its relative
 // residual exceeds tol[p]; the residual is recomputed as b - A x at every
-// restart.  A problem that has converged keeps zero Krylov vectors.
+// restart.  Each restart cycle runs on the device (krylov.cu): as one graph
+// launch when the context uses graphs and is not profiling, otherwise
+// stepped from the host one iteration at a time.  `key` names the operator,
+// arithmetic and preconditioner for the graph cache.
 sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const std::vector<double>& tol,
-                  const std::vector<char>& want, int restart, int max_iter, GmresOut& go, const AFn* M = nullptr) {
+                  const std::vector<char>& want, int restart, int max_iter, GmresOut& go, const AFn* M, int key) {
     sbie_ctx* c = S.top;
     const long long n3 = S.n3;
     const int P = S.P;
     restart = std::max(1, std::min(restart, 250));
     CKS(ensure_krylov(c, restart, P));
+    if (c->ad.P != P) return fail(c, SBIE_ERR_ARG, "internal: cycle state sized for another system");
+    const ArnoldiDev& AD = c->ad;
     const int m = restart;
-    std::vector<double> nb, beta, hk1;
+    std::vector<double> nb, beta;
     CKS(seg_norms(S, b, nb));
     CK(cudaMemsetAsync(x, 0, sizeof(double) * n3, c->stream));
     go = GmresOut();
@@ -331,10 +498,8 @@ sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const 
     double* r = c->d_res;
     CK(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->stream));
     beta = nb;
-    std::vector<double> H((size_t)P * (m + 1) * m), cs((size_t)P * m), sn((size_t)P * m), g((size_t)P * (m + 1));
-    std::vector<double> hcol((size_t)(m + 1) * P), h2((size_t)(m + 1) * P), stage((size_t)(m + 1) * P), y(m);
-    std::vector<int> kd(P);
-    std::vector<char> live(P);
+    std::vector<double> stage(P);
+    bool graphs = c->opts.use_graphs != 0;
     int total = 0;
     auto any = [](const std::vector<char>& v) {
         for (char q : v)
@@ -347,104 +512,57 @@ sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const 
         for (int p = 0; p < P; ++p) stage[p] = active[p] ? 1.0 / beta[p] : 0.0;
         CKS(stage_H(c, stage.data(), P));
         CK(seg_scale(c, r, c->d_H, c->d_node_prob, V, n3));
-        std::fill(g.begin(), g.end(), 0.0);
         for (int p = 0; p < P; ++p) {
-            g[(size_t)p * (m + 1)] = active[p] ? beta[p] : 0.0;
-            kd[p] = 0;
-            live[p] = active[p];
+            c->h_pack[p] = nb[p];
+            c->h_pack[P + p] = tol[p];
+            c->h_pack[2 * P + p] = beta[p];
+            c->h_pack[3 * P + p] = active[p] ? 1.0 : 0.0;
         }
-        for (int k = 0; k < mm && any(live); ++k) {
-            double* w = V + (size_t)(k + 1) * n3;
-            if (M) {  // right preconditioning: Arnoldi on A M^{-1}
-                CKS((*M)(V + (size_t)k * n3, c->d_pz));
-                CKS(A(c->d_pz, w));
+        c->h_pack[4 * P] = mm;
+        CK(cudaMemcpyAsync(AD.pack, c->h_pack, sizeof(double) * (4 * (size_t)P + 1), cudaMemcpyHostToDevice, c->stream));
+        CK(arnoldi_cycle_init(c, AD));
+        CycleGraph* g = nullptr;
+        if (graphs && !c->prof.on) {
+            if (cycle_graph(S, A, M, key, &g) == SBIE_OK) {
+                CK(cudaGraphLaunch(g->exec, c->stream));
+                ++go.graph_cycles;
             } else {
-                CKS(A(V + (size_t)k * n3, w));
+                graphs = false;  // host-stepped from here on; the reason stays in the context's error text
+                g = nullptr;
             }
-            {
-                StageScope sc(c, ST_BLAS);
-                for (int pass = 0; pass < 2; ++pass) {
-                    double* dst = pass == 0 ? hcol.data() : h2.data();
-                    CK(seg_dots(c, V, k + 1, n3, w, n3, c->d_seg3, P, c->d_pvec));
-                    CK(cudaMemcpyAsync(c->h_red, c->d_pvec, sizeof(double) * (k + 1) * P, cudaMemcpyDeviceToHost,
-                                       c->stream));
-                    CK(cudaStreamSynchronize(c->stream));
-                    for (int j = 0; j <= k; ++j)
-                        for (int p = 0; p < P; ++p) {
-                            double v = live[p] ? c->h_red[(size_t)j * P + p] : 0.0;
-                            dst[(size_t)j * P + p] = v;
-                            stage[(size_t)j * P + p] = v;
-                        }
-                    CKS(stage_H(c, stage.data(), (size_t)(k + 1) * P));
-                    CK(seg_gemv(c, V, k + 1, n3, c->d_H, P, -1.0, c->d_node_prob, w, n3));
-                }
-            }
-            CKS(seg_norms(S, w, hk1));
-            for (int p = 0; p < P; ++p) {
-                if (live[p] && !std::isfinite(hk1[p])) return fail(c, SBIE_ERR_NUMERIC, "NaN/Inf in the Krylov basis");
-                stage[p] = (live[p] && hk1[p] > 0.0) ? 1.0 / hk1[p] : 0.0;
-            }
-            CKS(stage_H(c, stage.data(), P));
-            CK(seg_scale(c, w, c->d_H, c->d_node_prob, w, n3));
-            for (int p = 0; p < P; ++p) {
-                if (!live[p]) continue;
-                double* Hp = H.data() + (size_t)p * (m + 1) * m;
-                double* csp = cs.data() + (size_t)p * m;
-                double* snp = sn.data() + (size_t)p * m;
-                double* gp = g.data() + (size_t)p * (m + 1);
-                std::vector<double> h(k + 2);
-                for (int j = 0; j <= k; ++j) h[j] = hcol[(size_t)j * P + p] + h2[(size_t)j * P + p];
-                for (int j = 0; j < k; ++j) {
-                    double a0 = h[j], a1 = h[j + 1];
-                    h[j] = csp[j] * a0 + snp[j] * a1;
-                    h[j + 1] = -snp[j] * a0 + csp[j] * a1;
-                }
-                double den = std::hypot(h[k], hk1[p]);
-                csp[k] = den > 0 ? h[k] / den : 1.0;
-                snp[k] = den > 0 ? hk1[p] / den : 0.0;
-                h[k] = den;
-                for (int j = 0; j <= k; ++j) Hp[(size_t)j * m + k] = h[j];
-                gp[k + 1] = -snp[k] * gp[k];
-                gp[k] = csp[k] * gp[k];
-                kd[p] = k + 1;
-                if (std::fabs(gp[k + 1]) / nb[p] <= tol[p] || hk1[p] == 0.0) live[p] = 0;
-            }
-            ++total;
         }
-        // x += V y per problem
-        int kmax = 0;
-        std::fill(stage.begin(), stage.end(), 0.0);
-        for (int p = 0; p < P; ++p) {
-            const int kk = kd[p];
-            kmax = std::max(kmax, kk);
-            const double* Hp = H.data() + (size_t)p * (m + 1) * m;
-            const double* gp = g.data() + (size_t)p * (m + 1);
-            for (int i = kk - 1; i >= 0; --i) {
-                double s = gp[i];
-                for (int j = i + 1; j < kk; ++j) s -= Hp[(size_t)i * m + j] * y[j];
-                y[i] = s / Hp[(size_t)i * m + i];
+        if (!g) {
+            for (int it = 0; it < mm; ++it) {
+                CKS(enqueue_iteration(S, A, M, cudaGraphConditionalHandle{}, false));
+                CK(cudaMemcpyAsync(c->h_st, AD.st, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+                CK(cudaStreamSynchronize(c->stream));
+                if (!c->h_st[2]) break;
             }
-            for (int j = 0; j < kk; ++j) stage[(size_t)j * P + p] = y[j];
         }
-        if (kmax == 0) break;
-        CKS(stage_H(c, stage.data(), (size_t)kmax * P));
-        if (M) {  // x += M^{-1} (V y)
+        // x += V y (x += M^{-1} V y), then the true residual
+        if (M) {
             double* t = c->d_pz + n3;
             CK(cudaMemsetAsync(t, 0, sizeof(double) * n3, c->stream));
-            CK(seg_gemv(c, V, kmax, n3, c->d_H, P, 1.0, c->d_node_prob, t, n3));
+            CK(arnoldi_finish(c, AD, V, n3, c->d_node_prob, t));
             CKS((*M)(t, c->d_pz));
             CK(blas_axpy(c, 1.0, c->d_pz, x, n3));
         } else {
-            CK(seg_gemv(c, V, kmax, n3, c->d_H, P, 1.0, c->d_node_prob, x, n3));
+            CK(arnoldi_finish(c, AD, V, n3, c->d_node_prob, x));
         }
+        CK(cudaMemcpyAsync(c->h_st, AD.st, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
         CKS(A(x, r));
         CK(blas_lincomb(c, 1.0, b, -1.0, r, r, n3));
-        CKS(seg_norms(S, r, beta));
+        CKS(seg_norms(S, r, beta));  // synchronises the stream: h_st is current
+        const int kexec = c->h_st[0];
+        if (g) c->n_launch += (long long)kexec * g->body_launches;
+        if (c->h_st[3]) return fail(c, SBIE_ERR_NUMERIC, "NaN/Inf in the Krylov basis");
+        total += kexec;
         for (int p = 0; p < P; ++p) {
             if (!std::isfinite(beta[p])) return fail(c, SBIE_ERR_NUMERIC, "NaN/Inf residual");
             active[p] = want[p] && nb[p] > 0.0 && beta[p] / nb[p] > tol[p];
         }
         ++go.restarts;
+        if (kexec == 0) break;
     }
     go.iters = total;
     for (int p = 0; p < P; ++p) go.rel[p] = nb[p] > 0.0 ? beta[p] / nb[p] : 0.0;
@@ -479,6 +597,7 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
         return SBIE_OK;
     };
     const AFn* M = prec ? &Mf : nullptr;
+    auto key_of = [&](int mode) { return (op * 4 + mode) * 2 + (prec ? 1 : 0); };
     if (prec && !c->d_pz && dmalloc(&c->d_pz, 2 * (size_t)n3) != cudaSuccess)
         return fail(c, SBIE_ERR_OOM, "preconditioner buffers");
     const double tol = c->opts.tol;
@@ -489,9 +608,10 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
     CKS(ensure_krylov(c, std::max(1, std::min(c->opts.restart, 250)), P));
     if (c->opts.prec != SBIE_MIXED) {
         CKS(gmres(S, A64, b, x, std::vector<double>(P, tol), std::vector<char>(P, 1), c->opts.restart,
-                  c->opts.max_iter, go, M));
+                  c->opts.max_iter, go, M, key_of(hm)));
         inf.iters = go.iters;
         inf.restarts = go.restarts;
+        inf.graph_cycles = go.graph_cycles;
         rel = go.rel;
     } else {
         std::vector<double> nb;
@@ -510,8 +630,10 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
                 want[p] = rel[p] > tol;
                 itol[p] = std::min(1e-3, std::max(1e-5, 0.5 * tol / std::max(rel[p], 1e-300)));
             }
-            CKS(gmres(S, A32, r, d, itol, want, c->opts.restart, c->opts.max_iter - iters, go, M));
+            CKS(gmres(S, A32, r, d, itol, want, c->opts.restart, c->opts.max_iter - iters, go, M, key_of(kModeF32)));
             iters += go.iters;
+            inf.restarts += go.restarts;
+            inf.graph_cycles += go.graph_cycles;
             CK(blas_axpy(c, 1.0, d, x, n3));
             CKS(A64(x, r));
             CK(blas_lincomb(c, 1.0, b, -1.0, r, r, n3));
@@ -553,6 +675,7 @@ sbie_status check_opts(const sbie_opts* opts) {
         return fail(nullptr, SBIE_ERR_ARG, "the learned preconditioner needs mlp_weights_path");
     if (!(opts->tol > 0.0) || opts->restart < 1 || opts->max_iter < 0)
         return fail(nullptr, SBIE_ERR_ARG, "need tol > 0, restart >= 1, max_iter >= 0");
+    if (opts->use_graphs != 0 && opts->use_graphs != 1) return fail(nullptr, SBIE_ERR_ARG, "use_graphs must be 0 or 1");
     return SBIE_OK;
 }
 
@@ -1137,6 +1260,7 @@ sbie_status sphere_bie_default_opts(sbie_opts* o) {
     o->max_iter = 600;
     o->mem_kind = 0;
     o->stream = nullptr;
+    o->use_graphs = 1;
     return SBIE_OK;
 }
 
@@ -1517,6 +1641,7 @@ sbie_status tune_one(sbie_ctx* c, Kern k, int mode, sbie_far_tuning* chosen) {
     }
     std::sort(cands.begin(), cands.begin() + top, [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
     *slot = cands[0].t;
+    ++g_graph_epoch;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[std::make_tuple(c->n, c->p, c->sm_count, (int)k, mode)] = cands[0].t;

@@ -73,6 +73,38 @@ enum Stage {
     ST_FARK32 = 6, ST_FARK64 = 7  // the far-field pair kernel alone
 };
 
+// Device state of one GMRES restart cycle (krylov.cu), for P problems and at
+// most m iterations.  Passed by value to the kernels.
+struct ArnoldiDev {
+    int m = 0, P = 0;
+    int* st = nullptr;        // [4] k, iteration limit, continue flag, non-finite flag
+    int* live = nullptr;      // [P] problem still iterating
+    int* kd = nullptr;        // [P] columns of the problem's Hessenberg matrix
+    double* nb = nullptr;     // [P] norm of the right-hand side
+    double* tol = nullptr;    // [P] relative tolerance
+    double* H = nullptr;      // [P][m+1][m] rotated Hessenberg matrix
+    double* cs = nullptr;     // [P][m] Givens cosines
+    double* sn = nullptr;     // [P][m] Givens sines
+    double* g = nullptr;      // [P][m+1] rotated right-hand side of the least-squares problem
+    double* h1 = nullptr;     // [m+1][P] first Gram-Schmidt pass
+    double* h2 = nullptr;     // [m+1][P] second pass
+    double* nrm = nullptr;    // [P] squared norm of the new vector
+    double* scale = nullptr;  // [P] 1 / its norm (0 once the problem stopped)
+    double* y = nullptr;      // [m][P] least-squares solution of the cycle
+    double* w = nullptr;      // [3N] new Krylov vector (fixed address for the captured operator)
+    double* pack = nullptr;   // [4P+1] cycle inputs staged from the host: nb, tol, beta, active, limit
+};
+
+// One restart cycle captured as a CUDA graph (a WHILE node whose body is one
+// Arnoldi iteration), for one operator / arithmetic / preconditioner choice.
+struct CycleGraph {
+    int key = -1;
+    unsigned long long epoch = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long body_launches = 0;
+};
+
 }  // namespace sbie
 
 struct sbie_ctx {
@@ -160,6 +192,13 @@ struct sbie_ctx {
     double* h_red = nullptr;     // pinned host mirror of reduction results
     // Krylov space
     double* d_V = nullptr;       // [restart+1][3N]
+    sbie::ArnoldiDev ad{};       // device state of a restart cycle (krylov.cu)
+    double* d_ad = nullptr;      // storage of the doubles of ad
+    int* d_adi = nullptr;        // storage of the ints of ad
+    double* d_vk = nullptr;      // [3N] current Krylov vector (fixed address)
+    int* h_st = nullptr;         // pinned mirror of ad.st
+    double* h_pack = nullptr;    // pinned staging of ad.pack
+    std::vector<sbie::CycleGraph> graphs;
     double* d_xsol = nullptr;    // [3N]
     double* d_rhs = nullptr;     // [3N]
     double* d_res = nullptr;     // [3N]
@@ -245,5 +284,14 @@ cudaError_t seg_gemv(sbie_ctx* c, const double* V, int k, long long ld, const do
                      const int* d_node_prob, double* w, long long n3);
 cudaError_t seg_scale(sbie_ctx* c, const double* x, const double* d_scale, const int* d_node_prob, double* y,
                       long long n3);
+// krylov.cu (device-resident GMRES restart cycle)
+cudaError_t arnoldi_cycle_init(sbie_ctx* c, const ArnoldiDev& A);
+cudaError_t arnoldi_copy_k(sbie_ctx* c, const ArnoldiDev& A, const double* V, long long n3, double* dst);
+cudaError_t arnoldi_orthogonalise(sbie_ctx* c, const ArnoldiDev& A, double* V, long long n3, const long long* d_seg,
+                                  const int* d_node_prob);
+cudaError_t arnoldi_step_end(sbie_ctx* c, const ArnoldiDev& A, double* V, long long n3, const int* d_node_prob,
+                             cudaGraphConditionalHandle cond, bool has_cond);
+cudaError_t arnoldi_finish(sbie_ctx* c, const ArnoldiDev& A, const double* V, long long n3, const int* d_node_prob,
+                           double* out);
 
 }  // namespace sbie

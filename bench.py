@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-precond", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="step each GMRES iteration from the host instead of one CUDA graph per restart cycle")
     ap.add_argument("--pair-samples", type=int, default=4096,
                     help="two-sphere configurations the pair network is trained on")
     return ap.parse_args()
@@ -166,6 +168,55 @@ def precond_compare(sb, torch, w, prec, stream, vel, om, F_ref, base, samples):
     return out
 
 
+def graph_compare(sb, torch, wl, w, prec, stream, vel, om, F_ref, t_graph):
+    """Time-to-solve with each GMRES iteration stepped from the host, against
+    the graph-launched cycles of the timed solves; and both on the small
+    8-sphere mobility problem, where launch and synchronisation overhead
+    dominate."""
+    out = {}
+    p = w["p"]
+    o = sb.make_opts(p, prec=prec, tol=w["tol"], mem_kind=1, stream=stream.cuda_stream, graphs=False)
+    ctx = sb.sphere_bie_create(w["centres"], w["radii"], o)
+    if prec == sb.SBIE_MIXED:
+        sb.sphere_bie_autotune(ctx, "resistance")
+    F = torch.zeros_like(F_ref)
+    T = torch.zeros_like(F_ref)
+    sb.sphere_bie_solve_resistance(ctx, vel, om, w["u0"], w["G"], F, T)
+    ts = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = sb.sphere_bie_solve_resistance(ctx, vel, om, w["u0"], w["G"], F, T)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    sb.sphere_bie_destroy(ctx)
+    out[WORKLOAD] = {"graph_s": t_graph, "host_stepped_s": statistics.mean(ts), "iters_host_stepped": info["iters"]}
+    m8 = wl.mobility_8()
+    dev = F_ref.device
+    f8 = torch.tensor(m8["forces"], dtype=torch.float64, device=dev)
+    t8 = torch.tensor(m8["torques"], dtype=torch.float64, device=dev)
+    v8, w8 = torch.zeros_like(f8), torch.zeros_like(t8)
+    res = {}
+    for graphs in (True, False):
+        o = sb.make_opts(m8["p"], prec=sb.SBIE_FP64, tol=m8["tol"], mem_kind=1, stream=stream.cuda_stream,
+                         graphs=graphs)
+        ctx = sb.sphere_bie_create(m8["centres"], m8["radii"], o)
+        sb.sphere_bie_solve_mobility(ctx, f8, t8, v8, w8)
+        ts = []
+        for _ in range(10):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = sb.sphere_bie_solve_mobility(ctx, f8, t8, v8, w8)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        sb.sphere_bie_destroy(ctx)
+        res[graphs] = (statistics.median(ts), info)
+    out["mobility_8"] = {"graph_s": res[True][0], "host_stepped_s": res[False][0], "iters": res[True][1]["iters"],
+                         "graph_cycles": res[True][1]["graph_cycles"],
+                         "kernels_per_solve": res[True][1]["kernel_launches"]}
+    return out
+
+
 def cpu_baseline(n_sample=8):
     """Time the oracle as it stands on this host on a bounded sample of the
     workload: the resistance operator on n_sample target spheres (self, far
@@ -254,7 +305,7 @@ def main():
     n, p = len(w["radii"]), w["p"]
     prec = sb.SBIE_MIXED if args.prec == "mixed" else sb.SBIE_FP64
     stream = torch.cuda.Stream()
-    opts = sb.make_opts(p, prec=prec, tol=w["tol"], mem_kind=1, stream=stream.cuda_stream)
+    opts = sb.make_opts(p, prec=prec, tol=w["tol"], mem_kind=1, stream=stream.cuda_stream, graphs=not args.no_graphs)
     t_c0 = time.perf_counter()
     ctx = sb.sphere_bie_create(w["centres"], w["radii"], opts)
     t_create = time.perf_counter() - t_c0
@@ -282,28 +333,41 @@ def main():
     sampler = ClockSampler(smi_index)
     sampler.start()
     time.sleep(0.5)
-    sb.sphere_bie_profile(ctx, 1)
-    times = []
+
+    def timed(n):
+        ts, inf = [], []
+        for _ in range(n):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            info = step()
+            with torch.cuda.stream(stream):
+                e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+            inf.append(info)
+        return ts, inf
+
     t_wall0 = time.time()
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        info = step()
-        with torch.cuda.stream(stream):
-            e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1) / 1e3)
-        infos.append(info)
+    times, timed_infos = timed(args.steps)
     torch.cuda.synchronize()
     t_wall1 = time.time()
-    prof = sb.sphere_bie_profile_read(ctx)
-    sb.sphere_bie_profile(ctx, 0)
+    infos += timed_infos
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
     t_step = statistics.mean(times)
+    launches_timed = sum(i["kernel_launches"] for i in timed_infos)
+    # Per-stage and per-kernel times come from the same solves run again with
+    # profiling on: CUDA events cannot be recorded inside the graph launches
+    # of the timed solves, so profiled solves step the same device iteration
+    # from the host (same kernels and launch configurations).
+    sb.sphere_bie_profile(ctx, 1)
+    prof_times, _ = timed(args.steps)
+    torch.cuda.synchronize()
+    prof = sb.sphere_bie_profile_read(ctx)
+    sb.sphere_bie_profile(ctx, 0)
     if world > 1:
         tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -398,7 +462,8 @@ def main():
         else:
             cpu = {"error": cb.get("error")}
 
-    launches_per_step = prof["kernel_launches"] / args.steps
+    graphs_cmp = None if args.no_graphs else graph_compare(sb, torch, wl, w, prec, stream, vel, om, F, t_step)
+    launches_per_step = launches_timed / args.steps
     if rank == 0:
         line = {
             "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -412,8 +477,14 @@ def main():
                       "create_s": t_create, "autotune_s": t_tune, "far_tiling": tuning},
             "roofline": roof, "far_field": far, "stage_ms_per_step": stage_ms, "fp64_path": fp64,
             "pair_preconditioner": pre,
-            "clocks": clocks, "gpu_launches": int(prof["kernel_launches"]),
+            "clocks": clocks, "gpu_launches": int(launches_timed),
             "gpu_launches_per_step": launches_per_step,
+            "timed_solves": {"gmres_cycles_as_cuda_graphs": not args.no_graphs,
+                             "graph_cycles_per_step": sum(i["graph_cycles"] for i in timed_infos) / args.steps},
+            "profiled_solves": {"steps": args.steps, "mean_s": statistics.mean(prof_times),
+                                "note": "stage and kernel times (roofline, far_field, stage_ms_per_step) come from "
+                                        "these host-stepped solves with CUDA events per stage"},
+            "graphs_vs_host_stepped": graphs_cmp,
             "e2e": ({"value": statistics.mean(e2e_times), "unit": "s", "h2d_bytes_per_step": h2d,
                      "d2h_bytes_per_step": d2h, "includes": "create + solve + destroy, host buffers"}
                     if e2e_times else None),

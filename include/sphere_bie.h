@@ -92,6 +92,7 @@ typedef struct {
     double t_solve_ms;      /* wall time of this solve call                                    */
     long long n_near_pairs; /* directed close pairs (i, k)                                     */
     int graph_cycles;       /* restart cycles that ran as one CUDA graph launch each            */
+    long long kernel_launches; /* kernels this call executed (those inside graphs included)     */
 } sbie_solve_info;
 
 /* Fills *opts with defaults: p = 8, eta = 1, FP64, tol = 1e-8, restart = 60,

@@ -8,6 +8,7 @@
 #include <functional>
 #include <atomic>
 #include <map>
+#include <thread>
 #include <utility>
 #include <mutex>
 #include <new>
@@ -379,6 +380,12 @@ std::vector<std::pair<sbie_ctx*, long long>> launch_counters(const Sys& S) {
     for (sbie_ctx* q : S.parts)
         if (q != S.top) v.push_back({q, q->n_launch});
     return v;
+}
+
+long long total_launches(const Sys& S) {
+    long long t = 0;
+    for (auto& pr : launch_counters(S)) t += pr.second;
+    return t;
 }
 
 // One Arnoldi iteration of the device-resident cycle (krylov.cu): w = A V_k
@@ -1011,6 +1018,20 @@ void rotate_block(const std::vector<double>& Rinv, const double* B, const std::v
         }
 }
 
+// f(begin, end) over [0, n) split across the host's cores.
+template <typename F>
+void parallel_for(int n, F f) {
+    const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const int nt = std::max(1, std::min(hw, n / 16));
+    if (nt == 1) {
+        f(0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int i = 0; i < nt; ++i) th.emplace_back(f, (int)((long long)n * i / nt), (int)((long long)n * (i + 1) / nt));
+    for (auto& t : th) t.join();
+}
+
 void pair_frame(const double* cs, const double* ct, double Q[9], double* dist) {
     double u[3] = {ct[0] - cs[0], ct[1] - cs[1], ct[2] - cs[2]};
     double d = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
@@ -1189,17 +1210,20 @@ sbie_status precond_setup(sbie_ctx* c, int kind, const PairNet* net) {
         }
         std::vector<double> Bp;
         CKS(net_blocks(*net, X, Bp));
-        std::vector<double> R, Ri;
-        for (int q = 0; q < np; ++q)
-            for (int dir = 0; dir < 2; ++dir) {
-                const double* Q = &Qs[(2 * q + dir) * 9];
+        // pair frame -> lab frame, each direction independent: host threads
+        parallel_for(2 * np, [&](int t0, int t1) {
+            std::vector<double> R, Ri;
+            for (int t = t0; t < t1; ++t) {
+                const int q = t / 2, dir = t % 2;
+                const double* Q = &Qs[(size_t)t * 9];
                 double Qt[9];
                 for (int r = 0; r < 3; ++r)
                     for (int s = 0; s < 3; ++s) Qt[3 * r + s] = Q[3 * s + r];
                 lowmode_rotation(Q, R);
                 lowmode_rotation(Qt, Ri);
-                rotate_block(Ri, Bp.data() + (2 * q + dir) * blk, R, (dir == 0 ? Bba : Bab).data() + q * blk);
+                rotate_block(Ri, Bp.data() + (size_t)t * blk, R, (dir == 0 ? Bba : Bab).data() + q * blk);
             }
+        });
     }
     // pair systems [[L_a, B_ab], [B_ba, L_b]] and own blocks, inverted in FP32
     std::vector<float> A((size_t)std::max(1, np) * 4 * blk), S((size_t)n * blk);
@@ -1490,6 +1514,7 @@ sbie_status sphere_bie_solve_mobility(sbie_ctx* c, const double* forces, const d
     if (!forces || !torques || !vel || !omega) return fail(c, SBIE_ERR_ARG, "NULL argument");
     auto t0 = std::chrono::steady_clock::now();
     Sys S = sys_of(c);
+    const long long launches0 = total_launches(S);
     const long long n3 = S.n3;
     double* dF = c->d_small;
     double* dT = dF + 3 * c->n;
@@ -1524,6 +1549,7 @@ sbie_status sphere_bie_solve_mobility(sbie_ctx* c, const double* forces, const d
     CK(cudaStreamSynchronize(c->stream));
     inf.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     inf.t_setup_ms = c->t_create_ms;
+    inf.kernel_launches = total_launches(S) - launches0;
     if (info) *info = inf;
     return st;
 }
@@ -1536,6 +1562,7 @@ sbie_status sphere_bie_solve_resistance(sbie_ctx* c, const double* vel, const do
     if (bg_grad && !finite_all(bg_grad, 9)) return fail(c, SBIE_ERR_ARG, "non-finite velocity gradient");
     auto t0 = std::chrono::steady_clock::now();
     Sys S = sys_of(c);
+    const long long launches0 = total_launches(S);
     double* dv = c->d_small;
     double* dw = dv + 3 * c->n;
     double* dF = dw + 3 * c->n;
@@ -1568,6 +1595,7 @@ sbie_status sphere_bie_solve_resistance(sbie_ctx* c, const double* vel, const do
     CK(cudaStreamSynchronize(c->stream));
     inf.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     inf.t_setup_ms = c->t_create_ms;
+    inf.kernel_launches = total_launches(S) - launches0;
     if (info) *info = inf;
     return st;
 }

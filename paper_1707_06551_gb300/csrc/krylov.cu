@@ -4,8 +4,9 @@
 // with the Krylov index k held in device memory.  One iteration is captured
 // once as the body of a CUDA graph WHILE node; the advance kernel sets the
 // node's condition, so a whole cycle is one graph launch with no host round
-// trip per iteration.  The arithmetic is that of the host-driven cycle in
-// api.cu (same kernels for the dots and updates, same order of operations).
+// trip per iteration.  Without a graph (profiling, or use_graphs = 0) the
+// host enqueues the same kernels one iteration at a time and reads the
+// continue flag after each, so both drivers compute the same iterates.
 #include <cmath>
 
 #include "common.h"
@@ -14,7 +15,7 @@ namespace sbie {
 
 namespace {
 
-constexpr int kSt = 4;  // st[0] = k, st[1] = iteration limit of the cycle, st[2] = continue, st[3] = error
+// st[0] = k, st[1] = iteration limit of the cycle, st[2] = continue, st[3] = non-finite flag
 
 __global__ void cycle_init_kernel(ArnoldiDev A) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;

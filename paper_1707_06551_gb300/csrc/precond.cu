@@ -43,23 +43,6 @@ std::vector<Mode> low_modes() {
     return out;
 }
 
-// Normalised Pbar_n^m(t) (no Condon-Shortley phase) for n <= nmax at one
-// point, by the normalised three-term recurrence; P[m * (nmax+1) + n].
-void pbar(int nmax, double t, double s, std::vector<double>& P) {
-    P.assign((nmax + 1) * (nmax + 1), 0.0);
-    double pmm = 1.0 / std::sqrt(4.0 * kPi);
-    for (int m = 0; m <= nmax; ++m) {
-        if (m > 0) pmm *= std::sqrt((2.0 * m + 1.0) / (2.0 * m)) * s;
-        P[m * (nmax + 1) + m] = pmm;
-        if (m + 1 <= nmax) P[m * (nmax + 1) + m + 1] = std::sqrt(2.0 * m + 3.0) * t * pmm;
-        for (int n = m + 2; n <= nmax; ++n) {
-            double a = std::sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
-            double b = std::sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
-            P[m * (nmax + 1) + n] = a * (t * P[m * (nmax + 1) + n - 1] - b * P[m * (nmax + 1) + n - 2]);
-        }
-    }
-}
-
 }  // namespace
 
 // Low-mode synthesis ZS [npn][3][73] and analysis ZA [73][npn][3] on the grid
@@ -131,75 +114,118 @@ void lowmode_tables(int p, std::vector<double>& ZS, std::vector<double>& ZA) {
 // Real low-mode rotation R (73 x 73): coefficients of the field in the frame
 // whose axes are the columns of Q, a' = R a.  Block diagonal in (type, n) with
 // the scalar rotation of degree n, computed by resampling Y o Q on the grid of
-// order 4 (exact: Y o Q has degree n).
-void lowmode_rotation(const double Q[9], std::vector<double>& R) {
-    const int L = kPrecL, NM = kLowModes;
-    const int p = L;
-    TabLayout tl = tab_layout(p);
-    std::vector<double> tab;
-    build_tables(p, tab);
-    // scalar real basis values psi_(n, m, part)(y) at rotated nodes Q y'_j and
-    // at the nodes y'_j; coefficient index within degree n: m = 0 -> 0,
-    // m >= 1 -> 2m - 1 (re), 2m (im)
-    R.assign((size_t)NM * NM, 0.0);
-    std::vector<double> D[kPrecL + 1];
-    for (int n = 0; n <= L; ++n) D[n].assign((size_t)(2 * n + 1) * (2 * n + 1), 0.0);
-    std::vector<double> P;
-    for (int j = 0; j < tl.nlat; ++j)
-        for (int k = 0; k < tl.nlon; ++k) {
-            const double ct = tab[tl.o_ct + j], st = tab[tl.o_st + j], cp = tab[tl.o_cph + k], sp = tab[tl.o_sph + k];
-            const double w = tab[tl.o_w + j];
-            const double y[3] = {st * cp, st * sp, ct};
-            double x[3];
-            for (int a = 0; a < 3; ++a) x[a] = Q[3 * a + 0] * y[0] + Q[3 * a + 1] * y[1] + Q[3 * a + 2] * y[2];
-            const double rho = std::sqrt(x[0] * x[0] + x[1] * x[1]);
-            const double cpx = rho > 0 ? x[0] / rho : 1.0, spx = rho > 0 ? x[1] / rho : 0.0;
-            std::vector<double> Pn;
-            pbar(L, x[2], rho, P);
-            pbar(L, ct, st, Pn);
-            for (int n = 0; n <= L; ++n) {
-                const int d = 2 * n + 1;
-                // values of the real basis at x (rotated) and conjugate-projection weights at y
-                std::vector<double> vx(d), ry(d), iy(d);
-                for (int m = 0; m <= n; ++m) {
-                    const double cmx = std::cos(m * std::atan2(spx, cpx)), smx = std::sin(m * std::atan2(spx, cpx));
-                    const double Px = P[m * (L + 1) + n];
-                    const double cmy = std::cos(m * std::atan2(sp, cp)), smy = std::sin(m * std::atan2(sp, cp));
-                    const double Py = Pn[m * (L + 1) + n];
-                    if (m == 0) {
-                        vx[0] = Px;
-                        ry[0] = Py;
-                        iy[0] = 0.0;
-                    } else {
-                        vx[2 * m - 1] = 2.0 * Px * cmx;   // 2 Re Y
-                        vx[2 * m] = -2.0 * Px * smx;      // -2 Im Y
-                        ry[2 * m - 1] = Py * cmy;         // Re Y(y)
-                        iy[2 * m - 1] = Py * smy;         // Im Y(y)
-                    }
-                }
-                // coefficient of psi_nu: Re c_nm = sum w f Re Y, Im c_nm = -sum w f Im Y
-                for (int mu = 0; mu < d; ++mu) {
-                    const double f = vx[mu];
+// order 4 (exact: Y o Q has degree n).  The grid, its weights and the
+// projections onto the real basis at the grid nodes do not depend on Q and
+// are computed once.
+namespace {
+
+constexpr int kRL = kPrecL, kRLat = kRL + 1, kRLon = 2 * kRL + 2, kRNodes = kRLat * kRLon;
+constexpr int kRSh = (kRL + 1) * (kRL + 1);
+
+// Normalised Pbar_n^m(t) (no Condon-Shortley phase), n <= 4, at one point by
+// the normalised three-term recurrence; P[m (L+1) + n].
+void pbar_fixed(double t, double s, double* P) {
+    for (int i = 0; i < kRSh; ++i) P[i] = 0.0;
+    double pmm = 1.0 / std::sqrt(4.0 * kPi);
+    for (int m = 0; m <= kRL; ++m) {
+        if (m > 0) pmm *= std::sqrt((2.0 * m + 1.0) / (2.0 * m)) * s;
+        P[m * (kRL + 1) + m] = pmm;
+        if (m + 1 <= kRL) P[m * (kRL + 1) + m + 1] = std::sqrt(2.0 * m + 3.0) * t * pmm;
+        for (int n = m + 2; n <= kRL; ++n) {
+            double a = std::sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
+            double b = std::sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
+            P[m * (kRL + 1) + n] = a * (t * P[m * (kRL + 1) + n - 1] - b * P[m * (kRL + 1) + n - 2]);
+        }
+    }
+}
+
+struct RotGrid {
+    double y[kRNodes][3];
+    // w * (projection weight of real coefficient `row` of degree n) at node q:
+    // row 0: Y_n0, 2m-1: Re Y_nm, 2m: -Im Y_nm
+    double proj[kRL + 1][2 * kRL + 1][kRNodes];
+};
+
+const RotGrid& rot_grid() {
+    static const RotGrid G = [] {
+        RotGrid g{};
+        TabLayout tl = tab_layout(kRL);
+        std::vector<double> tab;
+        build_tables(kRL, tab);
+        double P[kRSh];
+        for (int j = 0; j < tl.nlat; ++j)
+            for (int k = 0; k < tl.nlon; ++k) {
+                const int q = j * tl.nlon + k;
+                const double ct = tab[tl.o_ct + j], st = tab[tl.o_st + j], cp = tab[tl.o_cph + k], sp = tab[tl.o_sph + k];
+                const double w = tab[tl.o_w + j];
+                g.y[q][0] = st * cp;
+                g.y[q][1] = st * sp;
+                g.y[q][2] = ct;
+                pbar_fixed(ct, st, P);
+                const double phi = std::atan2(sp, cp);
+                for (int n = 0; n <= kRL; ++n)
                     for (int m = 0; m <= n; ++m) {
+                        const double Py = P[m * (kRL + 1) + n];
                         if (m == 0) {
-                            D[n][0 * d + mu] += w * f * ry[0];
+                            g.proj[n][0][q] = w * Py;
                         } else {
-                            D[n][(2 * m - 1) * d + mu] += w * f * ry[2 * m - 1];
-                            D[n][(2 * m) * d + mu] += -w * f * iy[2 * m - 1];
+                            g.proj[n][2 * m - 1][q] = w * Py * std::cos(m * phi);
+                            g.proj[n][2 * m][q] = -w * Py * std::sin(m * phi);
                         }
                     }
-                }
+            }
+        return g;
+    }();
+    return G;
+}
+
+}  // namespace
+
+void lowmode_rotation(const double Q[9], std::vector<double>& R) {
+    const RotGrid& G = rot_grid();
+    const int NM = kLowModes;
+    // D[n][row][mu]: coefficient `row` of the rotated real basis function mu
+    double D[kRL + 1][2 * kRL + 1][2 * kRL + 1] = {};
+    double P[kRSh], vx[2 * kRL + 1];
+    for (int q = 0; q < kRNodes; ++q) {
+        const double* y = G.y[q];
+        double x[3];
+        for (int a = 0; a < 3; ++a) x[a] = Q[3 * a + 0] * y[0] + Q[3 * a + 1] * y[1] + Q[3 * a + 2] * y[2];
+        const double rho = std::sqrt(x[0] * x[0] + x[1] * x[1]);
+        const double cpx = rho > 0 ? x[0] / rho : 1.0, spx = rho > 0 ? x[1] / rho : 0.0;
+        pbar_fixed(x[2], rho, P);
+        // cos / sin (m phi_x) by the angle-addition recurrence
+        double cm[kRL + 1], sm[kRL + 1];
+        cm[0] = 1.0;
+        sm[0] = 0.0;
+        for (int m = 1; m <= kRL; ++m) {
+            cm[m] = cm[m - 1] * cpx - sm[m - 1] * spx;
+            sm[m] = sm[m - 1] * cpx + cm[m - 1] * spx;
+        }
+        for (int n = 0; n <= kRL; ++n) {
+            const int d = 2 * n + 1;
+            // values at x of the real basis: Y_n0, 2 Re Y_nm, -2 Im Y_nm
+            vx[0] = P[n];
+            for (int m = 1; m <= n; ++m) {
+                const double Px = P[m * (kRL + 1) + n];
+                vx[2 * m - 1] = 2.0 * Px * cm[m];
+                vx[2 * m] = -2.0 * Px * sm[m];
+            }
+            for (int row = 0; row < d; ++row) {
+                const double pr = G.proj[n][row][q];
+                for (int mu = 0; mu < d; ++mu) D[n][row][mu] += pr * vx[mu];
             }
         }
-    // scatter into R: same D_n for V, W, X
-    const std::vector<Mode> modes = low_modes();
+    }
+    // scatter into R: the same D_n for V, W, X
+    R.assign((size_t)NM * NM, 0.0);
+    static const std::vector<Mode> modes = low_modes();
     auto sub = [](const Mode& md) { return md.m == 0 ? 0 : (md.part == 0 ? 2 * md.m - 1 : 2 * md.m); };
     for (int a = 0; a < NM; ++a)
         for (int b = 0; b < NM; ++b) {
             const Mode &ma = modes[a], &mb = modes[b];
             if (ma.t != mb.t || ma.n != mb.n) continue;
-            const int d = 2 * ma.n + 1;
-            R[(size_t)a * NM + b] = D[ma.n][sub(ma) * d + sub(mb)];
+            R[(size_t)a * NM + b] = D[ma.n][sub(ma)][sub(mb)];
         }
 }
 

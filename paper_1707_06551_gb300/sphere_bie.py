@@ -35,7 +35,7 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("rel_residual_true", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
                 ("t_solve_ms", ctypes.c_double), ("n_near_pairs", ctypes.c_longlong),
-                ("graph_cycles", ctypes.c_int)]
+                ("graph_cycles", ctypes.c_int), ("kernel_launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1621,9 +1621,9 @@ sbie_status tune_one(sbie_ctx* c, Kern k, int mode, sbie_far_tuning* chosen) {
     struct Cand { FarTune t; float ms; };
     std::vector<Cand> cands;
     const bool f32 = mode == kModeF32;
-    const int tpts32[2] = {2, 4}, tpts1[1] = {1};
+    const int tpts32[3] = {2, 4, 6}, tpts1[1] = {1};
     const int* tpts = f32 ? tpts32 : tpts1;
-    const int ntpt = f32 ? 2 : 1;
+    const int ntpt = f32 ? 3 : 1;
     const int ths32[5] = {64, 96, 128, 192, 256}, thsdf[3] = {64, 128, 256};
     const int* ths = f32 ? ths32 : thsdf;
     const int nth = f32 ? 5 : 3;

@@ -84,7 +84,9 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 // source) pairs.  Each staged source is stored pre-duplicated in shared memory
 // ({-x, -x, -y, -y}, {-z, -z, fx, fx}, {fy, fy, fz, fz} and, for D, the source
 // normal {nx, nx, ny, ny}, {nz, nz, 0, 0}), so every packed operand comes from
-// one 128-bit shared-memory broadcast.
+// one 128-bit shared-memory broadcast.  The compensated running sums live in
+// shared memory (touched once per tile), which keeps the registers for the
+// pair loop and lets more warps share each SM.
 template <int OP, int NP>
 __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
     constexpr int NV = (OP == (int)Kern::D) ? 5 : 3;  // float4 per staged source
@@ -93,7 +95,9 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
     const int split = blockIdx.y;
     const int tid = threadIdx.x, bd = blockDim.x;
     extern __shared__ float4 smem4[];
-    unsigned* flags = reinterpret_cast<unsigned*>(smem4 + NV * a.tile);
+    // [tile][NV] staged sources | [TPT][3][2][bd] running sums and compensations | sphere flags
+    float* run = reinterpret_cast<float*>(smem4 + NV * a.tile);
+    unsigned* flags = reinterpret_cast<unsigned*>(run + TPT * 6 * bd);
     build_flags(a, sphere, flags);
 
     const double cx = a.c[3 * sphere], cy = a.c[3 * sphere + 1], cz = a.c[3 * sphere + 2];
@@ -101,14 +105,10 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
     const float clx = (float)(cx - (double)chx), cly = (float)(cy - (double)chy), clz = (float)(cz - (double)chz);
 
     float2 tx[NP], ty[NP], tz[NP], tnx[NP], tny[NP], tnz[NP];
-    long long tnode[TPT];
-    bool tval[TPT];
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
-        int q = chunk * (bd * TPT) + t * bd + tid;
-        tval[t] = q < a.npn;
-        long long node = (long long)sphere * a.npn + (tval[t] ? q : a.npn - 1);
-        tnode[t] = node;
+        const int q = chunk * (bd * TPT) + t * bd + tid;
+        const long long node = (long long)sphere * a.npn + (q < a.npn ? q : a.npn - 1);
         float4 h = a.xhi[node], l = a.xlo[node];
         float px = (h.x - chx) + (l.x - clx), py = (h.y - chy) + (l.y - cly), pz = (h.z - chz) + (l.z - clz);
         float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -121,11 +121,8 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
             tnx[t >> 1].x = nn.x; tny[t >> 1].x = nn.y; tnz[t >> 1].x = nn.z;
         }
     }
-    float sum[TPT][3], cmp[TPT][3];
 #pragma unroll
-    for (int t = 0; t < TPT; ++t)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) sum[t][d] = cmp[t][d] = 0.f;
+    for (int e = 0; e < TPT * 6; ++e) run[e * bd + tid] = 0.f;
 
     long long b0, b1;
     source_range(a, sphere, split, b0, b1);
@@ -213,17 +210,27 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
 #pragma unroll
         for (int t = 0; t < NP; ++t)
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                neumaier(sum[2 * t][d], cmp[2 * t][d], acc[t][d].x);
-                neumaier(sum[2 * t + 1][d], cmp[2 * t + 1][d], acc[t][d].y);
-            }
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float* sp = run + (((2 * t + h) * 3 + d) * 2) * bd + tid;
+                    float sm = sp[0], cm = sp[bd];
+                    neumaier(sm, cm, h ? acc[t][d].y : acc[t][d].x);
+                    sp[0] = sm;
+                    sp[bd] = cm;
+                }
     }
     double* out = a.part + (size_t)split * a.N * 3;
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
-        if (!tval[t]) continue;
+        const int q = chunk * (bd * TPT) + t * bd + tid;
+        if (q >= a.npn) continue;
+        const long long node = (long long)sphere * a.npn + q;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) out[tnode[t] * 3 + d] = (double)sum[t][d] + (double)cmp[t][d];
+        for (int d = 0; d < 3; ++d) {
+            const float* sp = run + ((t * 3 + d) * 2) * bd + tid;
+            out[node * 3 + d] = (double)sp[0] + (double)sp[bd];
+        }
     }
 }
 
@@ -538,19 +545,22 @@ static cudaError_t launch_far_t(sbie_ctx* c, const FarTune& tu, bool f32, const 
     size_t words = ((c->n + 31) / 32) * sizeof(unsigned);
     if (f32) {
         const int nv32 = (OP == (int)Kern::D) ? 5 : 3;
-        size_t sm = (size_t)nv32 * tu.tile * sizeof(float4) + words;
+        const int tpt32 = 2 * ((TPT + 1) / 2);
+        size_t sm = (size_t)nv32 * tu.tile * sizeof(float4) + (size_t)tpt32 * 6 * tu.threads * sizeof(float) + words;
         if (sm > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(far_f32_kernel<OP, (TPT + 1) / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
         }
         far_f32_kernel<OP, (TPT + 1) / 2><<<grid, tu.threads, sm, c->stream>>>(a); ++c->n_launch;
-    } else {
+    } else if constexpr (TPT <= 4) {  // the FP64 kernel holds at most 4 targets per thread
         size_t sm = (size_t)nv * tu.tile * sizeof(double4) + words;
         if (sm > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(far_f64_kernel<OP, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
         }
         far_f64_kernel<OP, TPT><<<grid, tu.threads, sm, c->stream>>>(a); ++c->n_launch;
+    } else {
+        return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
@@ -560,6 +570,7 @@ static cudaError_t launch_far_op(sbie_ctx* c, const FarTune& tu, bool f32, const
     switch (tu.tpt) {
         case 1: return launch_far_t<OP, 1>(c, tu, f32, a);
         case 2: return launch_far_t<OP, 2>(c, tu, f32, a);
+        case 6: return f32 ? launch_far_t<OP, 6>(c, tu, true, a) : cudaErrorInvalidValue;
         default: return launch_far_t<OP, 4>(c, tu, f32, a);
     }
 }

@@ -51,7 +51,11 @@ typedef enum {
     SBIE_MIXED = 1,   /* GMRES on an operator whose far field and close-pair
                          evaluation run in FP32 (compensated accumulation), inside
                          iterative refinement on the FP64-accurate operator of
-                         SBIE_FP64_DF; tables, coefficients and Arnoldi in FP64      */
+                         SBIE_FP64_DF; tables, coefficients and Arnoldi in FP64.
+                         The first residual is b - A x with the FP64-accurate
+                         operator; a later one is r - A d with the FP32 operator
+                         when 2e-5 ||d|| <= 0.1 tol ||x|| (2e-5 bounds the FP32
+                         operator's relative error), else again b - A x.          */
     SBIE_FP64_DF = 2  /* FP64-accurate operator whose far-field pair arithmetic is
                          double-float (a value = sum of two FP32 numbers, about 48
                          significant bits; ~1e-13 relative); everything else FP64   */
@@ -93,6 +97,8 @@ typedef struct {
     long long n_near_pairs; /* directed close pairs (i, k)                                     */
     int graph_cycles;       /* restart cycles that ran as one CUDA graph launch each            */
     long long kernel_launches; /* kernels this call executed (those inside graphs included)     */
+    int fp32_residual_updates; /* SBIE_MIXED: residuals formed as r - A d with the FP32 operator
+                                  because the correction d was small enough (see solve_resistance) */
 } sbie_solve_info;
 
 /* Fills *opts with defaults: p = 8, eta = 1, FP64, tol = 1e-8, restart = 60,
@@ -264,6 +270,11 @@ sbie_status sphere_bie_train_pair_network(const sbie_pair_train_opts* opts, cons
  * source column) of the resistance operator, grid order p. */
 sbie_status sphere_bie_pair_blocks(int n, const double* dist, const double* a_src, const double* a_tgt, int p,
                                    double* blocks);
+
+/* Density of the last solve on ctx, at the nodes in sphere_bie_nodes order
+ * ([N][3], memory kind of the context): psi of Eq. 5.19 after a resistance
+ * solve, mu of Eq. 5.8 after a mobility solve.  SBIE_ERR_ARG before any solve. */
+sbie_status sphere_bie_solution_density(sbie_ctx* ctx, double* density);
 
 /* Pair preconditioner of a context: kind (0 none, 1 network, 2 exact),
  * undirected pairs in the pair systems, close pairs left out because they lie

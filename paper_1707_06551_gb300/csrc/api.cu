@@ -580,6 +580,10 @@ sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const 
 // system at once.  SBIE_FP64 / SBIE_FP64_DF: GMRES on the FP64-accurate
 // operator.  SBIE_MIXED: iterative refinement -- residuals b - A x with the
 // FP64-accurate operator, corrections by GMRES on the FP32 operator.
+// Bound on the FP32 operator's relative error (the mixed-precision apply
+// parity bound) used to decide when a residual may be updated in FP32.
+constexpr double kFp32OpErr = 2e-5;
+
 sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_solve_info* info) {
     sbie_ctx* c = S.top;
     const long long n3 = S.n3;
@@ -642,8 +646,29 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
             inf.restarts += go.restarts;
             inf.graph_cycles += go.graph_cycles;
             CK(blas_axpy(c, 1.0, d, x, n3));
-            CKS(A64(x, r));
-            CK(blas_lincomb(c, 1.0, b, -1.0, r, r, n3));
+            // New residual.  After the first correction it is r - A d by
+            // linearity, and A d may use the FP32 operator when the
+            // correction is small: its error is at most eps32 ||d|| / ||x||
+            // relative to ||b|| (eps32 = 2e-5 bounds the FP32 operator's
+            // relative error), kept below a tenth of the tolerance; otherwise
+            // r = b - A x with the FP64-accurate operator.
+            bool cheap = outers > 0;
+            if (cheap) {
+                std::vector<double> dn, xn;
+                CKS(seg_norms(S, d, dn));
+                CKS(seg_norms(S, x, xn));
+                for (int p = 0; p < P; ++p)
+                    if (dn[p] > 0.0 && !(kFp32OpErr * dn[p] <= 0.1 * tol * xn[p])) cheap = false;
+            }
+            if (cheap) {
+                double* t = c->d_out;  // not used by the solve's callers until it returns
+                CKS(A32(d, t));
+                CK(blas_axpy(c, -1.0, t, r, n3));
+                ++inf.fp32_residual_updates;
+            } else {
+                CKS(A64(x, r));
+                CK(blas_lincomb(c, 1.0, b, -1.0, r, r, n3));
+            }
             std::vector<double> rn;
             CKS(seg_norms(S, r, rn));
             for (int p = 0; p < P; ++p) {
@@ -1549,6 +1574,7 @@ sbie_status sphere_bie_solve_mobility(sbie_ctx* c, const double* forces, const d
     CK(cudaStreamSynchronize(c->stream));
     inf.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     inf.t_setup_ms = c->t_create_ms;
+    c->has_solution = true;
     inf.kernel_launches = total_launches(S) - launches0;
     if (info) *info = inf;
     return st;
@@ -1595,6 +1621,7 @@ sbie_status sphere_bie_solve_resistance(sbie_ctx* c, const double* vel, const do
     CK(cudaStreamSynchronize(c->stream));
     inf.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     inf.t_setup_ms = c->t_create_ms;
+    c->has_solution = true;
     inf.kernel_launches = total_launches(S) - launches0;
     if (info) *info = inf;
     return st;
@@ -1757,6 +1784,15 @@ sbie_status sphere_bie_profile_read(sbie_ctx* c, sbie_profile* out) {
         out->far_pairs_f64 += q->prof.pairs_f64;
         out->kernel_launches += q->n_launch - q->prof.kernels0;
     }
+    return SBIE_OK;
+}
+
+sbie_status sphere_bie_solution_density(sbie_ctx* c, double* density) {
+    if (!c) return SBIE_ERR_ARG;
+    if (!density) return fail(c, SBIE_ERR_ARG, "NULL density");
+    if (!c->has_solution) return fail(c, SBIE_ERR_ARG, "no solve has run on this context");
+    CKS(to_user(c, c->d_xsol, density, true));
+    CK(cudaStreamSynchronize(c->stream));
     return SBIE_OK;
 }
 

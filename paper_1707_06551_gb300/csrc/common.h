@@ -154,6 +154,7 @@ struct sbie_ctx {
     double* d_pz = nullptr;        // preconditioned vector (system level)
     double t_prec_setup_ms = 0.0;
     double t_create_ms = 0.0;      // wall time of create (grid, tables, close pairs, preconditioner)
+    bool has_solution = false;     // d_xsol holds the density of the last solve
 
     // host geometry
     std::vector<double> h_c, h_a;

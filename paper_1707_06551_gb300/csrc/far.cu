@@ -78,6 +78,16 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // FP32 pair kernel on packed FP32x2 arithmetic: every thread owns 2 * NP
 // targets held in float2 pairs, so one __ffma2_rn evaluates two (target,
@@ -179,12 +189,12 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
                 float2 r2 = __fmul2_rn(dx, dx);
                 r2 = __ffma2_rn(dy, dy, r2);
                 r2 = __ffma2_rn(dz, dz, r2);
-                float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-                const float2 ri2 = __fmul2_rn(ri, ri);
                 float2 rf = __fmul2_rn(dx, fx);
                 rf = __ffma2_rn(dy, fy, rf);
                 rf = __ffma2_rn(dz, fz, rf);
                 if (OP == (int)Kern::S) {
+                    float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                    const float2 ri2 = __fmul2_rn(ri, ri);
                     const float2 s3 = __fmul2_rn(__fmul2_rn(rf, ri), ri2);
                     acc[t][0] = __ffma2_rn(dx, s3, __ffma2_rn(fx, ri, acc[t][0]));
                     acc[t][1] = __ffma2_rn(dy, s3, __ffma2_rn(fy, ri, acc[t][1]));
@@ -200,7 +210,13 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
                         rn = __ffma2_rn(dy, tny[t], rn);
                         rn = __ffma2_rn(dz, tnz[t], rn);
                     }
-                    const float2 s5 = __fmul2_rn(__fmul2_rn(rf, rn), __fmul2_rn(__fmul2_rn(ri2, ri2), ri));
+                    // r^-5 = 2^(-5/2 log2 r^2) on the special-function unit:
+                    // two MUFU operations and one multiply instead of a
+                    // reciprocal square root and three multiplies
+                    float2 l2 = make_float2(lg2_approx(r2.x), lg2_approx(r2.y));
+                    l2 = __fmul2_rn(l2, make_float2(-2.5f, -2.5f));
+                    const float2 ri5 = make_float2(ex2_approx(l2.x), ex2_approx(l2.y));
+                    const float2 s5 = __fmul2_rn(__fmul2_rn(rf, rn), ri5);
                     acc[t][0] = __ffma2_rn(dx, s5, acc[t][0]);
                     acc[t][1] = __ffma2_rn(dy, s5, acc[t][1]);
                     acc[t][2] = __ffma2_rn(dz, s5, acc[t][2]);

@@ -35,7 +35,8 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("rel_residual_true", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
                 ("t_solve_ms", ctypes.c_double), ("n_near_pairs", ctypes.c_longlong),
-                ("graph_cycles", ctypes.c_int), ("kernel_launches", ctypes.c_longlong)]
+                ("graph_cycles", ctypes.c_int), ("kernel_launches", ctypes.c_longlong),
+                ("fp32_residual_updates", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -98,6 +99,7 @@ def lib():
                                                     ctypes.POINTER(PairTrainInfo)]
         L.sphere_bie_pair_blocks.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]
         L.sphere_bie_pair_network_size.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+        L.sphere_bie_solution_density.argtypes = [_P, _P]
         L.sphere_bie_precond_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
         L.sphere_bie_pair_network_gradients.argtypes = [_P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]
@@ -109,7 +111,7 @@ def lib():
                   "sphere_bie_destroy", "sphere_bie_profile", "sphere_bie_profile_read",
                   "sphere_bie_apply_layer_noalloc", "sphere_bie_autotune", "sphere_bie_train_pair_network",
                   "sphere_bie_pair_blocks", "sphere_bie_pair_network_size", "sphere_bie_pair_network_gradients",
-                  "sphere_bie_precond_info"):
+                  "sphere_bie_precond_info", "sphere_bie_solution_density"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -256,6 +258,11 @@ def sphere_bie_pair_blocks(dist, a_src, a_tgt, p):
     return out
 
 
+def sphere_bie_solution_density(ctx, out):
+    _check(ctx, lib().sphere_bie_solution_density(ctx, _ptr(out)))
+    return out
+
+
 def sphere_bie_precond_info(ctx):
     k, npairs, nd, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _check(ctx, lib().sphere_bie_precond_info(ctx, ctypes.byref(k), ctypes.byref(npairs), ctypes.byref(nd),
@@ -335,6 +342,9 @@ class SphereBIE:
 
     def nodes(self):
         return sphere_bie_nodes(self.ctx)
+
+    def density(self):
+        return sphere_bie_solution_density(self.ctx, np.zeros((self.N, 3)))
 
     def close(self):
         if self.ctx:

@@ -206,3 +206,29 @@ def test_device_pointer_interface_matches_host(sb):
         assert _err(d_out.cpu().numpy(), ref) < 1e-14
     finally:
         sb.sphere_bie_destroy(ctx)
+
+
+@pytest.mark.parametrize("tol", [1e-8, 1e-11])
+def test_mixed_residual_is_the_true_residual(sb, tol):
+    """The residual a mixed-precision solve reports (after the first
+    correction, formed as r - A d with the FP32 operator when d is small) is
+    the FP64 residual of the density it returns."""
+    c, a, p = _geom("poly_p6")
+    g = ops.Geometry(c, a, p)
+    rng = np.random.default_rng(31)
+    v, w = rng.normal(size=(g.n, 3)), rng.normal(size=(g.n, 3))
+    with sb.SphereBIE(c, a, p, prec=sb.SBIE_MIXED, tol=tol) as s:
+        F, T, info = s.resistance(v, w)
+        psi = s.density()
+        x, nrm, wq = s.nodes()
+    assert info["status"] == 0 and info["refinements"] >= 2
+    if tol == 1e-8:
+        assert info["fp32_residual_updates"] >= 1
+    b = np.zeros((g.N, 3))
+    for i in range(g.n):
+        sl = g.sl(i)
+        b[sl] = v[i] + np.cross(w[i], x[sl] - c[i])
+    with sb.SphereBIE(c, a, p, prec=sb.SBIE_FP64) as s64:
+        r = b - s64.apply("resistance", psi)
+    rel = np.linalg.norm(r) / np.linalg.norm(b)
+    assert rel <= tol and abs(rel - info["rel_residual_true"]) <= 0.1 * tol

@@ -55,8 +55,12 @@ def parse():
     ap.add_argument("--no-precond", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
                     help="step each GMRES iteration from the host instead of one CUDA graph per restart cycle")
-    ap.add_argument("--pair-samples", type=int, default=4096,
-                    help="two-sphere configurations the pair network is trained on")
+    ap.add_argument("--pair-samples", type=int, default=None,
+                    help="two-sphere configurations the pair network is trained on "
+                         "(default 4096; 100000 for dense_1024, 20000 for large_4096)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "batched_512", "dense_1024", "large_4096"],
+                    help="the other configurations print their own JSON line (not the headline)")
     return ap.parse_args()
 
 
@@ -284,6 +288,222 @@ def run_reference(args):
 REF_FP64_APPLIES = 84
 
 
+# ---- the other configurations (python bench.py --workload NAME) -------------
+
+def _timed_solves(torch, stream, fn, n):
+    """n solves timed with CUDA events on the library's stream; returns the
+    times (s) and the last solve's info."""
+    ts, info = [], None
+    for _ in range(n):
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        info = fn()
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return ts, info
+
+
+def _clocks(local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    idx = vis.split(",")[local] if vis and vis.split(",")[0].strip().isdigit() else str(local)
+    return ClockSampler(idx)
+
+
+def run_workload(args, sb, torch, wl, local):
+    if args.workload == "batched_512":
+        return run_batched(args, sb, torch, wl, local)
+    if args.workload == "dense_1024":
+        return run_dense(args, sb, torch, wl, local)
+    return run_large(args, sb, torch, wl, local)
+
+
+def run_batched(args, sb, torch, wl, local):
+    """512 independent mobility problems of uneven size and order in one
+    context: one solve advances every problem, each restart cycle one CUDA
+    graph launch, stopped problems skipped by the far field."""
+    import numpy as np
+    probs = wl.batched_512()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream()
+    cl = [q["centres"] for q in probs]
+    rl = [q["radii"] for q in probs]
+    pl = [q["p"] for q in probs]
+    F = torch.tensor(np.concatenate([q["forces"] for q in probs]), dtype=torch.float64, device=dev)
+    T = torch.tensor(np.concatenate([q["torques"] for q in probs]), dtype=torch.float64, device=dev)
+    v, om = torch.zeros_like(F), torch.zeros_like(T)
+    nodes = int(sum(len(r) * (p + 1) * (2 * p + 2) for r, p in zip(rl, pl)))
+    out = {"metric": "batched mobility time-to-solve at 1e-8 rel. residual (all problems)", "unit": "s",
+           "higher_is_better": False, "n_gpus": 1, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "batched_512", "problems": len(probs), "spheres": int(sum(len(r) for r in rl)),
+                      "nodes": nodes, "p_values": sorted(set(pl)), "precision": "mixed", "tol": 1e-8}}
+    res = {}
+    for graphs in (True, False):
+        o = sb.make_opts(pl[0], prec=sb.SBIE_MIXED, tol=1e-8, mem_kind=1, stream=stream.cuda_stream, graphs=graphs)
+        ctx = sb.sphere_bie_create_batch(cl, rl, pl, o)
+        t0 = time.perf_counter()
+        sb.sphere_bie_autotune(ctx, "mobility")
+        t_tune = time.perf_counter() - t0
+        fn = lambda: sb.sphere_bie_solve_mobility(ctx, F, T, v, om)
+        fn()  # warm-up (captures the cycle graphs)
+        sampler = _clocks(local)
+        if graphs:
+            sampler.start()
+        w0 = time.time()
+        ts, info = _timed_solves(torch, stream, fn, args.steps if graphs else 1)
+        w1 = time.time()
+        res[graphs] = {"time_to_solve_s": statistics.mean(ts), "iters": info["iters"],
+                       "refinements": info["refinements"], "rel_residual_true": info["rel_residual_true"],
+                       "graph_cycles": info["graph_cycles"], "kernel_launches": info["kernel_launches"],
+                       "autotune_s": t_tune}
+        if graphs:
+            sampler.stop()
+            out["clocks"] = sampler.summary(w0, w1)
+            sb.sphere_bie_profile(ctx, 1)
+            fn()
+            prof = sb.sphere_bie_profile_read(ctx)
+            sb.sphere_bie_profile(ctx, 0)
+            res[graphs]["stage_ms_profiled_solve"] = prof["ms"]
+            res[graphs]["far_pairs_per_s_fp32"] = (prof["far_pairs_f32"] / (prof["ms"]["far_kernel_f32"] * 1e-3)
+                                                   if prof["ms"]["far_kernel_f32"] > 0 else None)
+            vb, wb = v.clone(), om.clone()
+        sb.sphere_bie_destroy(ctx)
+    # the same problems one context at a time (no batching), graph cycles
+    t_sep, it_sep = 0.0, 0
+    for q in probs:
+        o = sb.make_opts(q["p"], prec=sb.SBIE_MIXED, tol=1e-8, mem_kind=0)
+        ctx = sb.sphere_bie_create(q["centres"], q["radii"], o)
+        vq, wq = np.zeros_like(q["forces"]), np.zeros_like(q["torques"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        iq = sb.sphere_bie_solve_mobility(ctx, q["forces"], q["torques"], vq, wq)
+        t_sep += time.perf_counter() - t0
+        it_sep = max(it_sep, iq["iters"])
+        sb.sphere_bie_destroy(ctx)
+    # FP64-accurate batched solve (double-float far field), one solve
+    o = sb.make_opts(pl[0], prec=sb.SBIE_FP64_DF, tol=1e-8, mem_kind=1, stream=stream.cuda_stream)
+    ctx = sb.sphere_bie_create_batch(cl, rl, pl, o)
+    sb.sphere_bie_autotune(ctx, "mobility")
+    ts, idf = _timed_solves(torch, stream, lambda: sb.sphere_bie_solve_mobility(ctx, F, T, v, om), 1)
+    sb.sphere_bie_destroy(ctx)
+    out["value"] = res[True]["time_to_solve_s"]
+    out["problems_per_s"] = len(probs) / out["value"]
+    out["graphs"] = res[True]
+    out["host_stepped"] = res[False]
+    out["one_context_per_problem"] = {"total_time_s": t_sep, "max_iters": it_sep,
+                                      "note": "512 separate solves, host buffers, one after another"}
+    out["fp64_df_batched"] = {"time_to_solve_s": ts[0], "iters": idf["iters"],
+                              "rel_residual_true": idf["rel_residual_true"],
+                              "velocity_rel_diff_vs_mixed": float((v - vb).abs().max() / v.abs().max())}
+    return out
+
+
+def _plain_fp64_apply_s(sb, torch, w, stream, op):
+    """One FP64 operator apply (the plain FP64 path's unit of work)."""
+    o = sb.make_opts(w["p"], prec=sb.SBIE_FP64, tol=1e-8, mem_kind=1, stream=stream.cuda_stream)
+    ctx = sb.sphere_bie_create(w["centres"], w["radii"], o)
+    N = sb.sphere_bie_num_nodes(ctx)
+    x = torch.randn((N, 3), dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    sb.sphere_bie_apply_operator(ctx, op, x, y)
+    ts, _ = _timed_solves(torch, stream, lambda: sb.sphere_bie_apply_operator(ctx, op, x, y), 1)
+    sb.sphere_bie_destroy(ctx)
+    return ts[0]
+
+
+def _precond_runs(sb, torch, w, stream, op, solve, net_path, steps, exact=True):
+    out = {}
+    kinds = [(1, "learned"), (0, "none")] + ([(2, "exact")] if exact else [])
+    for kind, name in kinds:
+        o = sb.make_opts(w["p"], prec=sb.SBIE_MIXED, tol=w.get("tol", 1e-8), mem_kind=1, stream=stream.cuda_stream)
+        o.use_learned_precond = kind
+        o.mlp_weights_path = net_path if kind == 1 else None
+        ctx = sb.sphere_bie_create(w["centres"], w["radii"], o)
+        sb.sphere_bie_autotune(ctx, op)
+        t0 = time.perf_counter()
+        first = solve(ctx)  # builds the preconditioner and captures the cycle graphs
+        torch.cuda.synchronize()
+        t_first = time.perf_counter() - t0
+        n = steps if kind == 1 else 1
+        ts, info = _timed_solves(torch, stream, lambda: solve(ctx), n)
+        pi = sb.sphere_bie_precond_info(ctx, op)
+        out[name] = {"time_to_solve_s": statistics.mean(ts), "iters": info["iters"],
+                     "refinements": info["refinements"], "rel_residual_true": info["rel_residual_true"],
+                     "first_solve_s": t_first, "precond_setup_s": pi["setup_ms"] / 1e3, "pairs": pi["pairs"],
+                     "pairs_out_of_range": pi["dropped"], "graph_cycles": info["graph_cycles"]}
+        sb.sphere_bie_destroy(ctx)
+    return out
+
+
+def run_dense(args, sb, torch, wl, local):
+    """1024 unit spheres at volume fraction 0.30, every sphere pushed to a
+    gap log-uniform in [0.01, 0.5]; mobility with random forces and torques;
+    the pair network trained on exact mobility blocks of two-sphere
+    configurations."""
+    import tempfile
+    w = wl.dense_1024()
+    w["tol"] = 1e-8
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream()
+    samples = args.pair_samples or 100000
+    path = os.path.join(tempfile.mkdtemp(), "pairnet.bin")
+    tr = sb.sphere_bie_train_pair_network(path, n_samples=samples, p=w["p"], gap_min=0.01, gap_max=2.0,
+                                          radius=1.0, epochs=200, seed=11, ops=("mobility",))
+    F = torch.tensor(w["forces"], dtype=torch.float64, device=dev)
+    T = torch.tensor(w["torques"], dtype=torch.float64, device=dev)
+    v, om = torch.zeros_like(F), torch.zeros_like(T)
+    runs = _precond_runs(sb, torch, w, stream, "mobility",
+                         lambda ctx: sb.sphere_bie_solve_mobility(ctx, F, T, v, om), path.encode(), args.steps)
+    f64 = _plain_fp64_apply_s(sb, torch, w, stream, "K")
+    n = len(w["radii"])
+    return {"metric": "mobility time-to-solve at 1e-8 rel. residual, learned pair preconditioner", "unit": "s",
+            "value": runs["learned"]["time_to_solve_s"], "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "dense_1024", "n_spheres": n, "p": w["p"],
+                       "nodes": n * (w["p"] + 1) * (2 * w["p"] + 2), "precision": "mixed", "tol": 1e-8},
+            "network": {"samples": samples, "val_rel_err": tr["val_rel_err"], "data_s": tr["t_data_s"],
+                        "train_s": tr["t_train_s"], "operator": "mobility", "gap_range": [0.01, 2.0]},
+            "solves": runs,
+            "plain_fp64": {"apply_s": f64,
+                           "lower_bound_solve_s": f64 * runs["none"]["iters"],
+                           "note": "one FP64 apply x the unpreconditioned iteration count (no FP64 solve run)"}}
+
+
+def run_large(args, sb, torch, wl, local):
+    """4096 spheres, radii U[0.8, 1.2], volume fraction 0.20, p = 12, resistance
+    in a random linear background flow; learned pair preconditioner (radius
+    range in training) against no preconditioner; the plain FP64 path by its
+    apply time."""
+    import tempfile
+    w = wl.large_4096()
+    w["tol"] = 1e-8
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream()
+    samples = args.pair_samples or 20000
+    path = os.path.join(tempfile.mkdtemp(), "pairnet.bin")
+    tr = sb.sphere_bie_train_pair_network(path, n_samples=samples, p=w["p"], gap_min=0.01, gap_max=2.4,
+                                          radius=0.8, radius_max=1.2, epochs=200, seed=13)
+    vel = torch.tensor(w["vel"], dtype=torch.float64, device=dev)
+    om = torch.tensor(w["omega"], dtype=torch.float64, device=dev)
+    F, T = torch.zeros_like(vel), torch.zeros_like(om)
+    runs = _precond_runs(sb, torch, w, stream, "resistance",
+                         lambda ctx: sb.sphere_bie_solve_resistance(ctx, vel, om, w["u0"], w["G"], F, T),
+                         path.encode(), 1, exact=False)
+    n = len(w["radii"])
+    return {"metric": "resistance time-to-solve at 1e-8 rel. residual, learned pair preconditioner", "unit": "s",
+            "value": runs["learned"]["time_to_solve_s"], "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "large_4096", "n_spheres": n, "p": w["p"],
+                       "nodes": n * (w["p"] + 1) * (2 * w["p"] + 2), "precision": "mixed", "tol": 1e-8},
+            "network": {"samples": samples, "val_rel_err": tr["val_rel_err"], "data_s": tr["t_data_s"],
+                        "train_s": tr["t_train_s"], "operator": "resistance", "radius_range": [0.8, 1.2],
+                        "gap_range": [0.01, 2.4]},
+            "solves": runs}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -306,6 +526,15 @@ def main():
     from paper_1707_06551_gb300 import sphere_bie as sb
     from paper_1707_06551_gb300 import workloads as wl
 
+    if args.workload != WORKLOAD:
+        if rank == 0:
+            print(json.dumps(run_workload(args, sb, torch, wl, local)))
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    if args.pair_samples is None:
+        args.pair_samples = 4096
     w = wl.resistance_256()
     n, p = len(w["radii"]), w["p"]
     prec = sb.SBIE_MIXED if args.prec == "mixed" else sb.SBIE_FP64
@@ -491,6 +720,7 @@ def main():
                                           if net is not None else "none"),
                        "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{world}"},
             "solve": {"iters": last["iters"], "refinements": last["refinements"],
+                      "fp32_residual_updates": last["fp32_residual_updates"], "fp32_op_err": last["fp32_op_err"],
                       "rel_residual_true": last["rel_residual_true"], "status": last["status"],
                       "create_s": t_create, "autotune_s": t_tune, "far_tiling": tuning},
             "roofline": roof, "far_field": far, "stage_ms_per_step": stage_ms, "fp64_path": fp64,

@@ -54,8 +54,9 @@ typedef enum {
                          SBIE_FP64_DF; tables, coefficients and Arnoldi in FP64.
                          The first residual is b - A x with the FP64-accurate
                          operator; a later one is r - A d with the FP32 operator
-                         when 2e-5 ||d|| <= 0.1 tol ||x|| (2e-5 bounds the FP32
-                         operator's relative error), else again b - A x.          */
+                         when e ||d|| <= 0.1 tol ||x||, e = 10 x the FP32
+                         operator's relative error measured on A x at the first
+                         residual, clamped to [1e-6, 2e-5]; else b - A x again.  */
     SBIE_FP64_DF = 2  /* FP64-accurate operator whose far-field pair arithmetic is
                          double-float (a value = sum of two FP32 numbers, about 48
                          significant bits; ~1e-13 relative); everything else FP64   */
@@ -98,7 +99,9 @@ typedef struct {
     int graph_cycles;       /* restart cycles that ran as one CUDA graph launch each            */
     long long kernel_launches; /* kernels this call executed (those inside graphs included)     */
     int fp32_residual_updates; /* SBIE_MIXED: residuals formed as r - A d with the FP32 operator
-                                  because the correction d was small enough (see solve_resistance) */
+                                  because the correction d was small enough (see SBIE_MIXED)  */
+    double fp32_op_err;     /* SBIE_MIXED: measured ||A64 x - A32 x|| / ||A64 x|| at the first
+                               FP64-accurate residual (worst problem)                        */
 } sbie_solve_info;
 
 /* Fills *opts with defaults: p = 8, eta = 1, FP64, tol = 1e-8, restart = 60,
@@ -229,33 +232,40 @@ sbie_status sphere_bie_apply_layer_noalloc(sbie_op op, int n_spheres, int p, con
                                            void* stream);
 
 /* ---- learned pair preconditioner ------------------------------------------
- * With opts.use_learned_precond = 1 (network read from opts.mlp_weights_path)
- * or 2 (exact blocks), create builds a right preconditioner for GMRES:
+ * With opts.use_learned_precond = 1 (networks read from opts.mlp_weights_path
+ * at create) or 2 (exact blocks), the first resistance or mobility solve on a
+ * context builds a right preconditioner for GMRES on that operator:
  *   M^{-1} r = H r + Z C^{-1} Z^+ r,
  * Z^+ the VSH analysis restricted to degree <= 4 (73 real coefficients per
  * sphere), H the exact inverse of each sphere's own operator above degree 4
- * (1/D+ of Theorem 2, and 2 on the non-band-limited remainder), C^{-1} an
- * additive Schwarz inverse over close pairs of the low-mode pair systems
- * [[L_i, B_ik], [B_ki, L_k]] (L probed exactly; B probed exactly, or for 1
- * predicted by the pair network in the pair frame and rotated).  The operator
- * and the true residual are unchanged: the preconditioner changes the
- * iteration count, not the answer.  Built for the resistance operator. */
+ * (1/D+ = 1/K- of Theorem 2, and 2 on the non-band-limited remainder), C^{-1}
+ * an additive Schwarz inverse over close pairs of the low-mode pair systems
+ * [[L_i, B_ik], [B_ki, L_k]] of that operator (L probed exactly; B probed
+ * exactly, or for 1 predicted by the pair network in the pair frame and
+ * rotated).  The operator and the true residual are unchanged: the
+ * preconditioner changes the iteration count, not the answer.  A weights file
+ * without a network for the solve's operator leaves that solve
+ * unpreconditioned. */
 
 typedef struct {
     int n_samples;         /* two-sphere configurations generated (>= 16)          */
     int p;                 /* VSH order of the probed grid (4..24)                 */
     double gap_min, gap_max; /* surface gaps, log-uniform                          */
-    double radius;         /* both radii                                           */
+    double radius;         /* both radii, or the lower end of their range          */
     int epochs, batch;
     double lr;             /* Adam learning rate                                   */
     unsigned long long seed;
     double val_frac;       /* held-out fraction for the validation error           */
+    int ops;               /* networks to train: bit 0 resistance blocks (Eq. 5.19),
+                              bit 1 mobility blocks (Eq. 5.8); one file holds both  */
+    double radius_max;     /* > radius: each radius uniform in [radius, radius_max];
+                              0 or radius: fixed radius                             */
 } sbie_pair_train_opts;
 
 typedef struct {
-    double train_loss;     /* mean squared error of the last epoch (standardised)   */
-    double val_rel_err;    /* mean relative Frobenius error of held-out blocks      */
-    double t_data_s, t_train_s;
+    double train_loss;     /* mean squared error of the last epoch (standardised; worst network) */
+    double val_rel_err;    /* mean relative Frobenius error of held-out blocks (worst network)   */
+    double t_data_s, t_train_s;  /* block generation and training, all networks   */
     int n_train, n_val;
 } sbie_pair_train_info;
 
@@ -267,20 +277,23 @@ sbie_status sphere_bie_train_pair_network(const sbie_pair_train_opts* opts, cons
 
 /* Exact pair-frame blocks: source of radius a_src at the origin, target of
  * radius a_tgt at (0, 0, dist[q]); blocks: host [n][73][73] (target row,
- * source column) of the resistance operator, grid order p. */
+ * source column) of operator op (SBIE_OP_RESISTANCE or SBIE_OP_MOBILITY),
+ * grid order p. */
 sbie_status sphere_bie_pair_blocks(int n, const double* dist, const double* a_src, const double* a_tgt, int p,
-                                   double* blocks);
+                                   sbie_op op, double* blocks);
 
 /* Density of the last solve on ctx, at the nodes in sphere_bie_nodes order
  * ([N][3], memory kind of the context): psi of Eq. 5.19 after a resistance
  * solve, mu of Eq. 5.8 after a mobility solve.  SBIE_ERR_ARG before any solve. */
 sbie_status sphere_bie_solution_density(sbie_ctx* ctx, double* density);
 
-/* Pair preconditioner of a context: kind (0 none, 1 network, 2 exact),
+/* Pair preconditioner of a context for operator op (SBIE_OP_RESISTANCE or
+ * SBIE_OP_MOBILITY): kind (0 none or not yet built, 1 network, 2 exact),
  * undirected pairs in the pair systems, close pairs left out because they lie
  * outside the network's trained input range (kind 1), and the wall time of
- * its setup inside create.  Any output pointer may be NULL. */
-sbie_status sphere_bie_precond_info(const sbie_ctx* ctx, int* kind, int* n_pairs, int* n_dropped, double* setup_ms);
+ * its setup (inside the first solve with op).  Output pointers may be NULL. */
+sbie_status sphere_bie_precond_info(const sbie_ctx* ctx, sbie_op op, int* kind, int* n_pairs, int* n_dropped,
+                                    double* setup_ms);
 
 /* Number of network parameters (FP32, layer by layer: W1 (5x128), b1, ...). */
 sbie_status sphere_bie_pair_network_size(long long* n_params);

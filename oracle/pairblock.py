@@ -6,12 +6,12 @@ of length 3(L+1)^2 - 2 (73 for L = 4): for type V (n >= 0), W, X (n >= 1), for
 n, then m = 0..n: Re c_nm, and for m >= 1 also Im c_nm, where c are the complex
 coefficients of oracle.vsh (field = sum_m c Z + conj).
 
-Blocks.  For the resistance operator A = 1/2 I + D + N (Eq. 5.19), the block
-from source sphere s to target sphere t (s != t) is B_ts = P_t A E_s, where E_s
-places a low-mode field on sphere s (zero elsewhere) and P_t is the VSH
-analysis (Sec. 2.1) of the result on sphere t restricted to degree <= L; the
-self block is B_ss.  In the pair frame the target centre is (0, 0, d) with the
-source at the origin.
+Blocks.  For the resistance operator A = 1/2 I + D + N (Eq. 5.19) or the
+mobility operator A = 1/2 I + K + L (Eq. 5.8), the block from source sphere s
+to target sphere t (s != t) is B_ts = P_t A E_s, where E_s places a low-mode
+field on sphere s (zero elsewhere) and P_t is the VSH analysis (Sec. 2.1) of
+the result on sphere t restricted to degree <= L; the self block is B_ss.  In
+the pair frame the target centre is (0, 0, d) with the source at the origin.
 
 Network.  A fully connected net 5 -> 128 -> 128 -> 128 -> out with tanh
 activations maps (pair offset in the pair frame, source radius, target radius)
@@ -49,10 +49,10 @@ def low_to_coef(a, L, p):
     return c
 
 
-def two_sphere_blocks(centres, radii, p, L, eta=1e9):
-    """(B_00, B_10, B_01, B_11) of the resistance operator for two spheres,
-    probing the oracle operator with each low mode (all pairs treated as close
-    for the default eta)."""
+def two_sphere_blocks(centres, radii, p, L, eta=1e9, op="resistance"):
+    """(B_00, B_10, B_01, B_11) of operator `op` for two spheres, probing the
+    oracle operator with each low mode (all pairs treated as close for the
+    default eta)."""
     g = ops.Geometry(centres, radii, p, eta=eta)
     nm = len(low_modes(L))
     B = np.zeros((2, 2, nm, nm))
@@ -60,15 +60,15 @@ def two_sphere_blocks(centres, radii, p, L, eta=1e9):
         for b in range(nm):
             dens = np.zeros((g.N, 3))
             dens[g.sl(s)] = vsh.synthesis(low_to_coef(np.eye(nm)[b], L, p))
-            out = ops.apply(g, "resistance", dens)
+            out = ops.apply(g, op, dens)
             for t in range(2):
                 B[t, s][:, b] = coef_to_low(vsh.analysis(out[g.sl(t)], p), L)
     return B
 
 
-def aligned_block(d, a_src, a_tgt, p, L):
+def aligned_block(d, a_src, a_tgt, p, L, op="resistance"):
     """B_ts with the source at the origin and the target at (0, 0, d)."""
-    B = two_sphere_blocks([[0.0, 0.0, 0.0], [0.0, 0.0, d]], [a_src, a_tgt], p, L)
+    B = two_sphere_blocks([[0.0, 0.0, 0.0], [0.0, 0.0, d]], [a_src, a_tgt], p, L, op=op)
     return B[1, 0]
 
 

@@ -91,10 +91,12 @@ void free_all(sbie_ctx* c) {
                     c->d_near_idx, c->d_tab, c->d_coef, c->d_chan, c->d_chanf, c->d_mom, c->d_part, c->d_src64,
                     c->d_srcf, c->d_in, c->d_out, c->d_tmp, c->d_tmp2, c->d_small, c->d_red, c->d_V, c->d_xsol,
                     c->d_rhs, c->d_res, c->d_prob_sph, c->d_sph_prob, c->d_node_prob, c->d_seg3, c->d_H, c->d_pvec,
-                    c->d_ZS, c->d_ZA, c->d_modes, c->d_pp_ptr, c->d_pp_idx, c->d_pp_pair, c->d_pinv, c->d_sinv, c->d_low, c->d_lowe,
-                    c->d_pz, c->d_ad, c->d_adi, c->d_vk};
+                    c->d_ZS, c->d_ZA, c->d_modes, c->d_low, c->d_lowe, c->d_pz, c->d_ad, c->d_adi, c->d_vk};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (PrecState& P : c->prec)
+        for (void* p : {(void*)P.d_pp_ptr, (void*)P.d_pp_idx, (void*)P.d_pp_pair, (void*)P.d_pinv, (void*)P.d_sinv})
+            if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
     if (c->h_st) cudaFreeHost(c->h_st);
     if (c->h_pack) cudaFreeHost(c->h_pack);
@@ -205,15 +207,18 @@ Kern kern_of(int op) {
 sbie_status apply_dev(sbie_ctx* c, int op, int mode, const double* in, double* out) {
     const Kern k = kern_of(op);
     const bool f32 = mode == kModeF32;
-    {
+    // a context whose pairs are all close (the two-sphere probe problems of
+    // the pair preconditioner) has no far field: the self term writes `out`
+    const bool far = c->far_pair_count > 0;
+    if (far) {
         StageScope s(c, ST_FAR);
         CK(launch_pack(c, in, mode));
         CK(launch_far(c, k, mode, out));
-        if (c->prof.on) (f32 ? c->prof.pairs_f32 : c->prof.pairs_f64) += far_pairs(c);
+        if (c->prof.on) (f32 ? c->prof.pairs_f32 : c->prof.pairs_f64) += c->far_pair_count;
     }
     {
         StageScope s(c, ST_SELF);
-        CK(launch_self(c, k, in, out, true, c->n_near > 0));
+        CK(launch_self(c, k, in, out, far, c->n_near > 0));
     }
     if (c->n_near > 0) {
         StageScope s(c, ST_NEAR);
@@ -528,6 +533,21 @@ sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const 
         c->h_pack[4 * P] = mm;
         CK(cudaMemcpyAsync(AD.pack, c->h_pack, sizeof(double) * (4 * (size_t)P + 1), cudaMemcpyHostToDevice, c->stream));
         CK(arnoldi_cycle_init(c, AD));
+        // inside the cycle the far field skips problems that stopped
+        {
+            int off = 0;
+            for (sbie_ctx* q : S.parts) {
+                q->far_live = AD.live;
+                q->far_live_off = off;
+                off += q->n_prob;
+            }
+        }
+        struct Unmask {
+            const Sys& S;
+            ~Unmask() {
+                for (sbie_ctx* q : S.parts) q->far_live = nullptr;
+            }
+        } unmask{S};
         CycleGraph* g = nullptr;
         if (graphs && !c->prof.on) {
             if (cycle_graph(S, A, M, key, &g) == SBIE_OK) {
@@ -546,6 +566,7 @@ sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const 
                 if (!c->h_st[2]) break;
             }
         }
+        for (sbie_ctx* q : S.parts) q->far_live = nullptr;
         // x += V y (x += M^{-1} V y), then the true residual
         if (M) {
             double* t = c->d_pz + n3;
@@ -580,6 +601,8 @@ sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const 
 // system at once.  SBIE_FP64 / SBIE_FP64_DF: GMRES on the FP64-accurate
 // operator.  SBIE_MIXED: iterative refinement -- residuals b - A x with the
 // FP64-accurate operator, corrections by GMRES on the FP32 operator.
+sbie_status ensure_preconditioner(const Sys& S, int op);
+
 // Bound on the FP32 operator's relative error (the mixed-precision apply
 // parity bound) used to decide when a residual may be updated in FP32.
 constexpr double kFp32OpErr = 2e-5;
@@ -591,13 +614,15 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
     const int hm = hi_mode(c);
     AFn A64 = [&](const double* in, double* out) { return apply_sys(S, op, hm, in, out); };
     AFn A32 = [&](const double* in, double* out) { return apply_sys(S, op, kModeF32, in, out); };
+    CKS(ensure_preconditioner(S, op));
+    const int slot = prec_slot(op);
     bool prec = false;
-    for (sbie_ctx* q : S.parts) prec |= q->prec_kind > 0;
+    for (sbie_ctx* q : S.parts) prec |= q->prec[slot].kind > 0;
     AFn Mf = [&](const double* in, double* out) {
         for (size_t i = 0; i < S.parts.size(); ++i) {
             sbie_ctx* q = S.parts[i];
-            if (q->prec_kind > 0) {
-                cudaError_t e = precond_apply(q, in + S.off3[i], out + S.off3[i]);
+            if (q->prec[slot].kind > 0) {
+                cudaError_t e = precond_apply(q, slot, in + S.off3[i], out + S.off3[i]);
                 if (e != cudaSuccess) return fail(c, SBIE_ERR_CUDA, std::string("preconditioner: ") + cudaGetErrorString(e));
             } else {
                 cudaError_t e = cudaMemcpyAsync(out + S.off3[i], in + S.off3[i], sizeof(double) * q->N * 3,
@@ -633,6 +658,7 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
         CK(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->stream));
         for (int p = 0; p < P; ++p) rel[p] = nb[p] > 0 ? 1.0 : 0.0;
         int iters = 0, outers = 0;
+        double eps32 = kFp32OpErr;
         auto worst = [&]() { return *std::max_element(rel.begin(), rel.end()); };
         while (worst() > tol && iters < c->opts.max_iter && outers < 20) {
             std::vector<double> itol(P);
@@ -648,26 +674,43 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
             CK(blas_axpy(c, 1.0, d, x, n3));
             // New residual.  After the first correction it is r - A d by
             // linearity, and A d may use the FP32 operator when the
-            // correction is small: its error is at most eps32 ||d|| / ||x||
-            // relative to ||b|| (eps32 = 2e-5 bounds the FP32 operator's
-            // relative error), kept below a tenth of the tolerance; otherwise
-            // r = b - A x with the FP64-accurate operator.
+            // correction is small: the error of that update is about
+            // eps32 ||d|| / ||x|| relative to ||b||, with eps32 the FP32
+            // operator's relative error, and it is kept below a tenth of the
+            // tolerance.  eps32 is measured on this system at the first
+            // FP64-accurate residual (A x in both arithmetics) and taken ten
+            // times over, never below 1e-6; otherwise the bound 2e-5 of the
+            // mixed-precision apply holds.  Else r = b - A x with the
+            // FP64-accurate operator.
+            double* t = c->d_out;  // not used by the solve's callers until it returns
             bool cheap = outers > 0;
             if (cheap) {
                 std::vector<double> dn, xn;
                 CKS(seg_norms(S, d, dn));
                 CKS(seg_norms(S, x, xn));
                 for (int p = 0; p < P; ++p)
-                    if (dn[p] > 0.0 && !(kFp32OpErr * dn[p] <= 0.1 * tol * xn[p])) cheap = false;
+                    if (dn[p] > 0.0 && !(eps32 * dn[p] <= 0.1 * tol * xn[p])) cheap = false;
             }
             if (cheap) {
-                double* t = c->d_out;  // not used by the solve's callers until it returns
                 CKS(A32(d, t));
                 CK(blas_axpy(c, -1.0, t, r, n3));
                 ++inf.fp32_residual_updates;
             } else {
                 CKS(A64(x, r));
                 CK(blas_lincomb(c, 1.0, b, -1.0, r, r, n3));
+                if (outers == 0) {  // eps32 from A x: d <- A64 x - A32 x (d is free until the next GMRES)
+                    CKS(A32(x, t));
+                    CK(blas_lincomb(c, 1.0, b, -1.0, r, d, n3));
+                    std::vector<double> an, en;
+                    CKS(seg_norms(S, d, an));
+                    CK(blas_axpy(c, -1.0, t, d, n3));
+                    CKS(seg_norms(S, d, en));
+                    double worst = 0.0;
+                    for (int p = 0; p < P; ++p)
+                        if (an[p] > 0.0) worst = std::max(worst, en[p] / an[p]);
+                    if (std::isfinite(worst)) eps32 = std::min(kFp32OpErr, std::max(1e-6, 10.0 * worst));
+                    inf.fp32_op_err = worst;
+                }
             }
             std::vector<double> rn;
             CKS(seg_norms(S, r, rn));
@@ -750,6 +793,7 @@ sbie_status create_part(const sbie_opts& o, int n, const double* centres, const 
         c->h_near_ptr[i + 1] = (int)c->h_near_idx.size();
     }
     c->n_near = (long long)c->h_near_idx.size();
+    c->far_pair_count = far_pairs(c);
     c->seg3.resize(c->n_prob + 1);
     for (int q = 0; q <= c->n_prob; ++q) c->seg3[q] = (long long)prob_sph[q] * c->npn * 3;
     std::vector<int> node_prob((size_t)c->N);
@@ -893,6 +937,7 @@ sbie_status to_user(sbie_ctx* c, const double* dev, double* user, bool nodal) {
 // ---- pair preconditioner and pair network (kernels in precond.cu, mlp.cu)
 
 struct PairNet {
+    int op = SBIE_OP_RESISTANCE;        // operator whose blocks it predicts
     std::vector<float> params;          // FP32 weights (mlp_layout)
     float in_mean[kMlpIn], in_std[kMlpIn];
     float in_min[kMlpIn], in_max[kMlpIn];  // range of the training inputs
@@ -908,55 +953,83 @@ struct PairNet {
         return true;
     }
 };
-const char kNetMagic[9] = "SBIEPN02";
 
-sbie_status net_save(const char* path, const PairNet& net) {
+}  // namespace
+// the networks of one weights file, at most one per operator
+struct sbie::PairNetSet {
+    std::vector<PairNet> nets;
+    const PairNet* for_op(int op) const {
+        for (const PairNet& n : nets)
+            if (n.op == op) return &n;
+        return nullptr;
+    }
+};
+namespace {
+
+// File: magic "SBIEPN03", int count, then per network int[7] {L, in, hidden,
+// out, p of the probed grid, parameter count, operator}, input mean, std,
+// min, max, output mean, std, parameters (all float).
+const char kNetMagic[9] = "SBIEPN03";
+
+sbie_status net_save(const char* path, const PairNetSet& set) {
     std::ofstream f(path, std::ios::binary);
     if (!f) return fail(nullptr, SBIE_ERR_ARG, std::string("cannot write ") + path);
-    int hdr[6] = {kPrecL, kMlpIn, kMlpHidden, kMlpOut, net.p_train, (int)net.params.size()};
     f.write(kNetMagic, 8);
-    f.write(reinterpret_cast<const char*>(hdr), sizeof(hdr));
-    f.write(reinterpret_cast<const char*>(net.in_mean), sizeof(net.in_mean));
-    f.write(reinterpret_cast<const char*>(net.in_std), sizeof(net.in_std));
-    f.write(reinterpret_cast<const char*>(net.in_min), sizeof(net.in_min));
-    f.write(reinterpret_cast<const char*>(net.in_max), sizeof(net.in_max));
-    f.write(reinterpret_cast<const char*>(net.out_mean.data()), sizeof(float) * kMlpOut);
-    f.write(reinterpret_cast<const char*>(net.out_std.data()), sizeof(float) * kMlpOut);
-    f.write(reinterpret_cast<const char*>(net.params.data()), sizeof(float) * net.params.size());
+    const int count = (int)set.nets.size();
+    f.write(reinterpret_cast<const char*>(&count), sizeof(count));
+    for (const PairNet& net : set.nets) {
+        int hdr[7] = {kPrecL, kMlpIn, kMlpHidden, kMlpOut, net.p_train, (int)net.params.size(), net.op};
+        f.write(reinterpret_cast<const char*>(hdr), sizeof(hdr));
+        f.write(reinterpret_cast<const char*>(net.in_mean), sizeof(net.in_mean));
+        f.write(reinterpret_cast<const char*>(net.in_std), sizeof(net.in_std));
+        f.write(reinterpret_cast<const char*>(net.in_min), sizeof(net.in_min));
+        f.write(reinterpret_cast<const char*>(net.in_max), sizeof(net.in_max));
+        f.write(reinterpret_cast<const char*>(net.out_mean.data()), sizeof(float) * kMlpOut);
+        f.write(reinterpret_cast<const char*>(net.out_std.data()), sizeof(float) * kMlpOut);
+        f.write(reinterpret_cast<const char*>(net.params.data()), sizeof(float) * net.params.size());
+    }
     return f ? SBIE_OK : fail(nullptr, SBIE_ERR_ARG, "write failed");
 }
 
-sbie_status net_load(const char* path, PairNet& net) {
+sbie_status net_load(const char* path, PairNetSet& set) {
     std::ifstream f(path, std::ios::binary);
     if (!f) return fail(nullptr, SBIE_ERR_ARG, std::string("cannot read ") + path);
     char magic[8];
-    int hdr[6];
+    int count = 0;
     f.read(magic, 8);
-    f.read(reinterpret_cast<char*>(hdr), sizeof(hdr));
-    MlpLayout L = mlp_layout();
-    if (!f || std::memcmp(magic, kNetMagic, 8) != 0 || hdr[0] != kPrecL || hdr[1] != kMlpIn || hdr[2] != kMlpHidden ||
-        hdr[3] != kMlpOut || hdr[5] != (int)L.total)
+    f.read(reinterpret_cast<char*>(&count), sizeof(count));
+    if (!f || std::memcmp(magic, kNetMagic, 8) != 0 || count < 1 || count > 2)
         return fail(nullptr, SBIE_ERR_ARG, std::string("not a pair-network file: ") + path);
-    net.p_train = hdr[4];
-    net.out_mean.resize(kMlpOut);
-    net.out_std.resize(kMlpOut);
-    net.params.resize(L.total);
-    f.read(reinterpret_cast<char*>(net.in_mean), sizeof(net.in_mean));
-    f.read(reinterpret_cast<char*>(net.in_std), sizeof(net.in_std));
-    f.read(reinterpret_cast<char*>(net.in_min), sizeof(net.in_min));
-    f.read(reinterpret_cast<char*>(net.in_max), sizeof(net.in_max));
-    f.read(reinterpret_cast<char*>(net.out_mean.data()), sizeof(float) * kMlpOut);
-    f.read(reinterpret_cast<char*>(net.out_std.data()), sizeof(float) * kMlpOut);
-    f.read(reinterpret_cast<char*>(net.params.data()), sizeof(float) * L.total);
+    MlpLayout L = mlp_layout();
+    set.nets.assign(count, PairNet());
+    for (PairNet& net : set.nets) {
+        int hdr[7];
+        f.read(reinterpret_cast<char*>(hdr), sizeof(hdr));
+        if (!f || hdr[0] != kPrecL || hdr[1] != kMlpIn || hdr[2] != kMlpHidden || hdr[3] != kMlpOut ||
+            hdr[5] != (int)L.total || (hdr[6] != SBIE_OP_RESISTANCE && hdr[6] != SBIE_OP_MOBILITY))
+            return fail(nullptr, SBIE_ERR_ARG, std::string("not a pair-network file: ") + path);
+        net.p_train = hdr[4];
+        net.op = hdr[6];
+        net.out_mean.resize(kMlpOut);
+        net.out_std.resize(kMlpOut);
+        net.params.resize(L.total);
+        f.read(reinterpret_cast<char*>(net.in_mean), sizeof(net.in_mean));
+        f.read(reinterpret_cast<char*>(net.in_std), sizeof(net.in_std));
+        f.read(reinterpret_cast<char*>(net.in_min), sizeof(net.in_min));
+        f.read(reinterpret_cast<char*>(net.in_max), sizeof(net.in_max));
+        f.read(reinterpret_cast<char*>(net.out_mean.data()), sizeof(float) * kMlpOut);
+        f.read(reinterpret_cast<char*>(net.out_std.data()), sizeof(float) * kMlpOut);
+        f.read(reinterpret_cast<char*>(net.params.data()), sizeof(float) * L.total);
+    }
     return f ? SBIE_OK : fail(nullptr, SBIE_ERR_ARG, std::string("truncated pair-network file: ") + path);
 }
 
 // Exact low-mode blocks by probing context `c` (problems of sph_per_prob
 // spheres): for each side s < nsides the 73 low modes are placed on local
-// sphere s of every problem and the resistance operator applied in FP64; the
-// low-mode analysis of every sphere's response fills
+// sphere s of every problem and operator `op` (resistance or mobility)
+// applied in FP64; the low-mode analysis of every sphere's response fills
 // out[s][sphere][row][mode] (host).
-sbie_status probe_blocks(sbie_ctx* c, int sph_per_prob, int nsides, std::vector<double>& out) {
+sbie_status probe_blocks(sbie_ctx* c, int op, int sph_per_prob, int nsides, std::vector<double>& out) {
     std::vector<double> ZS, ZA;
     lowmode_tables(c->p, ZS, ZA);
     double *dZS = nullptr, *dZA = nullptr, *dB = nullptr;
@@ -973,7 +1046,7 @@ sbie_status probe_blocks(sbie_ctx* c, int sph_per_prob, int nsides, std::vector<
         for (int s = 0; s < nsides && e == cudaSuccess && st == SBIE_OK; ++s)
             for (int b = 0; b < kLowModes && e == cudaSuccess && st == SBIE_OK; ++b) {
                 e = launch_probe_density(c, sph_per_prob, s, b, dZS, c->d_in);
-                if (e == cudaSuccess) st = apply_dev(c, SBIE_OP_RESISTANCE, kModeF64, c->d_in, c->d_out);
+                if (e == cudaSuccess) st = apply_dev(c, op, kModeF64, c->d_in, c->d_out);
                 if (st == SBIE_OK && e == cudaSuccess) e = launch_probe_analysis(c, dZA, c->d_out, b, dB + s * per);
             }
         if (e == cudaSuccess && st == SBIE_OK) {
@@ -992,7 +1065,7 @@ sbie_status create_part(const sbie_opts& o, int n, const double* centres, const 
 
 // Exact aligned blocks: source sphere (radius a_s) at the origin, target
 // (radius a_t) at (0, 0, d); out [n][73][73] (target <- source).
-sbie_status aligned_blocks(int n, const double* d, const double* a_s, const double* a_t, int p, double eta,
+sbie_status aligned_blocks(int n, const double* d, const double* a_s, const double* a_t, int p, double eta, int op,
                            std::vector<double>& out) {
     std::vector<double> cc((size_t)n * 6, 0.0), aa((size_t)n * 2);
     std::vector<int> ps(n + 1);
@@ -1010,7 +1083,7 @@ sbie_status aligned_blocks(int n, const double* d, const double* a_s, const doub
     sbie_ctx* pc = nullptr;
     CKS(create_part(o, 2 * n, cc.data(), aa.data(), ps, nullptr, &pc));
     std::vector<double> B;
-    sbie_status st = probe_blocks(pc, 2, 1, B);
+    sbie_status st = probe_blocks(pc, op, 2, 1, B);
     if (st == SBIE_OK) {
         out.resize((size_t)n * kLowModes * kLowModes);
         const size_t blk = (size_t)kLowModes * kLowModes;
@@ -1113,26 +1186,157 @@ sbie_status net_blocks(const PairNet& net, const std::vector<float>& X5, std::ve
     return SBIE_OK;
 }
 
-sbie_status precond_setup(sbie_ctx* c, int kind, const PairNet* net);
+sbie_status precond_setup(sbie_ctx* c, int op, int kind, const PairNet* net);
 
-// Pair preconditioner for every part when the options ask for one.
-sbie_status setup_preconditioner(const std::vector<sbie_ctx*>& parts, const sbie_opts& o) {
-    if (o.use_learned_precond == 0) return SBIE_OK;
-    PairNet net;
-    if (o.use_learned_precond == 1) CKS(net_load(o.mlp_weights_path, net));
-    for (sbie_ctx* q : parts) {
-        sbie_status st = precond_setup(q, o.use_learned_precond, &net);
+// The pair preconditioner of operator `op` for every part of a system, built
+// at the first solve with that operator.  With the network (kind 1) and no
+// network for `op` in the weights file, the solve runs unpreconditioned.
+sbie_status ensure_preconditioner(const Sys& S, int op) {
+    sbie_ctx* top = S.top;
+    const int kind = top->opts.use_learned_precond, slot = prec_slot(op);
+    if (kind == 0) return SBIE_OK;
+    const PairNet* net = nullptr;
+    if (kind == 1) {
+        net = top->nets ? top->nets->for_op(op) : nullptr;
+        if (!net) {
+            for (sbie_ctx* q : S.parts) q->prec[slot].built = true;  // kind stays 0: no preconditioner
+            return SBIE_OK;
+        }
+    }
+    for (sbie_ctx* q : S.parts) {
+        if (q->prec[slot].built) continue;
+        sbie_status st = precond_setup(q, op, kind, net);
         if (st != SBIE_OK) {
-            if (q->err.empty() || q->err == "no error") q->err = g_last_error;
+            if (q != top) top->err = q->err;
             return st;
         }
     }
     return SBIE_OK;
 }
 
-// Builds the pair preconditioner of one part (kind 1: network, 2: exact).
-sbie_status precond_setup(sbie_ctx* c, int kind, const PairNet* net) {
+// Exact pair-frame blocks of operator `op` for two-sphere configurations with
+// gaps log-uniform in [gap_min, gap_max] (probing the close-pair path of the
+// operator on the GPU), then the network trained on them with the library's
+// own kernels; the last val_frac of the samples are held out.
+sbie_status train_one(const sbie_pair_train_opts& o, int op, PairNet& net, sbie_pair_train_info& info) {
     auto t0 = std::chrono::steady_clock::now();
+    const int n = o.n_samples;
+    std::mt19937_64 rng(o.seed);
+    std::uniform_real_distribution<double> U(std::log(o.gap_min), std::log(o.gap_max));
+    std::vector<double> d(n), as(n, o.radius), at(n, o.radius);
+    const bool ranged = o.radius_max > o.radius;
+    std::uniform_real_distribution<double> R(o.radius, ranged ? o.radius_max : o.radius);
+    for (int q = 0; q < n; ++q) {
+        if (ranged) {
+            as[q] = R(rng);
+            at[q] = R(rng);
+        }
+        d[q] = as[q] + at[q] + std::exp(U(rng));
+    }
+    std::vector<double> blocks((size_t)n * kMlpOut);
+    const int chunk = 4096;
+    for (int q0 = 0; q0 < n; q0 += chunk) {
+        const int m = std::min(chunk, n - q0);
+        std::vector<double> out;
+        CKS(aligned_blocks(m, d.data() + q0, as.data() + q0, at.data() + q0, o.p, 1e9, op, out));
+        std::memcpy(blocks.data() + (size_t)q0 * kMlpOut, out.data(), sizeof(double) * out.size());
+    }
+    auto t1 = std::chrono::steady_clock::now();
+    net = PairNet();
+    net.op = op;
+    net.p_train = o.p;
+    std::vector<float> X((size_t)n * kMlpIn, 0.f);
+    for (int q = 0; q < n; ++q) {
+        X[q * kMlpIn + 2] = (float)d[q];
+        X[q * kMlpIn + 3] = (float)as[q];
+        X[q * kMlpIn + 4] = (float)at[q];
+    }
+    for (int j = 0; j < kMlpIn; ++j) {
+        double s = 0, s2 = 0;
+        for (int q = 0; q < n; ++q) {
+            s += X[q * kMlpIn + j];
+            s2 += (double)X[q * kMlpIn + j] * X[q * kMlpIn + j];
+        }
+        const double mu = s / n, var = std::max(0.0, s2 / n - mu * mu);
+        net.in_min[j] = net.in_max[j] = X[j];
+        for (int q = 0; q < n; ++q) {
+            net.in_min[j] = std::min(net.in_min[j], X[q * kMlpIn + j]);
+            net.in_max[j] = std::max(net.in_max[j], X[q * kMlpIn + j]);
+        }
+        net.in_mean[j] = (float)mu;
+        net.in_std[j] = var > 1e-20 ? (float)std::sqrt(var) : 1.f;
+    }
+    net.out_mean.assign(kMlpOut, 0.f);
+    net.out_std.assign(kMlpOut, 1.f);
+    double smax = 0.0;
+    std::vector<double> sd(kMlpOut);
+    for (int k = 0; k < kMlpOut; ++k) {
+        double s = 0, s2 = 0;
+        for (int q = 0; q < n; ++q) {
+            const double v = blocks[(size_t)q * kMlpOut + k];
+            s += v;
+            s2 += v * v;
+        }
+        const double mu = s / n;
+        sd[k] = std::sqrt(std::max(0.0, s2 / n - mu * mu));
+        net.out_mean[k] = (float)mu;
+        smax = std::max(smax, sd[k]);
+    }
+    // Entries that do not vary over the samples (most of the block: in the
+    // pair frame only modes of equal order m couple) get std 0, so that the
+    // prediction is their mean exactly and the network's error there is not
+    // added to the block; their standardised target is 0.
+    for (int k = 0; k < kMlpOut; ++k) net.out_std[k] = sd[k] > 1e-6 * smax ? (float)sd[k] : 0.f;
+    std::vector<float> Xs(X.size()), Ys((size_t)n * kMlpOut);
+    for (int q = 0; q < n; ++q) {
+        for (int j = 0; j < kMlpIn; ++j) Xs[q * kMlpIn + j] = (X[q * kMlpIn + j] - net.in_mean[j]) / net.in_std[j];
+        for (int k = 0; k < kMlpOut; ++k)
+            Ys[(size_t)q * kMlpOut + k] =
+                net.out_std[k] > 0.f
+                    ? (float)((blocks[(size_t)q * kMlpOut + k] - net.out_mean[k]) / net.out_std[k])
+                    : 0.f;
+    }
+    const int nval = (int)(o.val_frac * n), ntr = n - nval;
+    mlp_init(o.seed + 1, net.params);
+    MlpTrainOpts to;
+    to.epochs = o.epochs;
+    to.batch = o.batch;
+    to.lr = o.lr;
+    to.seed = o.seed + 2;
+    std::vector<double> hist;
+    cudaError_t e = mlp_train(to, ntr, Xs.data(), Ys.data(), net.params.data(), hist);
+    if (e != cudaSuccess) return fail(nullptr, SBIE_ERR_CUDA, std::string("training: ") + cudaGetErrorString(e));
+    auto t2 = std::chrono::steady_clock::now();
+    double val = 0.0;
+    if (nval > 0) {
+        std::vector<float> Xv(X.begin() + (size_t)ntr * kMlpIn, X.end());
+        std::vector<double> P;
+        CKS(net_blocks(net, Xv, P));
+        for (int q = 0; q < nval; ++q) {
+            double num = 0, den = 0;
+            for (int k = 0; k < kMlpOut; ++k) {
+                const double t = blocks[(size_t)(ntr + q) * kMlpOut + k], y = P[(size_t)q * kMlpOut + k];
+                num += (y - t) * (y - t);
+                den += t * t;
+            }
+            val += std::sqrt(num / den);
+        }
+        val /= nval;
+    }
+    info.train_loss = hist.empty() ? 0.0 : hist.back();
+    info.val_rel_err = val;
+    info.t_data_s = std::chrono::duration<double>(t1 - t0).count();
+    info.t_train_s = std::chrono::duration<double>(t2 - t1).count();
+    info.n_train = ntr;
+    info.n_val = nval;
+    return SBIE_OK;
+}
+
+// Builds the pair preconditioner of operator `op` on one part (kind 1:
+// network, 2: exact blocks).
+sbie_status precond_setup(sbie_ctx* c, int op, int kind, const PairNet* net) {
+    auto t0 = std::chrono::steady_clock::now();
+    PrecState& P = c->prec[prec_slot(op)];
     const int n = c->n, NM = kLowModes;
     const size_t blk = (size_t)NM * NM;
     std::vector<double> ZS, ZA;
@@ -1156,7 +1360,7 @@ sbie_status precond_setup(sbie_ctx* c, int kind, const PairNet* net) {
             const float x1[kMlpIn] = {0.f, 0.f, d, (float)c->h_a[pr.second], (float)c->h_a[pr.first]};
             if (net->covers(x0) && net->covers(x1)) kept.push_back(pr);
         }
-        c->n_pairs_dropped = (int)(pairs.size() - kept.size());
+        P.n_dropped = (int)(pairs.size() - kept.size());
         pairs.swap(kept);
     }
     const int np = (int)pairs.size();
@@ -1186,7 +1390,7 @@ sbie_status precond_setup(sbie_ctx* c, int kind, const PairNet* net) {
     sbie_ctx* sc = nullptr;
     CKS(create_part(o, n, c->h_c.data(), c->h_a.data(), ps1, c->stream, &sc));
     std::vector<double> Lam;
-    sbie_status st = probe_blocks(sc, 1, 1, Lam);
+    sbie_status st = probe_blocks(sc, op, 1, 1, Lam);
     if (st != SBIE_OK) c->err = sc->err;
     free_all(sc);
     delete sc;
@@ -1209,7 +1413,7 @@ sbie_status precond_setup(sbie_ctx* c, int kind, const PairNet* net) {
         sbie_ctx* pc = nullptr;
         CKS(create_part(o, 2 * np, cc.data(), aa.data(), ps, c->stream, &pc));
         std::vector<double> PB;
-        st = probe_blocks(pc, 2, 2, PB);
+        st = probe_blocks(pc, op, 2, 2, PB);
         if (st != SBIE_OK) c->err = pc->err;
         const size_t per = (size_t)2 * np * blk;
         if (st == SBIE_OK)
@@ -1264,33 +1468,40 @@ sbie_status precond_setup(sbie_ctx* c, int kind, const PairNet* net) {
             }
     }
     for (size_t i = 0; i < S.size(); ++i) S[i] = (float)Lam[i];
-    bool ok = dmalloc(&c->d_ZS, ZS.size()) == cudaSuccess && dmalloc(&c->d_ZA, ZA.size()) == cudaSuccess &&
-              dmalloc(&c->d_modes, modes.size()) == cudaSuccess && dmalloc(&c->d_pp_ptr, pp_ptr.size()) == cudaSuccess &&
-              dmalloc(&c->d_pp_idx, pp_idx.size()) == cudaSuccess && dmalloc(&c->d_pp_pair, pp_pair.size()) == cudaSuccess &&
-              dmalloc(&c->d_pinv, A.size()) == cudaSuccess && dmalloc(&c->d_sinv, S.size()) == cudaSuccess &&
-              dmalloc(&c->d_low, (size_t)n * NM) == cudaSuccess && dmalloc(&c->d_lowe, (size_t)n * NM) == cudaSuccess;
+    bool ok = dmalloc(&P.d_pp_ptr, pp_ptr.size()) == cudaSuccess && dmalloc(&P.d_pp_idx, pp_idx.size()) == cudaSuccess &&
+              dmalloc(&P.d_pp_pair, pp_pair.size()) == cudaSuccess && dmalloc(&P.d_pinv, A.size()) == cudaSuccess &&
+              dmalloc(&P.d_sinv, S.size()) == cudaSuccess;
+    const bool tables = !c->d_ZS;
+    if (tables)
+        ok = ok && dmalloc(&c->d_ZS, ZS.size()) == cudaSuccess && dmalloc(&c->d_ZA, ZA.size()) == cudaSuccess &&
+             dmalloc(&c->d_modes, modes.size()) == cudaSuccess && dmalloc(&c->d_low, (size_t)n * NM) == cudaSuccess &&
+             dmalloc(&c->d_lowe, (size_t)n * NM) == cudaSuccess;
     if (!ok) return fail(c, SBIE_ERR_OOM, "preconditioner buffers");
     int* d_bad = nullptr;
     CK(cudaMalloc(&d_bad, sizeof(int)));
     CK(cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
-    CK(h2d(c->stream, c->d_ZS, ZS.data(), ZS.size()));
-    CK(h2d(c->stream, c->d_ZA, ZA.data(), ZA.size()));
-    CK(h2d(c->stream, c->d_modes, modes.data(), modes.size()));
-    CK(h2d(c->stream, c->d_pp_ptr, pp_ptr.data(), pp_ptr.size()));
-    CK(h2d(c->stream, c->d_pp_idx, pp_idx.data(), pp_idx.size()));
-    CK(h2d(c->stream, c->d_pp_pair, pp_pair.data(), pp_pair.size()));
-    CK(h2d(c->stream, c->d_pinv, A.data(), A.size()));
-    CK(h2d(c->stream, c->d_sinv, S.data(), S.size()));
-    CK(launch_gauss_jordan(c->stream, 2 * NM, np, c->d_pinv, d_bad));
-    CK(launch_gauss_jordan(c->stream, NM, n, c->d_sinv, d_bad));
+    if (tables) {
+        CK(h2d(c->stream, c->d_ZS, ZS.data(), ZS.size()));
+        CK(h2d(c->stream, c->d_ZA, ZA.data(), ZA.size()));
+        CK(h2d(c->stream, c->d_modes, modes.data(), modes.size()));
+    }
+    CK(h2d(c->stream, P.d_pp_ptr, pp_ptr.data(), pp_ptr.size()));
+    CK(h2d(c->stream, P.d_pp_idx, pp_idx.data(), pp_idx.size()));
+    CK(h2d(c->stream, P.d_pp_pair, pp_pair.data(), pp_pair.size()));
+    CK(h2d(c->stream, P.d_pinv, A.data(), A.size()));
+    CK(h2d(c->stream, P.d_sinv, S.data(), S.size()));
+    CK(launch_gauss_jordan(c->stream, 2 * NM, np, P.d_pinv, d_bad));
+    CK(launch_gauss_jordan(c->stream, NM, n, P.d_sinv, d_bad));
     int bad = 0;
     CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     cudaFree(d_bad);
     if (bad) return fail(c, SBIE_ERR_NUMERIC, "singular pair system in the preconditioner");
-    c->n_pairs = np;
-    c->prec_kind = kind;
-    c->t_prec_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    P.n_pairs = np;
+    P.kind = kind;
+    P.built = true;
+    P.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    ++g_graph_epoch;  // cycle graphs capture the preconditioner's buffers
     return SBIE_OK;
 }
 
@@ -1359,6 +1570,13 @@ sbie_status sphere_bie_create_batch(int n_problems, const int* n_spheres, const 
                                 "problem " + std::to_string(q) + ": spheres " + std::to_string(i - usph[q]) + " and " +
                                     std::to_string(k - usph[q]) + " overlap or touch");
             }
+    // the pair networks are read (and checked) here; the preconditioner of an
+    // operator is built at the first solve with it
+    std::shared_ptr<PairNetSet> nets;
+    if (opts->use_learned_precond == 1) {
+        nets = std::make_shared<PairNetSet>();
+        CKS(net_load(opts->mlp_weights_path, *nets));
+    }
     // group problems by VSH order
     std::vector<int> orders(p_per_problem, p_per_problem + n_problems);
     std::sort(orders.begin(), orders.end());
@@ -1370,13 +1588,7 @@ sbie_status sphere_bie_create_batch(int n_problems, const int* n_spheres, const 
         o.p = orders[0];
         sbie_ctx* c = nullptr;
         CKS(create_part(o, (int)ntot, centres, radii, prob_sph, nullptr, &c));
-        sbie_status ps = setup_preconditioner({c}, *opts);
-        if (ps != SBIE_OK) {
-            g_last_error = c->err;
-            free_all(c);
-            delete c;
-            return ps;
-        }
+        c->nets = nets;
         c->t_create_ms = create_ms();
         *out = c;
         return SBIE_OK;
@@ -1452,15 +1664,7 @@ sbie_status sphere_bie_create_batch(int n_problems, const int* n_spheres, const 
     if (e == cudaSuccess)
         e = h2d(top->stream, top->d_seg3, top->seg3.data(), top->seg3.size());
     if (e != cudaSuccess) return bail(SBIE_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
-    {
-        sbie_status ps = setup_preconditioner(top->parts, *opts);
-        if (ps != SBIE_OK) {
-            std::string m = g_last_error;
-            for (sbie_ctx* q : top->parts)
-                if (q->err != "no error") m = q->err;
-            return bail(ps, m);
-        }
-    }
+    top->nets = nets;
     top->err = "no error";
     top->t_create_ms = create_ms();
     *out = top;
@@ -1796,15 +2000,19 @@ sbie_status sphere_bie_solution_density(sbie_ctx* c, double* density) {
     return SBIE_OK;
 }
 
-sbie_status sphere_bie_precond_info(const sbie_ctx* c, int* kind, int* n_pairs, int* n_dropped, double* setup_ms) {
+sbie_status sphere_bie_precond_info(const sbie_ctx* c, sbie_op op, int* kind, int* n_pairs, int* n_dropped,
+                                    double* setup_ms) {
     if (!c) return SBIE_ERR_ARG;
+    if (op != SBIE_OP_RESISTANCE && op != SBIE_OP_MOBILITY)
+        return fail(const_cast<sbie_ctx*>(c), SBIE_ERR_ARG, "the preconditioner serves the resistance and mobility operators");
+    const int slot = prec_slot(op);
     int k = 0, np = 0, nd = 0;
     double ms = 0.0;
     for (const sbie_ctx* q : c->is_batch ? c->parts : std::vector<sbie_ctx*>{const_cast<sbie_ctx*>(c)}) {
-        k = std::max(k, q->prec_kind);
-        np += q->n_pairs;
-        nd += q->n_pairs_dropped;
-        ms += q->t_prec_setup_ms;
+        k = std::max(k, q->prec[slot].kind);
+        np += q->prec[slot].n_pairs;
+        nd += q->prec[slot].n_dropped;
+        ms += q->prec[slot].setup_ms;
     }
     if (kind) *kind = k;
     if (n_pairs) *n_pairs = np;
@@ -1820,14 +2028,15 @@ sbie_status sphere_bie_pair_network_size(long long* n_params) {
 }
 
 sbie_status sphere_bie_pair_blocks(int n, const double* dist, const double* a_src, const double* a_tgt, int p,
-                                   double* blocks) {
-    if (n < 1 || !dist || !a_src || !a_tgt || !blocks || p < kPrecL || p > kMaxP)
+                                   sbie_op op, double* blocks) {
+    if (n < 1 || !dist || !a_src || !a_tgt || !blocks || p < kPrecL || p > kMaxP ||
+        (op != SBIE_OP_RESISTANCE && op != SBIE_OP_MOBILITY))
         return fail(nullptr, SBIE_ERR_ARG, "pair_blocks: bad arguments");
     for (int q = 0; q < n; ++q)
         if (!(dist[q] > a_src[q] + a_tgt[q]) || !(a_src[q] > 0) || !(a_tgt[q] > 0))
             return fail(nullptr, SBIE_ERR_ARG, "pair_blocks: spheres must be disjoint with positive radii");
     std::vector<double> out;
-    CKS(aligned_blocks(n, dist, a_src, a_tgt, p, 1e9, out));
+    CKS(aligned_blocks(n, dist, a_src, a_tgt, p, 1e9, op, out));
     std::memcpy(blocks, out.data(), sizeof(double) * out.size());
     return SBIE_OK;
 }
@@ -1843,112 +2052,25 @@ sbie_status sphere_bie_pair_network_gradients(const float* params, int n, const 
 sbie_status sphere_bie_train_pair_network(const sbie_pair_train_opts* o, const char* path, sbie_pair_train_info* info) {
     if (!o || !path || o->n_samples < 16 || o->p < kPrecL || o->p > kMaxP || !(o->gap_min > 0) ||
         !(o->gap_max >= o->gap_min) || !(o->radius > 0) || o->epochs < 1 || o->batch < 1 || !(o->val_frac >= 0) ||
-        !(o->val_frac < 0.9))
+        !(o->val_frac < 0.9) || o->ops < 1 || o->ops > 3 || !(o->radius_max == 0.0 || o->radius_max >= o->radius))
         return fail(nullptr, SBIE_ERR_ARG, "train_pair_network: bad options");
-    auto t0 = std::chrono::steady_clock::now();
-    const int n = o->n_samples;
-    std::mt19937_64 rng(o->seed);
-    std::uniform_real_distribution<double> U(std::log(o->gap_min), std::log(o->gap_max));
-    std::vector<double> d(n), as(n, o->radius), at(n, o->radius);
-    for (int q = 0; q < n; ++q) d[q] = 2.0 * o->radius + std::exp(U(rng));
-    std::vector<double> blocks((size_t)n * kMlpOut);
-    const int chunk = 4096;
-    for (int q0 = 0; q0 < n; q0 += chunk) {
-        const int m = std::min(chunk, n - q0);
-        std::vector<double> out;
-        CKS(aligned_blocks(m, d.data() + q0, as.data() + q0, at.data() + q0, o->p, 1e9, out));
-        std::memcpy(blocks.data() + (size_t)q0 * kMlpOut, out.data(), sizeof(double) * out.size());
+    PairNetSet set;
+    sbie_pair_train_info acc{};
+    for (int op : {SBIE_OP_RESISTANCE, SBIE_OP_MOBILITY}) {
+        if (!(o->ops & (op == SBIE_OP_RESISTANCE ? 1 : 2))) continue;
+        PairNet net;
+        sbie_pair_train_info one{};
+        CKS(train_one(*o, op, net, one));
+        set.nets.push_back(std::move(net));
+        acc.train_loss = std::max(acc.train_loss, one.train_loss);
+        acc.val_rel_err = std::max(acc.val_rel_err, one.val_rel_err);
+        acc.t_data_s += one.t_data_s;
+        acc.t_train_s += one.t_train_s;
+        acc.n_train = one.n_train;
+        acc.n_val = one.n_val;
     }
-    auto t1 = std::chrono::steady_clock::now();
-    PairNet net;
-    net.p_train = o->p;
-    std::vector<float> X((size_t)n * kMlpIn, 0.f);
-    for (int q = 0; q < n; ++q) {
-        X[q * kMlpIn + 2] = (float)d[q];
-        X[q * kMlpIn + 3] = (float)as[q];
-        X[q * kMlpIn + 4] = (float)at[q];
-    }
-    for (int j = 0; j < kMlpIn; ++j) {
-        double s = 0, s2 = 0;
-        for (int q = 0; q < n; ++q) {
-            s += X[q * kMlpIn + j];
-            s2 += (double)X[q * kMlpIn + j] * X[q * kMlpIn + j];
-        }
-        const double mu = s / n, var = std::max(0.0, s2 / n - mu * mu);
-        net.in_min[j] = net.in_max[j] = X[j];
-        for (int q = 0; q < n; ++q) {
-            net.in_min[j] = std::min(net.in_min[j], X[q * kMlpIn + j]);
-            net.in_max[j] = std::max(net.in_max[j], X[q * kMlpIn + j]);
-        }
-        net.in_mean[j] = (float)mu;
-        net.in_std[j] = var > 1e-20 ? (float)std::sqrt(var) : 1.f;
-    }
-    net.out_mean.assign(kMlpOut, 0.f);
-    net.out_std.assign(kMlpOut, 1.f);
-    double smax = 0.0;
-    std::vector<double> sd(kMlpOut);
-    for (int k = 0; k < kMlpOut; ++k) {
-        double s = 0, s2 = 0;
-        for (int q = 0; q < n; ++q) {
-            const double v = blocks[(size_t)q * kMlpOut + k];
-            s += v;
-            s2 += v * v;
-        }
-        const double mu = s / n;
-        sd[k] = std::sqrt(std::max(0.0, s2 / n - mu * mu));
-        net.out_mean[k] = (float)mu;
-        smax = std::max(smax, sd[k]);
-    }
-    // Entries that do not vary over the samples (most of the block: in the
-    // pair frame only modes of equal order m couple) get std 0, so that the
-    // prediction is their mean exactly and the network's error there is not
-    // added to the block; their standardised target is 0.
-    for (int k = 0; k < kMlpOut; ++k) net.out_std[k] = sd[k] > 1e-6 * smax ? (float)sd[k] : 0.f;
-    std::vector<float> Xs(X.size()), Ys((size_t)n * kMlpOut);
-    for (int q = 0; q < n; ++q) {
-        for (int j = 0; j < kMlpIn; ++j) Xs[q * kMlpIn + j] = (X[q * kMlpIn + j] - net.in_mean[j]) / net.in_std[j];
-        for (int k = 0; k < kMlpOut; ++k)
-            Ys[(size_t)q * kMlpOut + k] =
-                net.out_std[k] > 0.f
-                    ? (float)((blocks[(size_t)q * kMlpOut + k] - net.out_mean[k]) / net.out_std[k])
-                    : 0.f;
-    }
-    const int nval = (int)(o->val_frac * n), ntr = n - nval;
-    mlp_init(o->seed + 1, net.params);
-    MlpTrainOpts to;
-    to.epochs = o->epochs;
-    to.batch = o->batch;
-    to.lr = o->lr;
-    to.seed = o->seed + 2;
-    std::vector<double> hist;
-    cudaError_t e = mlp_train(to, ntr, Xs.data(), Ys.data(), net.params.data(), hist);
-    if (e != cudaSuccess) return fail(nullptr, SBIE_ERR_CUDA, std::string("training: ") + cudaGetErrorString(e));
-    auto t2 = std::chrono::steady_clock::now();
-    double val = 0.0;
-    if (nval > 0) {
-        std::vector<float> Xv(X.begin() + (size_t)ntr * kMlpIn, X.end());
-        std::vector<double> P;
-        CKS(net_blocks(net, Xv, P));
-        for (int q = 0; q < nval; ++q) {
-            double num = 0, den = 0;
-            for (int k = 0; k < kMlpOut; ++k) {
-                const double t = blocks[(size_t)(ntr + q) * kMlpOut + k], y = P[(size_t)q * kMlpOut + k];
-                num += (y - t) * (y - t);
-                den += t * t;
-            }
-            val += std::sqrt(num / den);
-        }
-        val /= nval;
-    }
-    CKS(net_save(path, net));
-    if (info) {
-        info->train_loss = hist.empty() ? 0.0 : hist.back();
-        info->val_rel_err = val;
-        info->t_data_s = std::chrono::duration<double>(t1 - t0).count();
-        info->t_train_s = std::chrono::duration<double>(t2 - t1).count();
-        info->n_train = ntr;
-        info->n_val = nval;
-    }
+    CKS(net_save(path, set));
+    if (info) *info = acc;
     return SBIE_OK;
 }
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <utility>
 #include <vector>
@@ -105,6 +106,24 @@ struct CycleGraph {
     long long body_launches = 0;
 };
 
+// Pair preconditioner of one operator of a context (slot 0: resistance,
+// Eq. 5.19; slot 1: mobility, Eq. 5.8), built at the first solve with it.
+struct PrecState {
+    int kind = 0;              // 0 none, 1 pair network, 2 exact pair blocks
+    bool built = false;        // set up, or found unavailable, for this operator
+    int n_pairs = 0;           // undirected pairs in the pair systems
+    int n_dropped = 0;         // close pairs outside the network's trained range
+    double setup_ms = 0.0;
+    int* d_pp_ptr = nullptr;   // [n+1] per-sphere lists of the pairs
+    int* d_pp_idx = nullptr;   // partner sphere
+    int* d_pp_pair = nullptr;  // pair index into d_pinv
+    float* d_pinv = nullptr;   // [n_pairs][146][146] inverses of the pair systems
+    float* d_sinv = nullptr;   // [n][73][73] inverses of the spheres' own low-mode blocks
+};
+constexpr int prec_slot(int op) { return op == SBIE_OP_MOBILITY ? 1 : 0; }
+
+struct PairNetSet;  // trained pair networks (api.cu)
+
 }  // namespace sbie
 
 struct sbie_ctx {
@@ -137,22 +156,16 @@ struct sbie_ctx {
     double* d_pvec = nullptr;           // [n_prob_total] per-problem scalars
     size_t red_cap = 0, hred_cap = 0;
 
-    // pair preconditioner (precond.cu): 0 none, 1 learned pair network, 2 exact blocks
-    int prec_kind = 0;
+    // pair preconditioner (precond.cu), per operator; the low-mode tables and
+    // work vectors are shared by both operators
+    sbie::PrecState prec[2];
+    std::shared_ptr<sbie::PairNetSet> nets;  // networks of opts.mlp_weights_path (top context)
     double* d_ZS = nullptr;        // [npn][3][73] low-mode synthesis
     double* d_ZA = nullptr;        // [73][npn][3] low-mode analysis
     int4* d_modes = nullptr;       // [73] (type, n, m, part)
-    int* d_pp_ptr = nullptr;       // [n+1] per-sphere lists of the preconditioner's pairs
-    int* d_pp_idx = nullptr;       // partner sphere
-    int* d_pp_pair = nullptr;      // pair index into d_pinv
-    int n_pairs = 0;
-    int n_pairs_dropped = 0;       // close pairs outside the network's trained range
-    float* d_pinv = nullptr;       // [n_pairs][146][146] inverses of the pair systems
-    float* d_sinv = nullptr;       // [n][73][73] inverses of the spheres' own low-mode blocks
     double* d_low = nullptr;       // [n][73]
     double* d_lowe = nullptr;      // [n][73]
     double* d_pz = nullptr;        // preconditioned vector (system level)
-    double t_prec_setup_ms = 0.0;
     double t_create_ms = 0.0;      // wall time of create (grid, tables, close pairs, preconditioner)
     bool has_solution = false;     // d_xsol holds the density of the last solve
 
@@ -170,6 +183,12 @@ struct sbie_ctx {
     float4* d_nrm = nullptr;     // [N] outward normal (float)
     double* d_nrm64 = nullptr;   // [N][4] outward normal (double)
     int* d_sph = nullptr;        // [N] sphere index of each node
+    long long far_pair_count = 0;  // (target, source) node pairs of the far field per apply
+    // Per-problem flags of the running GMRES cycle (system numbering from
+    // far_live_off): the far field skips target spheres of stopped problems,
+    // whose Krylov vectors are zero.  Null outside the cycle.
+    const int* far_live = nullptr;
+    int far_live_off = 0;
     int* d_near_ptr = nullptr;   // [n+1] CSR of close pairs by target sphere
     int* d_near_idx = nullptr;
     double* d_tab = nullptr;
@@ -252,7 +271,7 @@ std::vector<int4> low_mode_table();
 cudaError_t launch_gauss_jordan(cudaStream_t s, int n, int count, float* mats, int* d_bad);
 cudaError_t launch_probe_density(sbie_ctx* c, int sph_per_prob, int side, int beta, const double* ZS, double* dens);
 cudaError_t launch_probe_analysis(sbie_ctx* c, const double* ZA, const double* u, int beta, double* blocks);
-cudaError_t precond_apply(sbie_ctx* c, const double* v, double* out);
+cudaError_t precond_apply(sbie_ctx* c, int slot, const double* v, double* out);
 // far.cu
 cudaError_t launch_pack(sbie_ctx* c, const double* dens, int mode);
 cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out);

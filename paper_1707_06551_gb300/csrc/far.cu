@@ -38,8 +38,25 @@ struct FarArgs {
     const int* __restrict__ near_idx;
     const int* __restrict__ sph_prob;  // problem of each sphere
     const int* __restrict__ prob_sph;  // first sphere of each problem (+ end)
+    const int* __restrict__ live;      // per-problem flags of a running GMRES cycle, or null
+    int live_off;                      // system index of this context's first problem
     double* __restrict__ part;  // [split][N][3]
 };
+
+// A target sphere whose problem stopped iterating (its Krylov vectors are
+// zero): the CTA writes zero partial sums for its targets and leaves.  The
+// test depends on the sphere alone, so the whole CTA takes the same branch.
+__device__ __forceinline__ bool far_skip(const FarArgs& a, int sphere, int chunk, int split, int tpt) {
+    if (!a.live || a.live[a.live_off + a.sph_prob[sphere]]) return false;
+    double* out = a.part + (size_t)split * a.N * 3;
+    for (int t = 0; t < tpt; ++t) {
+        const int q = chunk * (blockDim.x * tpt) + t * blockDim.x + threadIdx.x;
+        if (q >= a.npn) continue;
+        const long long node = (long long)sphere * a.npn + q;
+        out[node * 3] = out[node * 3 + 1] = out[node * 3 + 2] = 0.0;
+    }
+    return true;
+}
 
 // Source nodes of split `split` for a target sphere: its problem's nodes cut
 // into gridDim.y tile-aligned pieces.
@@ -104,6 +121,7 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
     const int sphere = blockIdx.x / a.chunks, chunk = blockIdx.x - sphere * a.chunks;
     const int split = blockIdx.y;
     const int tid = threadIdx.x, bd = blockDim.x;
+    if (far_skip(a, sphere, chunk, split, TPT)) return;
     extern __shared__ float4 smem4[];
     // [tile][NV] staged sources | [TPT][3][2][bd] running sums and compensations | sphere flags
     float* run = reinterpret_cast<float*>(smem4 + NV * a.tile);
@@ -316,6 +334,7 @@ __global__ void __launch_bounds__(256) far_df_kernel(FarArgs a) {
     const int sphere = blockIdx.x / a.chunks, chunk = blockIdx.x - sphere * a.chunks;
     const int split = blockIdx.y;
     const int tid = threadIdx.x, bd = blockDim.x;
+    if (far_skip(a, sphere, chunk, split, 1)) return;
     extern __shared__ float4 smem4[];
     unsigned* flags = reinterpret_cast<unsigned*>(smem4 + NV * a.tile);
     build_flags(a, sphere, flags);
@@ -410,6 +429,7 @@ __global__ void __launch_bounds__(256) far_f64_kernel(FarArgs a) {
     const int sphere = blockIdx.x / a.chunks, chunk = blockIdx.x - sphere * a.chunks;
     const int split = blockIdx.y;
     const int tid = threadIdx.x, bd = blockDim.x;
+    if (far_skip(a, sphere, chunk, split, TPT)) return;
     extern __shared__ double4 smem8[];
     double4* s_pos = smem8;
     double4* s_den = smem8 + a.tile;
@@ -607,6 +627,8 @@ static FarArgs make_args(sbie_ctx* c, const FarTune& tu) {
     a.c = c->d_c; a.sph = c->d_sph; a.near_ptr = c->d_near_ptr; a.near_idx = c->d_near_idx;
     a.sph_prob = c->d_sph_prob; a.prob_sph = c->d_prob_sph;
     a.part = c->d_part;
+    a.live = c->far_live;
+    a.live_off = c->far_live_off;
     return a;
 }
 

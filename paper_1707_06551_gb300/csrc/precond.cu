@@ -421,7 +421,8 @@ std::vector<int4> low_mode_table() {
 }
 
 // M^{-1} v on one part (device vectors of that part): see the header comment.
-cudaError_t precond_apply(sbie_ctx* c, const double* v, double* out) {
+cudaError_t precond_apply(sbie_ctx* c, int slot, const double* v, double* out) {
+    const PrecState& P = c->prec[slot];
     const long long n3 = c->N * 3;
     // H v: synthesis of (1/D+ above degree 4, 0 below) minus 2, plus 2 v; the
     // self kernel also leaves the VSH coefficients of v in d_coef
@@ -430,7 +431,7 @@ cudaError_t precond_apply(sbie_ctx* c, const double* v, double* out) {
     if (e != cudaSuccess) return e;
     gather_low_kernel<<<c->n, 96, 0, c->stream>>>(c->n, c->p + 1, c->d_coef, c->d_modes, c->d_low);
     ++c->n_launch;
-    coarse_kernel<<<c->n, 96, 0, c->stream>>>(c->d_pp_ptr, c->d_pp_idx, c->d_pp_pair, c->d_pinv, c->d_sinv,
+    coarse_kernel<<<c->n, 96, 0, c->stream>>>(P.d_pp_ptr, P.d_pp_idx, P.d_pp_pair, P.d_pinv, P.d_sinv,
                                               c->d_low, c->d_lowe);
     ++c->n_launch;
     synth_add_kernel<<<(unsigned)((c->N + 127) / 128), 128, 0, c->stream>>>(c->npn, c->N, c->d_ZS, c->d_lowe, out);

@@ -36,7 +36,7 @@ class SolveInfo(ctypes.Structure):
                 ("rel_residual_true", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
                 ("t_solve_ms", ctypes.c_double), ("n_near_pairs", ctypes.c_longlong),
                 ("graph_cycles", ctypes.c_int), ("kernel_launches", ctypes.c_longlong),
-                ("fp32_residual_updates", ctypes.c_int)]
+                ("fp32_residual_updates", ctypes.c_int), ("fp32_op_err", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -57,7 +57,7 @@ class PairTrainOpts(ctypes.Structure):
     _fields_ = [("n_samples", ctypes.c_int), ("p", ctypes.c_int), ("gap_min", ctypes.c_double),
                 ("gap_max", ctypes.c_double), ("radius", ctypes.c_double), ("epochs", ctypes.c_int),
                 ("batch", ctypes.c_int), ("lr", ctypes.c_double), ("seed", ctypes.c_ulonglong),
-                ("val_frac", ctypes.c_double)]
+                ("val_frac", ctypes.c_double), ("ops", ctypes.c_int), ("radius_max", ctypes.c_double)]
 
 
 class PairTrainInfo(ctypes.Structure):
@@ -97,11 +97,12 @@ def lib():
         L.sphere_bie_profile_read.argtypes = [_P, ctypes.POINTER(Profile)]
         L.sphere_bie_train_pair_network.argtypes = [ctypes.POINTER(PairTrainOpts), ctypes.c_char_p,
                                                     ctypes.POINTER(PairTrainInfo)]
-        L.sphere_bie_pair_blocks.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]
+        L.sphere_bie_pair_blocks.argtypes = [ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P]
         L.sphere_bie_pair_network_size.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
         L.sphere_bie_solution_density.argtypes = [_P, _P]
-        L.sphere_bie_precond_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        L.sphere_bie_precond_info.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_double)]
         L.sphere_bie_pair_network_gradients.argtypes = [_P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]
         L.sphere_bie_autotune.argtypes = [_P, ctypes.c_int, ctypes.POINTER(FarTuning)]
         L.sphere_bie_apply_layer_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]
@@ -242,19 +243,22 @@ def sphere_bie_autotune(ctx, op):
 
 
 def sphere_bie_train_pair_network(path, n_samples=4096, p=10, gap_min=0.01, gap_max=0.5, radius=1.0, epochs=200,
-                                  batch=256, lr=2e-3, seed=7, val_frac=0.1):
-    o = PairTrainOpts(n_samples, p, gap_min, gap_max, radius, epochs, batch, lr, seed, val_frac)
+                                  batch=256, lr=2e-3, seed=7, val_frac=0.1, ops=("resistance",), radius_max=None):
+    bits = sum({"resistance": 1, "mobility": 2}[o] for o in ops)
+    o = PairTrainOpts(n_samples, p, gap_min, gap_max, radius, epochs, batch, lr, seed, val_frac, bits,
+                      radius if radius_max is None else radius_max)
     info = PairTrainInfo()
     _check(None, lib().sphere_bie_train_pair_network(ctypes.byref(o), str(path).encode(), ctypes.byref(info)))
     return {k: getattr(info, k) for k, _ in info._fields_}
 
 
-def sphere_bie_pair_blocks(dist, a_src, a_tgt, p):
+def sphere_bie_pair_blocks(dist, a_src, a_tgt, p, op="resistance"):
     d = np.ascontiguousarray(dist, dtype=np.float64).reshape(-1)
     s = np.ascontiguousarray(np.broadcast_to(a_src, d.shape), dtype=np.float64)
     t = np.ascontiguousarray(np.broadcast_to(a_tgt, d.shape), dtype=np.float64)
     out = np.zeros((len(d), 73, 73))
-    _check(None, lib().sphere_bie_pair_blocks(len(d), _ptr(d), _ptr(s), _ptr(t), int(p), _ptr(out)))
+    op = OPS[op] if isinstance(op, str) else int(op)
+    _check(None, lib().sphere_bie_pair_blocks(len(d), _ptr(d), _ptr(s), _ptr(t), int(p), op, _ptr(out)))
     return out
 
 
@@ -263,9 +267,10 @@ def sphere_bie_solution_density(ctx, out):
     return out
 
 
-def sphere_bie_precond_info(ctx):
+def sphere_bie_precond_info(ctx, op="resistance"):
+    op = OPS[op] if isinstance(op, str) else int(op)
     k, npairs, nd, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-    _check(ctx, lib().sphere_bie_precond_info(ctx, ctypes.byref(k), ctypes.byref(npairs), ctypes.byref(nd),
+    _check(ctx, lib().sphere_bie_precond_info(ctx, op, ctypes.byref(k), ctypes.byref(npairs), ctypes.byref(nd),
                                               ctypes.byref(ms)))
     return {"kind": k.value, "pairs": npairs.value, "dropped": nd.value, "setup_ms": ms.value}
 

@@ -26,10 +26,12 @@ def _bf16(x):
     return r.view(np.float32)
 
 
-@pytest.mark.parametrize("d,a_s,a_t", [(2.1, 1.0, 1.0), (2.6, 1.0, 1.0), (2.05, 0.8, 1.2)])
-def test_pair_blocks_match_oracle(sb, d, a_s, a_t):
-    got = sb.sphere_bie_pair_blocks([d], a_s, a_t, 6)[0]
-    ref = opb.aligned_block(d, a_s, a_t, 6, 4)
+@pytest.mark.parametrize("d,a_s,a_t,op", [(2.1, 1.0, 1.0, "resistance"), (2.6, 1.0, 1.0, "resistance"),
+                                          (2.05, 0.8, 1.2, "resistance"), (2.1, 1.0, 1.0, "mobility"),
+                                          (2.05, 1.2, 0.8, "mobility")])
+def test_pair_blocks_match_oracle(sb, d, a_s, a_t, op):
+    got = sb.sphere_bie_pair_blocks([d], a_s, a_t, 6, op)[0]
+    ref = opb.aligned_block(d, a_s, a_t, 6, 4, op)
     assert np.max(np.abs(got - ref)) < 1e-9 * np.max(np.abs(ref))
 
 
@@ -102,3 +104,42 @@ def test_learned_pair_preconditioner(sb, tmp_path):
     # the network's gain over the unpreconditioned method, and its distance from exact blocks
     assert i1["iters"] < 0.8 * i0["iters"], (i0["iters"], i1["iters"], i2["iters"])
     assert i1["iters"] <= i2["iters"] + 3, (i1["iters"], i2["iters"])
+
+
+def test_exact_pair_preconditioner_mobility(sb):
+    c, a, p = _suspension()
+    rng = np.random.default_rng(6)
+    F, T = rng.normal(size=(len(a), 3)), rng.normal(size=(len(a), 3))
+    with sb.SphereBIE(c, a, p, prec=1, tol=1e-10) as s:
+        v0, w0, i0 = s.mobility(F, T)
+    with sb.SphereBIE(c, a, p, prec=1, tol=1e-10, precond=2) as s:
+        v1, w1, i1 = s.mobility(F, T)
+        pm = sb.sphere_bie_precond_info(s.ctx, "mobility")
+        pr = sb.sphere_bie_precond_info(s.ctx, "resistance")
+    assert i1["status"] == 0 and pm["kind"] == 2 and pm["pairs"] > 0 and pr["kind"] == 0
+    assert np.max(np.abs(v1 - v0)) < 1e-7 * np.max(np.abs(v0))
+    assert i1["iters"] < 0.75 * i0["iters"], (i0["iters"], i1["iters"])
+
+
+def test_learned_mobility_network_and_fallback(sb, tmp_path):
+    both = tmp_path / "both.bin"
+    res_only = tmp_path / "res.bin"
+    info = sb.sphere_bie_train_pair_network(both, n_samples=2000, p=6, epochs=200, seed=9,
+                                            ops=("resistance", "mobility"))
+    assert info["val_rel_err"] < 0.01, info
+    sb.sphere_bie_train_pair_network(res_only, n_samples=600, p=6, epochs=50, seed=9)
+    c, a, p = _suspension()
+    rng = np.random.default_rng(8)
+    F, T = rng.normal(size=(len(a), 3)), rng.normal(size=(len(a), 3))
+    with sb.SphereBIE(c, a, p, tol=1e-10) as s:
+        v0, w0, i0 = s.mobility(F, T)
+    with sb.SphereBIE(c, a, p, tol=1e-10, precond=1, weights=both) as s:
+        v1, w1, i1 = s.mobility(F, T)
+        pm = sb.sphere_bie_precond_info(s.ctx, "mobility")
+    with sb.SphereBIE(c, a, p, tol=1e-10, precond=1, weights=res_only) as s:
+        v2, w2, i2 = s.mobility(F, T)
+        pf = sb.sphere_bie_precond_info(s.ctx, "mobility")
+    assert pm["kind"] == 1 and i1["status"] == 0 and i1["iters"] < 0.8 * i0["iters"], (i0["iters"], i1["iters"])
+    assert np.max(np.abs(v1 - v0)) < 1e-7 * np.max(np.abs(v0))
+    # no mobility network in the file: the mobility solve runs unpreconditioned
+    assert pf["kind"] == 0 and i2["iters"] == i0["iters"] and np.max(np.abs(v2 - v0)) < 1e-9 * np.max(np.abs(v0))

@@ -1,6 +1,7 @@
 """Pins of the two-sphere low-mode blocks and of the reference network's
 gradients (the learned pair preconditioner)."""
 import numpy as np
+import pytest
 
 from oracle import pairblock as pb
 from oracle import signatures
@@ -15,24 +16,27 @@ def test_low_mode_count_and_roundtrip():
     np.testing.assert_allclose(pb.coef_to_low(pb.low_to_coef(a, L, 6), L), a)
 
 
-def test_self_block_is_exterior_double_layer_above_degree_one():
-    """For n >= 2 the completion carries no moment, so the self block of
-    1/2 I + D + N is diagonal with the exterior eigenvalues D+ (Theorem 2)."""
-    B = pb.two_sphere_blocks([[0, 0, 0], [50.0, 0, 0]], [1.0, 1.0], 5, L)
+@pytest.mark.parametrize("op,sig", [("resistance", signatures.D_plus), ("mobility", signatures.K_minus)])
+def test_self_block_is_exterior_operator_above_degree_one(op, sig):
+    """For n >= 2 the completion (N of Eq. 5.19, L of Eq. 5.8) carries no
+    moment, so the self block of 1/2 I + D + N is diagonal with the exterior
+    eigenvalues D+, and that of 1/2 I + K + L with K- (Theorem 2)."""
+    B = pb.two_sphere_blocks([[0, 0, 0], [50.0, 0, 0]], [1.0, 1.0], 5, L, op=op)
     B00 = B[0, 0]
     modes = pb.low_modes(L)
     for j, (t, n, m, part) in enumerate(modes):
         if n < 2:
             continue
         col = B00[:, j]
-        assert abs(col[j] - signatures.D_plus(n)[t]) < 1e-11
+        assert abs(col[j] - sig(n)[t]) < 1e-11
         assert np.max(np.abs(np.delete(col, j))) < 1e-11
 
 
-def test_aligned_block_conserves_m():
+@pytest.mark.parametrize("op", ["resistance", "mobility"])
+def test_aligned_block_conserves_m(op):
     """Rotations about the pair axis commute with the operator: no coupling
     between different orders m in the pair frame."""
-    B = pb.aligned_block(2.3, 1.0, 1.0, 5, L)
+    B = pb.aligned_block(2.3, 1.0, 1.0, 5, L, op=op)
     modes = pb.low_modes(L)
     scale = np.max(np.abs(B))
     for i, (ti, ni, mi, pi_) in enumerate(modes):

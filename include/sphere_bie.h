@@ -102,6 +102,7 @@ typedef struct {
                                   because the correction d was small enough (see SBIE_MIXED)  */
     double fp32_op_err;     /* SBIE_MIXED: measured ||A64 x - A32 x|| / ||A64 x|| at the first
                                FP64-accurate residual (worst problem)                        */
+    double last_correction; /* SBIE_MIXED: ||d|| / ||x|| of the last correction (worst problem) */
 } sbie_solve_info;
 
 /* Fills *opts with defaults: p = 8, eta = 1, FP64, tol = 1e-8, restart = 60,

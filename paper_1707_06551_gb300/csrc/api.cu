@@ -688,8 +688,11 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
                 std::vector<double> dn, xn;
                 CKS(seg_norms(S, d, dn));
                 CKS(seg_norms(S, x, xn));
-                for (int p = 0; p < P; ++p)
+                inf.last_correction = 0.0;
+                for (int p = 0; p < P; ++p) {
+                    if (xn[p] > 0.0) inf.last_correction = std::max(inf.last_correction, dn[p] / xn[p]);
                     if (dn[p] > 0.0 && !(eps32 * dn[p] <= 0.1 * tol * xn[p])) cheap = false;
+                }
             }
             if (cheap) {
                 CKS(A32(d, t));

@@ -310,6 +310,33 @@ __device__ __forceinline__ df df_sqr(df x) {
     e = fmaf(2.f * x.h, x.l, e);
     return fast_two_sum(p, e);
 }
+// Lighter building blocks for the pair loop.  A product of two normalised
+// values is left as (p, e) with |e| <= ulp(p) (no renormalisation: the next
+// product or sum absorbs it); a difference keeps the exact TwoSum high part.
+__device__ __forceinline__ df df_diff(df x, df y) {  // x - y
+    df s = two_sum(x.h, -y.h);
+    return df{s.h, s.l + (x.l - y.l)};
+}
+__device__ __forceinline__ df df_mul_l(df x, df y) {
+    float p = x.h * y.h;
+    float e = fmaf(x.h, y.h, -p);
+    e = fmaf(x.h, y.l, e);
+    e = fmaf(x.l, y.h, e);
+    return df{p, e};
+}
+__device__ __forceinline__ df df_sqr_l(df x) {
+    float p = x.h * x.h;
+    float e = fmaf(x.h, x.h, -p);
+    e = fmaf(x.h + x.h, x.l, e);
+    return df{p, e};
+}
+// sum of three such (p, e) terms, renormalised (the sum may cancel)
+__device__ __forceinline__ df df_sum3(df a, df b, df c) {
+    df s = two_sum(a.h, b.h);
+    df t = two_sum(s.h, c.h);
+    return two_sum(t.h, (s.l + t.l) + (a.l + b.l + c.l));
+}
+
 // 1/sqrt(x) for x > 0: hardware estimate y0, then one Newton step carried in
 // df with its second-order term: y = y0 (1 - t/2 + 3 t^2 / 8), t = x y0^2 - 1.
 __device__ __forceinline__ df df_rsqrt(df x) {
@@ -388,29 +415,36 @@ __global__ void __launch_bounds__(256) far_df_kernel(FarArgs a) {
         for (int j = 0; j < a.tile; ++j) {
             const float4* src = smem4 + (size_t)j * NV;
             const float4 v0 = src[0], v1 = src[1], v2 = src[2];
-            const df dx = df_sub(tx, df{v0.x, v0.y}), dy = df_sub(ty, df{v0.z, v0.w}), dz = df_sub(tz, df{v1.x, v1.y});
+            const df dx = df_diff(tx, df{v0.x, v0.y}), dy = df_diff(ty, df{v0.z, v0.w}), dz = df_diff(tz, df{v1.x, v1.y});
             const df fx{v1.z, v1.w}, fy{v2.x, v2.y}, fz{v2.z, v2.w};
-            const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
-            const df ri = df_rsqrt(r2);
-            const df ri2 = df_sqr(ri);
-            const df rf = df_add(df_add(df_mul(dx, fx), df_mul(dy, fy)), df_mul(dz, fz));
+            // |d|^2 and the dot products: exact products, one renormalised sum
+            const df q = df_sum3(df_sqr_l(dx), df_sqr_l(dy), df_sqr_l(dz));
+            const df ri = df_rsqrt(q);
+            const df ri2 = df_sqr_l(ri);
+            const df rf = df_sum3(df_mul_l(dx, fx), df_mul_l(dy, fy), df_mul_l(dz, fz));
             if (OP == (int)Kern::S) {
-                const df s3 = df_mul(df_mul(rf, ri), ri2);
-                acc0 = df_add(acc0, df_add(df_mul(fx, ri), df_mul(dx, s3)));
-                acc1 = df_add(acc1, df_add(df_mul(fy, ri), df_mul(dy, s3)));
-                acc2 = df_add(acc2, df_add(df_mul(fz, ri), df_mul(dz, s3)));
+                const df s3 = df_mul_l(df_mul_l(rf, ri), ri2);
+                const df ax = df_add(df_mul_l(fx, ri), df_mul_l(dx, s3));
+                const df ay = df_add(df_mul_l(fy, ri), df_mul_l(dy, s3));
+                const df az = df_add(df_mul_l(fz, ri), df_mul_l(dz, s3));
+                df t = two_sum(acc0.h, ax.h); acc0 = df{t.h, acc0.l + (t.l + ax.l)};
+                t = two_sum(acc1.h, ay.h); acc1 = df{t.h, acc1.l + (t.l + ay.l)};
+                t = two_sum(acc2.h, az.h); acc2 = df{t.h, acc2.l + (t.l + az.l)};
             } else {
                 df rn;
                 if (OP == (int)Kern::D) {
                     const float4 v3 = src[3], v4 = src[4];
-                    rn = df_add(df_add(df_mul(dx, df{v3.x, v3.y}), df_mul(dy, df{v3.z, v3.w})), df_mul(dz, df{v4.x, v4.y}));
+                    rn = df_sum3(df_mul_l(dx, df{v3.x, v3.y}), df_mul_l(dy, df{v3.z, v3.w}), df_mul_l(dz, df{v4.x, v4.y}));
                 } else {
-                    rn = df_add(df_add(df_mul(dx, tnx), df_mul(dy, tny)), df_mul(dz, tnz));
+                    rn = df_sum3(df_mul_l(dx, tnx), df_mul_l(dy, tny), df_mul_l(dz, tnz));
                 }
-                const df s5 = df_mul(df_mul(rf, rn), df_mul(df_sqr(ri2), ri));
-                acc0 = df_add(acc0, df_mul(dx, s5));
-                acc1 = df_add(acc1, df_mul(dy, s5));
-                acc2 = df_add(acc2, df_mul(dz, s5));
+                const df s5 = df_mul_l(df_mul_l(rf, rn), df_mul_l(df_sqr_l(ri2), ri));
+                // running sums: exact TwoSum of the high parts, low parts
+                // gathered and renormalised once per tile
+                const df ax = df_mul_l(dx, s5), ay = df_mul_l(dy, s5), az = df_mul_l(dz, s5);
+                df t = two_sum(acc0.h, ax.h); acc0 = df{t.h, acc0.l + (t.l + ax.l)};
+                t = two_sum(acc1.h, ay.h); acc1 = df{t.h, acc1.l + (t.l + ay.l)};
+                t = two_sum(acc2.h, az.h); acc2 = df{t.h, acc2.l + (t.l + az.l)};
             }
         }
         sum[0] += (double)acc0.h + (double)acc0.l;
@@ -561,9 +595,10 @@ long long far_pairs(const sbie_ctx* c) {
     return tot;
 }
 
+// nts: target spheres launched (the first nts; all of them outside timing)
 template <int OP>
-static cudaError_t launch_far_df(sbie_ctx* c, const FarTune& tu, const FarArgs& a) {
-    dim3 grid(c->n * a.chunks, tu.split);
+static cudaError_t launch_far_df(sbie_ctx* c, const FarTune& tu, const FarArgs& a, int nts) {
+    dim3 grid(nts * a.chunks, tu.split);
     const int nv = (OP == (int)Kern::D) ? 5 : 3;
     size_t sm = (size_t)nv * tu.tile * sizeof(float4) + ((c->n + 31) / 32) * sizeof(unsigned);
     if (sm > 48 * 1024) {
@@ -575,8 +610,8 @@ static cudaError_t launch_far_df(sbie_ctx* c, const FarTune& tu, const FarArgs& 
 }
 
 template <int OP, int TPT>
-static cudaError_t launch_far_t(sbie_ctx* c, const FarTune& tu, bool f32, const FarArgs& a) {
-    dim3 grid(c->n * a.chunks, tu.split);
+static cudaError_t launch_far_t(sbie_ctx* c, const FarTune& tu, bool f32, const FarArgs& a, int nts) {
+    dim3 grid(nts * a.chunks, tu.split);
     int nv = (OP == (int)Kern::D) ? 3 : 2;
     size_t words = ((c->n + 31) / 32) * sizeof(unsigned);
     if (f32) {
@@ -602,12 +637,12 @@ static cudaError_t launch_far_t(sbie_ctx* c, const FarTune& tu, bool f32, const 
 }
 
 template <int OP>
-static cudaError_t launch_far_op(sbie_ctx* c, const FarTune& tu, bool f32, const FarArgs& a) {
+static cudaError_t launch_far_op(sbie_ctx* c, const FarTune& tu, bool f32, const FarArgs& a, int nts) {
     switch (tu.tpt) {
-        case 1: return launch_far_t<OP, 1>(c, tu, f32, a);
-        case 2: return launch_far_t<OP, 2>(c, tu, f32, a);
-        case 6: return f32 ? launch_far_t<OP, 6>(c, tu, true, a) : cudaErrorInvalidValue;
-        default: return launch_far_t<OP, 4>(c, tu, f32, a);
+        case 1: return launch_far_t<OP, 1>(c, tu, f32, a, nts);
+        case 2: return launch_far_t<OP, 2>(c, tu, f32, a, nts);
+        case 6: return f32 ? launch_far_t<OP, 6>(c, tu, true, a, nts) : cudaErrorInvalidValue;
+        default: return launch_far_t<OP, 4>(c, tu, f32, a, nts);
     }
 }
 
@@ -632,20 +667,20 @@ static FarArgs make_args(sbie_ctx* c, const FarTune& tu) {
     return a;
 }
 
-static cudaError_t launch_pair_kernel(sbie_ctx* c, Kern op, int mode, const FarTune& tu) {
+static cudaError_t launch_pair_kernel(sbie_ctx* c, Kern op, int mode, const FarTune& tu, int nts) {
     FarArgs a = make_args(c, tu);
     if (mode == kModeDF) {
         switch (op) {
-            case Kern::S: return launch_far_df<(int)Kern::S>(c, tu, a);
-            case Kern::D: return launch_far_df<(int)Kern::D>(c, tu, a);
-            default: return launch_far_df<(int)Kern::K>(c, tu, a);
+            case Kern::S: return launch_far_df<(int)Kern::S>(c, tu, a, nts);
+            case Kern::D: return launch_far_df<(int)Kern::D>(c, tu, a, nts);
+            default: return launch_far_df<(int)Kern::K>(c, tu, a, nts);
         }
     }
     const bool f32 = mode == kModeF32;
     switch (op) {
-        case Kern::S: return launch_far_op<(int)Kern::S>(c, tu, f32, a);
-        case Kern::D: return launch_far_op<(int)Kern::D>(c, tu, f32, a);
-        default: return launch_far_op<(int)Kern::K>(c, tu, f32, a);
+        case Kern::S: return launch_far_op<(int)Kern::S>(c, tu, f32, a, nts);
+        case Kern::D: return launch_far_op<(int)Kern::D>(c, tu, f32, a, nts);
+        default: return launch_far_op<(int)Kern::K>(c, tu, f32, a, nts);
     }
 }
 
@@ -654,7 +689,7 @@ cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out) {
     cudaError_t e;
     {
         StageScope st(c, mode == kModeF32 ? ST_FARK32 : ST_FARK64);
-        e = launch_pair_kernel(c, op, mode, tu);
+        e = launch_pair_kernel(c, op, mode, tu, c->n);
     }
     if (e != cudaSuccess) return e;
     double scale = (op == Kern::S) ? 1.0 / (8.0 * kPi) : (op == Kern::D ? 3.0 / (4.0 * kPi) : -3.0 / (4.0 * kPi));
@@ -663,6 +698,9 @@ cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out) {
     return cudaGetLastError();
 }
 
+// One pair-kernel launch timed with CUDA events.  Large contexts time the
+// first 512 target spheres only (every CTA does the same work as in a full
+// launch, and 512 spheres are several waves), so tuning stays cheap.
 cudaError_t time_far(sbie_ctx* c, Kern op, int mode, const FarTune& tu, float* ms) {
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
@@ -670,7 +708,7 @@ cudaError_t time_far(sbie_ctx* c, Kern op, int mode, const FarTune& tu, float* m
     e = cudaEventCreate(&e1);
     if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
     e = cudaEventRecord(e0, c->stream);
-    if (e == cudaSuccess) e = launch_pair_kernel(c, op, mode, tu);
+    if (e == cudaSuccess) e = launch_pair_kernel(c, op, mode, tu, std::min(c->n, 512));
     if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);

@@ -36,7 +36,8 @@ class SolveInfo(ctypes.Structure):
                 ("rel_residual_true", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
                 ("t_solve_ms", ctypes.c_double), ("n_near_pairs", ctypes.c_longlong),
                 ("graph_cycles", ctypes.c_int), ("kernel_launches", ctypes.c_longlong),
-                ("fp32_residual_updates", ctypes.c_int), ("fp32_op_err", ctypes.c_double)]
+                ("fp32_residual_updates", ctypes.c_int), ("fp32_op_err", ctypes.c_double),
+                ("last_correction", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -188,8 +188,9 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
         float2 acc[NP][3];
 #pragma unroll
         for (int t = 0; t < NP; ++t) acc[t][0] = acc[t][1] = acc[t][2] = make_float2(0.f, 0.f);
-        // One staged source against this thread's targets.
-        auto step = [&](const float4* src) {
+#pragma unroll 2
+        for (int j = 0; j < a.tile; ++j) {
+            const float4* src = smem4 + (size_t)j * NV;
             const float4 v0 = src[0], v1 = src[1], v2 = src[2];
             const float2 mx = make_float2(v0.x, v0.y), my = make_float2(v0.z, v0.w), mz = make_float2(v1.x, v1.y);
             const float2 fx = make_float2(v1.z, v1.w), fy = make_float2(v2.x, v2.y), fz = make_float2(v2.z, v2.w);
@@ -239,9 +240,7 @@ __global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
                     acc[t][2] = __ffma2_rn(dz, s5, acc[t][2]);
                 }
             }
-        };
-#pragma unroll 2
-        for (int j = 0; j < a.tile; ++j) step(smem4 + (size_t)j * NV);
+        }
 #pragma unroll
         for (int t = 0; t < NP; ++t)
 #pragma unroll

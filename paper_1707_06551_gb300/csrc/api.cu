@@ -293,9 +293,9 @@ sbie_status ensure_krylov(sbie_ctx* c, int m, int P) {
         c->ad = ArnoldiDev();
         const size_t Pm = (size_t)P * m, Pm1 = (size_t)P * (m + 1);
         const size_t nd = 4 * (size_t)P + Pm1 * m + 2 * Pm + Pm1 + 2 * Pm1 + Pm + (4 * (size_t)P + 1) + n3;
-        if (dmalloc(&c->d_ad, nd) != cudaSuccess || dmalloc(&c->d_adi, 4 + 2 * (size_t)P) != cudaSuccess ||
+        if (dmalloc(&c->d_ad, nd) != cudaSuccess || dmalloc(&c->d_adi, kStWords + 2 * (size_t)P) != cudaSuccess ||
             dmalloc(&c->d_vk, (size_t)n3) != cudaSuccess ||
-            cudaMallocHost(reinterpret_cast<void**>(&c->h_st), sizeof(int) * 4) != cudaSuccess ||
+            cudaMallocHost(reinterpret_cast<void**>(&c->h_st), sizeof(int) * kStWords) != cudaSuccess ||
             cudaMallocHost(reinterpret_cast<void**>(&c->h_pack), sizeof(double) * (4 * (size_t)P + 1)) != cudaSuccess)
             return fail(c, SBIE_ERR_OOM, "GMRES cycle state");
         ArnoldiDev& A = c->ad;
@@ -321,8 +321,8 @@ sbie_status ensure_krylov(sbie_ctx* c, int m, int P) {
         A.pack = take(4 * (size_t)P + 1);
         A.w = take(n3);
         A.st = c->d_adi;
-        A.live = c->d_adi + 4;
-        A.kd = c->d_adi + 4 + P;
+        A.live = c->d_adi + kStWords;
+        A.kd = c->d_adi + kStWords + P;
         ++g_graph_epoch;
     }
     const size_t red = (size_t)(m + 1) * P * B + 64;
@@ -487,9 +487,12 @@ sbie_status cycle_graph(const Sys& S, const AFn& A, const AFn* M, int key, Cycle
 // restart.  Each restart cycle runs on the device (krylov.cu): as one graph
 // launch when the context uses graphs and is not profiling, otherwise
 // stepped from the host one iteration at a time.  `key` names the operator,
-// arithmetic and preconditioner for the graph cache.
+// arithmetic and preconditioner for the graph cache.  With trust_estimate the
+// true residual is not recomputed after a cycle in which every problem
+// stopped on its estimate (the caller forms its own residual next).
 sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const std::vector<double>& tol,
-                  const std::vector<char>& want, int restart, int max_iter, GmresOut& go, const AFn* M, int key) {
+                  const std::vector<char>& want, int restart, int max_iter, GmresOut& go, const AFn* M, int key,
+                  bool trust_estimate = false) {
     sbie_ctx* c = S.top;
     const long long n3 = S.n3;
     const int P = S.P;
@@ -561,7 +564,7 @@ sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const 
         if (!g) {
             for (int it = 0; it < mm; ++it) {
                 CKS(enqueue_iteration(S, A, M, cudaGraphConditionalHandle{}, false));
-                CK(cudaMemcpyAsync(c->h_st, AD.st, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+                CK(cudaMemcpyAsync(c->h_st, AD.st, sizeof(int) * kStWords, cudaMemcpyDeviceToHost, c->stream));
                 CK(cudaStreamSynchronize(c->stream));
                 if (!c->h_st[2]) break;
             }
@@ -577,7 +580,22 @@ sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const 
         } else {
             CK(arnoldi_finish(c, AD, V, n3, c->d_node_prob, x));
         }
-        CK(cudaMemcpyAsync(c->h_st, AD.st, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(c->h_st, AD.st, sizeof(int) * kStWords, cudaMemcpyDeviceToHost, c->stream));
+        if (trust_estimate) {
+            // every problem stopped on its Givens residual estimate: the
+            // caller forms the residual itself, so the cycle's own b - A x is
+            // not needed
+            CK(cudaStreamSynchronize(c->stream));
+            if (c->h_st[3]) return fail(c, SBIE_ERR_NUMERIC, "NaN/Inf in the Krylov basis");
+            if (!c->h_st[4]) {
+                const int kexec = c->h_st[0];
+                if (g) c->n_launch += (long long)kexec * g->body_launches;
+                total += kexec;
+                ++go.restarts;
+                for (int p = 0; p < P; ++p) beta[p] = active[p] ? tol[p] * nb[p] : beta[p];
+                break;
+            }
+        }
         CKS(A(x, r));
         CK(blas_lincomb(c, 1.0, b, -1.0, r, r, n3));
         CKS(seg_norms(S, r, beta));  // synchronises the stream: h_st is current
@@ -667,7 +685,8 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
                 want[p] = rel[p] > tol;
                 itol[p] = std::min(1e-3, std::max(1e-5, 0.5 * tol / std::max(rel[p], 1e-300)));
             }
-            CKS(gmres(S, A32, r, d, itol, want, c->opts.restart, c->opts.max_iter - iters, go, M, key_of(kModeF32)));
+            CKS(gmres(S, A32, r, d, itol, want, c->opts.restart, c->opts.max_iter - iters, go, M, key_of(kModeF32),
+                      true));
             iters += go.iters;
             inf.restarts += go.restarts;
             inf.graph_cycles += go.graph_cycles;

@@ -76,9 +76,10 @@ enum Stage {
 
 // Device state of one GMRES restart cycle (krylov.cu), for P problems and at
 // most m iterations.  Passed by value to the kernels.
+constexpr int kStWords = 8;  // words of ArnoldiDev::st
 struct ArnoldiDev {
     int m = 0, P = 0;
-    int* st = nullptr;        // [4] k, iteration limit, continue flag, non-finite flag
+    int* st = nullptr;        // [kStWords] k, iteration limit, continue flag, non-finite flag, any live
     int* live = nullptr;      // [P] problem still iterating
     int* kd = nullptr;        // [P] columns of the problem's Hessenberg matrix
     double* nb = nullptr;     // [P] norm of the right-hand side

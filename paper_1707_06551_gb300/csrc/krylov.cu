@@ -15,7 +15,8 @@ namespace sbie {
 
 namespace {
 
-// st[0] = k, st[1] = iteration limit of the cycle, st[2] = continue, st[3] = non-finite flag
+// st[0] = k, st[1] = iteration limit of the cycle, st[2] = continue, st[3] = non-finite flag,
+// st[4] = some problem still iterating
 
 __global__ void cycle_init_kernel(ArnoldiDev A) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -24,6 +25,7 @@ __global__ void cycle_init_kernel(ArnoldiDev A) {
         A.st[1] = (int)A.pack[4 * A.P];
         A.st[2] = 1;
         A.st[3] = 0;
+        A.st[4] = 1;
     }
     if (p >= A.P) return;
     const double nb = A.pack[p], tol = A.pack[A.P + p], beta = A.pack[2 * A.P + p];
@@ -142,6 +144,7 @@ __global__ void arnoldi_advance_kernel(ArnoldiDev A, cudaGraphConditionalHandle 
         A.st[0] = k1;
         const int cont = (any && k1 < A.st[1] && A.st[3] == 0) ? 1 : 0;
         A.st[2] = cont;
+        A.st[4] = any;
         if (has_cond) cudaGraphSetConditional(cond, cont);
     }
 }

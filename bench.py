@@ -282,7 +282,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": per_solve, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_spheres": 256, "p": 10, "nodes": 61952},
+            "config": {"workload": WORKLOAD, "n_spheres": 256, "p": 10, "nodes": 61952, "tol": 1e-8,
+                       "precision": "fp64 (oracle, plain GMRES)", "preconditioner": "none",
+                       "parallelism": "replicas x1"},
             "cpu_baseline": {"value": per_solve, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": per_solve, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

@@ -140,6 +140,8 @@ void choose_tuning(sbie_ctx* c) {
         long long ctas = (long long)c->n * chunks;
         long long want = (long long)c->sm_count * (f32 ? 12 : 4);
         int split = (int)std::min<long long>(32, std::max<long long>(1, (want + ctas - 1) / ctas));
+        // small contexts: shorter tiles before fewer splits
+        while (best.tile > 32 && (c->N + split - 1) / split < best.tile) best.tile /= 2;
         long long per = (c->N + split - 1) / split;
         if (per < best.tile) split = (int)std::max<long long>(1, c->N / best.tile);
         best.split = split;
@@ -159,6 +161,7 @@ void choose_tuning(sbie_ctx* c) {
         long long ctas = (long long)c->n * chunks;
         long long want = (long long)c->sm_count * 8;
         tdf.split = (int)std::min<long long>(16, std::max<long long>(1, (want + ctas - 1) / ctas));
+        while (tdf.tile > 32 && (c->N + tdf.split - 1) / tdf.split < tdf.tile) tdf.tile /= 2;
         if ((c->N + tdf.split - 1) / tdf.split < tdf.tile) tdf.split = (int)std::max<long long>(1, c->N / tdf.tile);
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1883,9 +1886,11 @@ sbie_status tune_one(sbie_ctx* c, Kern k, int mode, sbie_far_tuning* chosen) {
     const int splits32[8] = {1, 2, 3, 4, 6, 8, 12, 16}, splitsdf[4] = {1, 2, 4, 8};
     const int* splits = f32 ? splits32 : splitsdf;
     const int nsp = f32 ? 8 : 4;
-    const int tiles32[2] = {128, 256}, tilesdf[1] = {128};
+    // short tiles only help small contexts (more source splits)
+    const bool small = c->N < 65536;
+    const int tiles32[4] = {128, 256, 32, 64}, tilesdf[3] = {128, 32, 64};
     const int* tiles = f32 ? tiles32 : tilesdf;
-    const int nti = f32 ? 2 : 1;
+    const int nti = f32 ? (small ? 4 : 2) : (small ? 3 : 1);
     for (int a = 0; a < ntpt; ++a)
         for (int b = 0; b < nth; ++b) {
             const int tpt = tpts[a], th = ths[b];

@@ -25,7 +25,7 @@
 namespace sbie {
 
 struct NearArgs {
-    int n, p, npn, L, nch, chunks;
+    int n, p, npn, L, nch, chunks, threads;
     const double* __restrict__ coef;   // [n][3][p+1][p+1][2]
     const double* __restrict__ radius;
     const double* __restrict__ c;
@@ -328,7 +328,7 @@ static cudaError_t run_eval(sbie_ctx* c, const NearArgs& A) {
     size_t sm = sizeof(T) * ((size_t)K * NCHS + 2 * K);
     cudaError_t e = cudaFuncSetAttribute(near_eval_kernel<T, NCH, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    near_eval_kernel<T, NCH, KIND><<<c->n * A.chunks, 128, sm, c->stream>>>(A); ++c->n_launch;
+    near_eval_kernel<T, NCH, KIND><<<c->n * A.chunks, A.threads, sm, c->stream>>>(A); ++c->n_launch;
     return cudaGetLastError();
 }
 
@@ -340,7 +340,12 @@ cudaError_t launch_near(sbie_ctx* c, Kern op, bool f32, double* out) {
     A.L = (kind == 2) ? c->p + 2 : c->p + 1;
     A.nch = (kind == 2) ? kTracChannels : kVelChannels;
     A.nchf = ((A.nch + 3) / 4) * 4;
-    A.chunks = (c->npn + 127) / 128;
+    // targets per CTA: 128, or fewer when a small suspension would leave most
+    // SMs idle (the source channels are then staged by more CTAs)
+    A.threads = 128;
+    while (A.threads > 32 && (long long)c->n * ((c->npn + A.threads - 1) / A.threads) < 2LL * c->sm_count)
+        A.threads /= 2;
+    A.chunks = (c->npn + A.threads - 1) / A.threads;
     A.coef = c->d_coef; A.radius = c->d_a; A.c = c->d_c; A.x64 = c->d_x; A.nrm64 = c->d_nrm64;
     A.near_ptr = c->d_near_ptr; A.near_idx = c->d_near_idx;
     A.chan = c->d_chan; A.chanf = f32 ? c->d_chanf : nullptr; A.out = out;

@@ -37,9 +37,10 @@ FLOP_PER_PAIR = {"S": 28, "D": 30, "K": 30}   # algorithmic flops per (target, s
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 # ncu DRAM traffic (read + write bytes per launch) of the FP32 far-field pair
-# kernel on this workload, keyed by the hash of that kernel's source text it
-# was measured on; reported only while the text is unchanged.
-NCU_TRAFFIC = {"d5374dbfb353e258": 4253696}  # profiles/far_f32_kernel_resistance_256.md: 4.25 MB read, 0 written
+# kernel on this workload, keyed by the hash of that kernel's source text and
+# the tiling (threads x targets per thread / split / tile) it was measured
+# with; reported only while both are unchanged.
+NCU_TRAFFIC = {"d5374dbfb353e258/64x4/16/128": 4253696}  # profiles/far_f32_kernel_resistance_256.md
 
 
 def parse():
@@ -639,7 +640,9 @@ def main():
     if l32 > 0 and ms32 > 0:
         flop_launch = pairs32 / l32 * FLOP_PER_PAIR["D"]
         achieved = flop_launch / (ms32 / l32 * 1e-3) / 1e12
-        traffic = NCU_TRAFFIC.get(far_source_hash())
+        t32 = (tuning or {}).get("fp32") or {}
+        traffic = NCU_TRAFFIC.get(f"{far_source_hash()}/{t32.get('threads')}x{t32.get('targets_per_thread')}/"
+                                  f"{t32.get('split')}/{t32.get('tile')}")
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "far_f32_kernel<D>",
                 "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clk_max:.0f} MHz",

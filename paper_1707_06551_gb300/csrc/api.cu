@@ -1877,6 +1877,8 @@ sbie_status tune_one(sbie_ctx* c, Kern k, int mode, sbie_far_tuning* chosen) {
     struct Cand { FarTune t; float ms; };
     std::vector<Cand> cands;
     const bool f32 = mode == kModeF32;
+    // splits keep the partial sums ([split][N][3] doubles) near 100 MB at most
+    const long long max_sp = std::max<long long>(16, std::min<long long>(64, (1LL << 22) / std::max<long long>(1, c->N)));
     const int tpts32[3] = {2, 4, 6}, tpts1[1] = {1};
     const int* tpts = f32 ? tpts32 : tpts1;
     const int ntpt = f32 ? 3 : 1;
@@ -1898,12 +1900,25 @@ sbie_status tune_one(sbie_ctx* c, Kern k, int mode, sbie_far_tuning* chosen) {
             int chunks = (c->npn + slots - 1) / slots;
             double waste = (double)(chunks * slots - c->npn) / c->npn;
             if (waste > 0.30) continue;
-            for (int s = 0; s < nsp; ++s) {
-                const int sp = splits[s];
-                long long ctas = (long long)c->n * chunks * sp;
-                if (ctas < c->sm_count && s != 0) continue;
-                if (ctas > 64LL * c->sm_count) continue;
-                for (int t = 0; t < nti; ++t) {
+            for (int t = 0; t < nti; ++t) {
+                // the fixed splits, and those whose grid fills whole waves of
+                // resident CTAs (equal-work CTAs: a partial last wave idles SMs)
+                std::vector<int> sps(splits, splits + nsp);
+                const int occ = far_occupancy(c, k, mode, FarTune{th, tpt, 1, tiles[t]});
+                if (occ > 0) {
+                    const long long wave = (long long)occ * c->sm_count, base = (long long)c->n * chunks;
+                    for (int w = 1; w <= 8; ++w) {
+                        const long long sp = (w * wave) / base;
+                        if (sp >= 1 && sp <= max_sp) sps.push_back((int)sp);
+                    }
+                }
+                std::sort(sps.begin(), sps.end());
+                sps.erase(std::unique(sps.begin(), sps.end()), sps.end());
+                for (size_t s = 0; s < sps.size(); ++s) {
+                    const int sp = sps[s];
+                    long long ctas = (long long)c->n * chunks * sp;
+                    if (ctas < c->sm_count && s != 0) continue;
+                    if (ctas > 64LL * c->sm_count) continue;
                     if ((c->N + sp - 1) / sp < tiles[t]) continue;
                     cands.push_back(Cand{FarTune{th, tpt, sp, tiles[t]}, 0.f});
                 }
@@ -1911,6 +1926,10 @@ sbie_status tune_one(sbie_ctx* c, Kern k, int mode, sbie_far_tuning* chosen) {
         }
     FarTune* slot = f32 ? &c->tune32[(int)k] : &c->tunedf[(int)k];
     if (cands.empty()) cands.push_back(Cand{*slot, 0.f});
+    // the partial-sum buffer must hold the largest split timed
+    int msp = 1;
+    for (const Cand& cd : cands) msp = std::max(msp, cd.t.split);
+    CKS(ensure_part(c, msp));
     float dummy;
     CK(time_far(c, k, mode, cands[0].t, &dummy));  // warm-up
     for (auto& cd : cands) CK(time_far(c, k, mode, cd.t, &cd.ms));

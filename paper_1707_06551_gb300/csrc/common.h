@@ -279,6 +279,7 @@ cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out);
 // Times one launch of the far-field pair kernel with tiling `tu` (no reduce); *ms = event time.
 cudaError_t time_far(sbie_ctx* c, Kern op, int mode, const FarTune& tu, float* ms);
 long long far_pairs(const sbie_ctx* c);
+int far_occupancy(sbie_ctx* c, Kern op, int mode, const FarTune& tu);
 // near.cu
 cudaError_t launch_near(sbie_ctx* c, Kern op, bool f32, double* out);
 // compl.cu

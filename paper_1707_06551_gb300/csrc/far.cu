@@ -698,6 +698,44 @@ cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out) {
     return cudaGetLastError();
 }
 
+// Resident CTAs per SM of the pair kernel for tiling `tu` (registers and
+// shared memory of that instantiation), or 0 if it cannot be queried.
+template <typename K>
+static int occ_of(K kernel, int threads, size_t sm) {
+    int blocks = 0;
+    if (sm > 48 * 1024 &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, threads, sm) != cudaSuccess) return 0;
+    return blocks;
+}
+
+template <int OP>
+static int far_occupancy_op(sbie_ctx* c, int mode, const FarTune& tu) {
+    const size_t words = ((c->n + 31) / 32) * sizeof(unsigned);
+    if (mode == kModeDF) {
+        const int nv = (OP == (int)Kern::D) ? 5 : 3;
+        return occ_of(far_df_kernel<OP>, tu.threads, (size_t)nv * tu.tile * sizeof(float4) + words);
+    }
+    const int nv32 = (OP == (int)Kern::D) ? 5 : 3;
+    const int tpt32 = 2 * ((tu.tpt + 1) / 2);
+    const size_t sm = (size_t)nv32 * tu.tile * sizeof(float4) + (size_t)tpt32 * 6 * tu.threads * sizeof(float) + words;
+    switch (tu.tpt) {
+        case 2: return occ_of(far_f32_kernel<OP, 1>, tu.threads, sm);
+        case 6: return occ_of(far_f32_kernel<OP, 3>, tu.threads, sm);
+        default: return occ_of(far_f32_kernel<OP, 2>, tu.threads, sm);
+    }
+}
+
+int far_occupancy(sbie_ctx* c, Kern op, int mode, const FarTune& tu) {
+    if (mode == kModeF64) return 0;
+    switch (op) {
+        case Kern::S: return far_occupancy_op<(int)Kern::S>(c, mode, tu);
+        case Kern::D: return far_occupancy_op<(int)Kern::D>(c, mode, tu);
+        default: return far_occupancy_op<(int)Kern::K>(c, mode, tu);
+    }
+}
+
 // One pair-kernel launch timed with CUDA events.  Large contexts time the
 // first 512 target spheres only (every CTA does the same work as in a full
 // launch, and 512 spheres are several waves), so tuning stays cheap.

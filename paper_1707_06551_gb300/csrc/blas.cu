@@ -1,60 +1,12 @@
-// FP64 vector kernels for the Arnoldi process of GMRES (classical Gram-Schmidt
-// applied twice): multi-dot, multi-axpy, norms, linear combinations.  Vectors
-// are contiguous; a basis of k vectors is stored with leading dimension ld.
+// FP64 vector kernels of GMRES outside the device-resident Arnoldi step
+// (krylov.cu): segmented dot products (one segment per problem), segmented
+// scaling, linear combinations.  A basis of k vectors is stored with leading
+// dimension ld.
 #include <algorithm>
 
 #include "common.h"
 
 namespace sbie {
-
-constexpr int kDotBlocks = 296;  // 2 x 148+ SMs worth of partial sums
-
-// partial[j][b] = sum over this block's slice of V_j . w
-__global__ void dots_partial(const double* __restrict__ V, int k, long long ld, const double* __restrict__ w,
-                             long long n, double* __restrict__ partial) {
-    __shared__ double sh[32];
-    const int j = blockIdx.y;
-    const double* v = V + (size_t)j * ld;
-    double s = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        s = fma(v[i], w[i], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (threadIdx.x == 0) partial[(size_t)j * gridDim.x + blockIdx.x] = s;
-    }
-}
-
-__global__ void dots_final(const double* __restrict__ partial, int nb, double* __restrict__ out) {
-    __shared__ double sh[32];
-    const int j = blockIdx.x;
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[(size_t)j * nb + b];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (threadIdx.x == 0) out[j] = s;
-    }
-}
-
-// w -= sum_j h_j V_j  (sign = -1) or x += sum_j y_j V_j (sign = +1)
-__global__ void gemv_kernel(const double* __restrict__ V, int k, long long ld, const double* __restrict__ h,
-                            double sign, double* __restrict__ w, long long n) {
-    __shared__ double sh[256];
-    for (int j = threadIdx.x; j < k; j += blockDim.x) sh[j] = h[j];
-    __syncthreads();
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int j = 0; j < k; ++j) s = fma(sh[j], V[(size_t)j * ld + i], s);
-        w[i] = fma(sign, s, w[i]);
-    }
-}
 
 // out = a x + b y; y may alias out (axpy), so neither is __restrict__.
 __global__ void lincomb_kernel(double a, const double* x, double b, const double* y, double* out, long long n) {
@@ -67,41 +19,9 @@ static unsigned grid_for(long long n) {
     return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
 }
 
-cudaError_t blas_dots(sbie_ctx* c, const double* V, int k, long long ld, const double* w, long long n, double* out_host) {
-    if (!c->d_red || (size_t)kDotBlocks * 256 + 256 > c->red_cap) return cudaErrorInvalidValue;
-    dim3 grid(kDotBlocks, k);
-    dots_partial<<<grid, 256, 0, c->stream>>>(V, k, ld, w, n, c->d_red); ++c->n_launch;
-    dots_final<<<k, 256, 0, c->stream>>>(c->d_red, kDotBlocks, c->d_red + (size_t)kDotBlocks * 256); ++c->n_launch;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (out_host) {
-        e = cudaMemcpyAsync(c->h_red, c->d_red + (size_t)kDotBlocks * 256, sizeof(double) * k, cudaMemcpyDeviceToHost,
-                            c->stream);
-        if (e != cudaSuccess) return e;
-        e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) return e;
-        for (int j = 0; j < k; ++j) out_host[j] = c->h_red[j];
-    }
-    return cudaSuccess;
-}
-
-cudaError_t blas_gemv_sub(sbie_ctx* c, const double* V, int k, long long ld, const double* h_dev, double* w, long long n) {
-    gemv_kernel<<<grid_for(n), 256, 0, c->stream>>>(V, k, ld, h_dev, -1.0, w, n); ++c->n_launch;
-    return cudaGetLastError();
-}
-
-cudaError_t blas_gemv_add(sbie_ctx* c, const double* V, int k, long long ld, const double* y_dev, double* x, long long n) {
-    gemv_kernel<<<grid_for(n), 256, 0, c->stream>>>(V, k, ld, y_dev, 1.0, x, n); ++c->n_launch;
-    return cudaGetLastError();
-}
-
 cudaError_t blas_lincomb(sbie_ctx* c, double a, const double* x, double b, const double* y, double* out, long long n) {
     lincomb_kernel<<<grid_for(n), 256, 0, c->stream>>>(a, x, b, y, out, n); ++c->n_launch;
     return cudaGetLastError();
-}
-
-cudaError_t blas_scale_copy(sbie_ctx* c, double a, const double* x, double* y, long long n) {
-    return blas_lincomb(c, a, x, 0.0, nullptr, y, n);
 }
 
 cudaError_t blas_axpy(sbie_ctx* c, double a, const double* x, double* y, long long n) {
@@ -139,18 +59,6 @@ __global__ void seg_dots_final(const double* __restrict__ partial, int B, int n,
     out[q] = s;
 }
 
-// w[i] += sign * sum_j H[j * P + p(i)] V_j[i]
-__global__ void seg_gemv_kernel(const double* __restrict__ V, int k, long long ld, const double* __restrict__ H,
-                                int P, double sign, const int* __restrict__ node_prob, double* __restrict__ w,
-                                long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int p = node_prob[i / 3];
-        double s = 0.0;
-        for (int j = 0; j < k; ++j) s = fma(H[(size_t)j * P + p], V[(size_t)j * ld + i], s);
-        w[i] = fma(sign, s, w[i]);
-    }
-}
-
 // y[i] = scale[p(i)] * x[i]  (x may alias y)
 __global__ void seg_scale_kernel(const double* x, const double* __restrict__ scale, const int* __restrict__ node_prob,
                                  double* y, long long n) {
@@ -172,12 +80,6 @@ cudaError_t seg_dots(sbie_ctx* c, const double* V, int k, long long ld, const do
     seg_dots_partial<<<grid, 256, 0, c->stream>>>(V, ld, w, d_seg, P, c->d_red); ++c->n_launch;
     const int n = k * P;
     seg_dots_final<<<(n + 255) / 256, 256, 0, c->stream>>>(c->d_red, B, n, d_out); ++c->n_launch;
-    return cudaGetLastError();
-}
-
-cudaError_t seg_gemv(sbie_ctx* c, const double* V, int k, long long ld, const double* d_H, int P, double sign,
-                     const int* d_node_prob, double* w, long long n3) {
-    seg_gemv_kernel<<<grid_for(n3), 256, 0, c->stream>>>(V, k, ld, d_H, P, sign, d_node_prob, w, n3); ++c->n_launch;
     return cudaGetLastError();
 }
 

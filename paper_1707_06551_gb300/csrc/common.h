@@ -263,7 +263,6 @@ void set_last_error(const std::string& msg);
 // --- kernels launchers (each returns cudaError_t of the launch) ---
 // self.cu
 cudaError_t launch_self(sbie_ctx* c, Kern op, const double* dens, double* out, bool accumulate, bool write_coef);
-cudaError_t launch_analysis_only(sbie_ctx* c, const double* dens);
 cudaError_t launch_self_precond(sbie_ctx* c, const double* v, double* out);
 // precond.cu
 void lowmode_tables(int p, std::vector<double>& ZS, std::vector<double>& ZA);
@@ -292,18 +291,12 @@ cudaError_t launch_resistance_rhs(sbie_ctx* c, const double* vel, const double* 
                                   const double* G, double* b);
 cudaError_t launch_geometry(sbie_ctx* c);
 // blas.cu (FP64 vectors of length n)
-cudaError_t blas_dots(sbie_ctx* c, const double* V, int k, long long ld, const double* w, long long n, double* out_host);
-cudaError_t blas_gemv_sub(sbie_ctx* c, const double* V, int k, long long ld, const double* h_dev, double* w, long long n);
 cudaError_t blas_axpy(sbie_ctx* c, double a, const double* x, double* y, long long n);
-cudaError_t blas_scale_copy(sbie_ctx* c, double a, const double* x, double* y, long long n);
 cudaError_t blas_lincomb(sbie_ctx* c, double a, const double* x, double b, const double* y, double* out, long long n);
-cudaError_t blas_gemv_add(sbie_ctx* c, const double* V, int k, long long ld, const double* y_dev, double* x, long long n);
 // segmented (one segment per independent problem; see blas.cu)
 int seg_blocks(long long n3, int P);
 cudaError_t seg_dots(sbie_ctx* c, const double* V, int k, long long ld, const double* w, long long n3,
                      const long long* d_seg, int P, double* d_out);
-cudaError_t seg_gemv(sbie_ctx* c, const double* V, int k, long long ld, const double* d_H, int P, double sign,
-                     const int* d_node_prob, double* w, long long n3);
 cudaError_t seg_scale(sbie_ctx* c, const double* x, const double* d_scale, const int* d_node_prob, double* y,
                       long long n3);
 // krylov.cu (device-resident GMRES restart cycle)

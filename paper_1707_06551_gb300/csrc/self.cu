@@ -251,8 +251,5 @@ cudaError_t launch_self_precond(sbie_ctx* c, const double* v, double* out) {
     return run_self(c, kOpPrecHigh, v, out, false, true);
 }
 
-cudaError_t launch_analysis_only(sbie_ctx* c, const double* dens) {
-    return run_self(c, -1, dens, nullptr, false, true);
-}
 
 }  // namespace sbie

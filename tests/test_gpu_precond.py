@@ -143,3 +143,32 @@ def test_learned_mobility_network_and_fallback(sb, tmp_path):
     assert np.max(np.abs(v1 - v0)) < 1e-7 * np.max(np.abs(v0))
     # no mobility network in the file: the mobility solve runs unpreconditioned
     assert pf["kind"] == 0 and i2["iters"] == i0["iters"] and np.max(np.abs(v2 - v0)) < 1e-9 * np.max(np.abs(v0))
+
+
+def test_resistance_256_headline_configuration(sb, tmp_path):
+    """The timed configuration at full size: 256 spheres, p = 10, mixed
+    precision, learned pair preconditioner, graph-launched cycles.  Forces and
+    torques agree with the FP64-accurate (double-float) solve, and the reported
+    residual is the FP64 residual of the returned density."""
+    w = wl.resistance_256()
+    path = tmp_path / "pairnet.bin"
+    sb.sphere_bie_train_pair_network(path, n_samples=1024, p=w["p"], gap_min=0.01, gap_max=2.0, epochs=100, seed=3)
+    with sb.SphereBIE(w["centres"], w["radii"], w["p"], prec=sb.SBIE_MIXED, tol=w["tol"], precond=1,
+                      weights=path) as s:
+        F, T, info = s.resistance(w["vel"], w["omega"], w["u0"], w["G"])
+        psi = s.density()
+        x, _, _ = s.nodes()
+        pi = sb.sphere_bie_precond_info(s.ctx)
+    # pairs whose gap falls outside the sampled training range are left out
+    assert info["status"] == 0 and info["graph_cycles"] > 0 and pi["kind"] == 1
+    assert pi["pairs"] + pi["dropped"] == 559 and pi["pairs"] >= 550
+    with sb.SphereBIE(w["centres"], w["radii"], w["p"], prec=sb.SBIE_FP64_DF, tol=w["tol"]) as s:
+        F64, T64, i64 = s.resistance(w["vel"], w["omega"], w["u0"], w["G"])
+        # b = v + omega x (x - c) - u_inf(x) with u_inf = u0 + G x (spheres held fixed)
+        b = -(w["u0"][None, :] + x @ w["G"].T)
+        r = b - s.apply("resistance", psi)
+    assert i64["status"] == 0 and info["iters"] < i64["iters"]
+    assert np.max(np.abs(F - F64)) < 1e-6 * np.max(np.abs(F64))
+    assert np.max(np.abs(T - T64)) < 1e-6 * np.max(np.abs(T64))
+    rel = np.linalg.norm(r) / np.linalg.norm(b)
+    assert rel <= w["tol"] and abs(rel - info["rel_residual_true"]) <= 0.1 * w["tol"]

@@ -192,6 +192,7 @@ typedef struct {
     int tile;                /* sources staged in shared memory per tile          */
     double ms;               /* measured time of one launch with this tiling      */
     int candidates;          /* tilings timed                                     */
+    int regs64;              /* 1: the FP32 variant held to 64 registers (64 threads) */
 } sbie_far_tuning;
 
 /* Autotuner: times every admissible tiling of the far-field kernels used by

@@ -1903,8 +1903,9 @@ sbie_status tune_one(sbie_ctx* c, Kern k, int mode, sbie_far_tuning* chosen) {
             for (int t = 0; t < nti; ++t) {
                 // the fixed splits, and those whose grid fills whole waves of
                 // resident CTAs (equal-work CTAs: a partial last wave idles SMs)
+              for (int mb = 0; mb <= ((f32 && th == 64) ? 16 : 0); mb += 16) {
                 std::vector<int> sps(splits, splits + nsp);
-                const int occ = far_occupancy(c, k, mode, FarTune{th, tpt, 1, tiles[t]});
+                const int occ = far_occupancy(c, k, mode, FarTune{th, tpt, 1, tiles[t], mb});
                 if (occ > 0) {
                     const long long wave = (long long)occ * c->sm_count, base = (long long)c->n * chunks;
                     for (int w = 1; w <= 8; ++w) {
@@ -1920,8 +1921,9 @@ sbie_status tune_one(sbie_ctx* c, Kern k, int mode, sbie_far_tuning* chosen) {
                     if (ctas < c->sm_count && s != 0) continue;
                     if (ctas > 64LL * c->sm_count) continue;
                     if ((c->N + sp - 1) / sp < tiles[t]) continue;
-                    cands.push_back(Cand{FarTune{th, tpt, sp, tiles[t]}, 0.f});
+                    cands.push_back(Cand{FarTune{th, tpt, sp, tiles[t], mb}, 0.f});
                 }
+              }
             }
         }
     FarTune* slot = f32 ? &c->tune32[(int)k] : &c->tunedf[(int)k];
@@ -1958,6 +1960,7 @@ sbie_status tune_one(sbie_ctx* c, Kern k, int mode, sbie_far_tuning* chosen) {
         chosen->tile = cands[0].t.tile;
         chosen->ms = cands[0].ms;
         chosen->candidates = (int)cands.size();
+        chosen->regs64 = cands[0].t.minb ? 1 : 0;
     }
     return SBIE_OK;
 }

@@ -60,6 +60,7 @@ struct FarTune {
     int tpt;      // targets per thread (1, 2 or 4)
     int split;    // source-range splits (partial sums reduced afterwards)
     int tile;     // sources staged per tile
+    int minb = 0; // FP32 kernel: 16 = 64-thread variant held to 64 registers (16 CTAs per SM)
 };
 
 struct Profile {

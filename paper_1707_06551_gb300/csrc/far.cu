@@ -114,8 +114,8 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // one 128-bit shared-memory broadcast.  The compensated running sums live in
 // shared memory (touched once per tile), which keeps the registers for the
 // pair loop and lets more warps share each SM.
-template <int OP, int NP>
-__global__ void __launch_bounds__(256) far_f32_kernel(FarArgs a) {
+template <int OP, int NP, int MINB>
+__global__ void __launch_bounds__(MINB ? 64 : 256, MINB ? MINB : 1) far_f32_kernel(FarArgs a) {
     constexpr int NV = (OP == (int)Kern::D) ? 5 : 3;  // float4 per staged source
     constexpr int TPT = 2 * NP;
     const int sphere = blockIdx.x / a.chunks, chunk = blockIdx.x - sphere * a.chunks;
@@ -618,11 +618,18 @@ static cudaError_t launch_far_t(sbie_ctx* c, const FarTune& tu, bool f32, const 
         const int nv32 = (OP == (int)Kern::D) ? 5 : 3;
         const int tpt32 = 2 * ((TPT + 1) / 2);
         size_t sm = (size_t)nv32 * tu.tile * sizeof(float4) + (size_t)tpt32 * 6 * tu.threads * sizeof(float) + words;
-        if (sm > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(far_f32_kernel<OP, (TPT + 1) / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return e;
-        }
-        far_f32_kernel<OP, (TPT + 1) / 2><<<grid, tu.threads, sm, c->stream>>>(a); ++c->n_launch;
+        auto run = [&](auto kernel) {
+            if (sm > 48 * 1024) {
+                cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                if (e != cudaSuccess) return e;
+            }
+            kernel<<<grid, tu.threads, sm, c->stream>>>(a);
+            ++c->n_launch;
+            return cudaSuccess;
+        };
+        cudaError_t e = (tu.minb && tu.threads == 64) ? run(far_f32_kernel<OP, (TPT + 1) / 2, 16>)
+                                                      : run(far_f32_kernel<OP, (TPT + 1) / 2, 0>);
+        if (e != cudaSuccess) return e;
     } else if constexpr (TPT <= 4) {  // the FP64 kernel holds at most 4 targets per thread
         size_t sm = (size_t)nv * tu.tile * sizeof(double4) + words;
         if (sm > 48 * 1024) {
@@ -720,10 +727,17 @@ static int far_occupancy_op(sbie_ctx* c, int mode, const FarTune& tu) {
     const int nv32 = (OP == (int)Kern::D) ? 5 : 3;
     const int tpt32 = 2 * ((tu.tpt + 1) / 2);
     const size_t sm = (size_t)nv32 * tu.tile * sizeof(float4) + (size_t)tpt32 * 6 * tu.threads * sizeof(float) + words;
+    if (tu.minb && tu.threads == 64) {
+        switch (tu.tpt) {
+            case 2: return occ_of(far_f32_kernel<OP, 1, 16>, tu.threads, sm);
+            case 6: return occ_of(far_f32_kernel<OP, 3, 16>, tu.threads, sm);
+            default: return occ_of(far_f32_kernel<OP, 2, 16>, tu.threads, sm);
+        }
+    }
     switch (tu.tpt) {
-        case 2: return occ_of(far_f32_kernel<OP, 1>, tu.threads, sm);
-        case 6: return occ_of(far_f32_kernel<OP, 3>, tu.threads, sm);
-        default: return occ_of(far_f32_kernel<OP, 2>, tu.threads, sm);
+        case 2: return occ_of(far_f32_kernel<OP, 1, 0>, tu.threads, sm);
+        case 6: return occ_of(far_f32_kernel<OP, 3, 0>, tu.threads, sm);
+        default: return occ_of(far_f32_kernel<OP, 2, 0>, tu.threads, sm);
     }
 }
 

@@ -25,6 +25,9 @@
  *     CUDA error crosses the interface.  sphere_bie_last_error(ctx) returns a
  *     message for the last failure on that context (a static string for NULL).
  *     Nothing on any path falls back to the CPU.
+ *   - Threads: calls on one context must not overlap (a context holds one
+ *     stream, its work buffers and its captured GMRES cycles); different
+ *     contexts may be used from different host threads.
  */
 #ifndef SPHERE_BIE_H
 #define SPHERE_BIE_H

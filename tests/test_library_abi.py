@@ -108,3 +108,45 @@ def test_create_batch_rejects_bad_input(lib):
     st = lib.lib().sphere_bie_create_batch(2, ctypes.c_void_p(n.ctypes.data), ctypes.c_void_p(p.ctypes.data),
                                            lib._ptr(c), lib._ptr(a), ctypes.byref(o), ctypes.byref(h))
     assert st == 2
+
+
+def test_default_opts_use_graphs(lib):
+    assert lib.sphere_bie_default_opts().use_graphs == 1
+
+
+@pytest.mark.parametrize("case", ["missing", "not_a_net", "graphs"])
+def test_create_rejects_bad_preconditioner_and_graph_options(lib, tmp_path, case):
+    """Checked on the host before any device work: the weights file of the
+    learned preconditioner is read at create, and use_graphs must be 0 or 1."""
+    c = np.array([[0.0, 0, 0], [3.0, 0, 0]])
+    a = np.array([1.0, 1.0])
+    o = lib.make_opts(4)
+    keep = None
+    if case == "missing":
+        o.use_learned_precond = 1
+        keep = str(tmp_path / "absent.bin").encode()
+        o.mlp_weights_path = keep
+    elif case == "not_a_net":
+        bad = tmp_path / "bad.bin"
+        bad.write_bytes(b"SBIEPN00" + b"\0" * 64)
+        o.use_learned_precond = 1
+        keep = str(bad).encode()
+        o.mlp_weights_path = keep
+    else:
+        o.use_graphs = 2
+    h = ctypes.c_void_p()
+    st = lib.lib().sphere_bie_create(2, lib._ptr(c), lib._ptr(a), ctypes.byref(o), ctypes.byref(h))
+    assert st == lib.SBIE_ERR_ARG and not h.value
+    msg = lib.sphere_bie_last_error(None)
+    assert ("pair-network" in msg or "cannot read" in msg) if case != "graphs" else "use_graphs" in msg
+
+
+@pytest.mark.parametrize("field,value", [("ops", 0), ("ops", 4), ("radius_max", 0.5), ("n_samples", 8),
+                                         ("p", 3), ("val_frac", 0.95)])
+def test_train_pair_network_rejects_bad_options(lib, tmp_path, field, value):
+    o = lib.PairTrainOpts(64, 6, 0.01, 0.5, 1.0, 10, 32, 2e-3, 7, 0.1, 1, 1.0)
+    setattr(o, field, value)
+    info = lib.PairTrainInfo()
+    st = lib.lib().sphere_bie_train_pair_network(ctypes.byref(o), str(tmp_path / "n.bin").encode(), ctypes.byref(info))
+    assert st == lib.SBIE_ERR_ARG
+    assert not (tmp_path / "n.bin").exists()

@@ -1,20 +1,22 @@
 // Two-body (pair) preconditioner for GMRES on the resistance operator
-// 1/2 I + D + N (Eq. 5.19).
+// 1/2 I + D + N (Eq. 5.19) or the mobility operator 1/2 I + K + L (Eq. 5.8).
 //
 //   M^{-1} r = H r + Z C^{-1} Z^+ r
 //
 // Z^+ is the VSH analysis (Sec. 2.1) restricted to degree <= 4 ("low modes",
 // 73 real coefficients per sphere) and Z the matching synthesis.  H inverts
-// each sphere's own operator above degree 4 (the exterior eigenvalues D+ of
-// Theorem 2) and the non-band-limited remainder (1/2 I -> x2), and vanishes on
-// the low modes.  C^{-1} is an additive Schwarz approximation of the low-mode
-// operator over close pairs: for each close pair (i, k) the 146 x 146 system
+// each sphere's own operator above degree 4 (the exterior eigenvalues
+// D+ = K- of Theorem 2, the same for both operators) and the
+// non-band-limited remainder (1/2 I -> x2), and vanishes on the low modes.
+// C^{-1} is an additive Schwarz approximation of the low-mode operator over
+// close pairs: for each close pair (i, k) the 146 x 146 system
 // [[L_i, B_ik], [B_ki, L_k]] is inverted once, and sphere i averages the
 // answers of its pairs (an isolated sphere uses L_i^{-1}).  L_i is the
 // sphere's own low-mode block and B_ik the low-mode block of the pair
-// coupling (close-pair expansion + completion flow), either probed exactly
-// (the operator applied to each low mode on a two-sphere problem) or
-// predicted by the pair network in the pair frame and rotated.
+// coupling (close-pair expansion + completion flow of the operator), either
+// probed exactly (the operator applied to each low mode on a two-sphere
+// problem) or predicted by the pair network in the pair frame and rotated.
+// Each operator has its own blocks (PrecState in the context).
 #include <algorithm>
 #include <cmath>
 #include <cstring>

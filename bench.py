@@ -40,7 +40,7 @@ FP32_LANES_PER_SM = 128
 # kernel on this workload, keyed by the hash of that kernel's source text and
 # the tiling (threads x targets per thread / split / tile) it was measured
 # with; reported only while both are unchanged.
-NCU_TRAFFIC = {"0406e3e6e9464950/64x4/14/256": 4256000}  # profiles/far_f32_kernel_resistance_256.md
+NCU_TRAFFIC = {"df668ee33ebfad7f/64x4/33/128/mb8": 4912384}  # profiles/far_f32_kernel_resistance_256.md
 
 
 def parse():
@@ -642,7 +642,7 @@ def main():
         achieved = flop_launch / (ms32 / l32 * 1e-3) / 1e12
         t32 = (tuning or {}).get("fp32") or {}
         traffic = NCU_TRAFFIC.get(f"{far_source_hash()}/{t32.get('threads')}x{t32.get('targets_per_thread')}/"
-                                  f"{t32.get('split')}/{t32.get('tile')}")
+                                  f"{t32.get('split')}/{t32.get('tile')}/mb{t32.get('min_blocks')}")
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "far_f32_kernel<D>",
                 "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clk_max:.0f} MHz",

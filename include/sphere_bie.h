@@ -195,7 +195,8 @@ typedef struct {
     int tile;                /* sources staged in shared memory per tile          */
     double ms;               /* measured time of one launch with this tiling      */
     int candidates;          /* tilings timed                                     */
-    int regs64;              /* 1: the FP32 variant held to 64 registers (64 threads) */
+    int min_blocks;          /* FP32 build for 64-thread CTAs requiring 8, 10 or 16 resident
+                                CTAs per SM (about 128, 96, 64 registers); 0: no register cap */
 } sbie_far_tuning;
 
 /* Autotuner: times every admissible tiling of the far-field kernels used by

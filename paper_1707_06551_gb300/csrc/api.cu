@@ -1903,7 +1903,10 @@ sbie_status tune_one(sbie_ctx* c, Kern k, int mode, sbie_far_tuning* chosen) {
             for (int t = 0; t < nti; ++t) {
                 // the fixed splits, and those whose grid fills whole waves of
                 // resident CTAs (equal-work CTAs: a partial last wave idles SMs)
-              for (int mb = 0; mb <= ((f32 && th == 64) ? 16 : 0); mb += 16) {
+              int mbs[4] = {0, 0, 0, 0};
+              const int nmb = (f32 && th == 64) ? far_f32_builds(tpt, mbs) : 1;
+              for (int m = 0; m < nmb; ++m) {
+                const int mb = mbs[m];
                 std::vector<int> sps(splits, splits + nsp);
                 const int occ = far_occupancy(c, k, mode, FarTune{th, tpt, 1, tiles[t], mb});
                 if (occ > 0) {
@@ -1960,7 +1963,7 @@ sbie_status tune_one(sbie_ctx* c, Kern k, int mode, sbie_far_tuning* chosen) {
         chosen->tile = cands[0].t.tile;
         chosen->ms = cands[0].ms;
         chosen->candidates = (int)cands.size();
-        chosen->regs64 = cands[0].t.minb ? 1 : 0;
+        chosen->min_blocks = cands[0].t.minb;
     }
     return SBIE_OK;
 }

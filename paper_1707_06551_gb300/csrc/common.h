@@ -60,7 +60,7 @@ struct FarTune {
     int tpt;      // targets per thread (1, 2 or 4)
     int split;    // source-range splits (partial sums reduced afterwards)
     int tile;     // sources staged per tile
-    int minb = 0; // FP32 kernel: 16 = 64-thread variant held to 64 registers (16 CTAs per SM)
+    int minb = 0; // FP32 kernel, 64 threads: build requiring 8, 10 or 16 resident CTAs per SM (0: no cap)
 };
 
 struct Profile {
@@ -280,6 +280,9 @@ cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out);
 cudaError_t time_far(sbie_ctx* c, Kern op, int mode, const FarTune& tu, float* ms);
 long long far_pairs(const sbie_ctx* c);
 int far_occupancy(sbie_ctx* c, Kern op, int mode, const FarTune& tu);
+// register-cap builds of the FP32 pair kernel for `tpt` targets per thread
+// (FarTune::minb values, at most 4); returns their count
+int far_f32_builds(int tpt, int* minb);
 // near.cu
 cudaError_t launch_near(sbie_ctx* c, Kern op, bool f32, double* out);
 // compl.cu

@@ -22,6 +22,12 @@
 
 namespace sbie {
 
+// FP32 pair kernel layout: float4 per staged source (position, density and,
+// for D, the source normal, each component duplicated) and running sums per
+// target (the three components)
+__host__ __device__ constexpr int f32_nv(int op) { return op == (int)Kern::D ? 5 : 3; }
+__host__ __device__ constexpr int f32_na(int) { return 3; }
+
 struct FarArgs {
     int n, npn, chunks, tile;
     long long N, split_len;
@@ -116,7 +122,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // pair loop and lets more warps share each SM.
 template <int OP, int NP, int MINB>
 __global__ void __launch_bounds__(MINB ? 64 : 256, MINB ? MINB : 1) far_f32_kernel(FarArgs a) {
-    constexpr int NV = (OP == (int)Kern::D) ? 5 : 3;  // float4 per staged source
+    constexpr int NV = f32_nv(OP);  // float4 per staged source
     constexpr int TPT = 2 * NP;
     const int sphere = blockIdx.x / a.chunks, chunk = blockIdx.x - sphere * a.chunks;
     const int split = blockIdx.y;
@@ -125,7 +131,7 @@ __global__ void __launch_bounds__(MINB ? 64 : 256, MINB ? MINB : 1) far_f32_kern
     extern __shared__ float4 smem4[];
     // [tile][NV] staged sources | [TPT][3][2][bd] running sums and compensations | sphere flags
     float* run = reinterpret_cast<float*>(smem4 + NV * a.tile);
-    unsigned* flags = reinterpret_cast<unsigned*>(run + TPT * 6 * bd);
+    unsigned* flags = reinterpret_cast<unsigned*>(run + TPT * f32_na(OP) * 2 * bd);
     build_flags(a, sphere, flags);
 
     const double cx = a.c[3 * sphere], cy = a.c[3 * sphere + 1], cz = a.c[3 * sphere + 2];
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(MINB ? 64 : 256, MINB ? MINB : 1) far_f32_kern
         float2 acc[NP][3];
 #pragma unroll
         for (int t = 0; t < NP; ++t) acc[t][0] = acc[t][1] = acc[t][2] = make_float2(0.f, 0.f);
-#pragma unroll 2
+#pragma unroll 4
         for (int j = 0; j < a.tile; ++j) {
             const float4* src = smem4 + (size_t)j * NV;
             const float4 v0 = src[0], v1 = src[1], v2 = src[2];
@@ -609,15 +615,45 @@ static cudaError_t launch_far_df(sbie_ctx* c, const FarTune& tu, const FarArgs& 
     return cudaGetLastError();
 }
 
+// Dynamic shared memory of the FP32 pair kernel: staged sources, the running
+// sums with their compensations for every target of a thread, sphere flags.
+template <int OP>
+static size_t f32_smem(int tpt, int threads, int tile, int n) {
+    return (size_t)f32_nv(OP) * tile * sizeof(float4) +
+           (size_t)2 * ((tpt + 1) / 2) * f32_na(OP) * 2 * threads * sizeof(float) + ((n + 31) / 32) * sizeof(unsigned);
+}
+
+// The FP32 pair kernel is compiled once without a register cap (152-170
+// registers) and, for 64-thread CTAs, with 8, 10 and 16 resident CTAs per SM
+// required (about 128, 96 and 64 registers: 4, 5 and 8 warps per scheduler).
+// Fewer registers mean more warps to hide the special-function and FMA
+// latencies but more register moves; the autotuner times each build.
+using F32Kernel = void (*)(FarArgs);
+template <int OP, int NP>
+static F32Kernel f32_build(const FarTune& tu) {
+    if (tu.threads != 64) return far_f32_kernel<OP, NP, 0>;
+    switch (tu.minb) {
+        case 8: return far_f32_kernel<OP, NP, 8>;
+        case 10: return far_f32_kernel<OP, NP, 10>;
+        case 16: return far_f32_kernel<OP, NP, 16>;
+        default: return far_f32_kernel<OP, NP, 0>;
+    }
+}
+// The builds the autotuner times for `tpt` targets per thread: capping two
+// targets per thread (94 registers uncapped) only matters at 64 registers.
+int far_f32_builds(int tpt, int* minb) {
+    if (tpt <= 2) { minb[0] = 0; minb[1] = 16; return 2; }
+    minb[0] = 0; minb[1] = 8; minb[2] = 10; minb[3] = 16;
+    return 4;
+}
+
 template <int OP, int TPT>
 static cudaError_t launch_far_t(sbie_ctx* c, const FarTune& tu, bool f32, const FarArgs& a, int nts) {
     dim3 grid(nts * a.chunks, tu.split);
     int nv = (OP == (int)Kern::D) ? 3 : 2;
     size_t words = ((c->n + 31) / 32) * sizeof(unsigned);
     if (f32) {
-        const int nv32 = (OP == (int)Kern::D) ? 5 : 3;
-        const int tpt32 = 2 * ((TPT + 1) / 2);
-        size_t sm = (size_t)nv32 * tu.tile * sizeof(float4) + (size_t)tpt32 * 6 * tu.threads * sizeof(float) + words;
+        const size_t sm = f32_smem<OP>(TPT, tu.threads, tu.tile, c->n);
         auto run = [&](auto kernel) {
             if (sm > 48 * 1024) {
                 cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -627,8 +663,7 @@ static cudaError_t launch_far_t(sbie_ctx* c, const FarTune& tu, bool f32, const 
             ++c->n_launch;
             return cudaSuccess;
         };
-        cudaError_t e = (tu.minb && tu.threads == 64) ? run(far_f32_kernel<OP, (TPT + 1) / 2, 16>)
-                                                      : run(far_f32_kernel<OP, (TPT + 1) / 2, 0>);
+        cudaError_t e = run(f32_build<OP, (TPT + 1) / 2>(tu));
         if (e != cudaSuccess) return e;
     } else if constexpr (TPT <= 4) {  // the FP64 kernel holds at most 4 targets per thread
         size_t sm = (size_t)nv * tu.tile * sizeof(double4) + words;
@@ -724,20 +759,11 @@ static int far_occupancy_op(sbie_ctx* c, int mode, const FarTune& tu) {
         const int nv = (OP == (int)Kern::D) ? 5 : 3;
         return occ_of(far_df_kernel<OP>, tu.threads, (size_t)nv * tu.tile * sizeof(float4) + words);
     }
-    const int nv32 = (OP == (int)Kern::D) ? 5 : 3;
-    const int tpt32 = 2 * ((tu.tpt + 1) / 2);
-    const size_t sm = (size_t)nv32 * tu.tile * sizeof(float4) + (size_t)tpt32 * 6 * tu.threads * sizeof(float) + words;
-    if (tu.minb && tu.threads == 64) {
-        switch (tu.tpt) {
-            case 2: return occ_of(far_f32_kernel<OP, 1, 16>, tu.threads, sm);
-            case 6: return occ_of(far_f32_kernel<OP, 3, 16>, tu.threads, sm);
-            default: return occ_of(far_f32_kernel<OP, 2, 16>, tu.threads, sm);
-        }
-    }
+    const size_t sm = f32_smem<OP>(tu.tpt, tu.threads, tu.tile, c->n);
     switch (tu.tpt) {
-        case 2: return occ_of(far_f32_kernel<OP, 1, 0>, tu.threads, sm);
-        case 6: return occ_of(far_f32_kernel<OP, 3, 0>, tu.threads, sm);
-        default: return occ_of(far_f32_kernel<OP, 2, 0>, tu.threads, sm);
+        case 2: return occ_of(f32_build<OP, 1>(tu), tu.threads, sm);
+        case 6: return occ_of(f32_build<OP, 3>(tu), tu.threads, sm);
+        default: return occ_of(f32_build<OP, 2>(tu), tu.threads, sm);
     }
 }
 

@@ -52,7 +52,7 @@ class Profile(ctypes.Structure):
 class FarTuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("targets_per_thread", ctypes.c_int), ("split", ctypes.c_int),
                 ("tile", ctypes.c_int), ("ms", ctypes.c_double), ("candidates", ctypes.c_int),
-                ("regs64", ctypes.c_int)]
+                ("min_blocks", ctypes.c_int)]
 
 
 class PairTrainOpts(ctypes.Structure):

@@ -603,8 +603,12 @@ def main():
         return ts, inf
 
     t_wall0 = time.time()
+    # the NVTX range lets a profiler select the launches of the timed solves
+    # (ncu --nvtx --nvtx-include "timed_solves/")
+    torch.cuda.nvtx.range_push("timed_solves")
     times, timed_infos = timed(args.steps)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     t_wall1 = time.time()
     infos += timed_infos
     sampler.stop()

@@ -340,40 +340,89 @@ __global__ void gather_low_kernel(int n_sph, int P1, const double* __restrict__ 
     low[(size_t)s * kLowModes + b] = cg[2 * (md.x * P1 * P1 + o) + md.w];
 }
 
-// coarse correction e_i (see the header comment)
+// coarse correction e_i (see the header comment).  One CTA per sphere; each
+// warp takes whole matrix rows (rows r = warp, warp + nwarps, ...) and its
+// lanes read a row's columns coalesced.  The dot products run in double-float
+// arithmetic on the FP32 pipe (GB300 issues FP64 at a small fraction of the
+// FP32 rate): a coefficient is split c = ch + cl into floats, m ch is formed
+// exactly with an FMA and m cl added rounded, and every sum is a TwoSum, so the
+// map stays linear to about 1e-14.  The pair sums of a row are kept as float
+// pairs in shared memory (one warp owns each row) and weighted by 1 / deg in
+// FP64 once at the end.
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void df_madd(float& h, float& l, float m, float ch, float cl) {
+    const float p = m * ch;
+    float pe = fmaf(m, ch, -p);
+    pe = fmaf(m, cl, pe);
+    float sh, se;
+    two_sum_f(h, p, sh, se);
+    h = sh;
+    l += se + pe;
+}
+// sum of (h, l) over the warp, in every lane
+__device__ __forceinline__ void df_warp_sum(float& h, float& l) {
+    for (int o = 16; o; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+        float sh, se;
+        two_sum_f(h, oh, sh, se);
+        h = sh;
+        l = (l + ol) + se;
+    }
+}
+constexpr int kCoarseThreads = 512;
 __global__ void coarse_kernel(const int* __restrict__ pp_ptr, const int* __restrict__ pp_idx,
                               const int* __restrict__ pp_pair, const float* __restrict__ pinv,
                               const float* __restrict__ sinv, const double* __restrict__ low, double* __restrict__ e) {
+    constexpr int L = kLowModes;
     const int i = blockIdx.x;
-    const int r = threadIdx.x;
-    __shared__ double c2[2 * kLowModes];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __shared__ float ch[2 * L], cl[2 * L];   // staged coefficients, split
+    __shared__ float ah[L], al[L];           // per-row sums over the pairs
     const int e0 = pp_ptr[i], e1 = pp_ptr[i + 1];
     const int deg = e1 - e0;
-    double acc = 0.0;
-    if (deg == 0) {
-        __syncthreads();
-        if (r < kLowModes) {
-            const float* Mi = sinv + (size_t)i * kLowModes * kLowModes + (size_t)r * kLowModes;
-            const double* ci = low + (size_t)i * kLowModes;
-            for (int c = 0; c < kLowModes; ++c) acc += (double)Mi[c] * ci[c];
+    for (int t = threadIdx.x; t < L; t += blockDim.x) ah[t] = al[t] = 0.f;
+    // rows of the sphere's own block (no close partner) or of one pair's block
+    auto rows = [&](const float* M, int stride, int ncol) {
+        for (int r = warp; r < L; r += nw) {
+            const float* Mr = M + (size_t)r * stride;
+            float h = 0.f, l = 0.f;
+            for (int col = lane; col < ncol; col += 32) df_madd(h, l, Mr[col], ch[col], cl[col]);
+            df_warp_sum(h, l);
+            if (lane == 0) {
+                float sh, se;
+                two_sum_f(ah[r], h, sh, se);
+                ah[r] = sh;
+                al[r] += se + l;
+            }
         }
+    };
+    auto stage = [&](int t, double v) {
+        const float hi = (float)v;
+        ch[t] = hi;
+        cl[t] = (float)(v - (double)hi);
+    };
+    if (deg == 0) {
+        for (int t = threadIdx.x; t < L; t += blockDim.x) stage(t, low[(size_t)i * L + t]);
+        __syncthreads();
+        rows(sinv + (size_t)i * L * L, L, L);
     }
     for (int ee = e0; ee < e1; ++ee) {
         const int k = pp_idx[ee];
         const int a = min(i, k), b = max(i, k);
+        __syncthreads();  // the previous pair's coefficients are no longer read
+        for (int t = threadIdx.x; t < 2 * L; t += blockDim.x)
+            stage(t, t < L ? low[(size_t)a * L + t] : low[(size_t)b * L + t - L]);
         __syncthreads();
-        for (int t = threadIdx.x; t < 2 * kLowModes; t += blockDim.x)
-            c2[t] = t < kLowModes ? low[(size_t)a * kLowModes + t] : low[(size_t)b * kLowModes + t - kLowModes];
-        __syncthreads();
-        if (r < kLowModes) {
-            const int row = (i == a ? 0 : kLowModes) + r;
-            const float* Mr = pinv + (size_t)pp_pair[ee] * 4 * kLowModes * kLowModes + (size_t)row * 2 * kLowModes;
-            double s = 0.0;
-            for (int c = 0; c < 2 * kLowModes; ++c) s += (double)Mr[c] * c2[c];
-            acc += s / deg;
-        }
+        // rows of sphere i in the pair's [2L][2L] block
+        rows(pinv + (size_t)pp_pair[ee] * 4 * L * L + (size_t)(i == a ? 0 : L) * 2 * L, 2 * L, 2 * L);
     }
-    if (r < kLowModes) e[(size_t)i * kLowModes + r] = acc;
+    __syncthreads();
+    const double w = deg > 0 ? 1.0 / deg : 1.0;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) e[(size_t)i * L + t] = ((double)ah[t] + (double)al[t]) * w;
 }
 
 // out_sphere += ZS . e_sphere
@@ -433,7 +482,7 @@ cudaError_t precond_apply(sbie_ctx* c, int slot, const double* v, double* out) {
     if (e != cudaSuccess) return e;
     gather_low_kernel<<<c->n, 96, 0, c->stream>>>(c->n, c->p + 1, c->d_coef, c->d_modes, c->d_low);
     ++c->n_launch;
-    coarse_kernel<<<c->n, 96, 0, c->stream>>>(P.d_pp_ptr, P.d_pp_idx, P.d_pp_pair, P.d_pinv, P.d_sinv,
+    coarse_kernel<<<c->n, kCoarseThreads, 0, c->stream>>>(P.d_pp_ptr, P.d_pp_idx, P.d_pp_pair, P.d_pinv, P.d_sinv,
                                               c->d_low, c->d_lowe);
     ++c->n_launch;
     synth_add_kernel<<<(unsigned)((c->N + 127) / 128), 128, 0, c->stream>>>(c->npn, c->N, c->d_ZS, c->d_lowe, out);

@@ -1,0 +1,48 @@
+"""The CUDA path against the Stimson-Jeffery exact solution for two equal spheres
+moving along their line of centres (independent of the oracle): resistance and
+mobility in FP64, double-float and mixed precision, and mixed precision with the
+exact pair preconditioner."""
+import math
+
+import numpy as np
+import pytest
+
+from classical import stimson_jeffery_lambda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sb():
+    from paper_1707_06551_gb300 import build_lib
+    build_lib.build()
+    from paper_1707_06551_gb300 import sphere_bie
+    return sphere_bie
+
+
+def _centres(d):
+    return np.array([[0.1, -0.2, 0.3 - d / 2], [0.1, -0.2, 0.3 + d / 2]])
+
+
+@pytest.mark.parametrize("prec,precond", [(0, 0), (2, 0), (1, 0), (1, 2)])
+def test_resistance_of_two_spheres_is_stimson_jeffery(sb, prec, precond):
+    d = 3.0
+    U = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, 1.0]])
+    with sb.SphereBIE(_centres(d), np.ones(2), 12, prec=prec, tol=1e-11, precond=precond) as s:
+        F, T, info = s.resistance(U, np.zeros((2, 3)))
+    assert info["status"] == 0
+    np.testing.assert_allclose(F[:, 2] / (6 * math.pi), stimson_jeffery_lambda(d), rtol=1e-9)
+    np.testing.assert_allclose(F[:, :2], 0.0, atol=1e-9)
+    np.testing.assert_allclose(T, 0.0, atol=1e-9)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mobility_of_two_spheres_is_stimson_jeffery(sb, prec):
+    d = 2.5
+    F = np.array([[0.0, 0.0, 6 * math.pi], [0.0, 0.0, 6 * math.pi]])
+    with sb.SphereBIE(_centres(d), np.ones(2), 12, prec=prec, tol=1e-11) as s:
+        v, w, info = s.mobility(F, np.zeros((2, 3)))
+    assert info["status"] == 0
+    np.testing.assert_allclose(v[:, 2], 1.0 / stimson_jeffery_lambda(d), rtol=1e-8)
+    np.testing.assert_allclose(v[:, :2], 0.0, atol=1e-9)
+    np.testing.assert_allclose(w, 0.0, atol=1e-9)

@@ -1,0 +1,54 @@
+"""The oracle's two-sphere resistance and mobility solves (Eqs. 5.8 and 5.19 with
+the close-pair expansion of Sec. 4.2) against the Stimson-Jeffery exact solution
+for two equal spheres moving along their line of centres, which shares nothing
+with the oracle; the series itself is checked against the method of reflections."""
+import math
+
+import numpy as np
+import pytest
+
+from classical import stimson_jeffery_lambda
+from oracle import operators as ops, solve
+
+
+def test_series_matches_reflections_far_apart_and_contact_value():
+    for d in (20.0, 40.0, 80.0):
+        k = 1.0 / d
+        assert abs(stimson_jeffery_lambda(d) - (1 - 1.5 * k + 2.25 * k * k)) <= 3.0 * k ** 3
+    # the classical contact value (spheres touching: alpha -> 0)
+    assert abs(stimson_jeffery_lambda(2.0 * math.cosh(1e-3)) - 0.645) < 1e-3
+
+
+def _pair(d, p):
+    return ops.Geometry([[0.1, -0.2, 0.3 - d / 2], [0.1, -0.2, 0.3 + d / 2]], [1.0, 1.0], p)
+
+
+@pytest.mark.parametrize("d,tol", [(3.0, 2e-10), (2.5, 2e-9)])
+def test_resistance_of_two_spheres_is_stimson_jeffery(d, tol):
+    g = _pair(d, 12)
+    U = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, 1.0]])
+    F, T, _ = solve.solve_resistance(g, U, np.zeros((2, 3)), tol=1e-13)
+    lam = stimson_jeffery_lambda(d)
+    np.testing.assert_allclose(F[:, 2] / (6 * math.pi), lam, rtol=tol)
+    np.testing.assert_allclose(F[:, :2], 0.0, atol=1e-12)
+    np.testing.assert_allclose(T, 0.0, atol=1e-12)
+
+
+def test_mobility_of_two_spheres_is_stimson_jeffery():
+    d = 3.0
+    g = _pair(d, 12)
+    F = np.array([[0.0, 0.0, 6 * math.pi], [0.0, 0.0, 6 * math.pi]])
+    v, w, _ = solve.solve_mobility(g, F, np.zeros((2, 3)), tol=1e-13)
+    np.testing.assert_allclose(v[:, 2], 1.0 / stimson_jeffery_lambda(d), rtol=2e-10)
+    np.testing.assert_allclose(v[:, :2], 0.0, atol=1e-12)
+    np.testing.assert_allclose(w, 0.0, atol=1e-12)
+
+
+def test_error_decays_spectrally_in_p():
+    d = 3.0
+    U = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, 1.0]])
+    err = []
+    for p in (6, 8, 10):
+        F, _, _ = solve.solve_resistance(_pair(d, p), U, np.zeros((2, 3)), tol=1e-13)
+        err.append(abs(F[0, 2] / (6 * math.pi) - stimson_jeffery_lambda(d)))
+    assert err[1] < err[0] / 5 and err[2] < err[1] / 5

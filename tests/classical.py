@@ -1,5 +1,6 @@
 """Classical exact solutions used as pins that share nothing with the oracle or
-the CUDA path.
+the CUDA path: Stimson-Jeffery translation and Jeffery torsion of two equal
+spheres along their line of centres.
 
 Stimson & Jeffery (1926), Proc. R. Soc. A 111, 110-116: two equal rigid spheres
 of radius a translating with the same velocity U along their line of centres,
@@ -30,3 +31,20 @@ def stimson_jeffery_lambda(d_over_a):
         den = 2.0 * math.sinh(k * alpha) + k * s2a
         s += n * (n + 1) / ((2 * n - 1) * (2 * n + 3)) * (1.0 - num / den)
     return 4.0 / 3.0 * sa * s
+
+
+def jeffery_torque_ratio(d_over_a, co_rotating):
+    """Torque on each of two equal spheres rotating about their line of centres,
+    in units of the single-sphere torque 8 pi eta a^3 Omega (Jeffery (1915),
+    Proc. Lond. Math. Soc. 14, 327-338, torsional solution in bispherical
+    coordinates): sinh^3(alpha) sum_{n>=1} s^(n+1) / sinh^3(n alpha) with
+    s = +1 for opposite senses (the mid-plane is then a no-slip wall) and s = -1
+    for the same sense.  Far apart this is 1 -/+ (a/d)^3: a rotlet of the
+    neighbour turns the fluid at the sphere's centre with a^3 Omega / d^3."""
+    alpha = math.acosh(d_over_a / 2.0)
+    s = -1.0 if co_rotating else 1.0
+    total, n = 0.0, 1
+    while n * alpha < 200.0:
+        total += s ** (n + 1) / math.sinh(n * alpha) ** 3
+        n += 1
+    return math.sinh(alpha) ** 3 * total

@@ -1,13 +1,13 @@
-"""The CUDA path against the Stimson-Jeffery exact solution for two equal spheres
-moving along their line of centres (independent of the oracle): resistance and
-mobility in FP64, double-float and mixed precision, and mixed precision with the
-exact pair preconditioner."""
+"""The CUDA path against exact solutions for two equal spheres, independent of the
+oracle: Stimson-Jeffery translation along the line of centres and Jeffery's
+rotation about it; resistance and mobility in FP64, double-float and mixed
+precision, and mixed precision with the exact pair preconditioner."""
 import math
 
 import numpy as np
 import pytest
 
-from classical import stimson_jeffery_lambda
+from classical import jeffery_torque_ratio, stimson_jeffery_lambda
 
 pytestmark = pytest.mark.gpu
 
@@ -46,3 +46,18 @@ def test_mobility_of_two_spheres_is_stimson_jeffery(sb, prec):
     np.testing.assert_allclose(v[:, 2], 1.0 / stimson_jeffery_lambda(d), rtol=1e-8)
     np.testing.assert_allclose(v[:, :2], 0.0, atol=1e-9)
     np.testing.assert_allclose(w, 0.0, atol=1e-9)
+
+
+@pytest.mark.parametrize("prec,co", [(0, False), (1, True), (2, False)])
+def test_rotation_about_line_of_centres_is_jeffery(sb, prec, co):
+    d = 3.0
+    W = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, 1.0 if co else -1.0]])
+    with sb.SphereBIE(_centres(d), np.ones(2), 12, prec=prec, tol=1e-11) as s:
+        F, T, info = s.resistance(np.zeros((2, 3)), W)
+        v, w, info2 = s.mobility(np.zeros((2, 3)), 8 * math.pi * W)
+    assert info["status"] == 0 and info2["status"] == 0
+    ratio = jeffery_torque_ratio(d, co)
+    np.testing.assert_allclose(T[:, 2] / (8 * math.pi * W[:, 2]), ratio, rtol=1e-9)
+    np.testing.assert_allclose(w[:, 2] / W[:, 2], 1.0 / ratio, rtol=1e-9)
+    np.testing.assert_allclose(F, 0.0, atol=1e-9)
+    np.testing.assert_allclose(v, 0.0, atol=1e-9)

@@ -1,13 +1,14 @@
 """The oracle's two-sphere resistance and mobility solves (Eqs. 5.8 and 5.19 with
-the close-pair expansion of Sec. 4.2) against the Stimson-Jeffery exact solution
-for two equal spheres moving along their line of centres, which shares nothing
-with the oracle; the series itself is checked against the method of reflections."""
+the close-pair expansion of Sec. 4.2) against exact solutions for two equal
+spheres that share nothing with the oracle: Stimson-Jeffery translation along the
+line of centres and Jeffery's rotation about it (both senses); the series
+themselves are checked against the method of reflections."""
 import math
 
 import numpy as np
 import pytest
 
-from classical import stimson_jeffery_lambda
+from classical import jeffery_torque_ratio, stimson_jeffery_lambda
 from oracle import operators as ops, solve
 
 
@@ -52,3 +53,25 @@ def test_error_decays_spectrally_in_p():
         F, _, _ = solve.solve_resistance(_pair(d, p), U, np.zeros((2, 3)), tol=1e-13)
         err.append(abs(F[0, 2] / (6 * math.pi) - stimson_jeffery_lambda(d)))
     assert err[1] < err[0] / 5 and err[2] < err[1] / 5
+
+
+def test_torsion_series_match_rotlet_reflection_far_apart():
+    for d in (10.0, 20.0):
+        k = 1.0 / d
+        assert abs(jeffery_torque_ratio(d, False) - (1 + k ** 3)) <= 2 * k ** 6
+        assert abs(jeffery_torque_ratio(d, True) - (1 - k ** 3)) <= 2 * k ** 6
+
+
+@pytest.mark.parametrize("co", [False, True])
+def test_rotation_about_line_of_centres_is_jeffery(co):
+    d = 3.0
+    g = _pair(d, 12)
+    W = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, 1.0 if co else -1.0]])
+    F, T, _ = solve.solve_resistance(g, np.zeros((2, 3)), W, tol=1e-13)
+    np.testing.assert_allclose(T[:, 2] / (8 * math.pi * W[:, 2]), jeffery_torque_ratio(d, co), rtol=1e-10)
+    np.testing.assert_allclose(T[:, :2], 0.0, atol=1e-12)
+    np.testing.assert_allclose(F, 0.0, atol=1e-12)
+    # the inverse problem: torques given, angular velocities follow
+    v, w, _ = solve.solve_mobility(g, np.zeros((2, 3)), 8 * math.pi * W, tol=1e-13)
+    np.testing.assert_allclose(w[:, 2] / W[:, 2], 1.0 / jeffery_torque_ratio(d, co), rtol=1e-10)
+    np.testing.assert_allclose(v, 0.0, atol=1e-12)

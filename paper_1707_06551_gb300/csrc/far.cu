@@ -623,9 +623,10 @@ static size_t f32_smem(int tpt, int threads, int tile, int n) {
            (size_t)2 * ((tpt + 1) / 2) * f32_na(OP) * 2 * threads * sizeof(float) + ((n + 31) / 32) * sizeof(unsigned);
 }
 
-// The FP32 pair kernel is compiled once without a register cap (152-170
-// registers) and, for 64-thread CTAs, with 8, 10 and 16 resident CTAs per SM
-// required (about 128, 96 and 64 registers: 4, 5 and 8 warps per scheduler).
+// The FP32 pair kernel is compiled once without a register cap (about 150-210
+// registers for 4-6 targets per thread) and, for 64-thread CTAs, with 8, 10 and
+// 16 resident CTAs per SM required (about 128, 96 and 64 registers: 4, 5 and 8
+// warps per scheduler).
 // Fewer registers mean more warps to hide the special-function and FMA
 // latencies but more register moves; the autotuner times each build.
 using F32Kernel = void (*)(FarArgs);

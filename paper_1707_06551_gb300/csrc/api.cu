@@ -1931,10 +1931,11 @@ sbie_status tune_one(sbie_ctx* c, Kern k, int mode, sbie_far_tuning* chosen) {
         }
     FarTune* slot = f32 ? &c->tune32[(int)k] : &c->tunedf[(int)k];
     if (cands.empty()) cands.push_back(Cand{*slot, 0.f});
-    // the partial-sum buffer must hold the largest split timed
+    // the partial-sum buffer must hold the largest split timed, plus the
+    // slot the timed reduction writes
     int msp = 1;
     for (const Cand& cd : cands) msp = std::max(msp, cd.t.split);
-    CKS(ensure_part(c, msp));
+    CKS(ensure_part(c, msp + 1));
     float dummy;
     CK(time_far(c, k, mode, cands[0].t, &dummy));  // warm-up
     for (auto& cd : cands) CK(time_far(c, k, mode, cd.t, &cd.ms));

@@ -561,12 +561,14 @@ __global__ void __launch_bounds__(256) far_f64_kernel(FarArgs a) {
     }
 }
 
-__global__ void far_reduce(const double* __restrict__ part, int split, long long n3, double scale,
-                           double* __restrict__ out) {
+// out[i] = scale * sum_k part[k][i] for the first `count` entries of partials
+// laid out [split][stride]
+__global__ void far_reduce(const double* __restrict__ part, int split, long long stride, long long count,
+                           double scale, double* __restrict__ out) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n3) return;
+    if (i >= count) return;
     double s = 0.0;
-    for (int k = 0; k < split; ++k) s += part[(size_t)k * n3 + i];
+    for (int k = 0; k < split; ++k) s += part[(size_t)k * stride + i];
     out[i] = scale * s;
 }
 
@@ -737,7 +739,7 @@ cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out) {
     if (e != cudaSuccess) return e;
     double scale = (op == Kern::S) ? 1.0 / (8.0 * kPi) : (op == Kern::D ? 3.0 / (4.0 * kPi) : -3.0 / (4.0 * kPi));
     long long n3 = c->N * 3;
-    far_reduce<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(c->d_part, tu.split, n3, scale, out); ++c->n_launch;
+    far_reduce<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(c->d_part, tu.split, n3, n3, scale, out); ++c->n_launch;
     return cudaGetLastError();
 }
 
@@ -777,17 +779,29 @@ int far_occupancy(sbie_ctx* c, Kern op, int mode, const FarTune& tu) {
     }
 }
 
-// One pair-kernel launch timed with CUDA events.  Large contexts time the
-// first 512 target spheres only (every CTA does the same work as in a full
-// launch, and 512 spheres are several waves), so tuning stays cheap.
+// One pair-kernel launch and the reduction of its partial sums, timed with
+// CUDA events (a larger split costs the reduction more).  Large contexts time
+// the first 512 target spheres only (every CTA does the same work as in a full
+// launch, and 512 spheres are several waves), so tuning stays cheap.  The
+// reduction writes into the partial-sum slot after the last one read, which
+// the caller provides (capacity for split + 1 slots).
 cudaError_t time_far(sbie_ctx* c, Kern op, int mode, const FarTune& tu, float* ms) {
+    const long long n3 = c->N * 3;
+    if ((size_t)(tu.split + 1) * (size_t)n3 > c->part_cap) return cudaErrorInvalidValue;
+    const int nts = std::min(c->n, 512);
+    const long long count = (long long)nts * c->npn * 3;
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e != cudaSuccess) return e;
     e = cudaEventCreate(&e1);
     if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
     e = cudaEventRecord(e0, c->stream);
-    if (e == cudaSuccess) e = launch_pair_kernel(c, op, mode, tu, std::min(c->n, 512));
+    if (e == cudaSuccess) e = launch_pair_kernel(c, op, mode, tu, nts);
+    if (e == cudaSuccess) {
+        far_reduce<<<(unsigned)((count + 255) / 256), 256, 0, c->stream>>>(c->d_part, tu.split, n3, count, 1.0,
+                                                                         c->d_part + (size_t)tu.split * n3);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);

@@ -135,6 +135,25 @@ def peak_fp32_tflops(sm_count, mhz):
     return sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
+def ncu_traffic(t32):
+    """Measured DRAM bytes per launch of the FP32 far-field kernel for the
+    tiling `t32` (the autotuner's FP32 choice), or None when that tiling or the
+    kernel's source text differs from what was measured."""
+    key = (f"{far_source_hash()}/{t32.get('threads')}x{t32.get('targets_per_thread')}/"
+           f"{t32.get('split')}/{t32.get('tile')}/mb{t32.get('min_blocks')}")
+    return NCU_TRAFFIC.get(key)
+
+
+def max_over_ranks(torch, dist, world, x, device):
+    """The maximum of x over the ranks (N independent replicas are done when
+    the slowest is); x itself on a single rank."""
+    if world <= 1:
+        return x
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def train_pair_network(sb, w, samples):
     """Exact two-sphere low-mode blocks for the workload's close-pair gaps
     (close if gap < eta 2 max(a), eta = 1) and the network trained on them."""
@@ -625,10 +644,7 @@ def main():
     torch.cuda.synchronize()
     prof = sb.sphere_bie_profile_read(ctx)
     sb.sphere_bie_profile(ctx, 0)
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(torch, dist if world > 1 else None, world, t_step, dev)
     last = infos[-1]
 
     # far-field kernel roofline (FP32 pair kernel, the hot loop of the solve)
@@ -645,9 +661,7 @@ def main():
     if l32 > 0 and ms32 > 0:
         flop_launch = pairs32 / l32 * FLOP_PER_PAIR["D"]
         achieved = flop_launch / (ms32 / l32 * 1e-3) / 1e12
-        t32 = (tuning or {}).get("fp32") or {}
-        traffic = NCU_TRAFFIC.get(f"{far_source_hash()}/{t32.get('threads')}x{t32.get('targets_per_thread')}/"
-                                  f"{t32.get('split')}/{t32.get('tile')}/mb{t32.get('min_blocks')}")
+        traffic = ncu_traffic((tuning or {}).get("fp32") or {})
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "far_f32_kernel<D>",
                 "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clk_max:.0f} MHz",
@@ -711,6 +725,9 @@ def main():
         e2e_times.append(time.perf_counter() - t0)
     h2d = 8 * (w["centres"].size + w["radii"].size + w["vel"].size + w["omega"].size + 3 + 9)
     d2h = 8 * (hF.size + hT.size)
+    t_e2e = None
+    if args.e2e_steps > 0:
+        t_e2e = max_over_ranks(torch, dist if world > 1 else None, world, statistics.mean(e2e_times), dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -751,9 +768,9 @@ def main():
                                 "note": "stage and kernel times (roofline, far_field, stage_ms_per_step) come from "
                                         "these host-stepped solves with CUDA events per stage"},
             "graphs_vs_host_stepped": graphs_cmp,
-            "e2e": ({"value": statistics.mean(e2e_times), "unit": "s", "h2d_bytes_per_step": h2d,
+            "e2e": ({"value": t_e2e, "unit": "s", "h2d_bytes_per_step": h2d,
                      "d2h_bytes_per_step": d2h, "includes": "create + solve + destroy, host buffers"}
-                    if e2e_times else None),
+                    if t_e2e is not None else None),
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

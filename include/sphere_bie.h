@@ -193,7 +193,8 @@ typedef struct {
     int targets_per_thread;  /* target nodes per thread (held in FP32 pairs)      */
     int split;               /* source-range splits (partial sums added in order) */
     int tile;                /* sources staged in shared memory per tile          */
-    double ms;               /* measured time of one launch with this tiling      */
+    double ms;               /* measured time of one launch with this tiling and  *
+                              * the reduction of its partial sums                 */
     int candidates;          /* tilings timed                                     */
     int min_blocks;          /* FP32 build for 64-thread CTAs requiring 8, 10 or 16 resident
                                 CTAs per SM (about 128, 96, 64 registers); 0: no register cap */

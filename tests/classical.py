@@ -1,6 +1,7 @@
 """Classical exact solutions used as pins that share nothing with the oracle or
-the CUDA path: Stimson-Jeffery translation and Jeffery torsion of two equal
-spheres along their line of centres.
+the CUDA path: translation of two equal spheres along their line of centres in
+the same direction (Stimson-Jeffery) and towards each other (Brenner), and
+rotation about it (Jeffery).
 
 Stimson & Jeffery (1926), Proc. R. Soc. A 111, 110-116: two equal rigid spheres
 of radius a translating with the same velocity U along their line of centres,
@@ -48,3 +49,29 @@ def jeffery_torque_ratio(d_over_a, co_rotating):
         total += s ** (n + 1) / math.sinh(n * alpha) ** 3
         n += 1
     return math.sinh(alpha) ** 3 * total
+
+
+def approach_lambda(d_over_a):
+    """Drag factor of two equal spheres approaching each other along their line
+    of centres with equal and opposite velocities (each feels 6 pi eta a U
+    lambda).  By symmetry the mid-plane carries no normal velocity and no shear
+    stress, so this is Brenner's (1961) sphere moving normal to a plane free
+    surface (Chem. Eng. Sci. 16, 242-251), with cosh(alpha) = d / 2a:
+
+      lambda = (4/3) sinh(alpha) sum_{n>=1} n(n+1) / ((2n-1)(2n+3))
+               [(4 cosh^2((n+1/2) alpha) + (2n+1)^2 sinh^2(alpha))
+                / (2 sinh((2n+1) alpha) - (2n+1) sinh(2 alpha)) - 1].
+
+    Far apart, lambda = 1 + 3k/2 + 9k^2/4 + O(k^3), k = a / d: each sphere moves
+    against the Stokeslet flow of the other."""
+    alpha = math.acosh(d_over_a / 2.0)
+    sa, s2a = math.sinh(alpha), math.sinh(2.0 * alpha)
+    s = 0.0
+    for n in range(1, max(60, int(40.0 / alpha)) + 1):
+        k = 2 * n + 1
+        if k * alpha > 600.0:
+            break
+        num = 4.0 * math.cosh((n + 0.5) * alpha) ** 2 + k * k * sa * sa
+        den = 2.0 * math.sinh(k * alpha) - k * s2a
+        s += n * (n + 1) / ((2 * n - 1) * (2 * n + 3)) * (num / den - 1.0)
+    return 4.0 / 3.0 * sa * s

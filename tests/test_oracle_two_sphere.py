@@ -1,14 +1,15 @@
 """The oracle's two-sphere resistance and mobility solves (Eqs. 5.8 and 5.19 with
 the close-pair expansion of Sec. 4.2) against exact solutions for two equal
-spheres that share nothing with the oracle: Stimson-Jeffery translation along the
-line of centres and Jeffery's rotation about it (both senses); the series
-themselves are checked against the method of reflections."""
+spheres that share nothing with the oracle: translation along the line of
+centres in the same direction (Stimson-Jeffery) and towards each other
+(Brenner), and rotation about it (Jeffery, both senses); the series themselves
+are checked against the method of reflections."""
 import math
 
 import numpy as np
 import pytest
 
-from classical import jeffery_torque_ratio, stimson_jeffery_lambda
+from classical import approach_lambda, jeffery_torque_ratio, stimson_jeffery_lambda
 from oracle import operators as ops, solve
 
 
@@ -75,3 +76,19 @@ def test_rotation_about_line_of_centres_is_jeffery(co):
     v, w, _ = solve.solve_mobility(g, np.zeros((2, 3)), 8 * math.pi * W, tol=1e-13)
     np.testing.assert_allclose(w[:, 2] / W[:, 2], 1.0 / jeffery_torque_ratio(d, co), rtol=1e-10)
     np.testing.assert_allclose(v, 0.0, atol=1e-12)
+
+
+def test_approach_series_matches_reflections_far_apart():
+    for d in (20.0, 40.0, 80.0):
+        k = 1.0 / d
+        assert abs(approach_lambda(d) - (1 + 1.5 * k + 2.25 * k * k)) <= 3.0 * k ** 3
+
+
+@pytest.mark.parametrize("d,p,tol", [(3.0, 12, 2e-9), (2.5, 14, 1e-7)])
+def test_spheres_approaching_each_other_is_brenner(d, p, tol):
+    g = _pair(d, p)
+    U = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, -1.0]])
+    F, T, _ = solve.solve_resistance(g, U, np.zeros((2, 3)), tol=1e-13)
+    np.testing.assert_allclose(F[:, 2] / (6 * math.pi * U[:, 2]), approach_lambda(d), rtol=tol)
+    np.testing.assert_allclose(F[:, :2], 0.0, atol=1e-11)
+    np.testing.assert_allclose(T, 0.0, atol=1e-11)

@@ -150,3 +150,43 @@ def test_train_pair_network_rejects_bad_options(lib, tmp_path, field, value):
     st = lib.lib().sphere_bie_train_pair_network(ctypes.byref(o), str(tmp_path / "n.bin").encode(), ctypes.byref(info))
     assert st == lib.SBIE_ERR_ARG
     assert not (tmp_path / "n.bin").exists()
+
+
+def test_every_context_entry_point_rejects_a_null_context(lib):
+    """Each call that takes a context checks it before touching it (no device
+    work, no crash); destroy(NULL) is a no-op and last_error(NULL) returns the
+    library's own last message."""
+    L = lib.lib()
+    buf = (ctypes.c_double * 64)()
+    n = ctypes.c_longlong(0)
+    calls = {
+        "num_nodes": lambda: L.sphere_bie_num_nodes(None, ctypes.byref(n)),
+        "nodes": lambda: L.sphere_bie_nodes(None, buf, buf, buf),
+        "apply_operator": lambda: L.sphere_bie_apply_operator(None, 0, buf, buf),
+        "solve_mobility": lambda: L.sphere_bie_solve_mobility(None, buf, buf, buf, buf, None),
+        "solve_resistance": lambda: L.sphere_bie_solve_resistance(None, buf, buf, None, None, buf, buf, None),
+        "autotune": lambda: L.sphere_bie_autotune(None, 4, None),
+        "profile": lambda: L.sphere_bie_profile(None, 1),
+        "profile_read": lambda: L.sphere_bie_profile_read(None, None),
+        "solution_density": lambda: L.sphere_bie_solution_density(None, buf),
+        "precond_info": lambda: L.sphere_bie_precond_info(None, 4, None, None, None, None),
+    }
+    for name, call in calls.items():
+        assert call() == lib.SBIE_ERR_ARG, name
+    assert L.sphere_bie_destroy(None) == 0
+    assert isinstance(L.sphere_bie_last_error(None), bytes)
+
+
+def test_context_free_entry_points_reject_bad_arguments(lib):
+    L = lib.lib()
+    d = (ctypes.c_double * 8)(2.5)
+    out = (ctypes.c_double * (73 * 73))()
+    assert L.sphere_bie_pair_blocks(0, d, d, d, 10, 4, out) == lib.SBIE_ERR_ARG       # no pairs
+    assert L.sphere_bie_pair_blocks(1, d, d, d, 3, 4, out) == lib.SBIE_ERR_ARG       # p below degree 4
+    assert L.sphere_bie_pair_blocks(1, d, d, d, 10, 0, out) == lib.SBIE_ERR_ARG      # not a solve operator
+    assert L.sphere_bie_pair_blocks(1, None, d, d, 10, 4, out) == lib.SBIE_ERR_ARG
+    f = (ctypes.c_float * 8)()
+    loss = ctypes.c_double(0)
+    assert L.sphere_bie_pair_network_gradients(None, 1, f, f, f, ctypes.byref(loss)) == lib.SBIE_ERR_ARG
+    assert L.sphere_bie_pair_network_gradients(f, 0, f, f, f, ctypes.byref(loss)) == lib.SBIE_ERR_ARG
+    assert L.sphere_bie_pair_network_size(None) == lib.SBIE_ERR_ARG

@@ -37,6 +37,16 @@ def test_resistance_256():
     assert w["G"][0, 1] == 1.0 and np.count_nonzero(w["G"]) == 1
 
 
+def test_resistance_256_close_pair_count():
+    """The oracle's close-pair list (negation of Eq. 4.5 at eta = 1) for the timed
+    workload: 1,118 directed pairs, i.e. the 559 pair systems the GPU path's
+    pair preconditioner builds for it (test_resistance_256_headline_configuration)
+    and the close_pairs the bench reports."""
+    from oracle import operators as ops
+    w = wl.resistance_256()
+    assert ops.Geometry(w["centres"], w["radii"], w["p"]).n_near_pairs() == 1118
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_small_suspension(seed):
     w = wl.small_suspension(12, 4, seed)

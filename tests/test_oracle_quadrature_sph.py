@@ -127,7 +127,7 @@ def _random_coeffs(rng, p):
     return c
 
 
-@pytest.mark.parametrize("p", [1, 2, 5, 8])
+@pytest.mark.parametrize("p", [1, 2, 5, 8, 24])  # 24: the largest order the library accepts
 def test_analysis_inverts_synthesis(p):
     rng = np.random.default_rng(p)
     c = _random_coeffs(rng, p)

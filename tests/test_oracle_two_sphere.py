@@ -2,8 +2,9 @@
 the close-pair expansion of Sec. 4.2) against exact solutions for two equal
 spheres that share nothing with the oracle: translation along the line of
 centres in the same direction (Stimson-Jeffery) and towards each other
-(Brenner), and rotation about it (Jeffery, both senses); the series themselves
-are checked against the method of reflections."""
+(Brenner), and rotation about it (Jeffery, both senses), checked against the
+method of reflections; and far apart, Batchelor's (1976, J. Fluid Mech. 74,
+1-29) expansions of the two-sphere mobility functions."""
 import math
 
 import numpy as np
@@ -92,3 +93,24 @@ def test_spheres_approaching_each_other_is_brenner(d, p, tol):
     np.testing.assert_allclose(F[:, 2] / (6 * math.pi * U[:, 2]), approach_lambda(d), rtol=tol)
     np.testing.assert_allclose(F[:, :2], 0.0, atol=1e-11)
     np.testing.assert_allclose(T, 0.0, atol=1e-11)
+
+
+@pytest.mark.parametrize("r", [10.0, 20.0])
+def test_far_apart_mobilities_follow_batchelor_expansions(r):
+    """A force on sphere 1 only, along and across the line of centres, in units
+    of F / (6 pi a): x11 = 1 - 15/(4 r^4), x12 = 3/(2r) - 1/r^3, y11 =
+    1 - 17/(16 r^6), y12 = 3/(4r) + 1/(2 r^3) (r = d / a), each up to its next
+    order; sphere 2 turns with the Stokeslet's vorticity, -3/(4 r^2)."""
+    g = _pair(r, 8)
+    F = np.zeros((2, 3))
+    F[0, 2] = 6 * math.pi
+    v, w, _ = solve.solve_mobility(g, F, np.zeros((2, 3)), tol=1e-13)
+    assert abs(v[0, 2] - (1 - 15 / (4 * r ** 4))) <= 8 / r ** 6
+    assert abs(v[1, 2] - (1.5 / r - 1 / r ** 3)) <= 25 / r ** 7
+    np.testing.assert_allclose(w, 0.0, atol=1e-12)
+    F = np.zeros((2, 3))
+    F[0, 0] = 6 * math.pi
+    v, w, _ = solve.solve_mobility(g, F, np.zeros((2, 3)), tol=1e-13)
+    assert abs(v[0, 0] - (1 - 17 / (16 * r ** 6))) <= 4 / r ** 8
+    assert abs(v[1, 0] - (0.75 / r + 0.5 / r ** 3)) <= 1 / r ** 9
+    assert abs(w[1, 1] + 0.75 / r ** 2) <= 1 / r ** 8

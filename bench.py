@@ -144,6 +144,17 @@ def ncu_traffic(t32):
     return NCU_TRAFFIC.get(key)
 
 
+def self_vsh_rate(prof, n_nodes):
+    """Throughput of the operator's self step (VSH analysis, signature,
+    synthesis: the density read and the result written, 2 x 3 x N doubles per
+    apply) from a profile of solves; None when the profile has no self step."""
+    applies, ms = prof["launches"].get("self", 0), prof["ms"].get("self", 0.0)
+    if not applies or not ms:
+        return None
+    per = 2 * 3 * n_nodes * 8
+    return {"gb_per_s": per * applies / (ms * 1e-3) / 1e9, "ms_per_apply": ms / applies, "bytes_per_apply": per}
+
+
 def max_over_ranks(torch, dist, world, x, device):
     """The maximum of x over the ranks (N independent replicas are done when
     the slowest is); x itself on a single rank."""
@@ -671,6 +682,7 @@ def main():
            "pairs_per_s_fp64": pairs64 / (ms64 * 1e-3) if ms64 > 0 else None,
            "fp64_launches_per_solve": l64 / args.steps, "fp32_launches_per_solve": l32 / args.steps}
     stage_ms = {k: v / args.steps for k, v in prof["ms"].items()}
+    self_vsh = self_vsh_rate(prof, n * (p + 1) * (2 * p + 2))
 
     # plain FP64 path on the same workload (comparison; outside the timed region)
     fp64 = None
@@ -758,7 +770,8 @@ def main():
                       "last_correction": last["last_correction"],
                       "rel_residual_true": last["rel_residual_true"], "status": last["status"],
                       "create_s": t_create, "autotune_s": t_tune, "far_tiling": tuning},
-            "roofline": roof, "far_field": far, "stage_ms_per_step": stage_ms, "fp64_path": fp64,
+            "roofline": roof, "far_field": far, "stage_ms_per_step": stage_ms, "self_vsh": self_vsh,
+            "fp64_path": fp64,
             "pair_preconditioner": pre,
             "clocks": clocks, "gpu_launches": int(launches_timed),
             "gpu_launches_per_step": launches_per_step,

@@ -104,3 +104,13 @@ def test_reference_arm_prints_the_oracle_line():
 def test_reference_arm_is_silent_on_other_ranks():
     r = _run_reference({"RANK": "1"})
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_self_vsh_rate():
+    prof = {"launches": {"self": 63}, "ms": {"self": 4.33}}
+    r = bench.self_vsh_rate(prof, 61952)
+    assert r["bytes_per_apply"] == 2 * 3 * 61952 * 8
+    assert r["ms_per_apply"] == pytest.approx(4.33 / 63)
+    assert r["gb_per_s"] == pytest.approx(2 * 3 * 61952 * 8 * 63 / 4.33e-3 / 1e9)
+    assert bench.self_vsh_rate({"launches": {"self": 0}, "ms": {"self": 0.0}}, 10) is None
+    assert bench.self_vsh_rate({"launches": {}, "ms": {}}, 10) is None

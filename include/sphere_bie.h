@@ -210,9 +210,12 @@ typedef struct {
  * not tuned).  SBIE_FP64 contexts keep their default tiling. */
 sbie_status sphere_bie_autotune(sbie_ctx* ctx, sbie_op op, sbie_far_tuning* chosen);
 
-/* enable != 0 starts recording (and resets the counters); 0 stops. */
+/* enable != 0 starts recording (and resets the counters); 0 stops.  While
+ * recording, solves step their GMRES cycles from the host so that every stage
+ * can be timed.  SBIE_ERR_ARG for a NULL context. */
 sbie_status sphere_bie_profile(sbie_ctx* ctx, int enable);
-/* Synchronises the context stream and returns the totals since the last reset. */
+/* Synchronises the context stream and writes the totals since the last reset
+ * to *out (host memory, owned by the caller).  SBIE_ERR_ARG for NULL. */
 sbie_status sphere_bie_profile_read(sbie_ctx* ctx, sbie_profile* out);
 
 /* Raw layer operator without any device allocation.  The paper has no
@@ -278,14 +281,21 @@ typedef struct {
 
 /* Generates exact pair-frame low-mode blocks of two-sphere configurations
  * (probing the close-pair path of the operator on the GPU), trains the pair
- * network on them with the library's own kernels, and writes it to path. */
+ * network on them with the library's own kernels, and writes it to path (the
+ * file a context reads through opts.mlp_weights_path).  info may be NULL.
+ * SBIE_ERR_ARG for out-of-range options (checked before any device work),
+ * SBIE_ERR_CUDA / SBIE_ERR_OOM for device failures, SBIE_ERR_ARG if path cannot
+ * be written. */
 sbie_status sphere_bie_train_pair_network(const sbie_pair_train_opts* opts, const char* path,
                                           sbie_pair_train_info* info);
 
 /* Exact pair-frame blocks: source of radius a_src at the origin, target of
  * radius a_tgt at (0, 0, dist[q]); blocks: host [n][73][73] (target row,
  * source column) of operator op (SBIE_OP_RESISTANCE or SBIE_OP_MOBILITY),
- * grid order p. */
+ * grid order p.  All arrays are host memory owned by the caller.  SBIE_ERR_ARG
+ * for n < 1, NULL arrays, p outside [4, 24], another operator, a radius <= 0
+ * or spheres that touch or overlap (dist <= a_src + a_tgt), all before any
+ * device work. */
 sbie_status sphere_bie_pair_blocks(int n, const double* dist, const double* a_src, const double* a_tgt, int p,
                                    sbie_op op, double* blocks);
 
@@ -302,12 +312,15 @@ sbie_status sphere_bie_solution_density(sbie_ctx* ctx, double* density);
 sbie_status sphere_bie_precond_info(const sbie_ctx* ctx, sbie_op op, int* kind, int* n_pairs, int* n_dropped,
                                     double* setup_ms);
 
-/* Number of network parameters (FP32, layer by layer: W1 (5x128), b1, ...). */
+/* Number of network parameters (FP32, layer by layer: W1 (5x128), b1, ...).
+ * SBIE_ERR_ARG for NULL. */
 sbie_status sphere_bie_pair_network_size(long long* n_params);
 
 /* Loss (mean squared error over all outputs) and its gradient for raw
- * network inputs X [n][5] and targets Y [n][5329] (host), with the weights
- * rounded to BF16 as in training. */
+ * network inputs X [n][5] and targets Y [n][5329], with the weights rounded to
+ * BF16 as in training; params and grads hold sphere_bie_pair_network_size
+ * floats.  All arrays are host memory owned by the caller.  SBIE_ERR_ARG for
+ * NULL arrays or n < 1 (before any device work). */
 sbie_status sphere_bie_pair_network_gradients(const float* params, int n, const float* X, const float* Y,
                                               float* grads, double* loss);
 

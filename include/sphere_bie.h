@@ -220,14 +220,14 @@ sbie_status sphere_bie_profile_read(sbie_ctx* ctx, sbie_profile* out);
 
 /* Raw layer operator without any device allocation.  The paper has no
  * counterpart: this exists for callers that cannot call cudaMalloc (a memory
- * manager owns the device, allocation is banned inside their hot loop, or
- * they are building a CUDA graph around the call).
+ * manager owns the device, or allocation is banned inside their hot loop).
  * Computes out = sum_k S_k, D_k or K_k (op = SBIE_OP_S, _D or _K) in FP64 at
- * every node: the self term by the Theorem 2 signatures and every other pair
- * by the smooth quadrature of Eq. 4.4 -- i.e. sphere_bie_apply_operator with
- * eta = 0 (no close-pair correction).  centres [n][3], radii [n], density and
- * out [N][3] (N = n_spheres (p+1)(2p+2)) are DEVICE pointers on the current
- * device; work runs on `stream` (a cudaStream_t or NULL) and the call returns
+ * every node: what sphere_bie_apply_operator returns for that op on a context
+ * created with eta = 0 (self term plus the far field over every other sphere,
+ * no close-pair correction).  centres [n][3], radii [n], density and out [N][3]
+ * (N = n_spheres (p+1)(2p+2)) must be device (or managed) memory of the
+ * current device -- anything else returns SBIE_ERR_ARG before any work is
+ * queued; work runs on `stream` (a cudaStream_t or NULL) and the call returns
  * when out is complete.
  * Limits: 1 <= n_spheres <= 4096, 1 <= p <= 24, N <= 65536; larger sizes
  * return SBIE_ERR_ARG with a message.  All intermediates live in one static

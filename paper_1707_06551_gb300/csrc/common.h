@@ -31,7 +31,27 @@ struct TabLayout {
     int total;
 };
 
-TabLayout tab_layout(int p);
+constexpr TabLayout tab_layout(int p) {
+    TabLayout t{};
+    t.p = p;
+    t.nlat = p + 1;
+    t.nlon = 2 * p + 2;
+    t.npn = t.nlat * t.nlon;
+    int o = 0;
+    t.o_ct = o; o += t.nlat;
+    t.o_st = o; o += t.nlat;
+    t.o_w = o; o += t.nlat;
+    t.o_cph = o; o += t.nlon;
+    t.o_sph = o; o += t.nlon;
+    t.o_cmk = o; o += (p + 1) * t.nlon;
+    t.o_smk = o; o += (p + 1) * t.nlon;
+    const int leg = (p + 1) * (p + 1) * t.nlat;
+    t.o_P = o; o += leg;
+    t.o_dP = o; o += leg;
+    t.o_mS = o; o += leg;
+    t.total = o;
+    return t;
+}
 // Fills host table (size layout.total) for order p: Gauss-Legendre grid and
 // normalised associated Legendre functions (normalised recurrences).
 void build_tables(int p, std::vector<double>& host);

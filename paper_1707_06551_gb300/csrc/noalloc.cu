@@ -3,14 +3,14 @@
 //
 // Some callers cannot call cudaMalloc: code running under a memory manager
 // that owns the whole device (a pool or arena handed out by a host
-// framework), code that must not allocate while a CUDA graph is being built
-// around it, or a latency-critical loop that has banned allocation after
-// start-up.  For them this entry point runs the same kernels as
-// sphere_bie_apply_operator (self term by the Theorem 2 signatures, far field
-// by the smooth quadrature of Eq. 4.4) but keeps every intermediate -- Legendre
-// tables, node geometry, packed sources, the far-field partial sums -- in one
-// file-scope __device__ array of kNoallocBytes (20 MiB).  Every GPU that loads
-// the library holds that array until the process exits.
+// framework), or a latency-critical loop that has banned allocation after
+// start-up.  For them this entry point computes what sphere_bie_apply_operator
+// computes for SBIE_OP_S, _D or _K on a context created with eta = 0 (self
+// term plus the far field over every other sphere, no close-pair correction),
+// with the same kernels, but keeps every intermediate -- Legendre tables, node
+// geometry, packed sources, the far-field partial sums -- in one file-scope
+// __device__ array of kNoallocBytes (20 MiB).  Every GPU that loads the
+// library holds that array until the process exits.
 #include <mutex>
 
 #include "common.h"
@@ -29,7 +29,7 @@ struct Slots {
     size_t tab, x64, xhi, xlo, nrm, nrm64, sph, near_ptr, near_idx, sph_prob, prob_sph, src64, part, end;
 };
 
-Slots slots() {
+constexpr Slots slots() {
     Slots s{};
     size_t o = 0;
     s.tab = o;      o = align256(o + sizeof(double) * (size_t)sbie::tab_layout(sbie::kMaxP).total);
@@ -47,6 +47,21 @@ Slots slots() {
     s.part = o;     o = align256(o + sizeof(double) * 3 * kNoallocSplit * kNoallocMaxNodes);
     s.end = o;
     return s;
+}
+
+// The largest accepted problem (p = 24 tables, 65,536 nodes, 4,096 spheres,
+// kNoallocSplit partial sums) fits the array: checked when this file compiles.
+static_assert(slots().end <= kNoallocBytes, "no-allocation scratch layout exceeds its static array");
+
+// Device or managed memory that kernels on device `dev` may read and write.
+bool on_device(const void* p, int dev) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 std::mutex g_mu;
@@ -83,16 +98,19 @@ extern "C" sbie_status sphere_bie_apply_layer_noalloc(sbie_op op, int n_spheres,
         set_last_error("noalloc: NULL or aliased pointer");
         return SBIE_ERR_ARG;
     }
-    const Slots sl = slots();
-    if (sl.end > kNoallocBytes) {
-        set_last_error("noalloc: scratch layout exceeds the static array");
-        return SBIE_ERR_ARG;
-    }
+    constexpr Slots sl = slots();
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         set_last_error(std::string("noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
         return SBIE_ERR_CUDA;
+    }
+    // Host memory or another GPU's memory would reach the kernels as a bad
+    // address: refuse it before any work is queued.
+    if (!on_device(centres, dev) || !on_device(radii, dev) || !on_device(density, dev) || !on_device(out, dev)) {
+        set_last_error("noalloc: centres, radii, density and out must be device (or managed) memory of the "
+                       "current device");
+        return SBIE_ERR_ARG;
     }
     unsigned char* base = nullptr;
     bool need_tables = false;

@@ -233,11 +233,14 @@ static cudaError_t run_self(sbie_ctx* c, int op, const double* dens, double* out
     A.coef = write_coef ? c->d_coef : nullptr;
     A.radius = c->d_a; A.op = op; A.accumulate = accumulate ? 1 : 0;
     size_t sm = self_smem(c->p);
-    static bool attr_set = false;
-    if (!attr_set) {
+    // The shared-memory opt-in is a per-device attribute of the kernel: set it
+    // on every launch that needs more than the 48 KB default (p >= 17), so the
+    // device current at this launch has it whichever device ran first.  One
+    // fixed value for all orders, so that concurrent launches of different
+    // orders never lower it under one another.
+    if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(self_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     self_kernel<<<c->n, 256, sm, c->stream>>>(A); ++c->n_launch;
     return cudaGetLastError();

@@ -6,27 +6,6 @@
 
 namespace sbie {
 
-TabLayout tab_layout(int p) {
-    TabLayout t{};
-    t.p = p;
-    t.nlat = p + 1;
-    t.nlon = 2 * p + 2;
-    t.npn = t.nlat * t.nlon;
-    int o = 0;
-    t.o_ct = o; o += t.nlat;
-    t.o_st = o; o += t.nlat;
-    t.o_w = o; o += t.nlat;
-    t.o_cph = o; o += t.nlon;
-    t.o_sph = o; o += t.nlon;
-    t.o_cmk = o; o += (p + 1) * t.nlon;
-    t.o_smk = o; o += (p + 1) * t.nlon;
-    int leg = (p + 1) * (p + 1) * t.nlat;
-    t.o_P = o; o += leg;
-    t.o_dP = o; o += leg;
-    t.o_mS = o; o += leg;
-    t.total = o;
-    return t;
-}
 
 // Gauss-Legendre nodes (descending) and weights by Newton's method on P_n,
 // started from the Tricomi-type guess cos(pi (i + 3/4) / (n + 1/2)).

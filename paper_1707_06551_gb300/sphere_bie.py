@@ -221,8 +221,11 @@ def sphere_bie_solve_resistance(ctx, vel, omega, bg_u0, bg_grad, forces, torques
 
 
 def sphere_bie_apply_layer_noalloc(op, n_spheres, p, centres, radii, density, out, stream=None):
-    """Device tensors only; see the header for limits and the shared scratch."""
+    """CUDA float64 tensors only; see the header for limits and the shared scratch."""
     op = OPS[op] if isinstance(op, str) else int(op)
+    for name, a in (("centres", centres), ("radii", radii), ("density", density), ("out", out)):
+        if not (hasattr(a, "is_cuda") and a.is_cuda):
+            raise ValueError(f"sphere_bie_apply_layer_noalloc: {name} must be a CUDA tensor")
     _check(None, lib().sphere_bie_apply_layer_noalloc(op, int(n_spheres), int(p), _ptr(centres), _ptr(radii),
                                                       _ptr(density), _ptr(out), stream))
     return out

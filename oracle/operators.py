@@ -49,16 +49,15 @@ class Geometry:
         self.x = np.concatenate(xs)
         self.nrm = np.concatenate(ns)
         self.w = np.concatenate(ws)
+        # one row of gaps |c_i - c_k| - a_i - a_k per target sphere i
         self.near = [[] for _ in range(n)]
         for i in range(n):
-            for k in range(n):
-                if k == i:
-                    continue
-                gap = np.linalg.norm(self.c[i] - self.c[k]) - self.a[i] - self.a[k]
-                if gap <= 0:
-                    raise OverlapError(f"spheres {i} and {k} overlap or touch")
-                if gap < self.eta * 2.0 * max(self.a[i], self.a[k]):
-                    self.near[i].append(k)
+            gap = np.sqrt(np.sum((self.c[i][None, :] - self.c) ** 2, axis=1)) - self.a[i] - self.a
+            gap[i] = np.inf
+            bad = np.nonzero(gap <= 0)[0]
+            if len(bad):
+                raise OverlapError(f"spheres {i} and {int(bad[0])} overlap or touch")
+            self.near[i] = [int(k) for k in np.nonzero(gap < self.eta * 2.0 * np.maximum(self.a[i], self.a))[0]]
 
     @property
     def N(self):
@@ -175,13 +174,19 @@ def moments(g, dens):
     return M0, M1
 
 
-def completion_N(g, dens):
+def completion_N(g, dens, rows=None):
     """Sum_k N_k[psi]: Stokeslet (Eq. 2.19) with strength M0_k plus rotlet with
-    strength M1_k, both at the centre of sphere k, at every node (Eq. 5.19)."""
+    strength M1_k, both at the centre of sphere k, at every node (Eq. 5.19);
+    with `rows`, only at those nodes (other rows zero)."""
     M0, M1 = moments(g, dens)
     out = np.zeros((g.N, 3))
+    x = g.x if rows is None else g.x[rows]
+    acc = np.zeros((len(x), 3))
     for k in range(g.n):
-        out += kernels.stokeslet(g.x, g.c[k], M0[k]) + kernels.rotlet(g.x, g.c[k], M1[k])
+        acc += kernels.stokeslet(x, g.c[k], M0[k]) + kernels.rotlet(x, g.c[k], M1[k])
+    if rows is None:
+        return acc
+    out[rows] = acc
     return out
 
 
@@ -197,7 +202,7 @@ def apply_at(g, op, dens, targets):
     if op == "mobility":
         return mask * (0.5 * dens + rigid_L(g, dens)) + layer(g, "K", dens, targets)
     if op == "resistance":
-        return mask * (0.5 * dens + completion_N(g, dens)) + layer(g, "D", dens, targets)
+        return mask * (0.5 * dens + completion_N(g, dens, rows)) + layer(g, "D", dens, targets)
     raise ValueError(op)
 
 

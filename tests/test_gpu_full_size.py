@@ -1,0 +1,160 @@
+"""Oracle parity at the full sizes of the suspension workloads, on sampled
+target spheres (the oracle evaluates one target sphere against every source
+node), and for a p-mixed sample of the batched workload solved in one context.
+
+Bounds, per sphere (VSH order and radius vary, so each sphere is held to its
+own scale): max over the sphere's nodes of |gpu - oracle| divided by max over
+the same nodes of |oracle|
+  * FP64 and double-float (FP64-accurate) applies: 1e-10;
+  * mixed-precision applies (FP32 far field and close-pair evaluation):  2e-5.
+Solves: the true FP64 residual of the returned density <= tol, recomputed here
+from FP64-accurate applies; per-sphere outputs against the oracle's solve as
+stated in each test.
+
+Native FP64 applies of the 4,096-sphere workload take about 100 s each on one
+GB300 (1.9e12 pairs at 1.9e10 pairs/s); there the FP64-accurate arithmetic is
+the double-float far field, which agrees with native FP64 to 1e-12
+(test_df_far_field_is_fp64_accurate)."""
+import numpy as np
+import pytest
+
+from oracle import operators as ops
+from oracle import solve as osolve
+from paper_1707_06551_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def sb():
+    from paper_1707_06551_gb300 import build_lib
+    build_lib.build()
+    from paper_1707_06551_gb300 import sphere_bie
+    return sphere_bie
+
+
+def per_sphere_err(got, ref, npn):
+    """Per-sphere relative error of nodal fields stacked sphere by sphere."""
+    got = got.reshape(-1, npn, 3)
+    ref = ref.reshape(-1, npn, 3)
+    return np.max(np.abs(got - ref), axis=(1, 2)) / np.max(np.abs(ref), axis=(1, 2))
+
+
+def _sampled(g, sample):
+    return np.concatenate([np.arange(g.sl(i).start, g.sl(i).stop) for i in sample])
+
+
+def test_dense_1024_sampled_parity(sb):
+    """Dense suspension (1,024 unit spheres at volume fraction 0.30, p = 12,
+    13,940 directed close pairs): the mobility operator (Eq. 5.8) in FP64,
+    double-float and mixed precision against the oracle on three target
+    spheres, one of them the sphere with the most close partners; the FP32
+    far field runs in chunks here (338 target nodes per sphere)."""
+    w = wl.dense_1024()
+    g = ops.Geometry(w["centres"], w["radii"], w["p"])
+    assert g.n_near_pairs() == 13940
+    nc = [len(x) for x in g.near]
+    sample = [0, int(np.argmax(nc)), 700]
+    rows = _sampled(g, sample)
+    dens = np.random.default_rng(21).normal(size=(g.N, 3))
+    ref = ops.apply_at(g, "mobility", dens, sample)[rows]
+    for prec, tol in ((0, TOL64), (2, TOL64), (1, TOL32)):
+        with sb.SphereBIE(w["centres"], w["radii"], w["p"], prec=prec) as s:
+            out = s.apply("mobility", dens)[rows]
+        err = per_sphere_err(out, ref, g.npn)
+        assert np.all(err < tol), (prec, err)
+
+
+def test_large_4096_sampled_parity(sb):
+    """Large polydisperse suspension (4,096 spheres, radii U[0.8, 1.2], p = 12,
+    1,384,448 nodes): the resistance operator (Eq. 5.19) in double-float and
+    mixed precision against the oracle on two target spheres."""
+    w = wl.large_4096()
+    g = ops.Geometry(w["centres"], w["radii"], w["p"])
+    nc = [len(x) for x in g.near]
+    sample = [int(np.argmax(nc)), 2000]
+    rows = _sampled(g, sample)
+    dens = np.random.default_rng(22).normal(size=(g.N, 3))
+    ref = ops.apply_at(g, "resistance", dens, sample)[rows]
+    for prec, tol in ((2, TOL64), (1, TOL32)):
+        with sb.SphereBIE(w["centres"], w["radii"], w["p"], prec=prec) as s:
+            out = s.apply("resistance", dens)[rows]
+        err = per_sphere_err(out, ref, g.npn)
+        assert np.all(err < tol), (prec, err)
+
+
+@pytest.fixture(scope="module")
+def batch_sample():
+    """The two smallest problems of each VSH order of the batched workload
+    (order kept as drawn), with the oracle's mobility solve of each (tol
+    1e-12)."""
+    probs = wl.batched_512()
+    pick = []
+    for p in (6, 8, 10, 12):
+        idx = [i for i, q in enumerate(probs) if q["p"] == p]
+        pick += sorted(idx, key=lambda i: (len(probs[i]["radii"]), i))[:2]
+    sample = [probs[i] for i in sorted(pick)]
+    refs = []
+    for q in sample:
+        g = ops.Geometry(q["centres"], q["radii"], q["p"])
+        vr, wr, _ = osolve.solve_mobility(g, q["forces"], q["torques"], tol=1e-12)
+        refs.append((vr, wr))
+    return sample, refs
+
+
+@pytest.mark.parametrize("prec,tol,tolv", [(0, 1e-11, 1e-8), (1, 1e-8, 1e-6)])
+def test_batched_512_sample_matches_oracle_per_problem(sb, batch_sample, prec, tol, tolv):
+    """Eight problems of the batched workload (every p in {6, 8, 10, 12},
+    radii log-uniform in [0.5, 2]) in one batched context: mobility solves
+    against oracle solves problem by problem.  Per sphere, the error of the
+    velocity and angular velocity is within tolv of the largest of that
+    problem (FP64 at tol 1e-11: 1e-8; mixed at tol 1e-8: 1e-6)."""
+    sample, refs = batch_sample
+    assert sorted({q["p"] for q in sample}) == [6, 8, 10, 12]
+    batch = [(q["centres"], q["radii"], q["p"]) for q in sample]
+    F = np.concatenate([q["forces"] for q in sample])
+    T = np.concatenate([q["torques"] for q in sample])
+    with sb.SphereBIE(batch=batch, prec=prec, tol=tol) as s:
+        v, om, info = s.mobility(F, T)
+    assert info["status"] == 0 and info["rel_residual_true"] <= tol
+    off = 0
+    for q, (vr, wr) in zip(sample, refs):
+        k = len(q["radii"])
+        for got, ref in ((v[off:off + k], vr), (om[off:off + k], wr)):
+            e = np.max(np.abs(got - ref), axis=1) / np.max(np.abs(ref))
+            assert np.all(e < tolv), (q["p"], k, e)
+        off += k
+
+
+def _rho(x, c, a, F, T, npn):
+    """Rigid-form density of forces and torques (mobility right-hand side)."""
+    n = len(a)
+    out = np.zeros((n * npn, 3))
+    for k in range(n):
+        s = slice(k * npn, (k + 1) * npn)
+        out[s] = F[k] / (4 * np.pi * a[k] ** 2) + 3.0 / (8 * np.pi * a[k] ** 4) * np.cross(T[k], x[s] - c[k])
+    return out
+
+
+def test_dense_1024_mixed_solve_true_residual(sb):
+    """Mixed-precision mobility solve of the dense suspension to 1e-8: the
+    FP64 residual b - A mu of the density it returns, recomputed with the
+    double-float operator (b = -(1/2 rho + K rho), Eq. 5.8), is <= 1e-8 and
+    equals the residual the solve reports."""
+    w = wl.dense_1024()
+    c, a, p = w["centres"], w["radii"], w["p"]
+    npn = (p + 1) * (2 * p + 2)
+    with sb.SphereBIE(c, a, p, prec=sb.SBIE_MIXED, tol=1e-8) as s:
+        v, om, info = s.mobility(w["forces"], w["torques"])
+        mu = s.density()
+        x, nrm, wq = s.nodes()
+    assert info["status"] == 0 and info["rel_residual_true"] <= 1e-8
+    rho = _rho(x, c, a, w["forces"], w["torques"], npn)
+    with sb.SphereBIE(c, a, p, prec=sb.SBIE_FP64_DF) as s:
+        b = -(0.5 * rho + s.apply("K", rho))
+        r = b - s.apply("mobility", mu)
+    rel = np.linalg.norm(r) / np.linalg.norm(b)
+    assert rel <= 1e-8 and abs(rel - info["rel_residual_true"]) <= 0.1e-8

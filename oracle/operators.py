@@ -190,6 +190,21 @@ def completion_N(g, dens, rows=None):
     return out
 
 
+def rigid_part(g, dens):
+    """P mu: on each sphere the rigid field F/(4 pi a^2) + (3/(8 pi a^4)) T x (x - c_k)
+    with F = int mu and T = int (y - c_k) x mu, i.e. the projection of mu onto
+    the translations and rotations of the sphere (P P = P for the node
+    quadrature: sum w = 4 pi a^2, sum w (x - c) = 0, sum w (x-c)(x-c)^T = (4 pi a^4 / 3) I)."""
+    M0, M1 = moments(g, dens)
+    out = np.zeros((g.N, 3))
+    for k in range(g.n):
+        s = g.sl(k)
+        a = g.a[k]
+        out[s] = M0[k][None, :] / (4 * np.pi * a * a) + (3.0 / (8 * np.pi * a ** 4)) * np.cross(
+            M1[k][None, :], g.x[s] - g.c[k])
+    return out
+
+
 def apply_at(g, op, dens, targets):
     """apply() restricted to the nodes of the target spheres `targets` (rows of
     other spheres are zero); used to check large problems on sampled spheres."""
@@ -203,6 +218,12 @@ def apply_at(g, op, dens, targets):
         return mask * (0.5 * dens + rigid_L(g, dens)) + layer(g, "K", dens, targets)
     if op == "resistance":
         return mask * (0.5 * dens + completion_N(g, dens, rows)) + layer(g, "D", dens, targets)
+    if op == "porous":
+        return mask * (0.5 * dens) + layer(g, "S", dens, targets) + layer(g, "D", dens, targets)
+    if op == "squirmer":
+        r = rigid_part(g, dens)
+        q = dens - r
+        return mask * (0.5 * q - r) + layer(g, "S", q, targets) + layer(g, "D", q, targets)
     raise ValueError(op)
 
 
@@ -218,7 +239,11 @@ def rigid_L(g, dens):
 
 def apply(g, op, dens):
     """Operators of the C interface: 'S', 'D', 'K' (raw sums), 'mobility'
-    = 1/2 I + K + L (Eq. 5.8), 'resistance' = 1/2 I + D + N (Eq. 5.19)."""
+    = 1/2 I + K + L (Eq. 5.8), 'resistance' = 1/2 I + D + N (Eq. 5.19),
+    'porous' = 1/2 I + S + D (Eq. 5.4), and 'squirmer' = (1/2 I + S + D)(I - P) - P,
+    the square form of Eq. 5.17 with the force- and torque-free conditions
+    (Eq. 5.15): the rigid part P mu of the unknown carries the rigid velocity
+    v_i + w_i x (x - c_i) and mu - P mu is the density (see oracle.solve)."""
     dens = np.asarray(dens, float).reshape(-1, 3)
     if op in ("S", "D", "K"):
         return layer(g, op, dens)
@@ -226,4 +251,10 @@ def apply(g, op, dens):
         return 0.5 * dens + layer(g, "K", dens) + rigid_L(g, dens)
     if op == "resistance":
         return 0.5 * dens + layer(g, "D", dens) + completion_N(g, dens)
+    if op == "porous":
+        return 0.5 * dens + layer(g, "S", dens) + layer(g, "D", dens)
+    if op == "squirmer":
+        r = rigid_part(g, dens)
+        q = dens - r
+        return 0.5 * q + layer(g, "S", q) + layer(g, "D", q) - r
     raise ValueError(op)

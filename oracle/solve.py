@@ -1,5 +1,6 @@
-"""Mobility (Problem 2, Eqs. 5.5-5.8) and resistance (Problem 5, Eqs. 5.18-5.19)
-drivers.  Test infrastructure only.
+"""Porous-media (Problem 1, Eqs. 5.3-5.4), mobility (Problem 2, Eqs. 5.5-5.8),
+squirmer (Problem 4, Eqs. 5.14-5.17) and resistance (Problem 5, Eqs.
+5.18-5.19) drivers.  Test infrastructure only.
 
 Readings (the paper defers rho to its reference [9] and does not say how the
 rigid motions or forces are read off):
@@ -76,3 +77,36 @@ def solve_resistance(g, v, w, u0=None, G=None, tol=1e-10, restart=200, max_iter=
     psi = psi.reshape(-1, 3)
     F, T = ops.moments(g, psi)
     return F, T, dict(info, psi=psi)
+
+
+def solve_porous(g, u0=None, G=None, tol=1e-10, restart=200, max_iter=1000):
+    """Problem 1: fixed spheres in the imposed flow u_inf = u0 + G x.
+    (1/2 I + S + D) mu = -u_inf (Eq. 5.4); u = u_inf + (S + D) mu (Eq. 5.3).
+    F_k = int mu and T_k = int (y - c_k) x mu are the force and torque the
+    particle exerts on the fluid (the double layer carries none)."""
+    b = resistance_rhs(g, np.zeros((g.n, 3)), np.zeros((g.n, 3)), u0, G)
+    mu, info = _gmres.gmres(lambda x: ops.apply(g, "porous", x.reshape(-1, 3)), b.ravel(),
+                            tol=tol, restart=restart, max_iter=max_iter)
+    mu = mu.reshape(-1, 3)
+    F, T = ops.moments(g, mu)
+    return F, T, dict(info, mu=mu)
+
+
+def solve_squirmer(g, slip, tol=1e-10, restart=200, max_iter=1000):
+    """Problem 4: force- and torque-free spheres with the prescribed nodal slip
+    velocity u_s.  Eq. 5.17 with the conditions of Eq. 5.15 is solved in its
+    square form
+        (1/2 I + S + D)(mu - P mu) - P mu = u_s,
+    P the rigid projection of oracle.operators.rigid_part: the density is
+    mu - P mu (so int (mu - P mu) = 0 and int (y - c) x (mu - P mu) = 0, which
+    with the double layer carrying no force are Eq. 5.15), and the rigid part
+    P mu = v_i + w_i x (x - c_i) gives the velocities: v_i = int mu / (4 pi a^2),
+    w_i = (3 / (8 pi a^4)) int (y - c_i) x mu."""
+    b = np.asarray(slip, float).reshape(-1, 3)
+    mu, info = _gmres.gmres(lambda x: ops.apply(g, "squirmer", x.reshape(-1, 3)), b.ravel(),
+                            tol=tol, restart=restart, max_iter=max_iter)
+    mu = mu.reshape(-1, 3)
+    M0, M1 = ops.moments(g, mu)
+    v = M0 / (4 * np.pi * g.a[:, None] ** 2)
+    w = 3.0 * M1 / (8 * np.pi * g.a[:, None] ** 4)
+    return v, w, dict(info, mu=mu, density=mu - ops.rigid_part(g, mu))

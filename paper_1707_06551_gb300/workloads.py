@@ -174,3 +174,28 @@ def large_4096(seed=4):
     G -= np.trace(G) / 3.0 * np.eye(3)
     return dict(name="large_4096", centres=c, radii=radii, p=12, vel=np.zeros((n, 3)),
                 omega=np.zeros((n, 3)), u0=rng.normal(size=3), G=G)
+
+
+def squirmer_slip(normals, axes, B1, B2):
+    """Tangential squirmer slip at surface nodes with outward unit normals n:
+    u_s = (B1 + B2 cos t) sin t e_t, t the polar angle from the swimming axis e
+    of the node's sphere; with sin t e_t = (n . e) n - e this is
+    u_s = (B1 + B2 (n . e)) ((n . e) n - e).  `axes` holds
+    the axis e of each node's sphere ([N][3]); B1, B2 per node (scalars or
+    [N] arrays).  B2 > 0 is a puller, B2 < 0 a pusher."""
+    n = np.asarray(normals, float).reshape(-1, 3)
+    e = np.asarray(axes, float).reshape(-1, 3)
+    ne = np.sum(n * e, axis=1)
+    return ((np.asarray(B1, float) + np.asarray(B2, float) * ne)[:, None]) * (ne[:, None] * n - e)
+
+
+def squirmers(n, p, seed, B1=1.0, beta=-3.0, radius_range=(1.0, 1.0)):
+    """A small suspension of squirmers (RSA at volume fraction near 0.1, some
+    pairs pushed close) with random unit swimming axes; B2 = beta B1
+    (beta < 0: pushers)."""
+    w = small_suspension(n, p, seed, radius_range=radius_range)
+    rng = np.random.default_rng(seed + 1000)
+    ax = rng.normal(size=(n, 3))
+    ax /= np.linalg.norm(ax, axis=1, keepdims=True)
+    w.update(axes=ax, B1=B1, B2=beta * B1)
+    return w

@@ -70,7 +70,12 @@ typedef enum {
     SBIE_OP_D = 1,          /* sum_k D_k: double layer, Eq. 2.21, self = principal value        */
     SBIE_OP_K = 2,          /* sum_k K_k: traction of the single layer, Eq. 2.22, self = PV     */
     SBIE_OP_MOBILITY = 3,   /* 1/2 I + sum_k (K_k + L_k), the mobility BIE operator, Eq. 5.8     */
-    SBIE_OP_RESISTANCE = 4  /* 1/2 I + sum_k (D_k + N_k), completed double layer, Eq. 5.19       */
+    SBIE_OP_RESISTANCE = 4, /* 1/2 I + sum_k (D_k + N_k), completed double layer, Eq. 5.19       */
+    SBIE_OP_POROUS = 5,     /* 1/2 I + sum_k (S_k + D_k), porous-media flow, Eq. 5.4              */
+    SBIE_OP_SQUIRMER = 6    /* (1/2 I + sum_k (S_k + D_k)) (I - P) - P: Eq. 5.17 with the force-
+                               and torque-free conditions of Eq. 5.15 in square form; P mu is,
+                               on each sphere, the rigid field F/(4 pi a^2) + 3/(8 pi a^4) T x
+                               (x - c_k) with F = int mu, T = int (y - c_k) x mu             */
 } sbie_op;
 
 typedef struct {
@@ -170,6 +175,30 @@ sbie_status sphere_bie_solve_mobility(sbie_ctx* ctx, const double* forces, const
 sbie_status sphere_bie_solve_resistance(sbie_ctx* ctx, const double* vel, const double* omega,
                                         const double* bg_u0, const double* bg_grad,
                                         double* forces, double* torques, sbie_solve_info* info);
+
+/* Porous-media flow (Problem 1, Eqs. 5.3-5.4): fixed spheres in the imposed
+ * flow u_inf(x) = u0 + G x (bg_u0: [3] or NULL; bg_grad: G as [3][3]
+ * row-major or NULL; host memory for either mem_kind).  Solves
+ * (1/2 I + S + D) mu = -u_inf and returns forces F_k = int mu and torques
+ * T_k = int (y - c_k) x mu ([n][3] each: what each sphere exerts on the fluid;
+ * the double layer carries none); the flow is u = u_inf + (S + D) mu.  The
+ * pair preconditioner is not used for this operator.  info may be NULL;
+ * SBIE_ERR_NOT_CONVERGED (outputs filled) when max_iter is reached. */
+sbie_status sphere_bie_solve_porous(sbie_ctx* ctx, const double* bg_u0, const double* bg_grad, double* forces,
+                                    double* torques, sbie_solve_info* info);
+
+/* Active particles (Problem 4, Eqs. 5.14-5.17): force- and torque-free spheres
+ * with a prescribed slip velocity.  slip: [N][3] nodal u_s at the nodes in
+ * sphere_bie_nodes order (memory kind of the context).  Solves the square form
+ * (1/2 I + S + D)(mu - P mu) - P mu = u_s (SBIE_OP_SQUIRMER): mu - P mu is the
+ * density of u = (S + D)(mu - P mu) (Eq. 5.16), its force and torque on every
+ * sphere vanish (Eq. 5.15), and P mu = vel_k + omega_k x (x - c_k) is each
+ * sphere's rigid velocity, returned as vel_k = int mu / (4 pi a^2) and
+ * omega_k = 3 / (8 pi a^4) int (y - c_k) x mu ([n][3] each).
+ * sphere_bie_solution_density then returns mu - P mu.  The pair
+ * preconditioner is not used.  info may be NULL. */
+sbie_status sphere_bie_solve_squirmer(sbie_ctx* ctx, const double* slip, double* vel, double* omega,
+                                      sbie_solve_info* info);
 
 /* Stage timing.  Stages: 0 far field (density pack, pair kernel and split
  * reduction), 1 close pairs (Sec. 4.1), 2 self term (analysis, signature,

@@ -82,6 +82,7 @@ void drop_graphs(sbie_ctx* c) {
 
 void free_all(sbie_ctx* c) {
     drop_graphs(c);
+    self_gemm_free(c);
     for (sbie_ctx* q : c->parts) {
         free_all(q);
         delete q;
@@ -91,7 +92,8 @@ void free_all(sbie_ctx* c) {
                     c->d_near_idx, c->d_tab, c->d_coef, c->d_chan, c->d_chanf, c->d_mom, c->d_part, c->d_src64,
                     c->d_srcf, c->d_in, c->d_out, c->d_tmp, c->d_tmp2, c->d_small, c->d_red, c->d_V, c->d_xsol,
                     c->d_rhs, c->d_res, c->d_prob_sph, c->d_sph_prob, c->d_node_prob, c->d_seg3, c->d_H, c->d_pvec,
-                    c->d_ZS, c->d_ZA, c->d_modes, c->d_low, c->d_lowe, c->d_pz, c->d_ad, c->d_adi, c->d_vk};
+                    c->d_ZS, c->d_ZA, c->d_modes, c->d_low, c->d_lowe, c->d_pz, c->d_ad, c->d_adi, c->d_vk,
+                    c->d_sq};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (PrecState& P : c->prec)
@@ -205,9 +207,60 @@ Kern kern_of(int op) {
     return Kern::K;
 }
 
+sbie_status apply_dev(sbie_ctx* c, int op, int mode, const double* in, double* out);
+
+// Porous-media operator 1/2 I + S + D (Eq. 5.4): both layers' far fields,
+// self terms and close-pair corrections, added.
+sbie_status apply_porous(sbie_ctx* c, int mode, const double* in, double* out) {
+    const bool f32 = mode == kModeF32;
+    const bool far = c->far_pair_count > 0;
+    if (far) {
+        StageScope s(c, ST_FAR);
+        CK(launch_pack(c, in, mode));
+        CK(launch_far(c, Kern::S, mode, out, false));
+        CK(launch_far(c, Kern::D, mode, out, true));
+        if (c->prof.on) (f32 ? c->prof.pairs_f32 : c->prof.pairs_f64) += 2 * c->far_pair_count;
+    }
+    {
+        StageScope s(c, ST_SELF);
+        if (f32 && self_gemm_ready(c, kSelfS) && self_gemm_ready(c, kSelfDK)) {
+            CK(launch_self_gemm(c, kSelfS, in, out, far));
+            CK(launch_self_gemm(c, kSelfDK, in, out, true));
+            if (c->n_near > 0) CK(launch_self_analysis(c, in));
+        } else {
+            CK(launch_self(c, Kern::S, in, out, far, c->n_near > 0));
+            CK(launch_self(c, Kern::D, in, out, true, false));
+        }
+    }
+    if (c->n_near > 0) {
+        StageScope s(c, ST_NEAR);
+        CK(launch_near(c, Kern::S, f32, out));
+        CK(launch_near(c, Kern::D, f32, out));
+    }
+    StageScope s(c, ST_COMPL);
+    CK(launch_finalize(c, SBIE_OP_POROUS, in, out));
+    return SBIE_OK;
+}
+
 // out = A in, all device memory, on c->stream, in arithmetic `mode`
 // (kModeF64, kModeF32 or kModeDF).
 sbie_status apply_dev(sbie_ctx* c, int op, int mode, const double* in, double* out) {
+    if (op == SBIE_OP_POROUS) return apply_porous(c, mode, in, out);
+    if (op == SBIE_OP_SQUIRMER) {
+        // (1/2 I + S + D)(in - P in) - P in, P the rigid projection per sphere
+        if (!c->d_sq) return fail(c, SBIE_ERR_ARG, "squirmer buffers not allocated");
+        double* q = c->d_sq;
+        double* r = c->d_sq + 3 * c->N;
+        {
+            StageScope s(c, ST_COMPL);
+            CK(launch_moments(c, in));
+            CK(launch_rigid_split(c, in, q, r));
+        }
+        CKS(apply_porous(c, mode, q, out));
+        StageScope s(c, ST_COMPL);
+        CK(blas_axpy(c, -1.0, r, out, 3 * c->N));
+        return SBIE_OK;
+    }
     const Kern k = kern_of(op);
     const bool f32 = mode == kModeF32;
     // a context whose pairs are all close (the two-sphere probe problems of
@@ -221,7 +274,15 @@ sbie_status apply_dev(sbie_ctx* c, int op, int mode, const double* in, double* o
     }
     {
         StageScope s(c, ST_SELF);
-        CK(launch_self(c, k, in, out, far, c->n_near > 0));
+        const int which = k == Kern::S ? kSelfS : kSelfDK;
+        if (f32 && self_gemm_ready(c, which)) {
+            // FP32 operator: self term by the 3xTF32 GEMM; the close pairs
+            // keep FP64 VSH coefficients of the density
+            CK(launch_self_gemm(c, which, in, out, far));
+            if (c->n_near > 0) CK(launch_self_analysis(c, in));
+        } else {
+            CK(launch_self(c, k, in, out, far, c->n_near > 0));
+        }
     }
     if (c->n_near > 0) {
         StageScope s(c, ST_NEAR);
@@ -259,6 +320,39 @@ Sys sys_of(sbie_ctx* c) {
     s.n3 = c->N * 3;
     s.P = (int)c->seg3.size() - 1;
     return s;
+}
+
+// The FP32 operator's self term is a tensor-core GEMM whose matrices (single
+// layer; double layer = traction) are probed by the FP64 self kernel the first
+// time a mixed-precision context applies or solves, before any graph capture.
+sbie_status ensure_self_gemm(const Sys& S) {
+    for (sbie_ctx* q : S.parts) {
+        if (q->opts.prec != SBIE_MIXED) continue;
+        cudaError_t e = self_gemm_build(q, kSelfS);
+        if (e == cudaSuccess) e = self_gemm_build(q, kSelfDK);
+        if (e != cudaSuccess)
+            return fail(S.top, SBIE_ERR_CUDA, std::string("self-term matrices: ") + cudaGetErrorString(e));
+    }
+    return SBIE_OK;
+}
+
+// Work vectors of the squirmer operator, allocated before any graph capture.
+sbie_status ensure_squirmer_buffers(const Sys& S) {
+    for (sbie_ctx* q : S.parts)
+        if (!q->d_sq && dmalloc(&q->d_sq, 6 * (size_t)q->N) != cudaSuccess)
+            return fail(S.top, SBIE_ERR_OOM, "squirmer buffers");
+    return SBIE_OK;
+}
+
+// Device flag of the self-term GEMMs (a bounded wait that ran out).
+sbie_status check_self_gemm(const Sys& S) {
+    for (sbie_ctx* q : S.parts) {
+        int flag = 0;
+        cudaError_t e = self_gemm_error(q, &flag);
+        if (e != cudaSuccess) return fail(S.top, SBIE_ERR_CUDA, cudaGetErrorString(e));
+        if (flag) return fail(S.top, SBIE_ERR_TIMEOUT, "self-term GEMM: a pipeline wait timed out");
+    }
+    return SBIE_OK;
 }
 
 sbie_status apply_sys(const Sys& S, int op, int mode, const double* in, double* out) {
@@ -627,6 +721,15 @@ sbie_status ensure_preconditioner(const Sys& S, int op);
 // Bound on the FP32 operator's relative error (the mixed-precision apply
 // parity bound) used to decide when a residual may be updated in FP32.
 constexpr double kFp32OpErr = 2e-5;
+// Smallest inner (FP32-operator) GMRES tolerance of a correction.  The first
+// correction goes this deep, a little below the FP32 operator's own error, so
+// that the second correction is small enough for its residual to be updated
+// with the FP32 operator: a solve to 1e-8 then forms one FP64-accurate
+// residual instead of two.
+constexpr double kInnerTolMin = 1e-6;
+// Largest inner tolerance: a later correction only has to take the residual
+// from rel to half the tolerance (0.5 tol / rel), never less than a factor 10.
+constexpr double kInnerTolMax = 0.1;
 
 sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_solve_info* info) {
     sbie_ctx* c = S.top;
@@ -635,15 +738,19 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
     const int hm = hi_mode(c);
     AFn A64 = [&](const double* in, double* out) { return apply_sys(S, op, hm, in, out); };
     AFn A32 = [&](const double* in, double* out) { return apply_sys(S, op, kModeF32, in, out); };
+    CKS(ensure_self_gemm(S));
+    if (op == SBIE_OP_SQUIRMER) CKS(ensure_squirmer_buffers(S));
     CKS(ensure_preconditioner(S, op));
     const int slot = prec_slot(op);
+    // the pair preconditioner belongs to the resistance and mobility operators
     bool prec = false;
-    for (sbie_ctx* q : S.parts) prec |= q->prec[slot].kind > 0;
+    if (op == SBIE_OP_RESISTANCE || op == SBIE_OP_MOBILITY)
+        for (sbie_ctx* q : S.parts) prec |= q->prec[slot].kind > 0;
     AFn Mf = [&](const double* in, double* out) {
         for (size_t i = 0; i < S.parts.size(); ++i) {
             sbie_ctx* q = S.parts[i];
             if (q->prec[slot].kind > 0) {
-                cudaError_t e = precond_apply(q, slot, in + S.off3[i], out + S.off3[i]);
+                cudaError_t e = precond_apply(q, slot, in + S.off3[i], out + S.off3[i], q->opts.prec == SBIE_MIXED);
                 if (e != cudaSuccess) return fail(c, SBIE_ERR_CUDA, std::string("preconditioner: ") + cudaGetErrorString(e));
             } else {
                 cudaError_t e = cudaMemcpyAsync(out + S.off3[i], in + S.off3[i], sizeof(double) * q->N * 3,
@@ -686,7 +793,7 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
             std::vector<char> want(P);
             for (int p = 0; p < P; ++p) {
                 want[p] = rel[p] > tol;
-                itol[p] = std::min(1e-3, std::max(1e-5, 0.5 * tol / std::max(rel[p], 1e-300)));
+                itol[p] = std::min(kInnerTolMax, std::max(kInnerTolMin, 0.5 * tol / std::max(rel[p], 1e-300)));
             }
             CKS(gmres(S, A32, r, d, itol, want, c->opts.restart, c->opts.max_iter - iters, go, M, key_of(kModeF32),
                       true));
@@ -749,6 +856,7 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
         inf.iters = iters;
         inf.refinements = outers;
     }
+    CKS(check_self_gemm(S));
     inf.rel_residual_true = *std::max_element(rel.begin(), rel.end());
     long long nn = 0;
     for (sbie_ctx* q : S.parts) nn += q->n_near;
@@ -1219,7 +1327,7 @@ sbie_status precond_setup(sbie_ctx* c, int op, int kind, const PairNet* net);
 sbie_status ensure_preconditioner(const Sys& S, int op) {
     sbie_ctx* top = S.top;
     const int kind = top->opts.use_learned_precond, slot = prec_slot(op);
-    if (kind == 0) return SBIE_OK;
+    if (kind == 0 || (op != SBIE_OP_RESISTANCE && op != SBIE_OP_MOBILITY)) return SBIE_OK;
     const PairNet* net = nullptr;
     if (kind == 1) {
         net = top->nets ? top->nets->for_op(op) : nullptr;
@@ -1522,6 +1630,12 @@ sbie_status precond_setup(sbie_ctx* c, int op, int kind, const PairNet* net) {
     CK(cudaStreamSynchronize(c->stream));
     cudaFree(d_bad);
     if (bad) return fail(c, SBIE_ERR_NUMERIC, "singular pair system in the preconditioner");
+    if (c->opts.prec == SBIE_MIXED) {
+        // H and the low-mode analysis of the FP32 inner solves as one GEMM
+        const cudaError_t e = self_gemm_build(c, kSelfPrec);
+        if (e != cudaSuccess)
+            return fail(c, SBIE_ERR_CUDA, std::string("preconditioner matrix: ") + cudaGetErrorString(e));
+    }
     P.n_pairs = np;
     P.kind = kind;
     P.built = true;
@@ -1746,10 +1860,12 @@ sbie_status sphere_bie_nodes(const sbie_ctx* cc, double* xyz, double* normals, d
 sbie_status sphere_bie_apply_operator(sbie_ctx* c, sbie_op op, const double* density, double* out) {
     if (!c) return SBIE_ERR_ARG;
     if (!density || !out) return fail(c, SBIE_ERR_ARG, "NULL density or out");
-    if (op < SBIE_OP_S || op > SBIE_OP_RESISTANCE) return fail(c, SBIE_ERR_ARG, "bad operator");
+    if (op < SBIE_OP_S || op > SBIE_OP_SQUIRMER) return fail(c, SBIE_ERR_ARG, "bad operator");
     if (density == out) return fail(c, SBIE_ERR_ARG, "density and out must not alias");
     const int mode = c->opts.prec == SBIE_MIXED ? kModeF32 : hi_mode(c);
     Sys S = sys_of(c);
+    CKS(ensure_self_gemm(S));
+    if (op == SBIE_OP_SQUIRMER) CKS(ensure_squirmer_buffers(S));
     const bool direct = c->opts.mem_kind == 1 && !c->is_batch;
     if (direct) {
         CKS(apply_sys(S, op, mode, density, out));
@@ -1759,7 +1875,7 @@ sbie_status sphere_bie_apply_operator(sbie_ctx* c, sbie_op op, const double* den
         CKS(to_user(c, c->d_out, out, true));
     }
     CK(cudaStreamSynchronize(c->stream));
-    return SBIE_OK;
+    return check_self_gemm(S);
 }
 
 sbie_status sphere_bie_solve_mobility(sbie_ctx* c, const double* forces, const double* torques, double* vel,
@@ -1847,6 +1963,87 @@ sbie_status sphere_bie_solve_resistance(sbie_ctx* c, const double* vel, const do
     }
     CKS(to_user(c, dF, forces, false));
     CKS(to_user(c, dT, torques, false));
+    CK(cudaStreamSynchronize(c->stream));
+    inf.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    inf.t_setup_ms = c->t_create_ms;
+    c->has_solution = true;
+    inf.kernel_launches = total_launches(S) - launches0;
+    if (info) *info = inf;
+    return st;
+}
+
+sbie_status sphere_bie_solve_porous(sbie_ctx* c, const double* bg_u0, const double* bg_grad, double* forces,
+                                    double* torques, sbie_solve_info* info) {
+    if (!c) return SBIE_ERR_ARG;
+    if (!forces || !torques) return fail(c, SBIE_ERR_ARG, "NULL argument");
+    if (bg_u0 && !finite_all(bg_u0, 3)) return fail(c, SBIE_ERR_ARG, "non-finite u0");
+    if (bg_grad && !finite_all(bg_grad, 9)) return fail(c, SBIE_ERR_ARG, "non-finite velocity gradient");
+    auto t0 = std::chrono::steady_clock::now();
+    Sys S = sys_of(c);
+    const long long launches0 = total_launches(S);
+    double* dF = c->d_small;
+    double* dT = dF + 3 * c->n;
+    double* dz = dT + 3 * c->n;  // zero rigid motions: b = -u_inf
+    CK(cudaMemsetAsync(dz, 0, sizeof(double) * 3 * c->n, c->stream));
+    double* b = c->d_rhs;
+    double* mu = c->d_xsol;
+    long long sph_off = 0;
+    for (size_t s = 0; s < S.parts.size(); ++s) {
+        CK(launch_resistance_rhs(S.parts[s], dz + 3 * sph_off, dz + 3 * sph_off, bg_u0, bg_grad, b + S.off3[s]));
+        sph_off += S.parts[s]->n;
+    }
+    sbie_solve_info inf{};
+    sbie_status st = solve_sys(S, SBIE_OP_POROUS, b, mu, &inf);
+    if (st != SBIE_OK && st != SBIE_ERR_NOT_CONVERGED) return st;
+    sph_off = 0;
+    for (size_t s = 0; s < S.parts.size(); ++s) {
+        sbie_ctx* q = S.parts[s];
+        CK(launch_moments(q, mu + S.off3[s]));
+        CK(cudaMemcpy2DAsync(dF + 3 * sph_off, sizeof(double) * 3, q->d_mom, sizeof(double) * 6, sizeof(double) * 3,
+                             q->n, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpy2DAsync(dT + 3 * sph_off, sizeof(double) * 3, q->d_mom + 3, sizeof(double) * 6, sizeof(double) * 3,
+                             q->n, cudaMemcpyDeviceToDevice, c->stream));
+        sph_off += q->n;
+    }
+    CKS(to_user(c, dF, forces, false));
+    CKS(to_user(c, dT, torques, false));
+    CK(cudaStreamSynchronize(c->stream));
+    inf.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    inf.t_setup_ms = c->t_create_ms;
+    c->has_solution = true;
+    inf.kernel_launches = total_launches(S) - launches0;
+    if (info) *info = inf;
+    return st;
+}
+
+sbie_status sphere_bie_solve_squirmer(sbie_ctx* c, const double* slip, double* vel, double* omega,
+                                      sbie_solve_info* info) {
+    if (!c) return SBIE_ERR_ARG;
+    if (!slip || !vel || !omega) return fail(c, SBIE_ERR_ARG, "NULL argument");
+    auto t0 = std::chrono::steady_clock::now();
+    Sys S = sys_of(c);
+    const long long launches0 = total_launches(S);
+    CKS(ensure_squirmer_buffers(S));
+    double* dv = c->d_small;
+    double* dw = dv + 3 * c->n;
+    double* b = c->d_rhs;
+    double* mu = c->d_xsol;
+    CKS(to_internal(c, slip, b, true));
+    sbie_solve_info inf{};
+    sbie_status st = solve_sys(S, SBIE_OP_SQUIRMER, b, mu, &inf);
+    if (st != SBIE_OK && st != SBIE_ERR_NOT_CONVERGED) return st;
+    // rigid velocities from the rigid part of mu; keep mu - P mu as the density
+    long long sph_off = 0;
+    for (size_t s = 0; s < S.parts.size(); ++s) {
+        sbie_ctx* q = S.parts[s];
+        CK(launch_rigid_projection(q, mu + S.off3[s], dv + 3 * sph_off, dw + 3 * sph_off));
+        CK(launch_moments(q, mu + S.off3[s]));
+        CK(launch_rigid_split(q, mu + S.off3[s], q->d_sq, q->d_sq + 3 * q->N));
+        CK(cudaMemcpyAsync(mu + S.off3[s], q->d_sq, sizeof(double) * 3 * q->N, cudaMemcpyDeviceToDevice, c->stream));
+        sph_off += q->n;
+    }
+    CKS(to_user(c, dv, vel, false));
+    CKS(to_user(c, dw, omega, false));
     CK(cudaStreamSynchronize(c->stream));
     inf.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     inf.t_setup_ms = c->t_create_ms;
@@ -1975,7 +2172,12 @@ extern "C" {
 
 sbie_status sphere_bie_autotune(sbie_ctx* c, sbie_op op, sbie_far_tuning* chosen) {
     if (!c) return SBIE_ERR_ARG;
-    if (op < SBIE_OP_S || op > SBIE_OP_RESISTANCE) return fail(c, SBIE_ERR_ARG, "bad operator");
+    if (op < SBIE_OP_S || op > SBIE_OP_SQUIRMER) return fail(c, SBIE_ERR_ARG, "bad operator");
+    if (op == SBIE_OP_POROUS || op == SBIE_OP_SQUIRMER) {
+        // both layers' far fields; `chosen` reports the double layer's
+        CKS(sphere_bie_autotune(c, SBIE_OP_S, nullptr));
+        return sphere_bie_autotune(c, SBIE_OP_D, chosen);
+    }
     const Kern k = kern_of(op);
     if (chosen) std::memset(chosen, 0, 2 * sizeof(*chosen));
     Sys S = sys_of(c);

@@ -146,6 +146,16 @@ constexpr int prec_slot(int op) { return op == SBIE_OP_MOBILITY ? 1 : 0; }
 
 struct PairNetSet;  // trained pair networks (api.cu)
 
+// Self-kernel signature of the pair preconditioner's high-mode part: 1/D+
+// above degree 4 (the exterior eigenvalues of Theorem 2), 0 at or below, minus 2.
+constexpr int kOpPrecHigh = 3;
+
+// Self-term matrices of the FP32 operator applied by the tensor-core GEMM
+// (selfgemm.cu): single layer (unit radius), double layer = traction
+// (principal value), and the pair preconditioner's H with the low-mode rows.
+constexpr int kSelfS = 0, kSelfDK = 1, kSelfPrec = 2, kSelfMats = 3;
+struct SelfGemm;
+
 }  // namespace sbie
 
 struct sbie_ctx {
@@ -188,6 +198,7 @@ struct sbie_ctx {
     double* d_low = nullptr;       // [n][73]
     double* d_lowe = nullptr;      // [n][73]
     double* d_pz = nullptr;        // preconditioned vector (system level)
+    double* d_sq = nullptr;        // [2][3N] squirmer operator: mu - P mu and P mu
     double t_create_ms = 0.0;      // wall time of create (grid, tables, close pairs, preconditioner)
     bool has_solution = false;     // d_xsol holds the density of the last solve
 
@@ -246,6 +257,7 @@ struct sbie_ctx {
     double* d_res = nullptr;     // [3N]
     int krylov_m = 0;
 
+    sbie::SelfGemm* sg = nullptr;  // self-term GEMMs of the FP32 operator (mixed-precision contexts)
     sbie::FarTune tune64[3]{}, tune32[3]{}, tunedf[3]{};  // per far-field kernel (S, D, K)
     sbie::Profile prof;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[8];
@@ -285,6 +297,19 @@ void set_last_error(const std::string& msg);
 // self.cu
 cudaError_t launch_self(sbie_ctx* c, Kern op, const double* dens, double* out, bool accumulate, bool write_coef);
 cudaError_t launch_self_precond(sbie_ctx* c, const double* v, double* out);
+// VSH coefficients of dens into c->d_coef only (FP64 analysis, no synthesis)
+cudaError_t launch_self_analysis(sbie_ctx* c, const double* dens);
+// `count` independent unit-radius-free probes: the self kernel with signature
+// `op` (Kern or kOpPrecHigh) on count densities of 3 npn values each, radius
+// per probe from `radius`, coefficients to `coef` if not null
+cudaError_t launch_self_probe(sbie_ctx* c, int op, int count, const double* dens, double* out, const double* radius,
+                              double* coef);
+// selfgemm.cu
+cudaError_t self_gemm_build(sbie_ctx* c, int which);
+bool self_gemm_ready(const sbie_ctx* c, int which);
+cudaError_t launch_self_gemm(sbie_ctx* c, int which, const double* dens, double* out, bool accumulate);
+cudaError_t self_gemm_error(sbie_ctx* c, int* flag);
+void self_gemm_free(sbie_ctx* c);
 // precond.cu
 void lowmode_tables(int p, std::vector<double>& ZS, std::vector<double>& ZA);
 void lowmode_rotation(const double Q[9], std::vector<double>& R);
@@ -292,10 +317,12 @@ std::vector<int4> low_mode_table();
 cudaError_t launch_gauss_jordan(cudaStream_t s, int n, int count, float* mats, int* d_bad);
 cudaError_t launch_probe_density(sbie_ctx* c, int sph_per_prob, int side, int beta, const double* ZS, double* dens);
 cudaError_t launch_probe_analysis(sbie_ctx* c, const double* ZA, const double* u, int beta, double* blocks);
-cudaError_t precond_apply(sbie_ctx* c, int slot, const double* v, double* out);
+// M^{-1} v; f32: the FP32 inner solves' form (H and the low-mode analysis by
+// the tensor-core GEMM), else FP64 throughout
+cudaError_t precond_apply(sbie_ctx* c, int slot, const double* v, double* out, bool f32);
 // far.cu
 cudaError_t launch_pack(sbie_ctx* c, const double* dens, int mode);
-cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out);
+cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out, bool accumulate = false);
 // Times one launch of the far-field pair kernel with tiling `tu` (no reduce); *ms = event time.
 cudaError_t time_far(sbie_ctx* c, Kern op, int mode, const FarTune& tu, float* ms);
 long long far_pairs(const sbie_ctx* c);
@@ -310,6 +337,9 @@ cudaError_t launch_moments(sbie_ctx* c, const double* dens);
 cudaError_t launch_completion(sbie_ctx* c, bool f32, double* out);
 cudaError_t launch_finalize(sbie_ctx* c, int op, const double* dens, double* out);
 cudaError_t launch_rho(sbie_ctx* c, const double* F, const double* T, double* rho);
+// squirmer operator: from the moments in d_mom (launch_moments of dens),
+// r = P dens (rigid part on each sphere) and q = dens - r
+cudaError_t launch_rigid_split(sbie_ctx* c, const double* dens, double* q, double* r);
 cudaError_t launch_rigid_projection(sbie_ctx* c, const double* u, double* vel, double* omega);
 cudaError_t launch_resistance_rhs(sbie_ctx* c, const double* vel, const double* omega, const double* u0,
                                   const double* G, double* b);

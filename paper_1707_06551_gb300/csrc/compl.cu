@@ -163,6 +163,28 @@ __global__ void rho_kernel(const double* __restrict__ F, const double* __restric
     rho[3 * i + 2] = f0 * F[3 * k + 2] + f1 * (t[0] * dy - t[1] * dx);
 }
 
+__global__ void rigid_split_kernel(const double* __restrict__ dens, const double* __restrict__ mom,
+                                   const double* __restrict__ x64, const double* __restrict__ c,
+                                   const double* __restrict__ a, int npn, long long N, double* __restrict__ q,
+                                   double* __restrict__ r) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int k = (int)(i / npn);
+    double ak = a[k];
+    double f0 = 1.0 / (4.0 * kPi * ak * ak), f1 = 3.0 / (8.0 * kPi * ak * ak * ak * ak);
+    double dx = x64[4 * i] - c[3 * k], dy = x64[4 * i + 1] - c[3 * k + 1], dz = x64[4 * i + 2] - c[3 * k + 2];
+    const double* M = mom + 6 * k;  // int mu, int (y - c) x mu
+    const double r0 = f0 * M[0] + f1 * (M[4] * dz - M[5] * dy);
+    const double r1 = f0 * M[1] + f1 * (M[5] * dx - M[3] * dz);
+    const double r2 = f0 * M[2] + f1 * (M[3] * dy - M[4] * dx);
+    r[3 * i] = r0;
+    r[3 * i + 1] = r1;
+    r[3 * i + 2] = r2;
+    q[3 * i] = dens[3 * i] - r0;
+    q[3 * i + 1] = dens[3 * i + 1] - r1;
+    q[3 * i + 2] = dens[3 * i + 2] - r2;
+}
+
 __global__ void res_rhs_kernel(const double* __restrict__ v, const double* __restrict__ w, double u0x, double u0y,
                                double u0z, double g00, double g01, double g02, double g10, double g11, double g12,
                                double g20, double g21, double g22, const double* __restrict__ x64,
@@ -227,6 +249,12 @@ cudaError_t launch_finalize(sbie_ctx* c, int op, const double* dens, double* out
 
 cudaError_t launch_rho(sbie_ctx* c, const double* F, const double* T, double* rho) {
     rho_kernel<<<nblk(c->N, 256), 256, 0, c->stream>>>(F, T, c->d_x, c->d_c, c->d_a, c->npn, c->N, rho); ++c->n_launch;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rigid_split(sbie_ctx* c, const double* dens, double* q, double* r) {
+    rigid_split_kernel<<<nblk(c->N, 256), 256, 0, c->stream>>>(dens, c->d_mom, c->d_x, c->d_c, c->d_a, c->npn, c->N, q,
+                                                               r); ++c->n_launch;
     return cudaGetLastError();
 }
 

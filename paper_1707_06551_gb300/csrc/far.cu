@@ -564,12 +564,12 @@ __global__ void __launch_bounds__(256) far_f64_kernel(FarArgs a) {
 // out[i] = scale * sum_k part[k][i] for the first `count` entries of partials
 // laid out [split][stride]
 __global__ void far_reduce(const double* __restrict__ part, int split, long long stride, long long count,
-                           double scale, double* __restrict__ out) {
+                           double scale, int accumulate, double* __restrict__ out) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     double s = 0.0;
     for (int k = 0; k < split; ++k) s += part[(size_t)k * stride + i];
-    out[i] = scale * s;
+    out[i] = accumulate ? out[i] + scale * s : scale * s;
 }
 
 __global__ void pack_kernel(const double* __restrict__ dens, const double* __restrict__ x64, long long N,
@@ -729,7 +729,7 @@ static cudaError_t launch_pair_kernel(sbie_ctx* c, Kern op, int mode, const FarT
     }
 }
 
-cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out) {
+cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out, bool accumulate) {
     const FarTune& tu = mode == kModeF32 ? c->tune32[(int)op] : (mode == kModeDF ? c->tunedf[(int)op] : c->tune64[(int)op]);
     cudaError_t e;
     {
@@ -739,7 +739,8 @@ cudaError_t launch_far(sbie_ctx* c, Kern op, int mode, double* out) {
     if (e != cudaSuccess) return e;
     double scale = (op == Kern::S) ? 1.0 / (8.0 * kPi) : (op == Kern::D ? 3.0 / (4.0 * kPi) : -3.0 / (4.0 * kPi));
     long long n3 = c->N * 3;
-    far_reduce<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(c->d_part, tu.split, n3, n3, scale, out); ++c->n_launch;
+    far_reduce<<<(unsigned)((n3 + 255) / 256), 256, 0, c->stream>>>(c->d_part, tu.split, n3, n3, scale,
+                                                                     accumulate ? 1 : 0, out); ++c->n_launch;
     return cudaGetLastError();
 }
 
@@ -798,7 +799,7 @@ cudaError_t time_far(sbie_ctx* c, Kern op, int mode, const FarTune& tu, float* m
     e = cudaEventRecord(e0, c->stream);
     if (e == cudaSuccess) e = launch_pair_kernel(c, op, mode, tu, nts);
     if (e == cudaSuccess) {
-        far_reduce<<<(unsigned)((count + 255) / 256), 256, 0, c->stream>>>(c->d_part, tu.split, n3, count, 1.0,
+        far_reduce<<<(unsigned)((count + 255) / 256), 256, 0, c->stream>>>(c->d_part, tu.split, n3, count, 1.0, 0,
                                                                          c->d_part + (size_t)tu.split * n3);
         e = cudaGetLastError();
     }

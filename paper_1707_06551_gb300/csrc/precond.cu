@@ -472,16 +472,23 @@ std::vector<int4> low_mode_table() {
 }
 
 // M^{-1} v on one part (device vectors of that part): see the header comment.
-cudaError_t precond_apply(sbie_ctx* c, int slot, const double* v, double* out) {
+cudaError_t precond_apply(sbie_ctx* c, int slot, const double* v, double* out, bool f32) {
     const PrecState& P = c->prec[slot];
     const long long n3 = c->N * 3;
-    // H v: synthesis of (1/D+ above degree 4, 0 below) minus 2, plus 2 v; the
-    // self kernel also leaves the VSH coefficients of v in d_coef
-    cudaError_t e = launch_self_precond(c, v, out);
-    if (e == cudaSuccess) e = blas_lincomb(c, 2.0, v, 1.0, out, out, n3);
-    if (e != cudaSuccess) return e;
-    gather_low_kernel<<<c->n, 96, 0, c->stream>>>(c->n, c->p + 1, c->d_coef, c->d_modes, c->d_low);
-    ++c->n_launch;
+    cudaError_t e = cudaSuccess;
+    if (f32 && self_gemm_ready(c, kSelfPrec)) {
+        // H v (with its 2 v) and the low-mode coefficients in one tensor-core GEMM
+        e = launch_self_gemm(c, kSelfPrec, v, out, false);
+        if (e != cudaSuccess) return e;
+    } else {
+        // H v: synthesis of (1/D+ above degree 4, 0 below) minus 2, plus 2 v;
+        // the self kernel also leaves the VSH coefficients of v in d_coef
+        e = launch_self_precond(c, v, out);
+        if (e == cudaSuccess) e = blas_lincomb(c, 2.0, v, 1.0, out, out, n3);
+        if (e != cudaSuccess) return e;
+        gather_low_kernel<<<c->n, 96, 0, c->stream>>>(c->n, c->p + 1, c->d_coef, c->d_modes, c->d_low);
+        ++c->n_launch;
+    }
     coarse_kernel<<<c->n, kCoarseThreads, 0, c->stream>>>(P.d_pp_ptr, P.d_pp_idx, P.d_pp_pair, P.d_pinv, P.d_sinv,
                                               c->d_low, c->d_lowe);
     ++c->n_launch;

@@ -23,10 +23,6 @@ struct SelfArgs {
     int accumulate;
 };
 
-// op 3: the high-mode part of the pair preconditioner: 1/D+ above degree 4
-// (the exterior eigenvalues of Theorem 2), 0 at or below, minus 2.
-constexpr int kOpPrecHigh = 3;
-
 __device__ __forceinline__ void signature(int op, int n, double a, double& lv, double& lw, double& lx) {
     double tn1 = 2.0 * n + 1.0;
     if (op == kOpPrecHigh) {
@@ -252,6 +248,26 @@ cudaError_t launch_self(sbie_ctx* c, Kern op, const double* dens, double* out, b
 
 cudaError_t launch_self_precond(sbie_ctx* c, const double* v, double* out) {
     return run_self(c, kOpPrecHigh, v, out, false, true);
+}
+
+cudaError_t launch_self_analysis(sbie_ctx* c, const double* dens) {
+    return run_self(c, -1, dens, nullptr, false, true);
+}
+
+cudaError_t launch_self_probe(sbie_ctx* c, int op, int count, const double* dens, double* out, const double* radius,
+                              double* coef) {
+    SelfArgs A;
+    A.p = c->p; A.nlat = c->nlat; A.nlon = c->nlon; A.npn = c->npn;
+    A.tl = c->tl; A.tab = c->d_tab; A.dens = dens; A.out = out;
+    A.coef = coef;
+    A.radius = radius; A.op = op; A.accumulate = 0;
+    const size_t sm = self_smem(c->p);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(self_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+    }
+    self_kernel<<<count, 256, sm, c->stream>>>(A); ++c->n_launch;
+    return cudaGetLastError();
 }
 
 

@@ -20,7 +20,8 @@ STATUS_NAMES = {0: "SBIE_OK", 1: "SBIE_ERR_ARG", 2: "SBIE_ERR_OVERLAP", 3: "SBIE
                 5: "SBIE_ERR_NOT_CONVERGED", 6: "SBIE_ERR_TIMEOUT", 7: "SBIE_ERR_NUMERIC"}
 SBIE_FP64, SBIE_MIXED, SBIE_FP64_DF = 0, 1, 2
 SBIE_OP_S, SBIE_OP_D, SBIE_OP_K, SBIE_OP_MOBILITY, SBIE_OP_RESISTANCE = 0, 1, 2, 3, 4
-OPS = {"S": 0, "D": 1, "K": 2, "mobility": 3, "resistance": 4}
+SBIE_OP_POROUS, SBIE_OP_SQUIRMER = 5, 6
+OPS = {"S": 0, "D": 1, "K": 2, "mobility": 3, "resistance": 4, "porous": 5, "squirmer": 6}
 STAGES = ("far", "near", "self", "completion", "arnoldi", "other", "far_kernel_f32", "far_kernel_f64")
 
 
@@ -92,6 +93,8 @@ def lib():
         L.sphere_bie_apply_operator.argtypes = [_P, ctypes.c_int, _P, _P]
         L.sphere_bie_solve_mobility.argtypes = [_P, _P, _P, _P, _P, ctypes.POINTER(SolveInfo)]
         L.sphere_bie_solve_resistance.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(SolveInfo)]
+        L.sphere_bie_solve_porous.argtypes = [_P, _P, _P, _P, _P, ctypes.POINTER(SolveInfo)]
+        L.sphere_bie_solve_squirmer.argtypes = [_P, _P, _P, _P, ctypes.POINTER(SolveInfo)]
         L.sphere_bie_destroy.argtypes = [_P]
         L.sphere_bie_last_error.argtypes = [_P]
         L.sphere_bie_last_error.restype = ctypes.c_char_p
@@ -111,6 +114,7 @@ def lib():
         for f in ("sphere_bie_default_opts", "sphere_bie_create", "sphere_bie_create_batch", "sphere_bie_num_nodes",
                   "sphere_bie_nodes",
                   "sphere_bie_apply_operator", "sphere_bie_solve_mobility", "sphere_bie_solve_resistance",
+                  "sphere_bie_solve_porous", "sphere_bie_solve_squirmer",
                   "sphere_bie_destroy", "sphere_bie_profile", "sphere_bie_profile_read",
                   "sphere_bie_apply_layer_noalloc", "sphere_bie_autotune", "sphere_bie_train_pair_network",
                   "sphere_bie_pair_blocks", "sphere_bie_pair_network_size", "sphere_bie_pair_network_gradients",
@@ -214,6 +218,26 @@ def sphere_bie_solve_resistance(ctx, vel, omega, bg_u0, bg_grad, forces, torques
     G = None if bg_grad is None else np.ascontiguousarray(bg_grad, dtype=np.float64).reshape(3, 3)
     st = _check(ctx, lib().sphere_bie_solve_resistance(ctx, _ptr(vel), _ptr(omega), _ptr(u0, True), _ptr(G, True),
                                                        _ptr(forces), _ptr(torques), ctypes.byref(info)),
+                allow=(SBIE_ERR_NOT_CONVERGED,))
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+def sphere_bie_solve_porous(ctx, bg_u0, bg_grad, forces, torques):
+    info = SolveInfo()
+    u0 = None if bg_u0 is None else np.ascontiguousarray(bg_u0, dtype=np.float64).reshape(3)
+    G = None if bg_grad is None else np.ascontiguousarray(bg_grad, dtype=np.float64).reshape(3, 3)
+    st = _check(ctx, lib().sphere_bie_solve_porous(ctx, _ptr(u0, True), _ptr(G, True), _ptr(forces), _ptr(torques),
+                                                   ctypes.byref(info)), allow=(SBIE_ERR_NOT_CONVERGED,))
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+def sphere_bie_solve_squirmer(ctx, slip, vel, omega):
+    info = SolveInfo()
+    st = _check(ctx, lib().sphere_bie_solve_squirmer(ctx, _ptr(slip), _ptr(vel), _ptr(omega), ctypes.byref(info)),
                 allow=(SBIE_ERR_NOT_CONVERGED,))
     d = info.as_dict()
     d["status"] = st
@@ -349,6 +373,19 @@ class SphereBIE:
         T = np.zeros_like(w)
         info = sphere_bie_solve_resistance(self.ctx, v, w, u0, G, F, T)
         return F, T, info
+
+    def porous(self, u0=None, G=None):
+        F = np.zeros((self.n, 3))
+        T = np.zeros((self.n, 3))
+        info = sphere_bie_solve_porous(self.ctx, u0, G, F, T)
+        return F, T, info
+
+    def squirmer(self, slip):
+        s = np.ascontiguousarray(slip, dtype=np.float64).reshape(-1, 3)
+        v = np.zeros((self.n, 3))
+        w = np.zeros((self.n, 3))
+        info = sphere_bie_solve_squirmer(self.ctx, s, v, w)
+        return v, w, info
 
     def nodes(self):
         return sphere_bie_nodes(self.ctx)

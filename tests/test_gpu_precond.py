@@ -148,8 +148,8 @@ def test_learned_mobility_network_and_fallback(sb, tmp_path):
 def test_resistance_256_headline_configuration(sb, tmp_path):
     """The timed configuration at full size: 256 spheres, p = 10, mixed
     precision, learned pair preconditioner, graph-launched cycles.  Forces and
-    torques agree with the FP64-accurate (double-float) solve, and the reported
-    residual is the FP64 residual of the returned density."""
+    torques agree with the FP64-accurate (double-float) solve to 1e-6, and the
+    reported residual is the FP64 residual of the returned density."""
     w = wl.resistance_256()
     path = tmp_path / "pairnet.bin"
     sb.sphere_bie_train_pair_network(path, n_samples=1024, p=w["p"], gap_min=0.01, gap_max=2.0, epochs=100, seed=3)
@@ -168,7 +168,12 @@ def test_resistance_256_headline_configuration(sb, tmp_path):
         b = -(w["u0"][None, :] + x @ w["G"].T)
         r = b - s.apply("resistance", psi)
     assert i64["status"] == 0 and info["iters"] < i64["iters"]
-    assert np.max(np.abs(F - F64)) < 1e-6 * np.max(np.abs(F64))
-    assert np.max(np.abs(T - T64)) < 1e-6 * np.max(np.abs(T64))
+    # per-result bound: the mixed solve at 1e-8 against the FP64-accurate solve
+    # to 1e-11 (two solves at 1e-8 differ by both of their errors)
+    with sb.SphereBIE(w["centres"], w["radii"], w["p"], prec=sb.SBIE_FP64_DF, tol=1e-11) as s:
+        Fr, Tr, ir = s.resistance(w["vel"], w["omega"], w["u0"], w["G"])
+    assert ir["status"] == 0
+    assert np.max(np.abs(F - Fr)) < 1e-6 * np.max(np.abs(Fr))
+    assert np.max(np.abs(T - Tr)) < 1e-6 * np.max(np.abs(Tr))
     rel = np.linalg.norm(r) / np.linalg.norm(b)
     assert rel <= w["tol"] and abs(rel - info["rel_residual_true"]) <= 0.1 * w["tol"]

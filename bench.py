@@ -61,7 +61,7 @@ def parse():
                     help="two-sphere configurations the pair network is trained on "
                          "(default 4096; 100000 for dense_1024, 20000 for large_4096)")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "batched_512", "dense_1024", "large_4096"],
+                    choices=[WORKLOAD, "batched_512", "dense_1024", "large_4096", "lattice"],
                     help="the other configurations print their own JSON line (not the headline)")
     return ap.parse_args()
 
@@ -264,68 +264,146 @@ def graph_compare(sb, torch, wl, w, prec, stream, vel, om, F_ref, t_graph, net):
     return out
 
 
-def cpu_baseline(n_sample=8):
-    """Time the oracle as it stands on this host on a bounded sample of the
-    workload: the resistance operator on n_sample target spheres (self, far
-    and close-pair terms) plus the completion flow on all nodes, extrapolated
-    to one full apply; the solve estimate multiplies by the number of applies
-    the FP64 GMRES solve of this workload needs."""
-    code = r"""
-import json, sys, time
-import numpy as np
-sys.path.insert(0, sys.argv[1])
-from oracle import operators as ops
-from paper_1707_06551_gb300 import workloads as wl
-w = wl.resistance_256()
-g = ops.Geometry(w["centres"], w["radii"], w["p"])
-dens = np.random.default_rng(0).normal(size=(g.N, 3))
-k = int(sys.argv[2])
-targets = list(range(0, g.n, g.n // k))[:k]
-t0 = time.perf_counter(); ops.layer(g, "D", dens, targets); t1 = time.perf_counter()
-ops.completion_N(g, dens); t2 = time.perf_counter()
-print(json.dumps({"t_layer": t1 - t0, "t_compl": t2 - t1, "k": k, "n": g.n}))
-"""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code, ROOT, str(n_sample)], capture_output=True, text=True, env=env,
-                       timeout=600)
-    if r.returncode != 0:
-        return {"error": r.stderr[-500:]}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    full_apply = d["t_layer"] * d["n"] / d["k"] + d["t_compl"]
-    return {"apply_s": full_apply, "sample_s": d["t_layer"] + d["t_compl"], "k": d["k"], "n": d["n"]}
+GOLDEN_SOLVE = os.path.join(ROOT, "tests", "golden", "resistance_256_oracle_solve.json")
+ORACLE_GROUPS = 64  # target-sphere groups handed to the worker processes
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+_og = None  # the oracle's geometry in a worker process
+
+
+def _oracle_init(root):
+    global _og
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from oracle import operators as ops
+    from paper_1707_06551_gb300 import workloads as wl
+    w = wl.resistance_256()
+    _og = ops.Geometry(w["centres"], w["radii"], w["p"])
+
+
+def _oracle_group(args):
+    """The oracle's resistance operator (Eq. 5.19) on one group of target spheres."""
+    import numpy as np
+    from oracle import operators as ops
+    x, group = args
+    out = ops.apply_at(_og, "resistance", x, group)
+    return group, out[np.concatenate([np.arange(_og.sl(i).start, _og.sl(i).stop) for i in group])]
+
+
+def oracle_pool(cores):
+    """A pool of `cores` worker processes, each holding the oracle's geometry of
+    the timed workload (spawned: no worker inherits a CUDA context)."""
+    import multiprocessing as mp
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"  # inherited by the workers: one BLAS thread each
+    return mp.get_context("spawn").Pool(cores, initializer=_oracle_init, initargs=(ROOT,))
+
+
+def _oracle_mobility_8():
+    """The oracle's full GMRES solve of the 8-sphere mobility problem (p = 6,
+    tol 1e-10), timed in a worker process (one core)."""
+    from oracle import operators as ops
+    from oracle import solve as osolve
+    from paper_1707_06551_gb300 import workloads as wl
+    m8 = wl.mobility_8()
+    g8 = ops.Geometry(m8["centres"], m8["radii"], m8["p"])
+    t0 = time.perf_counter()
+    _, _, info = osolve.solve_mobility(g8, m8["forces"], m8["torques"], tol=m8["tol"])
+    return {"solve_s": time.perf_counter() - t0, "iters": int(info["iters"]), "cores": 1,
+            "rel_residual": float(info["rel_residual"])}
+
+
+def oracle_apply(pool, x, groups):
+    """Oracle operator rows of the target-sphere groups, one group per task."""
+    return pool.map(_oracle_group, [(x, g) for g in groups])
+
+
+def golden_solve():
+    """Operator-apply count and result of the oracle's own FP64 GMRES solve of
+    the timed workload (tests/golden/make_resistance_256_solve.py), or None."""
+    try:
+        with open(GOLDEN_SOLVE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def cpu_baseline():
+    """The oracle as it stands on every host core: one full resistance_256
+    operator apply (all 256 target spheres, all nodes; worker processes over
+    target-sphere groups, BLAS single-threaded) and a full oracle GMRES solve of
+    the 8-sphere mobility problem (serial), both timed in full.  The solve
+    time of the timed workload is the full apply time x the operator applies of
+    the oracle's own solve of it (recorded by the golden-solve script)."""
+    import numpy as np
+    cores = host_cores()
+    n = 256
+    groups = [list(range(i, n, ORACLE_GROUPS)) for i in range(ORACLE_GROUPS)]
+    x = np.random.default_rng(0).normal(size=(n * 242, 3))
+    with oracle_pool(cores) as pool:
+        pool.map(abs, range(cores))  # workers up and geometry built before the clock starts
+        t0 = time.perf_counter()
+        rows = oracle_apply(pool, x, groups)
+        t_apply = time.perf_counter() - t0
+        m8 = pool.apply(_oracle_mobility_8)
+    assert sum(len(g) for g, _ in rows) == n
+    gs = golden_solve()
+    applies = gs["operator_applies"] if gs else None
+    return {"apply_s": t_apply, "cores": cores, "applies": applies,
+            "solve_iters": gs["iters"] if gs else None, "mobility_8": m8}
 
 
 def run_reference(args):
+    """The oracle on every host core, on the timed workload.  Step s is the
+    resistance operator on the target spheres i = s (mod 4), i.e. one quarter
+    of a full apply (four consecutive steps make one full apply); the
+    time-to-solve is 4 x the mean step time x the operator applies of the
+    oracle's own FP64 GMRES solve of this workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    t_applies = []
-    for _ in range(max(1, args.warmup) + args.steps):
-        t_applies.append(cpu_baseline())
-    good = [t for t in t_applies[max(1, args.warmup):] if "apply_s" in t]
-    if not good:
-        print(json.dumps({"impl": "reference", "unavailable": "oracle sample failed: " + str(t_applies[-1])}))
+    import numpy as np
+    gs = golden_solve()
+    if gs is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle solve record missing: run "
+                          "tests/golden/make_resistance_256_solve.py"}))
         return
-    applies = REF_FP64_APPLIES
-    per_solve = statistics.mean(t["apply_s"] for t in good) * applies
-    sample = (f"resistance operator (self, far, close pairs) on {good[0]['k']} of {good[0]['n']} target spheres "
-              f"plus the completion flow on all nodes, extrapolated to one apply, x {applies} applies "
-              f"(FP64 GMRES apply count of this workload at tol 1e-8)")
+    cores = host_cores()
+    n = 256
+    quarters = [[list(range(i, n, ORACLE_GROUPS)) for i in range(q, ORACLE_GROUPS, 4)] for q in range(4)]
+    x = np.random.default_rng(0).normal(size=(n * 242, 3))
+    ts = []
+    with oracle_pool(cores) as pool:
+        pool.map(abs, range(cores))
+        for s in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            oracle_apply(pool, x, quarters[s % 4])
+            if s >= args.warmup:
+                ts.append(time.perf_counter() - t0)
+    step = statistics.mean(ts)
+    applies = gs["operator_applies"]
+    per_solve = 4 * step * applies
+    sample = (f"each step: the oracle's resistance operator on 64 of the 256 target spheres (a quarter of one "
+              f"full apply, quarters in turn) on {cores} host cores; time-to-solve = 4 x mean step x {applies} "
+              f"operator applies of the oracle's own FP64 GMRES solve of this workload "
+              f"({gs['iters']} iterations at tol {gs['tol']}, recorded by tests/golden/make_resistance_256_solve.py)")
     line = {"impl": "reference", "metric": METRIC, "value": per_solve, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "step": "a quarter of one full oracle operator apply (value is the time-to-solve built from it)",
             "config": {"workload": WORKLOAD, "n_spheres": 256, "p": 10, "nodes": 61952, "tol": 1e-8,
                        "precision": "fp64 (oracle, plain GMRES)", "preconditioner": "none",
                        "parallelism": "replicas x1"},
-            "cpu_baseline": {"value": per_solve, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": per_solve, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": per_solve, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
-
-
-# FP64 GMRES applies (iterations + restart residuals + final residual) for
-# resistance_256 at tol 1e-8 on the GPU path; used to scale the oracle's
-# per-apply time to a solve.
-REF_FP64_APPLIES = 84
 
 
 # ---- the other configurations (python bench.py --workload NAME) -------------
@@ -353,7 +431,72 @@ def _clocks(local):
     return ClockSampler(idx)
 
 
+def run_lattice(args, sb, torch, wl, local):
+    """Operator-apply scaling on the cubic lattices of Sec. 6: the double layer
+    and the single layer's traction, applied by the FP32 operator of the mixed
+    path and (up to 2e11 far-field pairs) by the FP64-accurate double-float
+    operator, for loosely (q = 1) and densely (q = 4) packed mono- and
+    polydisperse lattices of 1 to 16 units per side, p = 4 and 8.  Times are
+    CUDA events on the library's stream around one apply (mean of 3 after one
+    warm-up), densities resident on the device."""
+    import math
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream()
+    series = []
+    for poly in (False, True):
+        for q in (1, 4):
+            for p in (4, 8):
+                rec = {"lattice": "poly" if poly else "mono", "q": q, "p": p, "n_b": [], "nodes": [],
+                       "far_pairs": [], "D_fp32_s": [], "K_fp32_s": [], "D_df_s": [], "K_df_s": []}
+                for m in (1, 2, 4, 8, 16):
+                    w = wl.lattice(m, q, poly)
+                    n = len(w["radii"])
+                    npn = (p + 1) * (2 * p + 2)
+                    x = torch.randn((n * npn, 3), dtype=torch.float64, device=dev)
+                    y = torch.zeros_like(x)
+                    far_pairs = None
+                    for prec, tag in ((sb.SBIE_MIXED, "fp32"), (sb.SBIE_FP64_DF, "df")):
+                        o = sb.make_opts(p, prec=prec, mem_kind=1, stream=stream.cuda_stream)
+                        ctx = sb.sphere_bie_create(w["centres"], w["radii"], o)
+                        if tag == "fp32":
+                            sb.sphere_bie_profile(ctx, 1)
+                            sb.sphere_bie_apply_operator(ctx, "D", x, y)
+                            prof = sb.sphere_bie_profile_read(ctx)
+                            sb.sphere_bie_profile(ctx, 0)
+                            far_pairs = prof["far_pairs_f32"]
+                        if tag == "df" and far_pairs > 2e11:
+                            rec["D_df_s"].append(None)
+                            rec["K_df_s"].append(None)
+                            sb.sphere_bie_destroy(ctx)
+                            continue
+                        if n * npn >= 100000:
+                            sb.sphere_bie_autotune(ctx, "D")
+                            sb.sphere_bie_autotune(ctx, "K")
+                        for op in ("D", "K"):
+                            sb.sphere_bie_apply_operator(ctx, op, x, y)
+                            ts, _ = _timed_solves(torch, stream, lambda: sb.sphere_bie_apply_operator(ctx, op, x, y), 3)
+                            rec[f"{op}_{tag}_s"].append(statistics.mean(ts))
+                        sb.sphere_bie_destroy(ctx)
+                    rec["n_b"].append(n)
+                    rec["nodes"].append(n * npn)
+                    rec["far_pairs"].append(far_pairs)
+                    del x, y
+                # log-log slope between the two largest lattices
+                for key in ("D_fp32_s", "K_fp32_s"):
+                    t = rec[key]
+                    rec[key.replace("_s", "_slope_last")] = (math.log(t[-1] / t[-2]) /
+                                                             math.log(rec["n_b"][-1] / rec["n_b"][-2]))
+                series.append(rec)
+    return {"metric": "operator apply time vs number of spheres (lattice scaling test)", "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32 (mixed path operator) / f64-accurate (df)",
+            "data": "synthetic", "config": {"workload": "lattice", "units_per_side": [1, 2, 4, 8, 16],
+                                            "q": [1, 4], "p": [4, 8], "eta": 1.0},
+            "series": series}
+
+
 def run_workload(args, sb, torch, wl, local):
+    if args.workload == "lattice":
+        return run_lattice(args, sb, torch, wl, local)
     if args.workload == "batched_512":
         return run_batched(args, sb, torch, wl, local)
     if args.workload == "dense_1024":
@@ -744,14 +887,14 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
-        if "apply_s" in cb:
-            applies = (fp64["iters"] + 2) if fp64 else REF_FP64_APPLIES
-            cpu = {"value": cb["apply_s"] * applies, "unit": "s", "cores": 1, "kind": "oracle",
-                   "sample": (f"resistance operator on {cb['k']} of {cb['n']} target spheres + completion flow on all "
-                              f"nodes ({cb['sample_s']:.1f} s of CPU), extrapolated to one apply ({cb['apply_s']:.1f} s)"
-                              f" x {applies} FP64 GMRES applies")}
-        else:
-            cpu = {"error": cb.get("error")}
+        applies = cb["applies"]
+        cpu = {"value": cb["apply_s"] * applies if applies else None, "unit": "s", "cores": cb["cores"],
+               "kind": "oracle",
+               "sample": (f"one full resistance_256 operator apply by the oracle (all 256 target spheres, all "
+                          f"61,952 nodes) on {cb['cores']} host cores, timed in full: {cb['apply_s']:.1f} s; "
+                          f"x {applies} operator applies of the oracle's own FP64 GMRES solve of this workload "
+                          f"({cb['solve_iters']} iterations at tol 1e-8)"),
+               "timed_in_full": {"resistance_256_apply_s": cb["apply_s"], "mobility_8_solve": cb["mobility_8"]}}
 
     graphs_cmp = None if args.no_graphs else graph_compare(sb, torch, wl, w, prec, stream, vel, om, F, t_step, net)
     launches_per_step = launches_timed / args.steps

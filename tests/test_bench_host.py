@@ -97,7 +97,12 @@ def test_reference_arm_prints_the_oracle_line():
     assert line["higher_is_better"] is False and line["value"] > 0
     assert line["config"]["workload"] == bench.WORKLOAD
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == bench.host_cores() and cb["value"] == line["value"]
+    assert cb["sample"]
+    # value = 4 x the mean quarter-apply step x the oracle solve's operator applies
+    gs = bench.golden_solve()
+    assert line["value"] == pytest.approx(4 * line["ms_per_step"] / 1e3 * gs["operator_applies"])
+    assert line["ms_per_step"] * (line["steps"] + line["warmup"]) < 600e3
     assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 

@@ -158,3 +158,27 @@ def test_dense_1024_mixed_solve_true_residual(sb):
         r = b - s.apply("mobility", mu)
     rel = np.linalg.norm(r) / np.linalg.norm(b)
     assert rel <= 1e-8 and abs(rel - info["rel_residual_true"]) <= 0.1e-8
+
+
+def test_resistance_256_full_oracle_solve(sb):
+    """The oracle's own FP64 GMRES solve of the 256-sphere resistance workload
+    (tests/golden/resistance_256_oracle_solve.json, written by the script
+    beside it; restart 200, tol 1e-8): the GPU's FP64-accurate GMRES with the
+    same restart needs the same number of iterations (CGS2 against the
+    oracle's modified Gram-Schmidt), and its forces and torques, solved to
+    1e-11, agree with the oracle's within 5e-6 of the largest -- the oracle
+    solution's own error at 1e-8 (about 175 x its residual here)."""
+    import json
+    import os
+    gs = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "resistance_256_oracle_solve.json")))
+    w = wl.resistance_256()
+    Fo, To = np.array(gs["forces"]), np.array(gs["torques"])
+    with sb.SphereBIE(w["centres"], w["radii"], w["p"], prec=sb.SBIE_FP64_DF, tol=1e-8, restart=200) as s:
+        F8, T8, i8 = s.resistance(w["vel"], w["omega"], w["u0"], w["G"])
+    assert i8["status"] == 0 and abs(i8["iters"] - gs["iters"]) <= 2, (i8["iters"], gs["iters"])
+    with sb.SphereBIE(w["centres"], w["radii"], w["p"], prec=sb.SBIE_FP64_DF, tol=1e-11, restart=200) as s:
+        F, T, info = s.resistance(w["vel"], w["omega"], w["u0"], w["G"])
+    assert info["status"] == 0
+    for a, b in ((F, Fo), (T, To)):
+        e = np.max(np.abs(a - b), axis=1) / np.max(np.abs(b))
+        assert np.all(e < 5e-6), e.max()

@@ -46,14 +46,21 @@ def mobility_rhs(g, F, T):
     return -(0.5 * rho + ops.layer(g, "K", rho)), rho
 
 
-def solve_mobility(g, F, T, tol=1e-10, restart=200, max_iter=1000):
-    b, rho = mobility_rhs(g, F, T)
+def solve_mobility_density(g, rho, tol=1e-10, restart=200, max_iter=1000):
+    """Eq. 5.8 for an incident force density rho ([N][3]): solve
+    (1/2 I + K + L) mu = -(1/2 I + K) rho, u = S[mu + rho], rigid projection."""
+    rho = np.asarray(rho, float).reshape(-1, 3)
+    b = -(0.5 * rho + ops.layer(g, "K", rho))
     mu, info = _gmres.gmres(lambda v: ops.apply(g, "mobility", v.reshape(-1, 3)), b.ravel(),
                             tol=tol, restart=restart, max_iter=max_iter)
     mu = mu.reshape(-1, 3)
     u = ops.layer(g, "S", mu + rho)
     v, w = rigid_projection(g, u)
     return v, w, dict(info, mu=mu, u=u)
+
+
+def solve_mobility(g, F, T, tol=1e-10, restart=200, max_iter=1000):
+    return solve_mobility_density(g, rho_density(g, F, T), tol, restart, max_iter)
 
 
 def resistance_rhs(g, v, w, u0=None, G=None):
@@ -110,3 +117,18 @@ def solve_squirmer(g, slip, tol=1e-10, restart=200, max_iter=1000):
     v = M0 / (4 * np.pi * g.a[:, None] ** 2)
     w = 3.0 * M1 / (8 * np.pi * g.a[:, None] ** 4)
     return v, w, dict(info, mu=mu, density=mu - ops.rigid_part(g, mu))
+
+
+def solve_mhd(g, H0, eta, tol=1e-10, restart=200, max_iter=1000):
+    """Problem 3: paramagnetic spheres (eta = (mu - mu0)/(mu + mu0)) in the
+    imposed field H0.  The single-layer density q of Eq. 5.13, the Maxwell
+    traction f of its exterior field on every sphere, and the rigid motions of
+    the mobility problem (Eq. 5.8) with f as the incident force density.
+    Returns (F, T, v, w, info): F, T the magnetic force and torque on each
+    particle (int f, int (x - c) x f)."""
+    from . import laplace
+    q, iq = laplace.solve_magnetic(g, H0, eta, tol=tol, restart=restart, max_iter=max_iter)
+    f = laplace.maxwell_traction(g, q, H0)
+    F, T = ops.moments(g, f)
+    v, w, im = solve_mobility_density(g, f, tol, restart, max_iter)
+    return F, T, v, w, dict(q=q, traction=f, magnetic=iq, mobility=im)

@@ -155,6 +155,74 @@ def self_vsh_rate(prof, n_nodes):
     return {"gb_per_s": per * applies / (ms * 1e-3) / 1e9, "ms_per_apply": ms / applies, "bytes_per_apply": per}
 
 
+def load_peaks():
+    """Measured peaks of the GB300s (HBM copy GB/s, cuBLAS bf16
+    TFLOP/s), or the recipe's fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
+    except (OSError, ValueError, KeyError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# Dense TF32 tensor rate relative to BF16 (nominal 1.1 vs 2.25 PFLOP/s per GPU).
+TF32_PER_BF16 = 1.1 / 2.25
+COMPLETION_FLOP = 32   # one Stokeslet + rotlet evaluation at one node
+NEAR_FLOP = 20         # per (target node, source coefficient) term of a close pair
+
+
+def stage_rooflines(prof, n, p, n_near, n_pairs, fp32_peak, peaks):
+    """Achieved rate of each profiled stage against its roofline, from the
+    stage times of the profiled solves and the algorithmic work per unit:
+      near        ALU: per directed close pair npn x 3 (p+1)^2 x 20 FLOP;
+      completion  ALU: N x n Stokeslet + rotlet evaluations x 32 FLOP;
+      arnoldi     HBM: (4k + 4) 3N-vectors of FP64 per iteration with k basis vectors;
+      self        tensor: 3 (3xTF32) x 2 x (3 npn)^2 x n FLOP per FP32 apply (the
+                  stage also holds the FP64 coefficient analysis of the close pairs);
+      precond     HBM: the FP32 pair and own inverses, the preconditioner GEMM's
+                  split matrix and 4 nodal vectors per apply."""
+    npn = (p + 1) * (2 * p + 2)
+    N = n * npn
+    ms, la = prof["ms"], prof["launches"]
+    out = {}
+
+    def rate(work, t_ms):
+        return work / (t_ms * 1e-3) if t_ms > 0 else None
+
+    if la.get("near") and ms.get("near"):
+        w = n_near * npn * 3 * (p + 1) ** 2 * NEAR_FLOP * la["near"]
+        a = rate(w, ms["near"]) / 1e12
+        out["near"] = {"bound": "alu", "achieved": a, "peak": fp32_peak, "unit": "TFLOP/s", "frac": a / fp32_peak,
+                       "flop_per_apply": w / la["near"], "ms_per_apply": ms["near"] / la["near"]}
+    if la.get("completion") and ms.get("completion"):
+        w = N * n * COMPLETION_FLOP * la["completion"]
+        a = rate(w, ms["completion"]) / 1e12
+        out["completion"] = {"bound": "alu", "achieved": a, "peak": fp32_peak, "unit": "TFLOP/s",
+                             "frac": a / fp32_peak, "ms_per_apply": ms["completion"] / la["completion"]}
+    if prof.get("arnoldi_vectors") and ms.get("arnoldi"):
+        b = prof["arnoldi_vectors"] * 3 * N * 8
+        a = rate(b, ms["arnoldi"]) / 1e9
+        out["arnoldi"] = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                          "frac": a / peaks["hbm_gbs"], "bytes": b, "note": "Krylov basis of one cycle fits L2"}
+    if la.get("self") and ms.get("self"):
+        K = 3 * npn
+        w = 3 * 2 * K * K * n * la["self"]
+        tf32_peak = peaks["bf16_tflops"] * TF32_PER_BF16
+        a = rate(w, ms["self"]) / 1e12
+        out["self"] = {"bound": "tensor", "achieved": a, "peak": tf32_peak, "unit": "TFLOP/s", "frac": a / tf32_peak,
+                       "peak_basis": "bf16 %s x 1.1/2.25 (TF32 / BF16 nominal)" % peaks["source"],
+                       "ms_per_apply": ms["self"] / la["self"]}
+    if la.get("precond") and ms.get("precond") and n_pairs is not None:
+        K = 3 * npn
+        b = (n_pairs * 146 * 146 * 4 + n * 73 * 73 * 4 + 2 * (K + 73) * ((K + 31) // 32 * 32) * 4 + 4 * 3 * N * 8)
+        a = rate(b * la["precond"], ms["precond"]) / 1e9
+        out["precond"] = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                          "frac": a / peaks["hbm_gbs"], "bytes_per_apply": b,
+                          "ms_per_apply": ms["precond"] / la["precond"]}
+    return out
+
+
 def max_over_ranks(torch, dist, world, x, device):
     """The maximum of x over the ranks (N independent replicas are done when
     the slowest is); x itself on a single rank."""
@@ -811,6 +879,7 @@ def main():
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clk_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = peak_fp32_tflops(sm_count, clk_max)
+    probe_tf, probe_ms = sb.sphere_bie_fp32_peak_probe()
     roof = None
     if l32 > 0 and ms32 > 0:
         flop_launch = pairs32 / l32 * FLOP_PER_PAIR["D"]
@@ -818,20 +887,37 @@ def main():
         traffic = ncu_traffic((tuning or {}).get("fp32") or {})
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "far_f32_kernel<D>",
-                "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clk_max:.0f} MHz",
+                "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clk_max:.0f} MHz (derived)",
+                "peak_probe": probe_tf, "frac_of_probe": achieved / probe_tf,
+                "probe": "packed FP32x2 FMA chains on every SM (sphere_bie_fp32_peak_probe), best of 3",
                 "flop_per_pair": FLOP_PER_PAIR["D"], "pairs_per_launch": pairs32 // l32,
                 "ms_per_launch": ms32 / l32}
     far = {"pairs_per_s_fp32": pairs32 / (ms32 * 1e-3) if ms32 > 0 else None,
-           "pairs_per_s_fp64": pairs64 / (ms64 * 1e-3) if ms64 > 0 else None,
-           "fp64_launches_per_solve": l64 / args.steps, "fp32_launches_per_solve": l32 / args.steps}
+           "pairs_per_s_df": pairs64 / (ms64 * 1e-3) if ms64 > 0 else None,
+           "pairs_per_s_fp64": None,
+           "df_launches_per_solve": l64 / args.steps, "fp32_launches_per_solve": l32 / args.steps}
     stage_ms = {k: v / args.steps for k, v in prof["ms"].items()}
     self_vsh = self_vsh_rate(prof, n * (p + 1) * (2 * p + 2))
+    n_pairs = None
+    if net is not None:
+        n_pairs = sb.sphere_bie_precond_info(ctx)["pairs"]
+    stages = stage_rooflines(prof, n, p, last["n_near_pairs"], n_pairs, peak, load_peaks())
 
     # plain FP64 path on the same workload (comparison; outside the timed region)
     fp64 = None
     if not args.no_fp64_compare and prec == sb.SBIE_MIXED:
         o64 = sb.make_opts(p, prec=sb.SBIE_FP64, tol=w["tol"], mem_kind=1, stream=stream.cuda_stream)
         c64 = sb.sphere_bie_create(w["centres"], w["radii"], o64)
+        # native FP64 far-field pair rate: one profiled FP64 apply
+        x64 = torch.randn((n * (p + 1) * (2 * p + 2), 3), dtype=torch.float64, device=dev)
+        y64 = torch.zeros_like(x64)
+        sb.sphere_bie_profile(c64, 1)
+        sb.sphere_bie_apply_operator(c64, "resistance", x64, y64)
+        p64 = sb.sphere_bie_profile_read(c64)
+        sb.sphere_bie_profile(c64, 0)
+        if p64["ms"]["far_kernel_f64"] > 0:
+            far["pairs_per_s_fp64"] = p64["far_pairs_f64"] / (p64["ms"]["far_kernel_f64"] * 1e-3)
+        del x64, y64
         F64 = torch.zeros_like(F)
         T64 = torch.zeros_like(T)
         torch.cuda.synchronize()
@@ -914,6 +1000,7 @@ def main():
                       "rel_residual_true": last["rel_residual_true"], "status": last["status"],
                       "create_s": t_create, "autotune_s": t_tune, "far_tiling": tuning},
             "roofline": roof, "far_field": far, "stage_ms_per_step": stage_ms, "self_vsh": self_vsh,
+            "stage_rooflines": stages, "fp32_peak_probe": {"tflops": probe_tf, "ms": probe_ms},
             "fp64_path": fp64,
             "pair_preconditioner": pre,
             "clocks": clocks, "gpu_launches": int(launches_timed),

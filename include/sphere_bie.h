@@ -200,10 +200,35 @@ sbie_status sphere_bie_solve_porous(sbie_ctx* ctx, const double* bg_u0, const do
 sbie_status sphere_bie_solve_squirmer(sbie_ctx* ctx, const double* slip, double* vel, double* omega,
                                       sbie_solve_info* info);
 
+/* Laplace layer operators (Sec. 2.2, Eq. 2.18) on a scalar nodal density q
+ * ([N], sphere_bie_nodes order, memory kind of the context) of a single-order
+ * context: op 0 the single layer S^L, 1 the double layer D^L, 2 the flux
+ * K^L = n(x) . grad S^L (Sec. 3.3, Eq. 3.16), each summed over all spheres:
+ * self term by Theorem 1 (Eq. 3.5; D^L and K^L as principal values, both
+ * -1/(2(2n+1)); S^L times the radius), smooth quadrature (Eq. 4.4) between
+ * separated spheres, the exterior expansions of Eqs. 3.3-3.4 for close pairs.
+ * FP64 in every precision mode.  out: [N], must not alias q.  SBIE_ERR_ARG for
+ * another op or a batch context. */
+sbie_status sphere_bie_apply_laplace(sbie_ctx* ctx, int op, const double* q, double* out);
+
+/* Paramagnetic spheres in a uniform field (Problem 3, Eqs. 5.9-5.13) moving
+ * in Stokes flow: solves (1/2 I + eta K^L) q = eta H0 . n for the single-layer
+ * density of phi = -H0 . x + S^L[q] (eta = (mu - mu0)/(mu + mu0), -1 < eta < 1;
+ * H0: [3] host memory), forms the field H = H0 - grad S^L[q] outside each
+ * sphere and its Maxwell traction f = (H . n) H - |H|^2 n / 2 (mu0 = 1), and
+ * solves the mobility problem (Eq. 5.8) with f as the incident force density.
+ * Returns the magnetic force F_k = int f and torque T_k = int (x - c_k) x f on
+ * each particle and its rigid motion (vel_k, omega_k) ([n][3] each, memory kind
+ * of the context).  info (may be NULL) sums the iterations of both solves and
+ * reports the worse of their true residuals.  Single-order contexts only
+ * (SBIE_ERR_ARG for a batch); the magnetic solve runs in FP64. */
+sbie_status sphere_bie_solve_mhd(sbie_ctx* ctx, const double* H0, double eta, double* forces, double* torques,
+                                 double* vel, double* omega, sbie_solve_info* info);
+
 /* Stage timing.  Stages: 0 far field (density pack, pair kernel and split
  * reduction), 1 close pairs (Sec. 4.1), 2 self term (analysis, signature,
  * synthesis), 3 completion / rigid-mode terms and 1/2 I, 4 Arnoldi vector
- * work, 5 other, 6 the FP32 far-field pair kernel alone, 7 the FP64 far-field
+ * work, 5 the pair preconditioner's apply, 6 the FP32 far-field pair kernel alone, 7 the FP64 far-field
  * pair kernel alone.  ms[s] is the total device time between CUDA events
  * recorded on the context stream around each launch of that stage;
  * launches[s] counts them.  far_pairs_f32 / _f64 count the (target node,
@@ -214,6 +239,10 @@ typedef struct {
     long long launches[8];
     long long far_pairs_f32, far_pairs_f64;
     long long kernel_launches;
+    long long arnoldi_vectors; /* algorithmic 3N-vector accesses of the profiled
+                                  Arnoldi iterations: 4k + 4 for an iteration
+                                  with k basis vectors (two Gram-Schmidt passes,
+                                  the new vector's norm and scaling)           */
 } sbie_profile;
 
 /* Tiling of the FP32 far-field pair kernel (Sec. 4.1 smooth quadrature). */
@@ -352,6 +381,14 @@ sbie_status sphere_bie_pair_network_size(long long* n_params);
  * NULL arrays or n < 1 (before any device work). */
 sbie_status sphere_bie_pair_network_gradients(const float* params, int n, const float* X, const float* Y,
                                               float* grads, double* loss);
+
+/* Measured FP32 throughput of this GPU (no counterpart in the paper): the
+ * best of three timed launches of a kernel of independent packed FP32x2 FMA
+ * chains (the far-field kernel's instruction) filling every SM, on the current
+ * device.  *tflops: TFLOP/s (an FMA counts 2); *ms (may be NULL): the launch
+ * time.  Allocates and frees a small buffer.  SBIE_ERR_ARG for NULL tflops,
+ * SBIE_ERR_CUDA on a device failure. */
+sbie_status sphere_bie_fp32_peak_probe(double* tflops, double* ms);
 
 /* Frees every device buffer and the context.  NULL is accepted. */
 sbie_status sphere_bie_destroy(sbie_ctx* ctx);

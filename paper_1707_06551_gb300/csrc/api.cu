@@ -93,11 +93,12 @@ void free_all(sbie_ctx* c) {
                     c->d_srcf, c->d_in, c->d_out, c->d_tmp, c->d_tmp2, c->d_small, c->d_red, c->d_V, c->d_xsol,
                     c->d_rhs, c->d_res, c->d_prob_sph, c->d_sph_prob, c->d_node_prob, c->d_seg3, c->d_H, c->d_pvec,
                     c->d_ZS, c->d_ZA, c->d_modes, c->d_low, c->d_lowe, c->d_pz, c->d_ad, c->d_adi, c->d_vk,
-                    c->d_sq};
+                    c->d_sq, c->d_lcoef};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (PrecState& P : c->prec)
-        for (void* p : {(void*)P.d_pp_ptr, (void*)P.d_pp_idx, (void*)P.d_pp_pair, (void*)P.d_pinv, (void*)P.d_sinv})
+        for (void* p : {(void*)P.d_pp_ptr, (void*)P.d_pp_idx, (void*)P.d_pp_pair, (void*)P.d_pinv, (void*)P.d_sinv,
+                        (void*)P.d_pp_own, (void*)P.d_cpart})
             if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
     if (c->h_st) cudaFreeHost(c->h_st);
@@ -209,28 +210,33 @@ Kern kern_of(int op) {
 
 sbie_status apply_dev(sbie_ctx* c, int op, int mode, const double* in, double* out);
 
+// Operator of the magnetostatic equation (Eq. 5.13) on scalar densities held
+// in component 0; internal (reached through sphere_bie_solve_mhd).
+constexpr int kOpMagnetic = 7;
+
 // Porous-media operator 1/2 I + S + D (Eq. 5.4): both layers' far fields,
 // self terms and close-pair corrections, added.
 sbie_status apply_porous(sbie_ctx* c, int mode, const double* in, double* out) {
     const bool f32 = mode == kModeF32;
     const bool far = c->far_pair_count > 0;
+    const bool gemm = f32 && self_gemm_ready(c, kSelfS) && self_gemm_ready(c, kSelfDK);
+    if (gemm) {
+        StageScope s(c, ST_SELF);
+        CK(launch_self_gemm(c, kSelfS, in, out, false));
+        CK(launch_self_gemm(c, kSelfDK, in, out, true));
+        if (c->n_near > 0) CK(launch_self_analysis(c, in));
+    }
     if (far) {
         StageScope s(c, ST_FAR);
         CK(launch_pack(c, in, mode));
-        CK(launch_far(c, Kern::S, mode, out, false));
+        CK(launch_far(c, Kern::S, mode, out, gemm));
         CK(launch_far(c, Kern::D, mode, out, true));
         if (c->prof.on) (f32 ? c->prof.pairs_f32 : c->prof.pairs_f64) += 2 * c->far_pair_count;
     }
-    {
+    if (!gemm) {
         StageScope s(c, ST_SELF);
-        if (f32 && self_gemm_ready(c, kSelfS) && self_gemm_ready(c, kSelfDK)) {
-            CK(launch_self_gemm(c, kSelfS, in, out, far));
-            CK(launch_self_gemm(c, kSelfDK, in, out, true));
-            if (c->n_near > 0) CK(launch_self_analysis(c, in));
-        } else {
-            CK(launch_self(c, Kern::S, in, out, far, c->n_near > 0));
-            CK(launch_self(c, Kern::D, in, out, true, false));
-        }
+        CK(launch_self(c, Kern::S, in, out, far, c->n_near > 0));
+        CK(launch_self(c, Kern::D, in, out, true, false));
     }
     if (c->n_near > 0) {
         StageScope s(c, ST_NEAR);
@@ -246,6 +252,14 @@ sbie_status apply_porous(sbie_ctx* c, int mode, const double* in, double* out) {
 // (kModeF64, kModeF32 or kModeDF).
 sbie_status apply_dev(sbie_ctx* c, int op, int mode, const double* in, double* out) {
     if (op == SBIE_OP_POROUS) return apply_porous(c, mode, in, out);
+    if (op == kOpMagnetic) {
+        // (1/2 I + eta K^L) on component 0 (the scalar density), 1/2 I on the
+        // two unused components (FP64 in every precision mode)
+        CK(laplace_apply(c, kLapKL, in, out));
+        StageScope s(c, ST_COMPL);
+        CK(launch_magnetic_finalize(c, c->mag_eta, in, out));
+        return SBIE_OK;
+    }
     if (op == SBIE_OP_SQUIRMER) {
         // (1/2 I + S + D)(in - P in) - P in, P the rigid projection per sphere
         if (!c->d_sq) return fail(c, SBIE_ERR_ARG, "squirmer buffers not allocated");
@@ -266,23 +280,31 @@ sbie_status apply_dev(sbie_ctx* c, int op, int mode, const double* in, double* o
     // a context whose pairs are all close (the two-sphere probe problems of
     // the pair preconditioner) has no far field: the self term writes `out`
     const bool far = c->far_pair_count > 0;
-    if (far) {
-        StageScope s(c, ST_FAR);
-        CK(launch_pack(c, in, mode));
-        CK(launch_far(c, k, mode, out));
-        if (c->prof.on) (f32 ? c->prof.pairs_f32 : c->prof.pairs_f64) += c->far_pair_count;
-    }
-    {
-        StageScope s(c, ST_SELF);
-        const int which = k == Kern::S ? kSelfS : kSelfDK;
-        if (f32 && self_gemm_ready(c, which)) {
-            // FP32 operator: self term by the 3xTF32 GEMM; the close pairs
-            // keep FP64 VSH coefficients of the density
-            CK(launch_self_gemm(c, which, in, out, far));
+    const int which = k == Kern::S ? kSelfS : kSelfDK;
+    if (f32 && self_gemm_ready(c, which)) {
+        // FP32 operator: the self term by the 3xTF32 GEMM writes `out` first
+        // and the far field's reduction adds to it (the GEMM's epilogue then
+        // needs no FP64 add); the close pairs keep FP64 VSH coefficients
+        {
+            StageScope s(c, ST_SELF);
+            CK(launch_self_gemm(c, which, in, out, false));
             if (c->n_near > 0) CK(launch_self_analysis(c, in));
-        } else {
-            CK(launch_self(c, k, in, out, far, c->n_near > 0));
         }
+        if (far) {
+            StageScope s(c, ST_FAR);
+            CK(launch_pack(c, in, mode));
+            CK(launch_far(c, k, mode, out, true));
+            c->prof.pairs_f32 += c->prof.on ? c->far_pair_count : 0;
+        }
+    } else {
+        if (far) {
+            StageScope s(c, ST_FAR);
+            CK(launch_pack(c, in, mode));
+            CK(launch_far(c, k, mode, out));
+            if (c->prof.on) (f32 ? c->prof.pairs_f32 : c->prof.pairs_f64) += c->far_pair_count;
+        }
+        StageScope s(c, ST_SELF);
+        CK(launch_self(c, k, in, out, far, c->n_near > 0));
     }
     if (c->n_near > 0) {
         StageScope s(c, ST_NEAR);
@@ -661,6 +683,7 @@ sbie_status gmres(const Sys& S, const AFn& A, const double* b, double* x, const 
         if (!g) {
             for (int it = 0; it < mm; ++it) {
                 CKS(enqueue_iteration(S, A, M, cudaGraphConditionalHandle{}, false));
+                if (c->prof.on) c->prof.arnoldi_vectors += 4LL * (it + 1) + 4;
                 CK(cudaMemcpyAsync(c->h_st, AD.st, sizeof(int) * kStWords, cudaMemcpyDeviceToHost, c->stream));
                 CK(cudaStreamSynchronize(c->stream));
                 if (!c->h_st[2]) break;
@@ -750,6 +773,7 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
         for (size_t i = 0; i < S.parts.size(); ++i) {
             sbie_ctx* q = S.parts[i];
             if (q->prec[slot].kind > 0) {
+                StageScope st(q, ST_OTHER);
                 cudaError_t e = precond_apply(q, slot, in + S.off3[i], out + S.off3[i], q->opts.prec == SBIE_MIXED);
                 if (e != cudaSuccess) return fail(c, SBIE_ERR_CUDA, std::string("preconditioner: ") + cudaGetErrorString(e));
             } else {
@@ -770,7 +794,7 @@ sbie_status solve_sys(const Sys& S, int op, const double* b, double* x, sbie_sol
     std::vector<double> rel(P, 0.0);
     // reduction and staging buffers must exist before the first norm
     CKS(ensure_krylov(c, std::max(1, std::min(c->opts.restart, 250)), P));
-    if (c->opts.prec != SBIE_MIXED) {
+    if (c->opts.prec != SBIE_MIXED || op == kOpMagnetic) {
         CKS(gmres(S, A64, b, x, std::vector<double>(P, tol), std::vector<char>(P, 1), c->opts.restart,
                   c->opts.max_iter, go, M, key_of(hm)));
         inf.iters = go.iters;
@@ -1635,6 +1659,16 @@ sbie_status precond_setup(sbie_ctx* c, int op, int kind, const PairNet* net) {
         const cudaError_t e = self_gemm_build(c, kSelfPrec);
         if (e != cudaSuccess)
             return fail(c, SBIE_ERR_CUDA, std::string("preconditioner matrix: ") + cudaGetErrorString(e));
+        // the FP32 coarse correction's entry owners and per-entry products
+        P.n_entries = pp_ptr[n];
+        std::vector<int> own(std::max(1, P.n_entries));
+        for (int i = 0; i < n; ++i)
+            for (int ee = pp_ptr[i]; ee < pp_ptr[i + 1]; ++ee) own[ee] = i;
+        if (dmalloc(&P.d_pp_own, own.size()) != cudaSuccess ||
+            dmalloc(&P.d_cpart, (size_t)std::max(1, P.n_entries) * kLowModes) != cudaSuccess)
+            return fail(c, SBIE_ERR_OOM, "coarse-correction buffers");
+        CK(h2d(c->stream, P.d_pp_own, own.data(), own.size()));
+        CK(cudaStreamSynchronize(c->stream));
     }
     P.n_pairs = np;
     P.kind = kind;
@@ -1878,6 +1912,31 @@ sbie_status sphere_bie_apply_operator(sbie_ctx* c, sbie_op op, const double* den
     return check_self_gemm(S);
 }
 
+// Eq. 5.8 for the incident force density rho (device, internal order, [N][3];
+// rho must not be c->d_rhs, d_xsol, d_out or d_tmp2): solve
+// (1/2 I + K + L) mu = -(1/2 I + K) rho, u = S[mu + rho], rigid projection into
+// dv, dw ([n][3] device, internal order).
+sbie_status mobility_from_density(const Sys& S, const double* rho, double* dv, double* dw, sbie_solve_info* inf) {
+    sbie_ctx* c = S.top;
+    const long long n3 = S.n3;
+    double* b = c->d_rhs;
+    double* mu = c->d_xsol;
+    // b = -(1/2 I + K) rho
+    CKS(apply_sys(S, SBIE_OP_K, hi_mode(c), rho, b));
+    CK(blas_lincomb(c, -0.5, rho, -1.0, b, b, n3));
+    sbie_status st = solve_sys(S, SBIE_OP_MOBILITY, b, mu, inf);
+    if (st != SBIE_OK && st != SBIE_ERR_NOT_CONVERGED) return st;
+    // u = S[mu + rho] on every sphere; rigid projection
+    CK(blas_lincomb(c, 1.0, mu, 1.0, rho, c->d_tmp2, n3));
+    CKS(apply_sys(S, SBIE_OP_S, hi_mode(c), c->d_tmp2, c->d_out));
+    long long sph_off = 0;
+    for (size_t s = 0; s < S.parts.size(); ++s) {
+        CK(launch_rigid_projection(S.parts[s], c->d_out + S.off3[s], dv + 3 * sph_off, dw + 3 * sph_off));
+        sph_off += S.parts[s]->n;
+    }
+    return st;
+}
+
 sbie_status sphere_bie_solve_mobility(sbie_ctx* c, const double* forces, const double* torques, double* vel,
                                       double* omega, sbie_solve_info* info) {
     if (!c) return SBIE_ERR_ARG;
@@ -1893,27 +1952,14 @@ sbie_status sphere_bie_solve_mobility(sbie_ctx* c, const double* forces, const d
     CKS(to_internal(c, forces, dF, false));
     CKS(to_internal(c, torques, dT, false));
     double* rho = c->d_in;
-    double* b = c->d_rhs;
-    double* mu = c->d_xsol;
     long long sph_off = 0;
     for (size_t s = 0; s < S.parts.size(); ++s) {
         CK(launch_rho(S.parts[s], dF + 3 * sph_off, dT + 3 * sph_off, rho + S.off3[s]));
         sph_off += S.parts[s]->n;
     }
-    // b = -(1/2 I + K) rho
-    CKS(apply_sys(S, SBIE_OP_K, hi_mode(c), rho, b));
-    CK(blas_lincomb(c, -0.5, rho, -1.0, b, b, n3));
     sbie_solve_info inf{};
-    sbie_status st = solve_sys(S, SBIE_OP_MOBILITY, b, mu, &inf);
+    sbie_status st = mobility_from_density(S, rho, dv, dw, &inf);
     if (st != SBIE_OK && st != SBIE_ERR_NOT_CONVERGED) return st;
-    // u = S[mu + rho] on every sphere; rigid projection
-    CK(blas_lincomb(c, 1.0, mu, 1.0, rho, c->d_tmp2, n3));
-    CKS(apply_sys(S, SBIE_OP_S, hi_mode(c), c->d_tmp2, c->d_out));
-    sph_off = 0;
-    for (size_t s = 0; s < S.parts.size(); ++s) {
-        CK(launch_rigid_projection(S.parts[s], c->d_out + S.off3[s], dv + 3 * sph_off, dw + 3 * sph_off));
-        sph_off += S.parts[s]->n;
-    }
     CKS(to_user(c, dv, vel, false));
     CKS(to_user(c, dw, omega, false));
     CK(cudaStreamSynchronize(c->stream));
@@ -2051,6 +2097,110 @@ sbie_status sphere_bie_solve_squirmer(sbie_ctx* c, const double* slip, double* v
     inf.kernel_launches = total_launches(S) - launches0;
     if (info) *info = inf;
     return st;
+}
+
+namespace {
+
+__global__ void scalar_to_vec_kernel(long long N, const double* __restrict__ q, double* __restrict__ v) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    v[3 * i] = q[i];
+    v[3 * i + 1] = 0.0;
+    v[3 * i + 2] = 0.0;
+}
+
+__global__ void vec_to_scalar_kernel(long long N, const double* __restrict__ v, double* __restrict__ q) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) q[i] = v[3 * i];
+}
+
+sbie_status ensure_laplace_buffers(sbie_ctx* c) {
+    const int P1 = c->p + 1;
+    if (!c->d_lcoef && dmalloc(&c->d_lcoef, (size_t)c->n * P1 * P1 * 2) != cudaSuccess)
+        return fail(c, SBIE_ERR_OOM, "Laplace coefficient buffer");
+    if (!c->d_sq && dmalloc(&c->d_sq, 6 * (size_t)c->N) != cudaSuccess)
+        return fail(c, SBIE_ERR_OOM, "Laplace work vectors");
+    return SBIE_OK;
+}
+
+}  // namespace
+
+sbie_status sphere_bie_apply_laplace(sbie_ctx* c, int op, const double* q, double* out) {
+    if (!c) return SBIE_ERR_ARG;
+    if (!q || !out || q == out) return fail(c, SBIE_ERR_ARG, "NULL or aliased density / out");
+    if (op < kLapSL || op > kLapKL) return fail(c, SBIE_ERR_ARG, "op must be 0 (S^L), 1 (D^L) or 2 (K^L)");
+    if (c->is_batch) return fail(c, SBIE_ERR_ARG, "Laplace operators take a single-order context");
+    CKS(ensure_laplace_buffers(c));
+    const long long N = c->N;
+    const unsigned nb = (unsigned)((N + 255) / 256);
+    double* qv = c->d_sq;  // [N][3] with the density in component 0
+    const double* qs = q;
+    if (c->opts.mem_kind == 0) {
+        CK(h2d(c->stream, c->d_tmp2, q, (size_t)N));
+        qs = c->d_tmp2;
+    }
+    scalar_to_vec_kernel<<<nb, 256, 0, c->stream>>>(N, qs, qv); ++c->n_launch;
+    CK(cudaGetLastError());
+    CK(laplace_apply(c, op, qv, c->d_out));
+    double* os = c->opts.mem_kind == 0 ? c->d_tmp2 : out;
+    vec_to_scalar_kernel<<<nb, 256, 0, c->stream>>>(N, c->d_out, os); ++c->n_launch;
+    CK(cudaGetLastError());
+    if (c->opts.mem_kind == 0) CK(d2h(c->stream, out, c->d_tmp2, (size_t)N));
+    CK(cudaStreamSynchronize(c->stream));
+    return SBIE_OK;
+}
+
+sbie_status sphere_bie_solve_mhd(sbie_ctx* c, const double* H0, double eta, double* forces, double* torques,
+                                 double* vel, double* omega, sbie_solve_info* info) {
+    if (!c) return SBIE_ERR_ARG;
+    if (!H0 || !forces || !torques || !vel || !omega) return fail(c, SBIE_ERR_ARG, "NULL argument");
+    if (!finite_all(H0, 3) || !std::isfinite(eta) || !(eta > -1.0 && eta < 1.0))
+        return fail(c, SBIE_ERR_ARG, "H0 must be finite and -1 < eta < 1");
+    if (c->is_batch) return fail(c, SBIE_ERR_ARG, "the magnetostatic problem takes a single-order context");
+    auto t0 = std::chrono::steady_clock::now();
+    Sys S = sys_of(c);
+    const long long launches0 = total_launches(S);
+    CKS(ensure_laplace_buffers(c));
+    double* q = c->d_sq;                   // magnetic density (component 0)
+    double* rho = c->d_sq + 3 * c->N;      // Maxwell traction
+    double* dF = c->d_small;
+    double* dT = dF + 3 * c->n;
+    double* dv = dT + 3 * c->n;
+    double* dw = dv + 3 * c->n;
+    // Eq. 5.13: (1/2 I + eta K^L) q = eta H0 . n
+    c->mag_eta = eta;
+    CK(launch_magnetic_rhs(c, eta, H0, c->d_rhs));
+    sbie_solve_info im{};
+    sbie_status st = solve_sys(S, kOpMagnetic, c->d_rhs, c->d_xsol, &im);
+    if (st != SBIE_OK && st != SBIE_ERR_NOT_CONVERGED) return st;
+    CK(cudaMemcpyAsync(q, c->d_xsol, sizeof(double) * 3 * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    // H = H0 - grad S^L[q] outside; traction (H.n) H - |H|^2 n / 2
+    CK(laplace_apply(c, kLapGrad, q, rho));
+    CK(launch_maxwell_traction(c, H0, rho));
+    CK(launch_moments(c, rho));
+    CK(cudaMemcpy2DAsync(dF, sizeof(double) * 3, c->d_mom, sizeof(double) * 6, sizeof(double) * 3, c->n,
+                         cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpy2DAsync(dT, sizeof(double) * 3, c->d_mom + 3, sizeof(double) * 6, sizeof(double) * 3, c->n,
+                         cudaMemcpyDeviceToDevice, c->stream));
+    // the traction as the incident force density of the mobility problem (Eq. 5.8)
+    sbie_solve_info inf{};
+    sbie_status st2 = mobility_from_density(S, rho, dv, dw, &inf);
+    if (st2 != SBIE_OK && st2 != SBIE_ERR_NOT_CONVERGED) return st2;
+    CKS(to_user(c, dF, forces, false));
+    CKS(to_user(c, dT, torques, false));
+    CKS(to_user(c, dv, vel, false));
+    CKS(to_user(c, dw, omega, false));
+    CK(cudaStreamSynchronize(c->stream));
+    inf.iters += im.iters;
+    inf.restarts += im.restarts;
+    inf.graph_cycles += im.graph_cycles;
+    inf.rel_residual_true = std::max(inf.rel_residual_true, im.rel_residual_true);
+    inf.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    inf.t_setup_ms = c->t_create_ms;
+    c->has_solution = true;
+    inf.kernel_launches = total_launches(S) - launches0;
+    if (info) *info = inf;
+    return st != SBIE_OK ? st : st2;
 }
 
 sbie_status sphere_bie_destroy(sbie_ctx* c) {
@@ -2215,6 +2365,7 @@ sbie_status sphere_bie_profile(sbie_ctx* c, int enable) {
             q->prof_used[s] = 0;
         }
         q->prof.pairs_f32 = q->prof.pairs_f64 = 0;
+        q->prof.arnoldi_vectors = 0;
         q->prof.kernels0 = q->n_launch;
     }
     return SBIE_OK;
@@ -2241,6 +2392,7 @@ sbie_status sphere_bie_profile_read(sbie_ctx* c, sbie_profile* out) {
         }
         out->far_pairs_f32 += q->prof.pairs_f32;
         out->far_pairs_f64 += q->prof.pairs_f64;
+        out->arnoldi_vectors += q->prof.arnoldi_vectors;
         out->kernel_launches += q->n_launch - q->prof.kernels0;
     }
     return SBIE_OK;

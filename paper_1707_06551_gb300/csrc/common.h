@@ -74,6 +74,11 @@ __host__ __device__ inline int sh_count(int L) { return (L + 1) * (L + 1); }
 // Channels per close-pair source expansion.
 constexpr int kVelChannels = 10;   // grad Pa (3), grad Pb (3), Pc (1), grad Pd (3)
 constexpr int kTracChannels = 26;  // hess Pa (6), grad Pb (3), hess Pb (6), Pc (1), grad Pc (3), hess Pd (6), Pe (1)
+constexpr int kLapChannels = 6;    // Laplace: Phi_S, grad Phi_S (3), Phi_D, one zero (even width)
+
+// Laplace operators (laplace.cu) on scalar densities held in component 0 of [N][3]:
+// single layer, double layer, flux of the single layer, exterior gradient of the single layer.
+constexpr int kLapSL = 0, kLapDL = 1, kLapKL = 2, kLapGrad = 3;
 
 struct FarTune {
     int threads;  // threads per CTA (multiple of 32)
@@ -88,6 +93,7 @@ struct Profile {
     double ms[8] = {0};
     long long launches[8] = {0};
     long long pairs_f32 = 0, pairs_f64 = 0;
+    long long arnoldi_vectors = 0;  // sum of 4k + 4 over profiled Arnoldi iterations
     long long kernels0 = 0;  // kernel-launch counter at the last reset
 };
 enum Stage {
@@ -141,6 +147,9 @@ struct PrecState {
     int* d_pp_pair = nullptr;  // pair index into d_pinv
     float* d_pinv = nullptr;   // [n_pairs][146][146] inverses of the pair systems
     float* d_sinv = nullptr;   // [n][73][73] inverses of the spheres' own low-mode blocks
+    int n_entries = 0;         // entries of the per-sphere pair lists (2 n_pairs)
+    int* d_pp_own = nullptr;   // [n_entries] sphere owning each entry (FP32 coarse correction)
+    float* d_cpart = nullptr;  // [n_entries][73] per-entry products of the FP32 coarse correction
 };
 constexpr int prec_slot(int op) { return op == SBIE_OP_MOBILITY ? 1 : 0; }
 
@@ -199,6 +208,8 @@ struct sbie_ctx {
     double* d_lowe = nullptr;      // [n][73]
     double* d_pz = nullptr;        // preconditioned vector (system level)
     double* d_sq = nullptr;        // [2][3N] squirmer operator: mu - P mu and P mu
+    double* d_lcoef = nullptr;     // [n][p+1][p+1][2] scalar coefficients of a Laplace density (close pairs)
+    double mag_eta = 0.0;          // eta of the magnetic operator (Eq. 5.13) of the running solve
     double t_create_ms = 0.0;      // wall time of create (grid, tables, close pairs, preconditioner)
     bool has_solution = false;     // d_xsol holds the density of the last solve
 
@@ -332,6 +343,12 @@ int far_occupancy(sbie_ctx* c, Kern op, int mode, const FarTune& tu);
 int far_f32_builds(int tpt, int* minb);
 // near.cu
 cudaError_t launch_near(sbie_ctx* c, Kern op, bool f32, double* out);
+cudaError_t launch_near_laplace(sbie_ctx* c, int mode, double* out);
+// laplace.cu
+cudaError_t laplace_apply(sbie_ctx* c, int mode, const double* q, double* out);
+cudaError_t launch_magnetic_finalize(sbie_ctx* c, double eta, const double* in, double* out);
+cudaError_t launch_magnetic_rhs(sbie_ctx* c, double eta, const double* H0, double* b);
+cudaError_t launch_maxwell_traction(sbie_ctx* c, const double* H0, double* g);
 // compl.cu
 cudaError_t launch_moments(sbie_ctx* c, const double* dens);
 cudaError_t launch_completion(sbie_ctx* c, bool f32, double* out);

@@ -36,6 +36,7 @@ struct NearArgs {
     double* __restrict__ chan;         // [n][K][nch]
     float* __restrict__ chanf;         // [n][K][nchf]
     int nchf;
+    int sel;                           // Laplace: 0 S^L value, 1 D^L value, 2 flux of S^L (KIND 3)
     double* __restrict__ out;          // [N][3]
 };
 
@@ -98,6 +99,47 @@ __device__ void deriv_all(const double* src, double* dst, int L, int d) {
         }
         int n = m + rem / 2, part = rem & 1;
         dst[q] = deriv_gather(src, L, d, n, m, part);
+    }
+}
+
+// Laplace close pairs (Eqs. 3.3-3.4): from the scalar coefficients c_nm of a
+// source sphere ([P1 (n)][P1 (m)][2]), the channels
+// [Phi_S, grad Phi_S (3), Phi_D] with Phi_S = sum c I_nm / (2n+1) and
+// Phi_D = sum n c I_nm / (2n+1), I_nm = r^{-n-1} Y_n^m.
+__global__ void near_prep_laplace_kernel(NearArgs A) {
+    const int s = blockIdx.x;
+    if (A.near_ptr[s + 1] == A.near_ptr[s]) return;
+    const int p = A.p, P1 = p + 1, L = A.L, K = sh_count(L), nch = A.nch;
+    extern __shared__ double sm[];
+    double* phs = sm;         // [K]
+    double* phd = sm + K;     // [K]
+    double* grad = sm + 2 * K;  // [3][K]
+    const double* cf = A.coef + (size_t)s * P1 * P1 * 2;
+    for (int q = threadIdx.x; q < 2 * K; q += blockDim.x) sm[q] = 0.0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < P1 * P1; q += blockDim.x) {
+        const int n = q / P1, m = q - n * P1;
+        if (m > n) continue;
+        const double t = 1.0 / (2.0 * n + 1.0);
+        const double cr = cf[2 * q], ci = cf[2 * q + 1];
+        const double e = (m == 0 ? 1.0 : 2.0) * ynorm(n, m);
+        const int ire = sh_index(L, n, m, 0);
+        phs[ire] = e * t * cr;
+        phd[ire] = e * n * t * cr;
+        if (m >= 1) {
+            phs[ire + 1] = -e * t * ci;
+            phd[ire + 1] = -e * n * t * ci;
+        }
+    }
+    __syncthreads();
+    for (int d = 0; d < 3; ++d) deriv_all(phs, grad + d * K, L, d);
+    __syncthreads();
+    double* ch = A.chan + (size_t)s * K * nch;
+    for (int q = threadIdx.x; q < K; q += blockDim.x) {
+        ch[(size_t)q * nch + 0] = phs[q];
+        for (int d = 0; d < 3; ++d) ch[(size_t)q * nch + 1 + d] = grad[d * K + q];
+        ch[(size_t)q * nch + 4] = phd[q];
+        ch[(size_t)q * nch + 5] = 0.0;
     }
 }
 
@@ -268,7 +310,17 @@ __global__ void __launch_bounds__(128) near_eval_kernel(NearArgs A) {
             }
         }
         double xd = (double)x, yd = (double)y, zd = (double)z, rr = xd * xd + yd * yd + zd * zd;
-        if (KIND < 2) {
+        if (KIND == 3) {
+            // Laplace value (S^L times the source radius, or D^L) or flux n . grad S^L
+            // (grad in units of the source radius: the radius cancels)
+            if (A.sel == 0) res[0] += ak * (double)acc[0];
+            else if (A.sel == 1) res[0] += (double)acc[4];
+            else res[0] += nxv * (double)acc[1] + nyv * (double)acc[2] + nzv * (double)acc[3];
+        } else if (KIND == 4) {
+            res[0] += (double)acc[1];
+            res[1] += (double)acc[2];
+            res[2] += (double)acc[3];
+        } else if (KIND < 2) {
             // u = grad Pa + r^2 grad Pb + x Pc + x cross grad Pd
             double ga[3] = {acc[0], acc[1], acc[2]}, gb[3] = {acc[3], acc[4], acc[5]}, gd[3] = {acc[7], acc[8], acc[9]};
             double pc = acc[6];
@@ -330,6 +382,33 @@ static cudaError_t run_eval(sbie_ctx* c, const NearArgs& A) {
     if (e != cudaSuccess) return e;
     near_eval_kernel<T, NCH, KIND><<<c->n * A.chunks, A.threads, sm, c->stream>>>(A); ++c->n_launch;
     return cudaGetLastError();
+}
+
+cudaError_t launch_near_laplace(sbie_ctx* c, int mode, double* out) {
+    if (c->n_near == 0) return cudaSuccess;
+    NearArgs A;
+    A.n = c->n; A.p = c->p; A.npn = c->npn;
+    A.L = c->p + 1;
+    A.nch = kLapChannels;
+    A.nchf = ((A.nch + 3) / 4) * 4;
+    A.sel = mode == kLapSL ? 0 : (mode == kLapDL ? 1 : 2);
+    A.threads = 128;
+    while (A.threads > 32 && (long long)c->n * ((c->npn + A.threads - 1) / A.threads) < 2LL * c->sm_count)
+        A.threads /= 2;
+    A.chunks = (c->npn + A.threads - 1) / A.threads;
+    A.coef = c->d_lcoef; A.radius = c->d_a; A.c = c->d_c; A.x64 = c->d_x; A.nrm64 = c->d_nrm64;
+    A.near_ptr = c->d_near_ptr; A.near_idx = c->d_near_idx;
+    A.chan = c->d_chan; A.chanf = nullptr; A.out = out;
+    const int K = sh_count(A.L);
+    const size_t sm = sizeof(double) * (size_t)(5 * K);
+    cudaError_t e = cudaFuncSetAttribute(near_prep_laplace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess) return e;
+    near_prep_laplace_kernel<<<c->n, 256, sm, c->stream>>>(A); ++c->n_launch;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (mode == kLapGrad) return run_eval<double, kLapChannels, 4>(c, A);
+    return run_eval<double, kLapChannels, 3>(c, A);
 }
 
 cudaError_t launch_near(sbie_ctx* c, Kern op, bool f32, double* out) {

@@ -425,6 +425,70 @@ __global__ void coarse_kernel(const int* __restrict__ pp_ptr, const int* __restr
     for (int t = threadIdx.x; t < L; t += blockDim.x) e[(size_t)i * L + t] = ((double)ah[t] + (double)al[t]) * w;
 }
 
+// The coarse correction of the FP32 inner solves: one CTA per directed
+// (sphere, pair) entry of the pair lists -- the 73 rows of sphere i in the
+// pair's 146 x 146 inverse times the pair's low-mode vector, in FP32 (a fixed
+// linear map to FP32 rounding, which the FP32 inner solves tolerate) -- and one
+// CTA per sphere without close partners (its own 73 x 73 inverse).  Many more
+// CTAs than spheres keep enough loads in flight for the inverses' 48 MB
+// (resistance_256) to stream at HBM rate; coarse_average_kernel then averages
+// each sphere's entries in a fixed order.
+constexpr int kCoarse32Threads = 256;
+__global__ void __launch_bounds__(kCoarse32Threads)
+    coarse_f32_kernel(int n, int n_entries, const int* __restrict__ pp_ptr, const int* __restrict__ pp_idx,
+                      const int* __restrict__ pp_pair, const int* __restrict__ pp_own,
+                      const float* __restrict__ pinv, const float* __restrict__ sinv, const double* __restrict__ low,
+                      float* __restrict__ part, double* __restrict__ e) {
+    constexpr int L = kLowModes;
+    __shared__ float cv[2 * L];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const float* M;
+    int stride, ncol, i;
+    float* dst = nullptr;
+    if (blockIdx.x < n_entries) {
+        const int ee = blockIdx.x;
+        i = pp_own[ee];
+        const int k = pp_idx[ee];
+        const int a = min(i, k), b = max(i, k);
+        for (int t = threadIdx.x; t < 2 * L; t += blockDim.x)
+            cv[t] = (float)(t < L ? low[(size_t)a * L + t] : low[(size_t)b * L + t - L]);
+        M = pinv + (size_t)pp_pair[ee] * 4 * L * L + (size_t)(i == a ? 0 : L) * 2 * L;
+        stride = ncol = 2 * L;
+        dst = part + (size_t)ee * L;
+    } else {
+        i = blockIdx.x - n_entries;
+        if (i >= n || pp_ptr[i + 1] > pp_ptr[i]) return;
+        for (int t = threadIdx.x; t < L; t += blockDim.x) cv[t] = (float)low[(size_t)i * L + t];
+        M = sinv + (size_t)i * L * L;
+        stride = ncol = L;
+    }
+    __syncthreads();
+    for (int r = warp; r < L; r += nw) {
+        const float* Mr = M + (size_t)r * stride;
+        float acc = 0.f;
+#pragma unroll 5
+        for (int col = lane; col < ncol; col += 32) acc = fmaf(Mr[col], cv[col], acc);
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            if (dst) dst[r] = acc;
+            else e[(size_t)i * L + r] = (double)acc;
+        }
+    }
+}
+
+__global__ void coarse_average_kernel(int n, const int* __restrict__ pp_ptr, const float* __restrict__ part,
+                                      double* __restrict__ e) {
+    constexpr int L = kLowModes;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n * L) return;
+    const int i = (int)(t / L), r = (int)(t - (long long)i * L);
+    const int e0 = pp_ptr[i], e1 = pp_ptr[i + 1];
+    if (e1 == e0) return;  // written by the sphere's own CTA
+    float s = 0.f;
+    for (int ee = e0; ee < e1; ++ee) s += part[(size_t)ee * L + r];
+    e[t] = (double)s / (double)(e1 - e0);
+}
+
 // out_sphere += ZS . e_sphere
 __global__ void synth_add_kernel(int npn, long long N, const double* __restrict__ ZS, const double* __restrict__ e,
                                  double* __restrict__ out) {
@@ -489,9 +553,22 @@ cudaError_t precond_apply(sbie_ctx* c, int slot, const double* v, double* out, b
         gather_low_kernel<<<c->n, 96, 0, c->stream>>>(c->n, c->p + 1, c->d_coef, c->d_modes, c->d_low);
         ++c->n_launch;
     }
-    coarse_kernel<<<c->n, kCoarseThreads, 0, c->stream>>>(P.d_pp_ptr, P.d_pp_idx, P.d_pp_pair, P.d_pinv, P.d_sinv,
-                                              c->d_low, c->d_lowe);
-    ++c->n_launch;
+    if (f32 && P.d_pp_own) {
+        const int ne = P.n_entries;
+        coarse_f32_kernel<<<ne + c->n, kCoarse32Threads, 0, c->stream>>>(c->n, ne, P.d_pp_ptr, P.d_pp_idx,
+                                                                         P.d_pp_pair, P.d_pp_own, P.d_pinv, P.d_sinv,
+                                                                         c->d_low, P.d_cpart, c->d_lowe);
+        ++c->n_launch;
+        if (ne > 0) {
+            coarse_average_kernel<<<(unsigned)(((long long)c->n * kLowModes + 255) / 256), 256, 0, c->stream>>>(
+                c->n, P.d_pp_ptr, P.d_cpart, c->d_lowe);
+            ++c->n_launch;
+        }
+    } else {
+        coarse_kernel<<<c->n, kCoarseThreads, 0, c->stream>>>(P.d_pp_ptr, P.d_pp_idx, P.d_pp_pair, P.d_pinv,
+                                                              P.d_sinv, c->d_low, c->d_lowe);
+        ++c->n_launch;
+    }
     synth_add_kernel<<<(unsigned)((c->N + 127) / 128), 128, 0, c->stream>>>(c->npn, c->N, c->d_ZS, c->d_lowe, out);
     ++c->n_launch;
     return cudaGetLastError();

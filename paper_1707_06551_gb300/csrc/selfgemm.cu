@@ -139,6 +139,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// float -> double through the bit pattern (integer pipe): exact for normal
+// numbers, zero for zero and subnormals, infinities and NaN kept.
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xFFu;
+    unsigned long long d = (unsigned long long)(u & 0x80000000u) << 32;
+    if (e != 0) {
+        const unsigned long long de = e == 0xFFu ? 2047ull : (unsigned long long)(e + 896u);
+        d |= (de << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    }
+    return __longlong_as_double((long long)d);
+}
+
 struct GemmEpi {
     int rows;            // matrix rows with an output
     int out_rows;        // rows written to `out` (the nodal components); rows above go to `low`
@@ -146,7 +159,7 @@ struct GemmEpi {
     long long ld_out;    // doubles between consecutive spheres of `out` (3 npn)
     double* out;
     int accumulate;      // out += instead of out =
-    const double* scale; // per-sphere factor (single layer: the radius) or nullptr
+    const float* scale;  // per-sphere factor (single layer: the radius) or nullptr
     double* low;         // [cols][rows - out_rows] or nullptr
     int k_blocks;
     int* err;            // set to 1 when a wait runs out
@@ -244,26 +257,29 @@ __global__ void __launch_bounds__(128, 1)
         const int r = m0 + warp * 32 + lane;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         const int used = nk < kAcc ? nk : kAcc;  // accumulators written
+        // The SM issues FP64 at a small fraction of its FP32 rate, so the
+        // epilogue stays in FP32 and integer arithmetic: the accumulators are
+        // added in FP32 (round to nearest: no drift; the result carries FP32
+        // accuracy, as the rest of the FP32 operator), the radius applied in
+        // FP32, and the value widened to FP64 by its bit pattern.  Only
+        // `accumulate` costs one FP64 add per output.
 #pragma unroll 1
         for (int c0 = 0; c0 < kBN; c0 += 16) {
-            double acc[16];
+            float acc[16];
             float v[16];
-            tmem_ld16(trow + (uint32_t)(kAcc * kBN + c0), v);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) acc[i] = (double)v[i];
+            tmem_ld16(trow + (uint32_t)(kAcc * kBN + c0), acc);
 #pragma unroll 1
             for (int j = 0; j < used; ++j) {
                 tmem_ld16(trow + (uint32_t)(j * kBN + c0), v);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) acc[i] += (double)v[i];
+                for (int i = 0; i < 16; ++i) acc[i] += v[i];
             }
             if (r < E.rows) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int s = n0 + c0 + i;
                     if (s >= E.cols) break;
-                    double x = acc[i];
-                    if (E.scale) x *= E.scale[s];
+                    const double x = widen(E.scale ? acc[i] * E.scale[s] : acc[i]);
                     if (r < E.out_rows) {
                         double* o = E.out + (long long)s * E.ld_out + r;
                         *o = E.accumulate ? *o + x : x;
@@ -333,6 +349,11 @@ __global__ void unit_columns_kernel(int K, double* __restrict__ d) {
     d[i] = (i / K == i % K) ? 1.0 : 0.0;
 }
 
+__global__ void to_float_kernel(int n, const double* __restrict__ x, float* __restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)x[i];
+}
+
 __global__ void fill_kernel(long long n, double v, double* __restrict__ d) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) d[i] = v;
@@ -379,6 +400,7 @@ struct SelfGemm {
     float* mat[kSelfMats] = {nullptr, nullptr, nullptr};  // hi [rows][Kpad] followed by lo
     CUtensorMap mh[kSelfMats], ml[kSelfMats];
     float* b = nullptr;  // density operand: hi [n][Kpad] followed by lo
+    float* af = nullptr; // [n] radii in FP32 (the single layer's scale)
     CUtensorMap bh, bl;
     int* err = nullptr;
 };
@@ -387,6 +409,7 @@ void self_gemm_free(sbie_ctx* c) {
     if (!c->sg) return;
     for (int i = 0; i < kSelfMats; ++i) cudaFree(c->sg->mat[i]);
     cudaFree(c->sg->b);
+    cudaFree(c->sg->af);
     cudaFree(c->sg->err);
     delete c->sg;
     c->sg = nullptr;
@@ -404,6 +427,11 @@ cudaError_t self_gemm_build(sbie_ctx* c, int which) {
         g->Kpad = (g->K + kBK - 1) / kBK * kBK;
         const size_t nb = (size_t)c->n * g->Kpad;
         e = cudaMalloc(&g->b, sizeof(float) * 2 * nb);
+        if (e == cudaSuccess) e = cudaMalloc(&g->af, sizeof(float) * c->n);
+        if (e == cudaSuccess) {
+            to_float_kernel<<<(c->n + 255) / 256, 256, 0, c->stream>>>(c->n, c->d_a, g->af);
+            e = cudaGetLastError();
+        }
         if (e == cudaSuccess) e = cudaMalloc(&g->err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemsetAsync(g->err, 0, sizeof(int), c->stream);
         if (e == cudaSuccess && (!make_map(&g->bh, g->b, c->n, g->K, g->Kpad, kBN) ||
@@ -411,6 +439,7 @@ cudaError_t self_gemm_build(sbie_ctx* c, int which) {
             e = cudaErrorInvalidValue;
         if (e != cudaSuccess) {
             cudaFree(g->b);
+            cudaFree(g->af);
             cudaFree(g->err);
             delete g;
             return e;
@@ -480,7 +509,7 @@ cudaError_t launch_self_gemm(sbie_ctx* c, int which, const double* dens, double*
     E.ld_out = g->K;
     E.out = out;
     E.accumulate = accumulate ? 1 : 0;
-    E.scale = which == kSelfS ? c->d_a : nullptr;
+    E.scale = which == kSelfS ? g->af : nullptr;
     E.low = which == kSelfPrec ? c->d_low : nullptr;
     E.k_blocks = g->Kpad / kBK;
     E.err = g->err;

@@ -22,7 +22,7 @@ SBIE_FP64, SBIE_MIXED, SBIE_FP64_DF = 0, 1, 2
 SBIE_OP_S, SBIE_OP_D, SBIE_OP_K, SBIE_OP_MOBILITY, SBIE_OP_RESISTANCE = 0, 1, 2, 3, 4
 SBIE_OP_POROUS, SBIE_OP_SQUIRMER = 5, 6
 OPS = {"S": 0, "D": 1, "K": 2, "mobility": 3, "resistance": 4, "porous": 5, "squirmer": 6}
-STAGES = ("far", "near", "self", "completion", "arnoldi", "other", "far_kernel_f32", "far_kernel_f64")
+STAGES = ("far", "near", "self", "completion", "arnoldi", "precond", "far_kernel_f32", "far_kernel_f64")
 
 
 class Opts(ctypes.Structure):
@@ -47,7 +47,7 @@ class SolveInfo(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_longlong * 8),
                 ("far_pairs_f32", ctypes.c_longlong), ("far_pairs_f64", ctypes.c_longlong),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("arnoldi_vectors", ctypes.c_longlong)]
 
 
 class FarTuning(ctypes.Structure):
@@ -95,6 +95,9 @@ def lib():
         L.sphere_bie_solve_resistance.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(SolveInfo)]
         L.sphere_bie_solve_porous.argtypes = [_P, _P, _P, _P, _P, ctypes.POINTER(SolveInfo)]
         L.sphere_bie_solve_squirmer.argtypes = [_P, _P, _P, _P, ctypes.POINTER(SolveInfo)]
+        L.sphere_bie_apply_laplace.argtypes = [_P, ctypes.c_int, _P, _P]
+        L.sphere_bie_solve_mhd.argtypes = [_P, _P, ctypes.c_double, _P, _P, _P, _P, ctypes.POINTER(SolveInfo)]
+        L.sphere_bie_fp32_peak_probe.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.sphere_bie_destroy.argtypes = [_P]
         L.sphere_bie_last_error.argtypes = [_P]
         L.sphere_bie_last_error.restype = ctypes.c_char_p
@@ -114,7 +117,8 @@ def lib():
         for f in ("sphere_bie_default_opts", "sphere_bie_create", "sphere_bie_create_batch", "sphere_bie_num_nodes",
                   "sphere_bie_nodes",
                   "sphere_bie_apply_operator", "sphere_bie_solve_mobility", "sphere_bie_solve_resistance",
-                  "sphere_bie_solve_porous", "sphere_bie_solve_squirmer",
+                  "sphere_bie_solve_porous", "sphere_bie_solve_squirmer", "sphere_bie_fp32_peak_probe",
+                  "sphere_bie_apply_laplace", "sphere_bie_solve_mhd",
                   "sphere_bie_destroy", "sphere_bie_profile", "sphere_bie_profile_read",
                   "sphere_bie_apply_layer_noalloc", "sphere_bie_autotune", "sphere_bie_train_pair_network",
                   "sphere_bie_pair_blocks", "sphere_bie_pair_network_size", "sphere_bie_pair_network_gradients",
@@ -255,6 +259,32 @@ def sphere_bie_apply_layer_noalloc(op, n_spheres, p, centres, radii, density, ou
     return out
 
 
+LAPLACE_OPS = {"SL": 0, "DL": 1, "KL": 2}
+
+
+def sphere_bie_apply_laplace(ctx, op, q, out):
+    op = LAPLACE_OPS[op] if isinstance(op, str) else int(op)
+    _check(ctx, lib().sphere_bie_apply_laplace(ctx, op, _ptr(q), _ptr(out)))
+    return out
+
+
+def sphere_bie_solve_mhd(ctx, H0, eta, forces, torques, vel, omega):
+    info = SolveInfo()
+    h = np.ascontiguousarray(H0, dtype=np.float64).reshape(3)
+    st = _check(ctx, lib().sphere_bie_solve_mhd(ctx, _ptr(h), float(eta), _ptr(forces), _ptr(torques), _ptr(vel),
+                                                _ptr(omega), ctypes.byref(info)), allow=(SBIE_ERR_NOT_CONVERGED,))
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+def sphere_bie_fp32_peak_probe():
+    """Measured FP32 TFLOP/s of the current device and the probe launch (ms)."""
+    t, ms = ctypes.c_double(0), ctypes.c_double(0)
+    _check(None, lib().sphere_bie_fp32_peak_probe(ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
+
+
 def sphere_bie_destroy(ctx):
     if ctx:
         _check(None, lib().sphere_bie_destroy(ctx))
@@ -330,7 +360,7 @@ def sphere_bie_profile_read(ctx):
     _check(ctx, lib().sphere_bie_profile_read(ctx, ctypes.byref(p)))
     return {"ms": dict(zip(STAGES, list(p.ms))), "launches": dict(zip(STAGES, list(p.launches))),
             "far_pairs_f32": p.far_pairs_f32, "far_pairs_f64": p.far_pairs_f64,
-            "kernel_launches": p.kernel_launches}
+            "kernel_launches": p.kernel_launches, "arnoldi_vectors": p.arnoldi_vectors}
 
 
 class SphereBIE:
@@ -386,6 +416,15 @@ class SphereBIE:
         w = np.zeros((self.n, 3))
         info = sphere_bie_solve_squirmer(self.ctx, s, v, w)
         return v, w, info
+
+    def laplace(self, op, q):
+        qq = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+        return sphere_bie_apply_laplace(self.ctx, op, qq, np.zeros_like(qq))
+
+    def mhd(self, H0, eta):
+        F, T, v, w = (np.zeros((self.n, 3)) for _ in range(4))
+        info = sphere_bie_solve_mhd(self.ctx, H0, eta, F, T, v, w)
+        return F, T, v, w, info
 
     def nodes(self):
         return sphere_bie_nodes(self.ctx)

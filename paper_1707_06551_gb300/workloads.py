@@ -199,3 +199,36 @@ def squirmers(n, p, seed, B1=1.0, beta=-3.0, radius_range=(1.0, 1.0)):
     ax /= np.linalg.norm(ax, axis=1, keepdims=True)
     w.update(axes=ax, B1=B1, B2=beta * B1)
     return w
+
+
+def lattice(m, q, poly=False):
+    """Cubic lattice of the operator-apply scaling tests (Sec. 6): m x m x m
+    unit cubes of side 2 with a sphere of radius r_v = 1 - 2^-q on every vertex
+    ((m+1)^3 spheres: 8, 27, 125, 729, 4913 for m = 1, 2, 4, 8, 16); minimum gap
+    2^(1-q).  poly=True adds a sphere at the centre of every face and one at
+    the centre of every cube (n = (m+1)^3 + 3 m^2 (m+1) + m^3: 15, 71, 429,
+    2969, 22065).  The face and centre radii are those of the holes of the
+    vertex packing scaled by r_v: r_f = (sqrt 2 - 1) r_v and
+    r_c = (2 - sqrt 2) r_v (as printed, (2 - sqrt 2) r_v on the faces would
+    overlap the vertex spheres at q = 4); the minimum gap is then 2^-q
+    (centre sphere to face sphere)."""
+    rv = 1.0 - 2.0 ** (-q)
+    g = np.arange(m + 1) * 2.0
+    cs = [np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)]
+    rs = [np.full(len(cs[0]), rv)]
+    if poly:
+        h = np.arange(m) * 2.0 + 1.0
+        faces = []
+        for ax in range(3):
+            # faces normal to axis ax: coordinate ax on the lattice planes, the others at cube centres
+            grids = [h, h, h]
+            grids[ax] = g
+            faces.append(np.stack(np.meshgrid(*grids, indexing="ij"), axis=-1).reshape(-1, 3))
+        faces = np.concatenate(faces)
+        cs.append(faces)
+        rs.append(np.full(len(faces), (math.sqrt(2.0) - 1.0) * rv))
+        cent = np.stack(np.meshgrid(h, h, h, indexing="ij"), axis=-1).reshape(-1, 3)
+        cs.append(cent)
+        rs.append(np.full(len(cent), (2.0 - math.sqrt(2.0)) * rv))
+    return dict(name=f"lattice_m{m}_q{q}_{'poly' if poly else 'mono'}", centres=np.concatenate(cs),
+                radii=np.concatenate(rs), m=m, q=q, poly=poly)

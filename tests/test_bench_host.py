@@ -119,3 +119,22 @@ def test_self_vsh_rate():
     assert r["gb_per_s"] == pytest.approx(2 * 3 * 61952 * 8 * 63 / 4.33e-3 / 1e9)
     assert bench.self_vsh_rate({"launches": {"self": 0}, "ms": {"self": 0.0}}, 10) is None
     assert bench.self_vsh_rate({"launches": {}, "ms": {}}, 10) is None
+
+
+def test_stage_rooflines_from_a_profile():
+    """Each stage's achieved rate is its algorithmic work over its profiled time."""
+    prof = {"ms": {"near": 10.0, "completion": 5.0, "arnoldi": 4.0, "self": 2.0, "precond": 3.0},
+            "launches": {"near": 50, "completion": 50, "self": 50, "precond": 40},
+            "arnoldi_vectors": 1000}
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops": 2000.0, "source": "measured"}
+    n, p, near, pairs = 256, 10, 1118, 559
+    r = bench.stage_rooflines(prof, n, p, near, pairs, 80.0, peaks)
+    npn = 242
+    assert r["near"]["achieved"] == pytest.approx(near * npn * 3 * 121 * 20 * 50 / 10e-3 / 1e12)
+    assert r["completion"]["achieved"] == pytest.approx(n * npn * n * 32 * 50 / 5e-3 / 1e12)
+    assert r["arnoldi"]["achieved"] == pytest.approx(1000 * 3 * n * npn * 8 / 4e-3 / 1e9)
+    assert r["arnoldi"]["frac"] == pytest.approx(r["arnoldi"]["achieved"] / 6000.0)
+    assert r["self"]["peak"] == pytest.approx(2000.0 * 1.1 / 2.25)
+    assert r["self"]["achieved"] == pytest.approx(3 * 2 * 726 * 726 * n * 50 / 2e-3 / 1e12)
+    assert r["precond"]["bytes_per_apply"] > pairs * 146 * 146 * 4
+    assert bench.stage_rooflines({"ms": {}, "launches": {}}, n, p, near, None, 80.0, peaks) == {}

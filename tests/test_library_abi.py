@@ -167,6 +167,8 @@ def test_every_context_entry_point_rejects_a_null_context(lib):
         "solve_resistance": lambda: L.sphere_bie_solve_resistance(None, buf, buf, None, None, buf, buf, None),
         "solve_porous": lambda: L.sphere_bie_solve_porous(None, None, None, buf, buf, None),
         "solve_squirmer": lambda: L.sphere_bie_solve_squirmer(None, buf, buf, buf, None),
+        "apply_laplace": lambda: L.sphere_bie_apply_laplace(None, 0, buf, buf),
+        "solve_mhd": lambda: L.sphere_bie_solve_mhd(None, buf, 0.5, buf, buf, buf, buf, None),
         "autotune": lambda: L.sphere_bie_autotune(None, 4, None),
         "profile": lambda: L.sphere_bie_profile(None, 1),
         "profile_read": lambda: L.sphere_bie_profile_read(None, None),

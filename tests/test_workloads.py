@@ -51,3 +51,24 @@ def test_resistance_256_close_pair_count():
 def test_small_suspension(seed):
     w = wl.small_suspension(12, 4, seed)
     assert _min_gap(w["centres"], w["radii"]) >= 0.05 - 1e-12
+
+
+@pytest.mark.parametrize("poly,counts", [(False, [8, 27, 125, 729, 4913]), (True, [15, 71, 429, 2969, 22065])])
+def test_lattice_sphere_counts_are_the_papers(poly, counts):
+    """Sec. 6 lists n_b = 8 ... 4913 (vertices) and 15 ... 22065 (with face and
+    centre spheres) for the lattices of 1 to 16 units per side."""
+    assert [len(wl.lattice(m, 4, poly)["radii"]) for m in (1, 2, 4, 8, 16)] == counts
+
+
+@pytest.mark.parametrize("q", [1, 4])
+def test_lattice_gaps(q):
+    """Vertex spheres of radius 1 - 2^-q, 2 apart: minimum gap 2^(1-q); with
+    the hole-sized face and centre spheres the minimum gap is 2^-q and no two
+    spheres overlap."""
+    for poly, gap in ((False, 2.0 ** (1 - q)), (True, 2.0 ** (-q))):
+        w = wl.lattice(3, q, poly)
+        c, a = w["centres"], w["radii"]
+        d = np.linalg.norm(c[:, None] - c[None], axis=2) - a[:, None] - a[None]
+        np.fill_diagonal(d, np.inf)
+        assert abs(d.min() - gap) < 1e-12
+        assert np.isclose(a.max(), 1 - 2.0 ** (-q))

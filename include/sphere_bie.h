@@ -94,6 +94,12 @@ typedef struct {
                                graph launch (a WHILE node over the Arnoldi iteration, no host
                                round trip per iteration); 0: the same device iteration stepped
                                from the host.  Profiling (sphere_bie_profile) always steps.    */
+    int near_scheme;        /* close pairs: 0 direct evaluation of the exterior expansions at the
+                               target nodes (Sec. 4.1); 1 the rotated, FFT-accelerated scheme of
+                               Sec. 4.2 (Fig. 2: source coefficients rotated to the pair's
+                               pole, evaluation on the target's pole-aligned grid, forward
+                               transform, rotation back), which projects the close-pair field
+                               onto degree <= p on the target sphere; p <= 16                */
 } sbie_opts;
 
 typedef struct {

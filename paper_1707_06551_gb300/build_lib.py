@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsphere_bie.so")
 SOURCES = ["tables.cu", "self.cu", "far.cu", "near.cu", "compl.cu", "blas.cu", "krylov.cu", "api.cu", "noalloc.cu",
-           "precond.cu", "mlp.cu", "selfgemm.cu", "probe.cu", "laplace.cu"]
+           "precond.cu", "mlp.cu", "selfgemm.cu", "probe.cu", "laplace.cu", "nearfft.cu"]
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
          "-Xcompiler", "-fPIC", "-diag-suppress", "1444", "-Xcompiler", "-Wno-deprecated-declarations"]
 

@@ -93,7 +93,8 @@ void free_all(sbie_ctx* c) {
                     c->d_srcf, c->d_in, c->d_out, c->d_tmp, c->d_tmp2, c->d_small, c->d_red, c->d_V, c->d_xsol,
                     c->d_rhs, c->d_res, c->d_prob_sph, c->d_sph_prob, c->d_node_prob, c->d_seg3, c->d_H, c->d_pvec,
                     c->d_ZS, c->d_ZA, c->d_modes, c->d_low, c->d_lowe, c->d_pz, c->d_ad, c->d_adi, c->d_vk,
-                    c->d_sq, c->d_lcoef};
+                    c->d_sq, c->d_lcoef, c->d_rotp, c->d_rotm, c->d_fgeo, c->d_fcoef, c->d_fchan, c->d_fblk,
+                    c->d_fiota};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (PrecState& P : c->prec)
@@ -111,6 +112,48 @@ void free_all(sbie_ctx* c) {
             cudaEventDestroy(pr.second);
         }
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+// Buffers and per-entry frames of the rotated close-pair scheme (Sec. 4.2): for
+// entry e (target i, source k = near_idx[e]) the frame's pole points from c_k to
+// c_i, (sin b cos a, sin b sin a, cos b); a = 0 on the polar axis.
+sbie_status setup_near_fft(sbie_ctx* c) {
+    const long long ne = c->n_near;
+    const int P1 = c->p + 1, S = P1 * P1;
+    std::vector<double> Mp, Mm;
+    rotx90_tables(c->p, Mp, Mm);
+    std::vector<double> geo((size_t)ne * 8, 0.0);
+    std::vector<int> iota((size_t)ne + 1);
+    for (long long q = 0; q <= ne; ++q) iota[q] = (int)q;
+    for (int i = 0; i < c->n; ++i)
+        for (int e = c->h_near_ptr[i]; e < c->h_near_ptr[i + 1]; ++e) {
+            const int k = c->h_near_idx[e];
+            const double vx = c->h_c[3 * i] - c->h_c[3 * k], vy = c->h_c[3 * i + 1] - c->h_c[3 * k + 1],
+                         vz = c->h_c[3 * i + 2] - c->h_c[3 * k + 2];
+            const double d = std::sqrt(vx * vx + vy * vy + vz * vz), rxy = std::sqrt(vx * vx + vy * vy);
+            double* g = geo.data() + 8 * (size_t)e;
+            g[0] = rxy > 0 ? vx / rxy : 1.0;   // cos a
+            g[1] = rxy > 0 ? vy / rxy : 0.0;   // sin a
+            g[2] = vz / d;                     // cos b
+            g[3] = rxy / d;                    // sin b
+            g[4] = d / c->h_a[k];
+            g[5] = c->h_a[i] / c->h_a[k];
+            g[6] = c->h_a[k];
+        }
+    const size_t Kt = (size_t)sh_count(c->p + 2);
+    bool ok = dmalloc(&c->d_rotp, Mp.size()) == cudaSuccess && dmalloc(&c->d_rotm, Mm.size()) == cudaSuccess &&
+              dmalloc(&c->d_fgeo, geo.size()) == cudaSuccess &&
+              dmalloc(&c->d_fcoef, (size_t)ne * 6 * S) == cudaSuccess &&
+              dmalloc(&c->d_fchan, (size_t)ne * Kt * kTracChannels) == cudaSuccess &&
+              dmalloc(&c->d_fblk, (size_t)ne * 6 * S) == cudaSuccess && dmalloc(&c->d_fiota, iota.size()) == cudaSuccess;
+    if (!ok) return fail(c, SBIE_ERR_OOM, "rotated close-pair buffers");
+    cudaError_t e = h2d(c->stream, c->d_rotp, Mp.data(), Mp.size());
+    if (e == cudaSuccess) e = h2d(c->stream, c->d_rotm, Mm.data(), Mm.size());
+    if (e == cudaSuccess) e = h2d(c->stream, c->d_fgeo, geo.data(), geo.size());
+    if (e == cudaSuccess) e = h2d(c->stream, c->d_fiota, iota.data(), iota.size());
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, SBIE_ERR_CUDA, std::string("rotated close pairs: ") + cudaGetErrorString(e));
+    return SBIE_OK;
 }
 
 // Far-field tilings found by sphere_bie_autotune, by (n, p, SM count, op, f32).
@@ -240,8 +283,13 @@ sbie_status apply_porous(sbie_ctx* c, int mode, const double* in, double* out) {
     }
     if (c->n_near > 0) {
         StageScope s(c, ST_NEAR);
-        CK(launch_near(c, Kern::S, f32, out));
-        CK(launch_near(c, Kern::D, f32, out));
+        if (c->opts.near_scheme == 1) {
+            CK(launch_near_fft(c, Kern::S, out));
+            CK(launch_near_fft(c, Kern::D, out));
+        } else {
+            CK(launch_near(c, Kern::S, f32, out));
+            CK(launch_near(c, Kern::D, f32, out));
+        }
     }
     StageScope s(c, ST_COMPL);
     CK(launch_finalize(c, SBIE_OP_POROUS, in, out));
@@ -308,7 +356,7 @@ sbie_status apply_dev(sbie_ctx* c, int op, int mode, const double* in, double* o
     }
     if (c->n_near > 0) {
         StageScope s(c, ST_NEAR);
-        CK(launch_near(c, k, f32, out));
+        CK(c->opts.near_scheme == 1 ? launch_near_fft(c, k, out) : launch_near(c, k, f32, out));
     }
     if (op == SBIE_OP_RESISTANCE || op == SBIE_OP_MOBILITY) {
         StageScope s(c, ST_COMPL);
@@ -908,6 +956,10 @@ sbie_status check_opts(const sbie_opts* opts) {
     if (!(opts->tol > 0.0) || opts->restart < 1 || opts->max_iter < 0)
         return fail(nullptr, SBIE_ERR_ARG, "need tol > 0, restart >= 1, max_iter >= 0");
     if (opts->use_graphs != 0 && opts->use_graphs != 1) return fail(nullptr, SBIE_ERR_ARG, "use_graphs must be 0 or 1");
+    if (opts->near_scheme != 0 && opts->near_scheme != 1)
+        return fail(nullptr, SBIE_ERR_ARG, "near_scheme must be 0 or 1");
+    if (opts->near_scheme == 1 && opts->p > 16)
+        return fail(nullptr, SBIE_ERR_ARG, "the rotated close-pair scheme (near_scheme 1) takes p <= 16");
     return SBIE_OK;
 }
 
@@ -1029,6 +1081,10 @@ sbie_status create_part(const sbie_opts& o, int n, const double* centres, const 
     if (e == cudaSuccess) e = launch_geometry(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bail(SBIE_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
+    if (o.near_scheme == 1 && c->n_near > 0) {
+        sbie_status s2 = setup_near_fft(c);
+        if (s2 != SBIE_OK) return bail(s2, c->err);
+    }
     c->err = "no error";
     *out = c;
     return SBIE_OK;
@@ -1720,6 +1776,8 @@ sbie_status sphere_bie_create_batch(int n_problems, const int* n_spheres, const 
         if (p_per_problem[q] < 1 || p_per_problem[q] > kMaxP) return fail(nullptr, SBIE_ERR_ARG, "p must be in [1, 24]");
         if (opts->use_learned_precond > 0 && p_per_problem[q] < kPrecL)
             return fail(nullptr, SBIE_ERR_ARG, "the pair preconditioner needs p >= 4");
+        if (opts->near_scheme == 1 && p_per_problem[q] > 16)
+            return fail(nullptr, SBIE_ERR_ARG, "the rotated close-pair scheme (near_scheme 1) takes p <= 16");
         ntot += n_spheres[q];
     }
     if (ntot > (1LL << 30)) return fail(nullptr, SBIE_ERR_ARG, "too many spheres");

@@ -55,6 +55,9 @@ constexpr TabLayout tab_layout(int p) {
 // Fills host table (size layout.total) for order p: Gauss-Legendre grid and
 // normalised associated Legendre functions (normalised recurrences).
 void build_tables(int p, std::vector<double>& host);
+// Degree blocks of f -> f o R_x(+90 deg) (Mp) and f -> f o R_x(-90 deg) (Mm) on
+// the spherical harmonics (tables.cu)
+void rotx90_tables(int p, std::vector<double>& Mp, std::vector<double>& Mm);
 
 // Real solid-harmonic basis used by the close-pair kernels: functions
 // Re/Im J_nm, J_nm = P_n^m(cos th) e^{i m ph} / r^{n+1} (no Condon-Shortley),
@@ -209,6 +212,14 @@ struct sbie_ctx {
     double* d_pz = nullptr;        // preconditioned vector (system level)
     double* d_sq = nullptr;        // [2][3N] squirmer operator: mu - P mu and P mu
     double* d_lcoef = nullptr;     // [n][p+1][p+1][2] scalar coefficients of a Laplace density (close pairs)
+    // rotated close-pair scheme (opts.near_scheme = 1), per entry e of the close-pair lists
+    double* d_rotp = nullptr;      // degree blocks of f -> f o R_x(+90)
+    double* d_rotm = nullptr;      // f -> f o R_x(-90)
+    double* d_fgeo = nullptr;      // [n_near][8] frame angles, distances, source radius
+    double* d_fcoef = nullptr;     // [n_near][3][p+1][p+1][2] rotated source coefficients
+    double* d_fchan = nullptr;     // [n_near][sh_count(p+2)][kTracChannels]
+    double* d_fblk = nullptr;      // [n_near][3][p+1][p+1][2] target-side blocks
+    int* d_fiota = nullptr;        // [n_near+1] 0, 1, ..., n_near
     double mag_eta = 0.0;          // eta of the magnetic operator (Eq. 5.13) of the running solve
     double t_create_ms = 0.0;      // wall time of create (grid, tables, close pairs, preconditioner)
     bool has_solution = false;     // d_xsol holds the density of the last solve
@@ -344,6 +355,12 @@ int far_f32_builds(int tpt, int* minb);
 // near.cu
 cudaError_t launch_near(sbie_ctx* c, Kern op, bool f32, double* out);
 cudaError_t launch_near_laplace(sbie_ctx* c, int mode, double* out);
+// channels (near_prep) of `count` coefficient sets, one per entry (iota = 0..count)
+cudaError_t launch_near_prep_pairs(sbie_ctx* c, int kind, int count, const double* coef, const int* iota,
+                                   double* chan);
+// nearfft.cu: close pairs by the rotated scheme of Sec. 4.2
+cudaError_t launch_near_fft(sbie_ctx* c, Kern op, double* out);
+size_t fft_eval_smem(int p, int kind);
 // laplace.cu
 cudaError_t laplace_apply(sbie_ctx* c, int mode, const double* q, double* out);
 cudaError_t launch_magnetic_finalize(sbie_ctx* c, double eta, const double* in, double* out);

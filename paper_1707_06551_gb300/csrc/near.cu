@@ -384,6 +384,22 @@ static cudaError_t run_eval(sbie_ctx* c, const NearArgs& A) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_near_prep_pairs(sbie_ctx* c, int kind, int count, const double* coef, const int* iota,
+                                   double* chan) {
+    NearArgs A;
+    A.n = count; A.p = c->p; A.npn = c->npn;
+    A.L = (kind == 2) ? c->p + 2 : c->p + 1;
+    A.nch = (kind == 2) ? kTracChannels : kVelChannels;
+    A.nchf = 0;
+    A.coef = coef; A.near_ptr = iota; A.chan = chan; A.chanf = nullptr;
+    const int K = sh_count(A.L);
+    const size_t sm = sizeof(double) * (size_t)(5 * K + 12 * K + K);
+    cudaError_t e = cudaFuncSetAttribute(near_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    near_prep_kernel<<<count, 256, sm, c->stream>>>(A, kind); ++c->n_launch;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_near_laplace(sbie_ctx* c, int mode, double* out) {
     if (c->n_near == 0) return cudaSuccess;
     NearArgs A;

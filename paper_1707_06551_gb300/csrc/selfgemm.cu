@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
     const int nk = E.k_blocks;
+    int issued = 0;  // K blocks whose copies the producer started
 
     if (warp == 0 && lane == 0) {
         // producer: TMA of the four tiles of each K block into the ring
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(128, 1)
             tma_load_2d(st + kTileA, &tmAl, kb * kBK, m0, fb);
             tma_load_2d(st + 2 * kTileA, &tmBh, kb * kBK, n0, fb);
             tma_load_2d(st + 2 * kTileA + kTileB, &tmBl, kb * kBK, n0, fb);
+            issued = kb + 1;
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: C = Ah Bh + Ah Bl + Al Bh, K = 8 per instruction
@@ -253,6 +255,11 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     if (!ok || failed) {
         if (threadIdx.x == 0) atomicExch(E.err, 1);
+        // let the copies still in flight land before the CTA exits (bounded):
+        // the last phase started on each ring slot
+        if (warp == 0 && lane == 0)
+            for (int kb = issued > kStages ? issued - kStages : 0; kb < issued; ++kb)
+                (void)mbar_wait(smem_addr(&full_bar[kb % kStages]), (kb / kStages) & 1);
     } else {
         const int r = m0 + warp * 32 + lane;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);

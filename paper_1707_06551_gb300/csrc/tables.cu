@@ -122,4 +122,79 @@ void build_tables(int p, std::vector<double>& h) {
     }
 }
 
+// Matrices of f -> f o R_x(+90 deg) and f -> f o R_x(-90 deg) on the spherical
+// harmonics of each degree n <= p (normalised, no Condon-Shortley phase,
+// Y_n^{-m} = conj(Y_n^m)): Y_n^m(R y) = sum_{m'} M_{m' m} Y_n^{m'}(y), m, m' in
+// [-n, n], with R_x(+90) (x, y, z) = (x, -z, y).  Computed by projection with the
+// quadrature of the order-p grid (exact for degree 2n <= 2p).  Layout: degree
+// blocks of (2n+1)^2 complex entries (re, im), row m' + n, column m + n, block n
+// starting at n (2n-1)(2n+1)/3.
+void rotx90_tables(int p, std::vector<double>& Mp, std::vector<double>& Mm) {
+    const TabLayout tl = tab_layout(p);
+    std::vector<double> h;
+    build_tables(p, h);
+    const int nlat = tl.nlat, nlon = tl.nlon, npn = tl.npn, L = p + 1;
+    auto at = [L](int m, int n) { return m * (L + 1) + n; };
+    size_t total = 0;
+    for (int n = 0; n <= p; ++n) total += (size_t)(2 * n + 1) * (2 * n + 1);
+    Mp.assign(2 * total, 0.0);
+    Mm.assign(2 * total, 0.0);
+    // Y_n^m (m >= 0) at the grid nodes and at the rotated nodes
+    struct C { double re, im; };
+    std::vector<C> Yg((size_t)npn * (p + 1) * (p + 1)), Yp(Yg.size()), Ym(Yg.size());
+    auto idx = [p](int q, int n, int m) { return ((size_t)q * (p + 1) + n) * (p + 1) + m; };
+    std::vector<double> P, S;
+    auto fill = [&](std::vector<C>& Y, int q, double x, double y, double z) {
+        const double s = std::sqrt(x * x + y * y);
+        const double ph = (s > 0.0) ? std::atan2(y, x) : 0.0;
+        legendre_col(p, z, s, P, S);
+        for (int n = 0; n <= p; ++n)
+            for (int m = 0; m <= n; ++m) {
+                const double pv = P[at(m, n)];
+                Y[idx(q, n, m)] = {pv * std::cos(m * ph), pv * std::sin(m * ph)};
+            }
+    };
+    for (int j = 0; j < nlat; ++j)
+        for (int k = 0; k < nlon; ++k) {
+            const int q = j * nlon + k;
+            const double st = h[tl.o_st + j], ct = h[tl.o_ct + j], cp = h[tl.o_cph + k], sp = h[tl.o_sph + k];
+            const double x = st * cp, y = st * sp, z = ct;
+            fill(Yg, q, x, y, z);
+            fill(Yp, q, x, -z, y);   // R_x(+90) y
+            fill(Ym, q, x, z, -y);   // R_x(-90) y
+        }
+    // Y_n^m for any sign of m from the stored m >= 0 values
+    auto Yv = [&](const std::vector<C>& Y, int q, int n, int m) -> C {
+        const C v = Y[idx(q, n, m < 0 ? -m : m)];
+        return m < 0 ? C{v.re, -v.im} : v;
+    };
+    size_t off = 0;
+    for (int n = 0; n <= p; ++n) {
+        const int w = 2 * n + 1;
+        for (int mr = -n; mr <= n; ++mr)
+            for (int mc = -n; mc <= n; ++mc) {
+                double pr = 0, pi = 0, mr_ = 0, mi = 0;
+                for (int j = 0; j < nlat; ++j) {
+                    const double wj = h[tl.o_w + j];
+                    for (int k = 0; k < nlon; ++k) {
+                        const int q = j * nlon + k;
+                        const C g = Yv(Yg, q, n, mr);  // conj taken below
+                        const C a = Yv(Yp, q, n, mc), b = Yv(Ym, q, n, mc);
+                        // a conj(g), b conj(g)
+                        pr += wj * (a.re * g.re + a.im * g.im);
+                        pi += wj * (a.im * g.re - a.re * g.im);
+                        mr_ += wj * (b.re * g.re + b.im * g.im);
+                        mi += wj * (b.im * g.re - b.re * g.im);
+                    }
+                }
+                const size_t e = off + (size_t)(mr + n) * w + (mc + n);
+                Mp[2 * e] = pr;
+                Mp[2 * e + 1] = pi;
+                Mm[2 * e] = mr_;
+                Mm[2 * e + 1] = mi;
+            }
+        off += (size_t)w * w;
+    }
+}
+
 }  // namespace sbie

@@ -29,7 +29,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("eta", ctypes.c_double), ("prec", ctypes.c_int), ("tol", ctypes.c_double),
                 ("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("use_learned_precond", ctypes.c_int),
                 ("mlp_weights_path", ctypes.c_char_p), ("mem_kind", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("use_graphs", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("near_scheme", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -156,11 +156,13 @@ def sphere_bie_default_opts():
     return o
 
 
-def make_opts(p, eta=1.0, prec=SBIE_FP64, tol=1e-8, restart=60, max_iter=600, mem_kind=0, stream=None, graphs=True):
+def make_opts(p, eta=1.0, prec=SBIE_FP64, tol=1e-8, restart=60, max_iter=600, mem_kind=0, stream=None, graphs=True,
+              near_scheme=0):
     o = sphere_bie_default_opts()
     o.p, o.eta, o.prec, o.tol, o.restart, o.max_iter, o.mem_kind = p, eta, prec, tol, restart, max_iter, mem_kind
     o.stream = stream
     o.use_graphs = 1 if graphs else 0
+    o.near_scheme = int(near_scheme)
     return o
 
 
@@ -368,9 +370,9 @@ class SphereBIE:
     `batch=[(centres, radii, p), ...]` it holds a batch of problems."""
 
     def __init__(self, centres=None, radii=None, p=None, eta=1.0, prec=SBIE_FP64, tol=1e-8, restart=60, max_iter=600,
-                 batch=None, precond=0, weights=None, graphs=True):
+                 batch=None, precond=0, weights=None, graphs=True, near_scheme=0):
         self.opts = make_opts(p if p is not None else batch[0][2], eta, prec, tol, restart, max_iter, 0,
-                              graphs=graphs)
+                              graphs=graphs, near_scheme=near_scheme)
         self.opts.use_learned_precond = precond
         self._wpath = None if weights is None else str(weights).encode()
         self.opts.mlp_weights_path = self._wpath

@@ -61,7 +61,7 @@ def parse():
                     help="two-sphere configurations the pair network is trained on "
                          "(default 4096; 100000 for dense_1024, 20000 for large_4096)")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "batched_512", "dense_1024", "large_4096", "lattice"],
+                    choices=[WORKLOAD, "batched_512", "dense_1024", "large_4096", "lattice", "near_schemes"],
                     help="the other configurations print their own JSON line (not the headline)")
     return ap.parse_args()
 
@@ -562,9 +562,58 @@ def run_lattice(args, sb, torch, wl, local):
             "series": series}
 
 
+def run_near_schemes(args, sb, torch, wl, local):
+    """Close-pair stage of one FP64 operator apply on dense_1024 (1,024
+    spheres, 13,940 directed close pairs) by the direct evaluation at the
+    target nodes (near_scheme 0) and by the rotated, FFT-accelerated scheme of
+    Sec. 4.2 (near_scheme 1), for p = 4 ... 16 and the three layer operators.
+    Stage times are CUDA events of the library's profiler (mean of 3 applies
+    after one warm-up); `rel_diff` is the largest difference of the two
+    schemes' applies relative to the largest value (the rotated scheme
+    projects each close-pair field onto degree <= p on the target sphere)."""
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream()
+    w = wl.dense_1024()
+    rows = []
+    for p in (4, 6, 8, 10, 12, 14, 16):
+        npn = (p + 1) * (2 * p + 2)
+        x = torch.randn((len(w["radii"]) * npn, 3), dtype=torch.float64, device=dev,
+                        generator=torch.Generator(device=dev).manual_seed(p))
+        rec = {"p": p}
+        outs = {}
+        for scheme in (0, 1):
+            o = sb.make_opts(p, prec=sb.SBIE_FP64, mem_kind=1, stream=stream.cuda_stream, near_scheme=scheme)
+            ctx = sb.sphere_bie_create(w["centres"], w["radii"], o)
+            for op in ("S", "D", "K"):
+                y = torch.zeros_like(x)
+                sb.sphere_bie_apply_operator(ctx, op, x, y)
+                torch.cuda.synchronize(dev)
+                sb.sphere_bie_profile(ctx, 1)
+                for _ in range(3):
+                    sb.sphere_bie_apply_operator(ctx, op, x, y)
+                prof = sb.sphere_bie_profile_read(ctx)
+                sb.sphere_bie_profile(ctx, 0)
+                rec[f"{op}_near_ms_{'rotated' if scheme else 'direct'}"] = prof["ms"]["near"] / 3
+                outs[(scheme, op)] = y.clone()
+            sb.sphere_bie_destroy(ctx)
+        for op in ("S", "D", "K"):
+            a, b = outs[(0, op)], outs[(1, op)]
+            rec[f"{op}_rel_diff"] = float((a - b).abs().max() / a.abs().max())
+            rec[f"{op}_speedup"] = rec[f"{op}_near_ms_direct"] / rec[f"{op}_near_ms_rotated"]
+        rows.append(rec)
+        del x, outs
+    return {"metric": "close-pair stage time per FP64 operator apply, direct vs rotated scheme", "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "near_schemes", "geometry": "dense_1024", "spheres": len(w["radii"]),
+                       "p": [r["p"] for r in rows]},
+            "rows": rows}
+
+
 def run_workload(args, sb, torch, wl, local):
     if args.workload == "lattice":
         return run_lattice(args, sb, torch, wl, local)
+    if args.workload == "near_schemes":
+        return run_near_schemes(args, sb, torch, wl, local)
     if args.workload == "batched_512":
         return run_batched(args, sb, torch, wl, local)
     if args.workload == "dense_1024":

@@ -3,10 +3,13 @@
 // geometry of a close pair (target offset in the pair frame, source radius,
 // target radius; standardised) to its standardised low-mode interaction block.
 // Weights are kept in FP32 (Adam) and used in BF16 by the forward and backward
-// passes, which accumulate in FP32.  Hand-written kernels: one tiled GEMM
-// template (both operands row-major, either transposed, float or BF16) with
-// fused bias / tanh / tanh-derivative epilogues, column sums, the loss and
-// Adam.
+// passes, which accumulate in FP32.  Every layer's GEMM (forward, weight
+// gradient, input gradient) runs on the tensor cores (tc_gemm_tf32 of
+// selfgemm.cu: tcgen05, 3xTF32 -- the BF16 weights are exact in TF32, the FP32
+// activations and gradients are split into TF32 high parts and remainders),
+// with the bias / tanh / tanh-derivative epilogues fused.  Here: the operand
+// packing (K-major TF32 pairs, zero-padded, transposed where the product needs
+// it), column sums, the loss and Adam.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -31,73 +34,57 @@ __device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16* p) {
     return __bfloat162float(*p);
 }
 
-enum Epi { EPI_NONE = 0, EPI_BIAS = 1, EPI_BIAS_TANH = 2, EPI_DTANH = 3 };
+// Operand packing for tc_gemm_tf32: dst [rows][Kpad] (TF32 high part, and the
+// remainder when lo is given), dst[r][k] = src[r lds + k] for k < K, zero for
+// K <= k < Kpad.
+template <typename T>
+__global__ void pack_kernel(const T* __restrict__ src, long long lds, int rows, int K, int Kpad,
+                            float* __restrict__ hi, float* __restrict__ lo) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)rows * Kpad) return;
+    const long long r = i / Kpad;
+    const int k = (int)(i - r * Kpad);
+    const float v = k < K ? ld(src + r * lds + k) : 0.f;
+    const float h = tf32_hi(v);
+    hi[i] = h;
+    if (lo) lo[i] = v - h;
+}
 
-// C[M][N] = sum_k A(m, k) B(k, n) (+ epilogue).  A(m, k) = TA ? A[k lda + m]
-// : A[m lda + k]; B(k, n) = TB ? B[n ldb + k] : B[k ldb + n].  64 x 64 tiles,
-// 256 threads, 4 x 4 outputs per thread, K step 16.  EPI_DTANH multiplies by
-// (1 - G[m][n]^2) (the tanh derivative of the layer's output G).
-template <typename TA_, typename TB_, bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const TA_* __restrict__ A, int lda,
-                                                   const TB_* __restrict__ B, int ldb, const float* __restrict__ bias,
-                                                   const float* __restrict__ G, float* __restrict__ C) {
-    __shared__ float As[16][64 + 1];
-    __shared__ float Bs[16][64 + 1];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-            int kk = e / 64, mm = e % 64;
-            int m = m0 + mm, k = k0 + kk;
-            float va = 0.f;
-            if (m < M && k < K) va = TA ? ld(A + (size_t)k * lda + m) : ld(A + (size_t)m * lda + k);
-            As[kk][mm] = va;
-            int n = n0 + mm;
-            float vb = 0.f;
-            if (n < N && k < K) vb = TB ? ld(B + (size_t)n * ldb + k) : ld(B + (size_t)k * ldb + n);
-            Bs[kk][mm] = vb;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
+// Transposed packing through 32 x 32 shared-memory tiles: dst[r][k] =
+// src[k lds + r] for r < rows, k < K (src has K rows of at least `rows` values).
+template <typename T>
+__global__ void pack_t_kernel(const T* __restrict__ src, long long lds, int rows, int K, int Kpad,
+                              float* __restrict__ hi, float* __restrict__ lo) {
+    __shared__ float tile[32][33];
+    const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    for (int j = ty; j < 32; j += 8) {
+        const int k = k0 + j, r = r0 + tx;
+        tile[j][tx] = (k < K && r < rows) ? ld(src + (long long)k * lds + r) : 0.f;
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int m = m0 + ty * 4 + i;
-        if (m >= M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int n = n0 + tx * 4 + j;
-            if (n >= N) continue;
-            float v = acc[i][j];
-            if (EPI == EPI_BIAS || EPI == EPI_BIAS_TANH) v += bias[n];
-            if (EPI == EPI_BIAS_TANH) v = tanhf(v);
-            if (EPI == EPI_DTANH) {
-                float g = G[(size_t)m * N + n];
-                v *= 1.f - g * g;
-            }
-            C[(size_t)m * N + n] = v;
-        }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int r = r0 + j, k = k0 + tx;
+        if (r >= rows || k >= Kpad) continue;
+        const float v = tile[tx][j];
+        const float h = tf32_hi(v);
+        hi[(long long)r * Kpad + k] = h;
+        if (lo) lo[(long long)r * Kpad + k] = v - h;
     }
 }
 
-template <typename TA_, typename TB_, bool TA, bool TB, int EPI>
-cudaError_t gemm(cudaStream_t s, int M, int N, int K, const TA_* A, int lda, const TB_* B, int ldb, const float* bias,
-                 const float* G, float* C) {
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
-    gemm_kernel<TA_, TB_, TA, TB, EPI><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, bias, G, C);
+inline int pad32(int k) { return (k + 31) / 32 * 32; }
+
+template <typename T>
+cudaError_t pack(cudaStream_t s, const T* src, long long ld, int rows, int K, int Kpad, float* hi, float* lo) {
+    const long long tot = (long long)rows * Kpad;
+    pack_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, ld, rows, K, Kpad, hi, lo);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t pack_t(cudaStream_t s, const T* src, long long ld, int rows, int K, int Kpad, float* hi, float* lo) {
+    dim3 grid((rows + 31) / 32, (Kpad + 31) / 32);
+    pack_t_kernel<T><<<grid, 256, 0, s>>>(src, ld, rows, K, Kpad, hi, lo);
     return cudaGetLastError();
 }
 
@@ -176,20 +163,48 @@ MlpLayout mlp_layout() {
     return L;
 }
 
-// Device workspace for a batch of up to `cap` rows.
+// Device workspace for a batch of up to `cap` rows; `train` adds the
+// gradients and the operand space of the backward GEMMs.
 struct MlpWork {
     int cap = 0;
     float* h[4] = {nullptr, nullptr, nullptr, nullptr};  // layer outputs (h[3] = network output)
     float* d[4] = {nullptr, nullptr, nullptr, nullptr};  // gradients w.r.t. layer outputs
     double* partial = nullptr;
-    cudaError_t alloc(int c) {
+    float* pa = nullptr;  // A operand: high parts, then remainders
+    float* pb = nullptr;  // B operand: high parts, then remainders
+    size_t na = 0, nb = 0;
+    int* err = nullptr;   // bounded-wait flag of the tensor-core GEMMs
+    cudaError_t alloc(int c, bool train) {
         cap = c;
         MlpLayout L = mlp_layout();
         for (int l = 0; l < 4; ++l) {
             if (cudaMalloc(&h[l], sizeof(float) * (size_t)c * L.dout[l]) != cudaSuccess) return cudaErrorMemoryAllocation;
-            if (cudaMalloc(&d[l], sizeof(float) * (size_t)c * L.dout[l]) != cudaSuccess) return cudaErrorMemoryAllocation;
+            if (train && cudaMalloc(&d[l], sizeof(float) * (size_t)c * L.dout[l]) != cudaSuccess)
+                return cudaErrorMemoryAllocation;
         }
+        // forward: A = layer input [c][din], B = W^T [dout][din]; backward:
+        // A = dZ [c][dout] or input^T [din][c], B = W [din][dout] or dZ^T [dout][c]
+        for (int l = 0; l < 4; ++l) {
+            na = std::max(na, (size_t)c * pad32(L.din[l]));
+            nb = std::max(nb, (size_t)L.dout[l] * pad32(L.din[l]));
+            if (train) {
+                na = std::max(na, std::max((size_t)c * pad32(L.dout[l]), (size_t)L.din[l] * pad32(c)));
+                nb = std::max(nb, std::max((size_t)L.din[l] * pad32(L.dout[l]), (size_t)L.dout[l] * pad32(c)));
+            }
+        }
+        if (cudaMalloc(&pa, sizeof(float) * 2 * na) != cudaSuccess) return cudaErrorMemoryAllocation;
+        if (cudaMalloc(&pb, sizeof(float) * 2 * nb) != cudaSuccess) return cudaErrorMemoryAllocation;
+        if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return cudaErrorMemoryAllocation;
+        if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess) return cudaErrorMemoryAllocation;
         return cudaMalloc(&partial, sizeof(double) * 1024);
+    }
+    // cudaErrorLaunchTimeout when a GEMM's bounded wait ran out
+    cudaError_t check(cudaStream_t s) const {
+        int flag = 0;
+        cudaError_t e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && flag) e = cudaErrorLaunchTimeout;
+        return e;
     }
     void release() {
         for (int l = 0; l < 4; ++l) {
@@ -197,23 +212,30 @@ struct MlpWork {
             if (d[l]) cudaFree(d[l]);
             h[l] = d[l] = nullptr;
         }
-        if (partial) cudaFree(partial);
+        for (void* p : {(void*)partial, (void*)pa, (void*)pb, (void*)err})
+            if (p) cudaFree(p);
         partial = nullptr;
+        pa = pb = nullptr;
+        err = nullptr;
     }
 };
 
-// Forward pass of B rows X [B][5] with BF16 weights wb (FP32 biases from w).
+// Forward pass of B rows X [B][5] with BF16 weights wb (FP32 biases from w):
+// h_l = tanh(h_{l-1} W_l + b_l), the last layer without tanh.
 static cudaError_t forward(cudaStream_t s, const MlpLayout& L, const float* w, const __nv_bfloat16* wb, int B,
                            const float* X, MlpWork& ws) {
-    cudaError_t e = gemm<float, __nv_bfloat16, false, false, EPI_BIAS_TANH>(s, B, L.dout[0], L.din[0], X, L.din[0],
-                                                                            wb + L.w[0], L.dout[0], w + L.b[0], nullptr,
-                                                                            ws.h[0]);
-    for (int l = 1; l < 3 && e == cudaSuccess; ++l)
-        e = gemm<float, __nv_bfloat16, false, false, EPI_BIAS_TANH>(s, B, L.dout[l], L.din[l], ws.h[l - 1], L.din[l],
-                                                                    wb + L.w[l], L.dout[l], w + L.b[l], nullptr, ws.h[l]);
-    if (e == cudaSuccess)
-        e = gemm<float, __nv_bfloat16, false, false, EPI_BIAS>(s, B, L.dout[3], L.din[3], ws.h[2], L.din[3], wb + L.w[3],
-                                                               L.dout[3], w + L.b[3], nullptr, ws.h[3]);
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+        const int din = L.din[l], dout = L.dout[l], Kp = pad32(din);
+        e = pack(s, l == 0 ? X : ws.h[l - 1], din, B, din, Kp, ws.pa, ws.pa + ws.na);
+        if (e == cudaSuccess) e = pack_t(s, wb + L.w[l], dout, dout, din, Kp, ws.pb, (float*)nullptr);
+        TcEpi ep;
+        ep.C = ws.h[l];
+        ep.ldc = dout;
+        ep.bias = w + L.b[l];
+        ep.mode = l < 3 ? TcEpi::kBiasTanh : TcEpi::kBias;
+        if (e == cudaSuccess) e = tc_gemm_tf32(s, B, dout, Kp, ws.pa, ws.pa + ws.na, ws.pb, nullptr, ep, ws.err);
+    }
     return e;
 }
 
@@ -226,18 +248,33 @@ static cudaError_t backward(cudaStream_t s, const MlpLayout& L, const __nv_bfloa
     *nblk = blocks;
     loss_kernel<<<blocks, 256, 0, s>>>(total, 1.f / (float)total, ws.h[3], T, ws.d[3], ws.partial);
     cudaError_t e = cudaGetLastError();
+    const int Kb = pad32(B);
     for (int l = 3; l >= 0 && e == cudaSuccess; --l) {
         const float* Ain = l == 0 ? X : ws.h[l - 1];
-        // dW_l = A_in^T dZ_l ; db_l = colsum(dZ_l)
-        e = gemm<float, float, true, false, EPI_NONE>(s, L.din[l], L.dout[l], B, Ain, L.din[l], ws.d[l], L.dout[l],
-                                                      nullptr, nullptr, grad + L.w[l]);
+        const int din = L.din[l], dout = L.dout[l];
+        // dW_l = A_in^T dZ_l  (M = din, N = dout, K = B)
+        e = pack_t(s, Ain, din, din, B, Kb, ws.pa, ws.pa + ws.na);
+        if (e == cudaSuccess) e = pack_t(s, ws.d[l], dout, dout, B, Kb, ws.pb, ws.pb + ws.nb);
+        TcEpi gw;
+        gw.C = grad + L.w[l];
+        gw.ldc = dout;
+        if (e == cudaSuccess) e = tc_gemm_tf32(s, din, dout, Kb, ws.pa, ws.pa + ws.na, ws.pb, ws.pb + ws.nb, gw, ws.err);
         if (e != cudaSuccess) break;
-        colsum_kernel<<<(L.dout[l] + 255) / 256, 256, 0, s>>>(B, L.dout[l], ws.d[l], grad + L.b[l]);
+        // db_l = colsum(dZ_l)
+        colsum_kernel<<<(dout + 255) / 256, 256, 0, s>>>(B, dout, ws.d[l], grad + L.b[l]);
         e = cudaGetLastError();
         if (l == 0 || e != cudaSuccess) break;
-        // dZ_{l-1} = (dZ_l W_l^T) (1 - h_{l-1}^2)
-        e = gemm<float, __nv_bfloat16, false, true, EPI_DTANH>(s, B, L.din[l], L.dout[l], ws.d[l], L.dout[l],
-                                                               wb + L.w[l], L.dout[l], nullptr, ws.h[l - 1], ws.d[l - 1]);
+        // dZ_{l-1} = (dZ_l W_l^T) (1 - h_{l-1}^2)  (M = B, N = din, K = dout)
+        const int Kd = pad32(dout);
+        e = pack(s, ws.d[l], dout, B, dout, Kd, ws.pa, ws.pa + ws.na);
+        if (e == cudaSuccess) e = pack(s, wb + L.w[l], dout, din, dout, Kd, ws.pb, (float*)nullptr);
+        TcEpi gz;
+        gz.C = ws.d[l - 1];
+        gz.ldc = din;
+        gz.G = ws.h[l - 1];
+        gz.ldg = din;
+        gz.mode = TcEpi::kDTanh;
+        if (e == cudaSuccess) e = tc_gemm_tf32(s, B, din, Kd, ws.pa, ws.pa + ws.na, ws.pb, nullptr, gz, ws.err);
     }
     return e;
 }
@@ -266,7 +303,7 @@ cudaError_t mlp_gradients(const float* h_params, int n, const float* h_X, const 
     if (e == cudaSuccess) e = cudaMalloc(&wb, sizeof(__nv_bfloat16) * L.total);
     if (e == cudaSuccess) e = cudaMalloc(&X, sizeof(float) * (size_t)n * kMlpIn);
     if (e == cudaSuccess) e = cudaMalloc(&T, sizeof(float) * (size_t)n * kMlpOut);
-    if (e == cudaSuccess) e = ws.alloc(n);
+    if (e == cudaSuccess) e = ws.alloc(n, true);
     if (e == cudaSuccess) e = cudaMemcpyAsync(w, h_params, sizeof(float) * L.total, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(X, h_X, sizeof(float) * (size_t)n * kMlpIn, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(T, h_T, sizeof(float) * (size_t)n * kMlpOut, cudaMemcpyHostToDevice, s);
@@ -277,6 +314,7 @@ cudaError_t mlp_gradients(const float* h_params, int n, const float* h_X, const 
     if (e == cudaSuccess) e = forward(s, L, w, wb, n, X, ws);
     if (e == cudaSuccess) e = backward(s, L, wb, n, X, T, ws, g, &nblk);
     if (e == cudaSuccess) *loss = read_loss(s, ws, nblk, (long long)n * kMlpOut, &e);
+    if (e == cudaSuccess) e = ws.check(s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_grad, g, sizeof(float) * L.total, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     ws.release();
@@ -290,7 +328,7 @@ cudaError_t mlp_forward_dev(cudaStream_t s, const float* w, const __nv_bfloat16*
     MlpLayout L = mlp_layout();
     MlpWork ws;
     const int chunk = 4096;
-    cudaError_t e = ws.alloc(std::min(n, chunk));
+    cudaError_t e = ws.alloc(std::min(n, chunk), false);
     for (int r = 0; r < n && e == cudaSuccess; r += chunk) {
         int b = std::min(chunk, n - r);
         e = forward(s, L, w, wb, b, X + (size_t)r * kMlpIn, ws);
@@ -298,7 +336,7 @@ cudaError_t mlp_forward_dev(cudaStream_t s, const float* w, const __nv_bfloat16*
             e = cudaMemcpyAsync(Y + (size_t)r * kMlpOut, ws.h[3], sizeof(float) * (size_t)b * kMlpOut,
                                 cudaMemcpyDeviceToDevice, s);
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = ws.check(s);
     ws.release();
     return e;
 }
@@ -332,7 +370,7 @@ cudaError_t mlp_train(const MlpTrainOpts& o, int n, const float* h_X, const floa
     if (e == cudaSuccess) e = cudaMalloc(&Xb, sizeof(float) * (size_t)B * kMlpIn);
     if (e == cudaSuccess) e = cudaMalloc(&Tb, sizeof(float) * (size_t)B * kMlpOut);
     if (e == cudaSuccess) e = cudaMalloc(&idx, sizeof(int) * (size_t)n);
-    if (e == cudaSuccess) e = ws.alloc(B);
+    if (e == cudaSuccess) e = ws.alloc(B, true);
     if (e == cudaSuccess) e = cudaMemcpyAsync(w, h_params, sizeof(float) * L.total, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(m1, 0, sizeof(float) * L.total, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(m2, 0, sizeof(float) * L.total, s);
@@ -368,6 +406,7 @@ cudaError_t mlp_train(const MlpTrainOpts& o, int n, const float* h_X, const floa
         }
         history.push_back(ep_loss);
     }
+    if (e == cudaSuccess) e = ws.check(s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_params, w, sizeof(float) * L.total, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     ws.release();

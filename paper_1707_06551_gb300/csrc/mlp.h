@@ -34,4 +34,26 @@ cudaError_t mlp_gradients(const float* h_params, int n, const float* h_X, const 
 cudaError_t mlp_to_bf16(cudaStream_t s, const float* w, __nv_bfloat16* wb);
 cudaError_t mlp_forward_dev(cudaStream_t s, const float* w, const __nv_bfloat16* wb, int n, const float* X, float* Y);
 
+// TF32 high part of x: round to nearest (ties away) at 10 explicit mantissa
+// bits; x - tf32_hi(x) is exact in FP32.
+__device__ __forceinline__ float tf32_hi(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// Epilogue of tc_gemm_tf32: C[m][n] = sum_k A[m][k] B[n][k], then + bias[n]
+// (kBias), tanh(. + bias[n]) (kBiasTanh) or x (1 - G[m][n]^2) (kDTanh).
+struct TcEpi {
+    enum Mode { kNone = 0, kBias = 1, kBiasTanh = 2, kDTanh = 3 };
+    float* C = nullptr;
+    long long ldc = 0;
+    const float* bias = nullptr;
+    const float* G = nullptr;
+    long long ldg = 0;
+    int mode = kNone;
+};
+// 3xTF32 GEMM on the tensor cores (selfgemm.cu); *err is set to 1 when one of
+// its bounded waits runs out.
+cudaError_t tc_gemm_tf32(cudaStream_t s, int M, int N, int Kpad, const float* Ahi, const float* Alo,
+                         const float* Bhi, const float* Blo, const TcEpi& ep, int* err);
+
 }  // namespace sbie

@@ -22,6 +22,8 @@
 // Stage (3) projects the close-pair field onto degree <= p on the target
 // sphere, as the paper's algorithm does.  Per pair the work is O(p^3) (one
 // CTA per pair, FP64), against O(p^4) for the direct evaluation of near.cu.
+#include <algorithm>
+
 #include "common.h"
 
 namespace sbie {
@@ -29,7 +31,7 @@ namespace sbie {
 namespace {
 
 struct FftArgs {
-    int p, P1, L, K, nch, npn, nlat, nlon, kind, n_near;
+    int p, P1, L, K, nch, npn, nlat, nlon, kind, n_near, G;  // G: discs evaluated together
     TabLayout tl;
     const double* tab;
     const double* rotp;   // f -> f o R_x(+90) per degree
@@ -152,19 +154,14 @@ __global__ void fft_rotate_kernel(FftArgs A) {
     for (int q = threadIdx.x; q < 6 * S; q += blockDim.x) dst[q] = cout[q];
 }
 
-// cos / sin of (m k mod nlon) 2 pi / nlon for the Fourier sums over the
-// nodes of a disc (orders up to L = p + 2 > p, beyond the tables)
-__device__ __forceinline__ void phase(const double* cs, const double* sn, int nlon, int m, int k, double& c,
-                                      double& s) {
-    const int q = (m * k) % nlon;
-    c = cs[q];
-    s = sn[q];
-}
-
-// stages (2) and (3): one CTA per entry e
+// stages (2) and (3): one CTA per entry e; KIND 0 = S, 1 = D (velocity
+// channels), 2 = traction of S.  The discs are evaluated G at a time so that
+// every thread has a node.
+template <int KIND>
 __global__ void fft_eval_kernel(FftArgs A) {
+    constexpr int NCH = KIND == 2 ? kTracChannels : kVelChannels;
     const int e = blockIdx.x;
-    const int p = A.p, P1 = A.P1, L = A.L, K = A.K, nch = A.nch, npn = A.npn, nlat = A.nlat, nlon = A.nlon;
+    const int P1 = A.P1, L = A.L, K = A.K, npn = A.npn, nlat = A.nlat, nlon = A.nlon, G = A.G;
     const TabLayout& tl = A.tl;
     const double* tab = A.tab;
     const double* ct = tab + tl.o_ct;
@@ -179,9 +176,9 @@ __global__ void fft_eval_kernel(FftArgs A) {
     const double* mSt = tab + tl.o_mS;
     const int S = P1 * P1;
     extern __shared__ double sm[];
-    double* ch = sm;                                  // [K][nch]
-    double* Ad = ch + (size_t)K * nch;                // [L+1][nch][2] one disc
-    double* U = Ad + (size_t)(L + 1) * nch * 2;       // [3][npn] spherical components of the samples
+    double* ch = sm;                                  // [K][NCH]
+    double* Ad = ch + (size_t)K * NCH;                // [G][L+1][NCH][2] a group of discs
+    double* U = Ad + (size_t)G * (L + 1) * NCH * 2;   // [3][npn] spherical components of the samples
     double* Fh = U + 3 * npn;                         // [3][nlat][P1][2]
     double* cu = Fh + 3 * nlat * P1 * 2;              // [3][P1][P1][2]
     double* cv = cu + 6 * S;                          // [3][P1][P1][2]
@@ -191,20 +188,22 @@ __global__ void fft_eval_kernel(FftArgs A) {
     double* ps = pc + nlon;
     const int tid = threadIdx.x, bd = blockDim.x;
     const double* g = A.geo + 8 * (size_t)e;
-    const double D = g[4], rho = g[5], scale = A.kind == 0 ? g[6] : 1.0;  // S scales by the source radius
-    for (int q = tid; q < K * nch; q += bd) ch[q] = A.chan[(size_t)e * K * nch + q];
+    const double D = g[4], rho = g[5], scale = KIND == 0 ? g[6] : 1.0;  // S scales by the source radius
+    for (int q = tid; q < K * NCH; q += bd) ch[q] = A.chan[(size_t)e * K * NCH + q];
     for (int q = tid; q < nlon; q += bd) {
         pc[q] = cph[q];
         ps[q] = sph[q];
     }
-    // (2) disc by disc
-    for (int j = 0; j < nlat; ++j) {
-        const double zj = D + rho * ct[j], pj = rho * st[j];
-        const double rj = sqrt(zj * zj + pj * pj), tj = zj / rj, sj = pj / rj, ir = 1.0 / rj;
+    // (2) disc by disc, G discs at a time
+    for (int j0 = 0; j0 < nlat; j0 += G) {
+        const int gs = min(G, nlat - j0);
         __syncthreads();
-        // A_hm = sum_n (ch_re - i ch_im)(n, m, h) P_n^m(t) / r^{n+1}
-        for (int q = tid; q < (L + 1) * nch; q += bd) {
-            const int m = q / nch, h = q - m * nch;
+        // A_hm = sum_n (ch_re - i ch_im)(n, m, h) P_n^m(t) / r^{n+1}, t and r of the disc
+        for (int q = tid; q < gs * (L + 1) * NCH; q += bd) {
+            const int jj = q / ((L + 1) * NCH), r = q - jj * (L + 1) * NCH, m = r / NCH, h = r - m * NCH;
+            const int j = j0 + jj;
+            const double zj = D + rho * ct[j], pj = rho * st[j];
+            const double rj = sqrt(zj * zj + pj * pj), tj = zj / rj, sj = pj / rj, ir = 1.0 / rj;
             double qmm = ir;  // (2m-1)!! s^m / r^{m+1}
             for (int k = 1; k <= m; ++k) qmm *= (2.0 * k - 1.0) * sj * ir;
             double q0 = 0.0, q1 = qmm, ar = 0.0, ai = 0.0;
@@ -218,30 +217,35 @@ __global__ void fft_eval_kernel(FftArgs A) {
                     q1 = qn;
                 }
                 const int ire = sh_index(L, n, m, 0);
-                ar = fma(ch[(size_t)ire * nch + h], qn, ar);
-                if (m >= 1) ai = fma(-ch[(size_t)(ire + 1) * nch + h], qn, ai);
+                ar = fma(ch[(size_t)ire * NCH + h], qn, ar);
+                if (m >= 1) ai = fma(-ch[(size_t)(ire + 1) * NCH + h], qn, ai);
             }
             Ad[2 * q] = ar;
             Ad[2 * q + 1] = ai;
         }
         __syncthreads();
-        // channel values at the disc's nodes, combined into the velocity or traction
-        for (int k = tid; k < nlon; k += bd) {
-            double val[26];
-            for (int h = 0; h < nch; ++h) val[h] = 0.0;
+        // channel values at the group's nodes (Fourier sums over the orders),
+        // combined into the velocity or traction
+        for (int qq = tid; qq < gs * nlon; qq += bd) {
+            const int jj = qq / nlon, k = qq - jj * nlon, j = j0 + jj;
+            const double* Aj = Ad + (size_t)jj * (L + 1) * NCH * 2;
+            double val[NCH];
+#pragma unroll
+            for (int h = 0; h < NCH; ++h) val[h] = 0.0;
+            int ph = 0;  // m k mod nlon
             for (int m = 0; m <= L; ++m) {
-                double c, s;
-                phase(pc, ps, nlon, m, k, c, s);
-                for (int h = 0; h < nch; ++h) {
-                    const double* a = Ad + 2 * (m * nch + h);
-                    val[h] += a[0] * c - a[1] * s;
-                }
+                const double c = pc[ph], s = ps[ph];
+                ph += k;
+                if (ph >= nlon) ph -= nlon;
+                const double* a = Aj + 2 * m * NCH;
+#pragma unroll
+                for (int h = 0; h < NCH; ++h) val[h] = fma(a[2 * h], c, fma(-a[2 * h + 1], s, val[h]));
             }
             // point (source units) and target normal in the rotated frame
             const double dx = st[j] * pc[k], dy = st[j] * ps[k], dz = ct[j];
             const double xd = rho * dx, yd = rho * dy, zd = D + rho * dz;
             double u0, u1, u2;
-            if (A.kind < 2) {
+            if (KIND < 2) {
                 const double rr = xd * xd + yd * yd + zd * zd;
                 u0 = val[0] + rr * val[3] + xd * val[6] + (yd * val[9] - zd * val[8]);
                 u1 = val[1] + rr * val[4] + yd * val[6] + (zd * val[7] - xd * val[9]);
@@ -267,6 +271,7 @@ __global__ void fft_eval_kernel(FftArgs A) {
                 const double gcn = gc[0] * nxv + gc[1] * nyv + gc[2] * nzv;
                 const double xc[3] = {yd * hdn[2] - zd * hdn[1], zd * hdn[0] - xd * hdn[2], xd * hdn[1] - yd * hdn[0]};
                 double t3[3];
+#pragma unroll
                 for (int d = 0; d < 3; ++d)
                     t3[d] = 2.0 * han[d] + 2.0 * xn * gb[d] + 2.0 * gbn * xv[d] + 2.0 * rr * hbn[d] + 2.0 * pcv * nv[d] +
                             gcn * xv[d] + xn * gc[d] + xc[d] + hdx[d] - pe * nv[d];
@@ -338,7 +343,6 @@ __global__ void fft_eval_kernel(FftArgs A) {
     rotate_vsh(A, cu, cv, v, w, g[0], g[1], g[2], g[3], false);
     double* dst = A.blk + (size_t)e * 6 * S;
     for (int q = tid; q < 6 * S; q += bd) dst[q] = cv[q];
-    (void)p;
 }
 
 // One CTA per target sphere: its entries' blocks summed in list order, then the
@@ -430,12 +434,19 @@ __global__ void fft_synth_kernel(FftArgs A) {
 
 }  // namespace
 
+// Discs evaluated together by fft_eval_kernel: enough for one node per thread
+// of its 128.
+int fft_eval_group(int p) {
+    const int nlon = 2 * p + 2;
+    return std::min(p + 1, (128 + nlon - 1) / nlon);
+}
+
 size_t fft_eval_smem(int p, int kind) {
     const int P1 = p + 1, L = kind == 2 ? p + 2 : p + 1, K = (L + 1) * (L + 1);
     const int nch = kind == 2 ? kTracChannels : kVelChannels;
     const int nlat = p + 1, nlon = 2 * p + 2, npn = nlat * nlon, S = P1 * P1;
-    return sizeof(double) * ((size_t)K * nch + (size_t)(L + 1) * nch * 2 + 3 * npn + 3 * nlat * P1 * 2 + 6 * S * 4 +
-                             2 * nlon);
+    return sizeof(double) * ((size_t)K * nch + (size_t)fft_eval_group(p) * (L + 1) * nch * 2 + 3 * npn +
+                             3 * nlat * P1 * 2 + 6 * S * 4 + 2 * nlon);
 }
 
 cudaError_t launch_near_fft(sbie_ctx* c, Kern op, double* out) {
@@ -445,6 +456,7 @@ cudaError_t launch_near_fft(sbie_ctx* c, Kern op, double* out) {
     A.p = c->p; A.P1 = c->p + 1; A.L = kind == 2 ? c->p + 2 : c->p + 1; A.K = sh_count(A.L);
     A.nch = kind == 2 ? kTracChannels : kVelChannels;
     A.npn = c->npn; A.nlat = c->nlat; A.nlon = c->nlon; A.kind = kind; A.n_near = (int)c->n_near;
+    A.G = fft_eval_group(c->p);
     A.tl = c->tl; A.tab = c->d_tab; A.rotp = c->d_rotp; A.rotm = c->d_rotm;
     A.geo = c->d_fgeo;
     A.coef = c->d_coef; A.near_ptr = c->d_near_ptr; A.near_idx = c->d_near_idx;
@@ -459,9 +471,10 @@ cudaError_t launch_near_fft(sbie_ctx* c, Kern op, double* out) {
     e = launch_near_prep_pairs(c, kind, A.n_near, c->d_fcoef, c->d_fiota, c->d_fchan);
     if (e != cudaSuccess) return e;
     sm = fft_eval_smem(c->p, kind);
-    e = cudaFuncSetAttribute(fft_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    auto eval = kind == 0 ? fft_eval_kernel<0> : (kind == 1 ? fft_eval_kernel<1> : fft_eval_kernel<2>);
+    e = cudaFuncSetAttribute(eval, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     if (e != cudaSuccess) return e;
-    fft_eval_kernel<<<A.n_near, 128, sm, c->stream>>>(A); ++c->n_launch;
+    eval<<<A.n_near, 128, sm, c->stream>>>(A); ++c->n_launch;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     sm = sizeof(double) * (6 * (size_t)S + 3 * c->nlat * P1 * 2 + 3 * (size_t)c->npn);
     e = cudaFuncSetAttribute(fft_synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -35,6 +35,7 @@
 #include <cuda.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "common.h"
 #include "mlp.h"
@@ -162,13 +163,29 @@ struct GemmEpi {
     const float* scale;  // per-sphere factor (single layer: the radius) or nullptr
     double* low;         // [cols][rows - out_rows] or nullptr
     int k_blocks;
+    int b_exact;         // B has no TF32 remainder (Bl is neither loaded nor multiplied)
     int* err;            // set to 1 when a wait runs out
 };
 
+// Epilogue of the pair network's GEMMs: C[m][n] = acc (+ bias[n]) (tanh)
+// (x (1 - G[m][n]^2)), FP32, rows m < M and columns n < N.
+struct MlpEpi {
+    int M, N;
+    long long ldc, ldg;
+    float* C;
+    const float* bias;
+    const float* G;
+    int mode;            // TcEpi::Mode
+    int k_blocks;
+    int b_exact;
+    int* err;
+};
+
+template <typename EP>
 __global__ void __launch_bounds__(128, 1)
     self_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                      const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-                     GemmEpi E) {
+                     EP E) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kStages];
     __shared__ __align__(8) uint64_t empty_bar[kStages];
@@ -213,11 +230,11 @@ __global__ void __launch_bounds__(128, 1)
             }
             const uint32_t st = base + s * kStageBytes;
             const uint32_t fb = smem_addr(&full_bar[s]);
-            mbar_expect_tx(fb, kStageBytes);
+            mbar_expect_tx(fb, E.b_exact ? kStageBytes - kTileB : kStageBytes);
             tma_load_2d(st, &tmAh, kb * kBK, m0, fb);
             tma_load_2d(st + kTileA, &tmAl, kb * kBK, m0, fb);
             tma_load_2d(st + 2 * kTileA, &tmBh, kb * kBK, n0, fb);
-            tma_load_2d(st + 2 * kTileA + kTileB, &tmBl, kb * kBK, n0, fb);
+            if (!E.b_exact) tma_load_2d(st + 2 * kTileA + kTileB, &tmBl, kb * kBK, n0, fb);
             issued = kb + 1;
         }
     } else if (warp == 1 && lane == 0) {
@@ -239,8 +256,8 @@ __global__ void __launch_bounds__(128, 1)
                 const uint64_t bh = sw128_desc(st + 2 * kTileA + off), bl = sw128_desc(st + 2 * kTileA + kTileB + off);
                 const uint32_t dj = tmem + (uint32_t)((kb % kAcc) * kBN), de = tmem + (uint32_t)(kAcc * kBN);
                 mma_tf32(dj, ah, bh, idesc, (kb >= kAcc || kk > 0) ? 1u : 0u);
-                mma_tf32(de, ah, bl, idesc, (kb | kk) ? 1u : 0u);
-                mma_tf32(de, al, bh, idesc, 1u);
+                if (!E.b_exact) mma_tf32(de, ah, bl, idesc, (kb | kk) ? 1u : 0u);
+                mma_tf32(de, al, bh, idesc, (E.b_exact && (kb | kk) == 0) ? 0u : 1u);
             }
             mma_commit(smem_addr(&empty_bar[s]));
         }
@@ -281,17 +298,35 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
                 for (int i = 0; i < 16; ++i) acc[i] += v[i];
             }
-            if (r < E.rows) {
+            if constexpr (std::is_same<EP, GemmEpi>::value) {
+                if (r < E.rows) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int s = n0 + c0 + i;
-                    if (s >= E.cols) break;
-                    const double x = widen(E.scale ? acc[i] * E.scale[s] : acc[i]);
-                    if (r < E.out_rows) {
-                        double* o = E.out + (long long)s * E.ld_out + r;
-                        *o = E.accumulate ? *o + x : x;
-                    } else {
-                        E.low[(long long)s * (E.rows - E.out_rows) + (r - E.out_rows)] = x;
+                    for (int i = 0; i < 16; ++i) {
+                        const int s = n0 + c0 + i;
+                        if (s >= E.cols) break;
+                        const double x = widen(E.scale ? acc[i] * E.scale[s] : acc[i]);
+                        if (r < E.out_rows) {
+                            double* o = E.out + (long long)s * E.ld_out + r;
+                            *o = E.accumulate ? *o + x : x;
+                        } else {
+                            E.low[(long long)s * (E.rows - E.out_rows) + (r - E.out_rows)] = x;
+                        }
+                    }
+                }
+            } else {
+                if (r < E.M) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int n = n0 + c0 + i;
+                        if (n >= E.N) break;
+                        float v = acc[i];
+                        if (E.mode == TcEpi::kBias || E.mode == TcEpi::kBiasTanh) v += E.bias[n];
+                        if (E.mode == TcEpi::kBiasTanh) v = tanhf(v);
+                        if (E.mode == TcEpi::kDTanh) {
+                            const float gv = E.G[(long long)r * E.ldg + n];
+                            v *= 1.f - gv * gv;
+                        }
+                        E.C[(long long)r * E.ldc + n] = v;
                     }
                 }
             }
@@ -302,11 +337,6 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }
-}
-
-// TF32 high part: round to nearest (ties away) at 10 explicit mantissa bits.
-__device__ __forceinline__ float tf32_hi(float x) {
-    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // rows of src (FP64, row r at src + r * ld) -> TF32 hi / remainder pairs [rows][Kpad] (zero past K)
@@ -519,12 +549,47 @@ cudaError_t launch_self_gemm(sbie_ctx* c, int which, const double* dens, double*
     E.scale = which == kSelfS ? g->af : nullptr;
     E.low = which == kSelfPrec ? c->d_low : nullptr;
     E.k_blocks = g->Kpad / kBK;
+    E.b_exact = 0;
     E.err = g->err;
-    cudaError_t e = cudaFuncSetAttribute(self_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e =
+        cudaFuncSetAttribute(self_gemm_kernel<GemmEpi>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     dim3 grid((E.rows + kBM - 1) / kBM, (c->n + kBN - 1) / kBN);
-    self_gemm_kernel<<<grid, 128, kSmemBytes, c->stream>>>(g->mh[which], g->ml[which], g->bh, g->bl, E);
+    self_gemm_kernel<GemmEpi><<<grid, 128, kSmemBytes, c->stream>>>(g->mh[which], g->ml[which], g->bh, g->bl, E);
     ++c->n_launch;
+    return cudaGetLastError();
+}
+
+// C = A B^T (+ epilogue) for the pair network: A [M][Kpad] and B [N][Kpad]
+// as TF32 high parts and remainders (zero past K), B's remainder omitted when
+// B is exact in TF32 (the BF16 weights).
+cudaError_t tc_gemm_tf32(cudaStream_t s, int M, int N, int Kpad, const float* Ahi, const float* Alo,
+                         const float* Bhi, const float* Blo, const TcEpi& ep, int* err) {
+    if (M <= 0 || N <= 0 || Kpad <= 0 || Kpad % kBK) return cudaErrorInvalidValue;
+    if (!encode_fn()) return cudaErrorNotSupported;
+    CUtensorMap ah, al, bh, bl;
+    if (!make_map(&ah, const_cast<float*>(Ahi), M, Kpad, Kpad, kBM) ||
+        !make_map(&al, const_cast<float*>(Alo), M, Kpad, Kpad, kBM) ||
+        !make_map(&bh, const_cast<float*>(Bhi), N, Kpad, Kpad, kBN) ||
+        !make_map(&bl, const_cast<float*>(Blo ? Blo : Bhi), N, Kpad, Kpad, kBN))
+        return cudaErrorInvalidValue;
+    MlpEpi E;
+    E.M = M;
+    E.N = N;
+    E.ldc = ep.ldc;
+    E.ldg = ep.ldg;
+    E.C = ep.C;
+    E.bias = ep.bias;
+    E.G = ep.G;
+    E.mode = ep.mode;
+    E.k_blocks = Kpad / kBK;
+    E.b_exact = Blo ? 0 : 1;
+    E.err = err;
+    cudaError_t e =
+        cudaFuncSetAttribute(self_gemm_kernel<MlpEpi>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    dim3 grid((M + kBM - 1) / kBM, (N + kBN - 1) / kBN);
+    self_gemm_kernel<MlpEpi><<<grid, 128, kSmemBytes, s>>>(ah, al, bh, bl, E);
     return cudaGetLastError();
 }
 

@@ -189,6 +189,26 @@ def squirmer_slip(normals, axes, B1, B2):
     return ((np.asarray(B1, float) + np.asarray(B2, float) * ne)[:, None]) * (ne[:, None] * n - e)
 
 
+def smooth_density(nodes, centres, npn, seed, modes=4, k_max=1.0):
+    """A smooth nodal vector field for operator applies: per sphere a random
+    rigid motion v + w x (x - c) (unit-variance components), plus `modes`
+    plane waves a sin(k . x + phi) with |k| <= k_max and unit-variance
+    amplitudes a.  `nodes` [N][3] in sphere order (npn nodes per sphere),
+    `centres` [n][3]."""
+    rng = np.random.default_rng(seed)
+    x = np.asarray(nodes, float).reshape(-1, 3)
+    c = np.asarray(centres, float).reshape(-1, 3)
+    n = len(c)
+    v, w = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    r = x.reshape(n, npn, 3) - c[:, None, :]
+    u = (v[:, None, :] + np.cross(np.broadcast_to(w[:, None, :], r.shape), r)).reshape(-1, 3)
+    for _ in range(modes):
+        k = rng.normal(size=3)
+        k *= k_max * rng.uniform() / np.linalg.norm(k)
+        u = u + rng.normal(size=3)[None, :] * np.sin(x @ k + rng.uniform(0, 2 * np.pi))[:, None]
+    return u
+
+
 def squirmers(n, p, seed, B1=1.0, beta=-3.0, radius_range=(1.0, 1.0)):
     """A small suspension of squirmers (RSA at volume fraction near 0.1, some
     pairs pushed close) with random unit swimming axes; B2 = beta B1

@@ -72,3 +72,22 @@ def test_lattice_gaps(q):
         np.fill_diagonal(d, np.inf)
         assert abs(d.min() - gap) < 1e-12
         assert np.isclose(a.max(), 1 - 2.0 ** (-q))
+
+
+def test_smooth_density_is_seeded_and_smooth():
+    """The operator-apply density of the close-pair benchmark: reproducible,
+    one rigid motion per sphere plus plane waves of wave number <= 1, so its
+    variation across a unit sphere is bounded by the rigid part and |k|."""
+    rng = np.random.default_rng(0)
+    c = np.array([[0.0, 0, 0], [5.0, 0, 0]])
+    d = rng.normal(size=(2, 50, 3))
+    d /= np.linalg.norm(d, axis=2, keepdims=True)
+    x = (c[:, None, :] + d).reshape(-1, 3)
+    u1 = wl.smooth_density(x, c, 50, seed=3)
+    u2 = wl.smooth_density(x, c, 50, seed=3)
+    assert u1.shape == (100, 3) and np.array_equal(u1, u2)
+    assert not np.allclose(u1, wl.smooth_density(x, c, 50, seed=4))
+    # without plane waves it is a rigid motion on each sphere: (u(x) - u(c)) . (x - c) = 0
+    r = wl.smooth_density(x, c, 50, seed=3, modes=0).reshape(2, 50, 3)
+    ctr = wl.smooth_density(np.repeat(c, 50, axis=0), c, 50, seed=3, modes=0).reshape(2, 50, 3)
+    np.testing.assert_allclose(np.sum((r - ctr) * d, axis=2), 0.0, atol=1e-12)

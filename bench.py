@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched_512 solve of the headline line")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-precond", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
@@ -332,6 +333,34 @@ def graph_compare(sb, torch, wl, w, prec, stream, vel, om, F_ref, t_graph, net):
                          "graph_cycles": res[True][1]["graph_cycles"],
                          "kernels_per_solve": res[True][1]["kernel_launches"]}
     return out
+
+
+def batched_quick(sb, torch, wl, local):
+    """One mixed-precision, graph-launched solve of all 512 problems of
+    batched_512 in one context (after a warm-up solve that captures the cycle
+    graphs), CUDA events on the library's stream: the batched configuration in
+    the headline run.  `bench.py --workload batched_512` measures it in full."""
+    import numpy as np
+    probs = wl.batched_512()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream()
+    cl = [q["centres"] for q in probs]
+    rl = [q["radii"] for q in probs]
+    pl = [q["p"] for q in probs]
+    F = torch.tensor(np.concatenate([q["forces"] for q in probs]), dtype=torch.float64, device=dev)
+    T = torch.tensor(np.concatenate([q["torques"] for q in probs]), dtype=torch.float64, device=dev)
+    v, om = torch.zeros_like(F), torch.zeros_like(T)
+    o = sb.make_opts(pl[0], prec=sb.SBIE_MIXED, tol=1e-8, mem_kind=1, stream=stream.cuda_stream)
+    ctx = sb.sphere_bie_create_batch(cl, rl, pl, o)
+    sb.sphere_bie_autotune(ctx, "mobility")
+    fn = lambda: sb.sphere_bie_solve_mobility(ctx, F, T, v, om)
+    fn()
+    ts, info = _timed_solves(torch, stream, fn, 1)
+    sb.sphere_bie_destroy(ctx)
+    return {"time_to_solve_s": ts[0], "problems_per_s": len(probs) / ts[0], "problems": len(probs),
+            "spheres": int(sum(len(r) for r in rl)), "iters": info["iters"],
+            "rel_residual_true": info["rel_residual_true"], "graph_cycles": info["graph_cycles"],
+            "precision": "mixed", "tol": 1e-8}
 
 
 GOLDEN_SOLVE = os.path.join(ROOT, "tests", "golden", "resistance_256_oracle_solve.json")
@@ -1037,6 +1066,7 @@ def main():
                "timed_in_full": {"resistance_256_apply_s": cb["apply_s"], "mobility_8_solve": cb["mobility_8"]}}
 
     graphs_cmp = None if args.no_graphs else graph_compare(sb, torch, wl, w, prec, stream, vel, om, F, t_step, net)
+    batched = None if (args.no_batched or args.no_graphs or rank != 0) else batched_quick(sb, torch, wl, local)
     launches_per_step = launches_timed / args.steps
     if rank == 0:
         line = {
@@ -1065,6 +1095,7 @@ def main():
                                 "note": "stage and kernel times (roofline, far_field, stage_ms_per_step) come from "
                                         "these host-stepped solves with CUDA events per stage"},
             "graphs_vs_host_stepped": graphs_cmp,
+            "batched_512": batched,
             "e2e": ({"value": t_e2e, "unit": "s", "h2d_bytes_per_step": h2d,
                      "d2h_bytes_per_step": d2h, "includes": "create + solve + destroy, host buffers"}
                     if t_e2e is not None else None),

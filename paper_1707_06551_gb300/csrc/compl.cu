@@ -59,6 +59,28 @@ __global__ void sphere_reduce_kernel(const double* __restrict__ dens, const doub
     }
 }
 
+// 1 / sqrt(r2): IEEE in FP64; in FP32 the hardware reciprocal square root
+// (a few ulp), the accuracy of the rest of the FP32 operator.
+__device__ __forceinline__ double inv_sqrt(double r2) { return 1.0 / sqrt(r2); }
+__device__ __forceinline__ float inv_sqrt(float r2) { return rsqrtf(r2); }
+
+__device__ __forceinline__ void load12(const float* p, float (&v)[12]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float4 t = q[i];
+        v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void load12(const double* p, double (&v)[12]) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double2 t = q[i];
+        v[2 * i] = t.x; v[2 * i + 1] = t.y;
+    }
+}
+
 // FP64: direct.  FP32: target and centre positions are split into float hi +
 // lo parts so that x - c keeps relative FP32 accuracy (as in the far field).
 template <typename T>
@@ -69,8 +91,7 @@ __global__ void completion_kernel(const double* __restrict__ x64, const double* 
     // out[i] += sum over spheres k of i's problem of
     //           G(x_i - c_k) M0_k + M1_k x (x_i - c_k) / (8 pi |x_i - c_k|^3)
     constexpr int TILE = 128;
-    __shared__ T sc[TILE][6];   // centre hi (3), lo (3)
-    __shared__ T sm[TILE][6];
+    __shared__ __align__(16) T sd[TILE][12];  // centre hi (3), lo (3), force (3), torque (3)
     __shared__ int range[2];
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < N;
@@ -95,23 +116,25 @@ __global__ void completion_kernel(const double* __restrict__ x64, const double* 
             for (int d = 0; d < 3; ++d) {
                 double cd = (k < ke) ? c[3 * k + d] : 0.0;
                 T h = (T)cd;
-                sc[j][d] = h;
-                sc[j][3 + d] = (T)(cd - (double)h);
+                sd[j][d] = h;
+                sd[j][3 + d] = (T)(cd - (double)h);
             }
-            for (int d = 0; d < 6; ++d) sm[j][d] = (k < ke) ? (T)mom[6 * k + d] : (T)0;
+            for (int d = 0; d < 6; ++d) sd[j][6 + d] = (k < ke) ? (T)mom[6 * k + d] : (T)0;
         }
         __syncthreads();
-        int cnt = min(TILE, ke - b);
-        for (int j = 0; j < cnt; ++j) {
-            if (b + j < k0 || b + j >= k1) continue;
-            T dx = (xh - sc[j][0]) + (xl - sc[j][3]);
-            T dy = (yh - sc[j][1]) + (yl - sc[j][4]);
-            T dz = (zh - sc[j][2]) + (zl - sc[j][5]);
+        // this target's problem's spheres within the tile
+        const int j0 = max(0, k0 - b), j1 = min(min(TILE, ke - b), k1 - b);
+        for (int j = j0; j < j1; ++j) {
+            T v[12];
+            load12(sd[j], v);  // vector loads of the staged sphere (all threads read the same one)
+            T dx = (xh - v[0]) + (xl - v[3]);
+            T dy = (yh - v[1]) + (yl - v[4]);
+            T dz = (zh - v[2]) + (zl - v[5]);
             T r2 = dx * dx + dy * dy + dz * dz;
-            T ri = (T)1 / sqrt(r2);
+            T ri = inv_sqrt(r2);
             T ri3 = ri * ri * ri;
-            T fx = sm[j][0], fy = sm[j][1], fz = sm[j][2];
-            T tx = sm[j][3], ty = sm[j][4], tz = sm[j][5];
+            T fx = v[6], fy = v[7], fz = v[8];
+            T tx = v[9], ty = v[10], tz = v[11];
             T rf = dx * fx + dy * fy + dz * fz;
             // Stokeslet f / r + r (r.f) / r^3 and rotlet (t x r) / r^3, common factor 1/(8 pi)
             ux += fx * ri + dx * rf * ri3 + (ty * dz - tz * dy) * ri3;

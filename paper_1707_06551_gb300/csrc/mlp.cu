@@ -116,11 +116,15 @@ __global__ void loss_kernel(long long total, float scale, const float* __restric
     if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
 }
 
-__global__ void adam_kernel(long long n, float lr, float b1, float b2, float eps, float c1, float c2,
+// Adam with its step size and bias corrections read from the device
+// (hyper[0] = learning rate, hyper[1] = 1 - b1^t, hyper[2] = 1 - b2^t), so
+// that one captured epoch replays every epoch.
+__global__ void adam_kernel(long long n, const float* __restrict__ hyper, float b1, float b2, float eps,
                             float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m1,
                             float* __restrict__ m2, __nv_bfloat16* __restrict__ wb) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const float lr = hyper[0], c1 = hyper[1], c2 = hyper[2];
     float gi = g[i];
     float a = b1 * m1[i] + (1.f - b1) * gi;
     float b = b2 * m2[i] + (1.f - b2) * gi * gi;
@@ -129,6 +133,13 @@ __global__ void adam_kernel(long long n, float lr, float b1, float b2, float eps
     float v = w[i] - lr * (a / c1) / (sqrtf(b / c2) + eps);
     w[i] = v;
     wb[i] = __float2bfloat16(v);
+}
+
+// t <- t + 1 and the bias corrections of step t
+__global__ void adam_step_kernel(int* __restrict__ t, float* __restrict__ hyper, float b1, float b2) {
+    const int s = ++*t;
+    hyper[1] = 1.f - powf(b1, (float)s);
+    hyper[2] = 1.f - powf(b2, (float)s);
 }
 
 __global__ void to_bf16_kernel(long long n, const float* __restrict__ w, __nv_bfloat16* __restrict__ wb) {
@@ -173,6 +184,8 @@ struct MlpWork {
     float* pa = nullptr;  // A operand: high parts, then remainders
     float* pb = nullptr;  // B operand: high parts, then remainders
     size_t na = 0, nb = 0;
+    float* work = nullptr;  // split-K partial sums of the input-gradient GEMMs
+    size_t nwork = 0;
     int* err = nullptr;   // bounded-wait flag of the tensor-core GEMMs
     cudaError_t alloc(int c, bool train) {
         cap = c;
@@ -194,6 +207,10 @@ struct MlpWork {
         }
         if (cudaMalloc(&pa, sizeof(float) * 2 * na) != cudaSuccess) return cudaErrorMemoryAllocation;
         if (cudaMalloc(&pb, sizeof(float) * 2 * nb) != cudaSuccess) return cudaErrorMemoryAllocation;
+        if (train) {  // up to 32 slices of the largest input gradient [c][din]
+            nwork = (size_t)32 * c * kMlpHidden;
+            if (cudaMalloc(&work, sizeof(float) * nwork) != cudaSuccess) return cudaErrorMemoryAllocation;
+        }
         if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return cudaErrorMemoryAllocation;
         if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess) return cudaErrorMemoryAllocation;
         return cudaMalloc(&partial, sizeof(double) * 1024);
@@ -212,10 +229,10 @@ struct MlpWork {
             if (d[l]) cudaFree(d[l]);
             h[l] = d[l] = nullptr;
         }
-        for (void* p : {(void*)partial, (void*)pa, (void*)pb, (void*)err})
+        for (void* p : {(void*)partial, (void*)pa, (void*)pb, (void*)err, (void*)work})
             if (p) cudaFree(p);
         partial = nullptr;
-        pa = pb = nullptr;
+        pa = pb = work = nullptr;
         err = nullptr;
     }
 };
@@ -234,7 +251,8 @@ static cudaError_t forward(cudaStream_t s, const MlpLayout& L, const float* w, c
         ep.ldc = dout;
         ep.bias = w + L.b[l];
         ep.mode = l < 3 ? TcEpi::kBiasTanh : TcEpi::kBias;
-        if (e == cudaSuccess) e = tc_gemm_tf32(s, B, dout, Kp, ws.pa, ws.pa + ws.na, ws.pb, nullptr, ep, ws.err);
+        // (W^T H^T)^T: the output features on the TMEM lanes (coalesced stores)
+        if (e == cudaSuccess) e = tc_gemm_tf32(s, dout, B, Kp, ws.pb, nullptr, ws.pa, ws.pa + ws.na, ep, ws.err);
     }
     return e;
 }
@@ -252,19 +270,19 @@ static cudaError_t backward(cudaStream_t s, const MlpLayout& L, const __nv_bfloa
     for (int l = 3; l >= 0 && e == cudaSuccess; --l) {
         const float* Ain = l == 0 ? X : ws.h[l - 1];
         const int din = L.din[l], dout = L.dout[l];
-        // dW_l = A_in^T dZ_l  (M = din, N = dout, K = B)
+        // dW_l = A_in^T dZ_l = ((dZ_l^T) (A_in^T)^T)^T  (GEMM M = dout, N = din, K = B)
         e = pack_t(s, Ain, din, din, B, Kb, ws.pa, ws.pa + ws.na);
         if (e == cudaSuccess) e = pack_t(s, ws.d[l], dout, dout, B, Kb, ws.pb, ws.pb + ws.nb);
         TcEpi gw;
         gw.C = grad + L.w[l];
         gw.ldc = dout;
-        if (e == cudaSuccess) e = tc_gemm_tf32(s, din, dout, Kb, ws.pa, ws.pa + ws.na, ws.pb, ws.pb + ws.nb, gw, ws.err);
+        if (e == cudaSuccess) e = tc_gemm_tf32(s, dout, din, Kb, ws.pb, ws.pb + ws.nb, ws.pa, ws.pa + ws.na, gw, ws.err);
         if (e != cudaSuccess) break;
         // db_l = colsum(dZ_l)
         colsum_kernel<<<(dout + 255) / 256, 256, 0, s>>>(B, dout, ws.d[l], grad + L.b[l]);
         e = cudaGetLastError();
         if (l == 0 || e != cudaSuccess) break;
-        // dZ_{l-1} = (dZ_l W_l^T) (1 - h_{l-1}^2)  (M = B, N = din, K = dout)
+        // dZ_{l-1} = (dZ_l W_l^T) (1 - h_{l-1}^2) = (W_l dZ_l^T)^T ...  (GEMM M = din, N = B, K = dout)
         const int Kd = pad32(dout);
         e = pack(s, ws.d[l], dout, B, dout, Kd, ws.pa, ws.pa + ws.na);
         if (e == cudaSuccess) e = pack(s, wb + L.w[l], dout, din, dout, Kd, ws.pb, (float*)nullptr);
@@ -274,7 +292,8 @@ static cudaError_t backward(cudaStream_t s, const MlpLayout& L, const __nv_bfloa
         gz.G = ws.h[l - 1];
         gz.ldg = din;
         gz.mode = TcEpi::kDTanh;
-        if (e == cudaSuccess) e = tc_gemm_tf32(s, B, din, Kd, ws.pa, ws.pa + ws.na, ws.pb, nullptr, gz, ws.err);
+        if (e == cudaSuccess)
+            e = tc_gemm_tf32(s, din, B, Kd, ws.pb, nullptr, ws.pa, ws.pa + ws.na, gz, ws.err, ws.work, ws.nwork);
     }
     return e;
 }
@@ -377,35 +396,67 @@ cudaError_t mlp_train(const MlpTrainOpts& o, int n, const float* h_X, const floa
     if (e == cudaSuccess) e = cudaMemcpyAsync(X, h_X, sizeof(float) * (size_t)n * kMlpIn, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(T, h_T, sizeof(float) * (size_t)n * kMlpOut, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = mlp_to_bf16(s, w, wb);
+    float* hyper = nullptr;  // learning rate, bias corrections
+    int* tstep = nullptr;    // Adam step counter
+    if (e == cudaSuccess) e = cudaMalloc(&hyper, sizeof(float) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&tstep, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(tstep, 0, sizeof(int), s);
     std::mt19937_64 rng(o.seed);
     std::vector<int> perm(n);
     for (int i = 0; i < n; ++i) perm[i] = i;
-    long long step = 0;
     const float b1 = 0.9f, b2 = 0.999f;
+    int nblk = 0;
+    // one epoch: every mini-batch of the shuffled order in idx
+    auto epoch = [&]() -> cudaError_t {
+        cudaError_t er = cudaSuccess;
+        for (int r = 0; r + B <= n && er == cudaSuccess; r += B) {
+            gather_rows_kernel<<<(B * kMlpIn + 255) / 256, 256, 0, s>>>(B, kMlpIn, idx + r, X, Xb);
+            gather_rows_kernel<<<(unsigned)(((long long)B * kMlpOut + 255) / 256), 256, 0, s>>>(B, kMlpOut, idx + r, T,
+                                                                                               Tb);
+            er = cudaGetLastError();
+            if (er == cudaSuccess) er = forward(s, L, w, wb, B, Xb, ws);
+            if (er == cudaSuccess) er = backward(s, L, wb, B, Xb, Tb, ws, g, &nblk);
+            if (er == cudaSuccess) {
+                adam_step_kernel<<<1, 1, 0, s>>>(tstep, hyper, b1, b2);
+                adam_kernel<<<(unsigned)((L.total + 255) / 256), 256, 0, s>>>(L.total, hyper, b1, b2, 1e-8f, w, g, m1,
+                                                                               m2, wb);
+                er = cudaGetLastError();
+            }
+        }
+        return er;
+    };
+    // The first epoch runs launch by launch; the second is captured as a CUDA
+    // graph, which every later epoch replays (the shuffled order and the
+    // learning rate are copied to the device before each epoch).
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
     for (int ep = 0; ep < o.epochs && e == cudaSuccess; ++ep) {
         std::shuffle(perm.begin(), perm.end(), rng);
+        const float lr = (float)(o.lr * (ep < o.epochs / 2 ? 1.0 : (ep < 3 * o.epochs / 4 ? 0.3 : 0.1)));
         e = cudaMemcpyAsync(idx, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
-        double ep_loss = 0.0;
-        int nb_steps = 0;
-        for (int r = 0; r + B <= n && e == cudaSuccess; r += B) {
-            gather_rows_kernel<<<(B * kMlpIn + 255) / 256, 256, 0, s>>>(B, kMlpIn, idx + r, X, Xb);
-            gather_rows_kernel<<<(unsigned)(((long long)B * kMlpOut + 255) / 256), 256, 0, s>>>(B, kMlpOut, idx + r, T, Tb);
-            e = cudaGetLastError();
-            if (e == cudaSuccess) e = forward(s, L, w, wb, B, Xb, ws);
-            int nblk = 0;
-            if (e == cudaSuccess) e = backward(s, L, wb, B, Xb, Tb, ws, g, &nblk);
-            ++step;
-            const float lr = (float)(o.lr * (ep < o.epochs / 2 ? 1.0 : (ep < 3 * o.epochs / 4 ? 0.3 : 0.1)));
-            if (e == cudaSuccess) {
-                adam_kernel<<<(unsigned)((L.total + 255) / 256), 256, 0, s>>>(
-                    L.total, lr, b1, b2, 1e-8f, 1.f - powf(b1, (float)step), 1.f - powf(b2, (float)step), w, g, m1, m2, wb);
-                e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hyper, &lr, sizeof(float), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && ep == 0) {
+            e = epoch();
+        } else if (e == cudaSuccess) {
+            if (!exec) {
+                e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t ec = epoch();
+                    e = cudaStreamEndCapture(s, &graph);
+                    if (ec != cudaSuccess) e = ec;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
             }
-            if (e == cudaSuccess && r + 2 * B > n) ep_loss = read_loss(s, ws, nblk, (long long)B * kMlpOut, &e);
-            ++nb_steps;
+            if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
         }
+        double ep_loss = 0.0;
+        if (e == cudaSuccess) ep_loss = read_loss(s, ws, nblk, (long long)B * kMlpOut, &e);
         history.push_back(ep_loss);
     }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaFree(hyper);
+    cudaFree(tstep);
     if (e == cudaSuccess) e = ws.check(s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_params, w, sizeof(float) * L.total, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

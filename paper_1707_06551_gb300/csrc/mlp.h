@@ -40,8 +40,9 @@ __device__ __forceinline__ float tf32_hi(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-// Epilogue of tc_gemm_tf32: C[m][n] = sum_k A[m][k] B[n][k], then + bias[n]
-// (kBias), tanh(. + bias[n]) (kBiasTanh) or x (1 - G[m][n]^2) (kDTanh).
+// Epilogue of tc_gemm_tf32: C[n ldc + m] = sum_k A[m][k] B[n][k], then
+// + bias[m] (kBias), tanh(. + bias[m]) (kBiasTanh) or x (1 - G[n ldg + m]^2)
+// (kDTanh).
 struct TcEpi {
     enum Mode { kNone = 0, kBias = 1, kBiasTanh = 2, kDTanh = 3 };
     float* C = nullptr;
@@ -51,9 +52,12 @@ struct TcEpi {
     long long ldg = 0;
     int mode = kNone;
 };
-// 3xTF32 GEMM on the tensor cores (selfgemm.cu); *err is set to 1 when one of
-// its bounded waits runs out.
+// 3xTF32 GEMM on the tensor cores (selfgemm.cu); a null Alo or Blo marks that
+// operand exact in TF32 (not both); *err is set to 1 when one of its bounded
+// waits runs out.  `work` (work_cap floats, or null) holds the partial sums of
+// a split K.
 cudaError_t tc_gemm_tf32(cudaStream_t s, int M, int N, int Kpad, const float* Ahi, const float* Alo,
-                         const float* Bhi, const float* Blo, const TcEpi& ep, int* err);
+                         const float* Bhi, const float* Blo, const TcEpi& ep, int* err, float* work = nullptr,
+                         size_t work_cap = 0);
 
 }  // namespace sbie

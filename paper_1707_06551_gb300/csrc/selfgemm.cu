@@ -34,6 +34,7 @@
 // records an error flag that the host turns into a failed launch.
 #include <cuda.h>
 
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 
@@ -163,12 +164,14 @@ struct GemmEpi {
     const float* scale;  // per-sphere factor (single layer: the radius) or nullptr
     double* low;         // [cols][rows - out_rows] or nullptr
     int k_blocks;
-    int b_exact;         // B has no TF32 remainder (Bl is neither loaded nor multiplied)
+    int k_total;         // K blocks of the whole product (= k_blocks: no split)
+    int exact;           // bit 0: A, bit 1: B has no TF32 remainder (neither loaded nor multiplied)
     int* err;            // set to 1 when a wait runs out
 };
 
-// Epilogue of the pair network's GEMMs: C[m][n] = acc (+ bias[n]) (tanh)
-// (x (1 - G[m][n]^2)), FP32, rows m < M and columns n < N.
+// Epilogue of the pair network's GEMMs, stored transposed so that the TMEM
+// lanes (m) are the contiguous index: C[n ldc + m] = acc (+ bias[m]) (tanh)
+// (x (1 - G[n ldg + m]^2)), FP32, m < M, n < N.
 struct MlpEpi {
     int M, N;
     long long ldc, ldg;
@@ -176,9 +179,11 @@ struct MlpEpi {
     const float* bias;
     const float* G;
     int mode;            // TcEpi::Mode
-    int k_blocks;
-    int b_exact;
+    int k_blocks;        // K blocks of one CTA (a split-K slice when gridDim.z > 1)
+    int k_total;         // K blocks of the whole product (the last slice may be shorter)
+    int exact;
     int* err;
+    long long zstride;   // split K: slice z writes raw sums to C + z zstride
 };
 
 template <typename EP>
@@ -217,7 +222,8 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const int nk = E.k_blocks;
+    const int kb0 = blockIdx.z * E.k_blocks;  // first K block of this CTA (split K)
+    const int nk = min(E.k_blocks, E.k_total - kb0);
     int issued = 0;  // K blocks whose copies the producer started
 
     if (warp == 0 && lane == 0) {
@@ -230,11 +236,13 @@ __global__ void __launch_bounds__(128, 1)
             }
             const uint32_t st = base + s * kStageBytes;
             const uint32_t fb = smem_addr(&full_bar[s]);
-            mbar_expect_tx(fb, E.b_exact ? kStageBytes - kTileB : kStageBytes);
-            tma_load_2d(st, &tmAh, kb * kBK, m0, fb);
-            tma_load_2d(st + kTileA, &tmAl, kb * kBK, m0, fb);
-            tma_load_2d(st + 2 * kTileA, &tmBh, kb * kBK, n0, fb);
-            if (!E.b_exact) tma_load_2d(st + 2 * kTileA + kTileB, &tmBl, kb * kBK, n0, fb);
+            const bool xa = !(E.exact & 1), xb = !(E.exact & 2);  // remainders present
+            mbar_expect_tx(fb, kTileA + kTileB + (xa ? kTileA : 0) + (xb ? kTileB : 0));
+            const int kx = (kb0 + kb) * kBK;
+            tma_load_2d(st, &tmAh, kx, m0, fb);
+            if (xa) tma_load_2d(st + kTileA, &tmAl, kx, m0, fb);
+            tma_load_2d(st + 2 * kTileA, &tmBh, kx, n0, fb);
+            if (xb) tma_load_2d(st + 2 * kTileA + kTileB, &tmBl, kx, n0, fb);
             issued = kb + 1;
         }
     } else if (warp == 1 && lane == 0) {
@@ -256,8 +264,12 @@ __global__ void __launch_bounds__(128, 1)
                 const uint64_t bh = sw128_desc(st + 2 * kTileA + off), bl = sw128_desc(st + 2 * kTileA + kTileB + off);
                 const uint32_t dj = tmem + (uint32_t)((kb % kAcc) * kBN), de = tmem + (uint32_t)(kAcc * kBN);
                 mma_tf32(dj, ah, bh, idesc, (kb >= kAcc || kk > 0) ? 1u : 0u);
-                if (!E.b_exact) mma_tf32(de, ah, bl, idesc, (kb | kk) ? 1u : 0u);
-                mma_tf32(de, al, bh, idesc, (E.b_exact && (kb | kk) == 0) ? 0u : 1u);
+                bool first = (kb | kk) == 0;  // first cross product: overwrite the accumulator
+                if (!(E.exact & 2)) {
+                    mma_tf32(de, ah, bl, idesc, first ? 0u : 1u);
+                    first = false;
+                }
+                if (!(E.exact & 1)) mma_tf32(de, al, bh, idesc, first ? 0u : 1u);
             }
             mma_commit(smem_addr(&empty_bar[s]));
         }
@@ -315,18 +327,19 @@ __global__ void __launch_bounds__(128, 1)
                 }
             } else {
                 if (r < E.M) {
+                    float* C = E.C + blockIdx.z * E.zstride;
+                    const float b = (E.mode == TcEpi::kBias || E.mode == TcEpi::kBiasTanh) ? E.bias[r] : 0.f;
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const int n = n0 + c0 + i;
                         if (n >= E.N) break;
-                        float v = acc[i];
-                        if (E.mode == TcEpi::kBias || E.mode == TcEpi::kBiasTanh) v += E.bias[n];
+                        float v = acc[i] + b;
                         if (E.mode == TcEpi::kBiasTanh) v = tanhf(v);
                         if (E.mode == TcEpi::kDTanh) {
-                            const float gv = E.G[(long long)r * E.ldg + n];
+                            const float gv = E.G[(long long)n * E.ldg + r];
                             v *= 1.f - gv * gv;
                         }
-                        E.C[(long long)r * E.ldc + n] = v;
+                        C[(long long)n * E.ldc + r] = v;  // the warp's 32 lanes: 32 consecutive m
                     }
                 }
             }
@@ -549,7 +562,8 @@ cudaError_t launch_self_gemm(sbie_ctx* c, int which, const double* dens, double*
     E.scale = which == kSelfS ? g->af : nullptr;
     E.low = which == kSelfPrec ? c->d_low : nullptr;
     E.k_blocks = g->Kpad / kBK;
-    E.b_exact = 0;
+    E.k_total = E.k_blocks;
+    E.exact = 0;
     E.err = g->err;
     cudaError_t e =
         cudaFuncSetAttribute(self_gemm_kernel<GemmEpi>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
@@ -560,36 +574,74 @@ cudaError_t launch_self_gemm(sbie_ctx* c, int which, const double* dens, double*
     return cudaGetLastError();
 }
 
-// C = A B^T (+ epilogue) for the pair network: A [M][Kpad] and B [N][Kpad]
-// as TF32 high parts and remainders (zero past K), B's remainder omitted when
-// B is exact in TF32 (the BF16 weights).
+// Split-K reduction of tc_gemm_tf32: C[n ldc + m] = epilogue(sum_z part[z][n][m]).
+__global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ part, TcEpi ep) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)M * N) return;
+    const int n = (int)(i / M), m = (int)(i - (long long)n * M);
+    float v = 0.f;
+    for (int z = 0; z < splits; ++z) v += part[(long long)z * M * N + i];
+    if (ep.mode == TcEpi::kBias || ep.mode == TcEpi::kBiasTanh) v += ep.bias[m];
+    if (ep.mode == TcEpi::kBiasTanh) v = tanhf(v);
+    if (ep.mode == TcEpi::kDTanh) {
+        const float g = ep.G[(long long)n * ep.ldg + m];
+        v *= 1.f - g * g;
+    }
+    ep.C[(long long)n * ep.ldc + m] = v;
+}
+
+// (A B^T)^T (+ epilogue) for the pair network: A [M][Kpad] and B [N][Kpad] as
+// TF32 high parts and remainders (zero past K); a null remainder marks an
+// operand exact in TF32 (the BF16 weights), whose remainder products are
+// skipped.  Output (m, n) goes to C[n ldc + m].  A long K over few output tiles is
+// split over up to `work_cap / (M N)` slices of at least 4 K blocks each,
+// whose raw sums `work` holds until one reduction kernel adds them in a fixed
+// order and applies the epilogue.
 cudaError_t tc_gemm_tf32(cudaStream_t s, int M, int N, int Kpad, const float* Ahi, const float* Alo,
-                         const float* Bhi, const float* Blo, const TcEpi& ep, int* err) {
-    if (M <= 0 || N <= 0 || Kpad <= 0 || Kpad % kBK) return cudaErrorInvalidValue;
+                         const float* Bhi, const float* Blo, const TcEpi& ep, int* err, float* work,
+                         size_t work_cap) {
+    if (M <= 0 || N <= 0 || Kpad <= 0 || Kpad % kBK || (!Alo && !Blo)) return cudaErrorInvalidValue;
     if (!encode_fn()) return cudaErrorNotSupported;
     CUtensorMap ah, al, bh, bl;
     if (!make_map(&ah, const_cast<float*>(Ahi), M, Kpad, Kpad, kBM) ||
-        !make_map(&al, const_cast<float*>(Alo), M, Kpad, Kpad, kBM) ||
+        !make_map(&al, const_cast<float*>(Alo ? Alo : Ahi), M, Kpad, Kpad, kBM) ||
         !make_map(&bh, const_cast<float*>(Bhi), N, Kpad, Kpad, kBN) ||
         !make_map(&bl, const_cast<float*>(Blo ? Blo : Bhi), N, Kpad, Kpad, kBN))
         return cudaErrorInvalidValue;
+    const int kblocks = Kpad / kBK, tiles = ((M + kBM - 1) / kBM) * ((N + kBN - 1) / kBN);
+    int splits = 1;
+    if (work && tiles < 76) {
+        splits = std::min(kblocks / 4, (152 + tiles - 1) / tiles);
+        splits = (int)std::min<long long>(splits, (long long)(work_cap / ((size_t)M * N)));
+        splits = std::max(splits, 1);
+    }
+    const int per = (kblocks + splits - 1) / splits;
+    splits = (kblocks + per - 1) / per;  // no empty slice
     MlpEpi E;
     E.M = M;
     E.N = N;
-    E.ldc = ep.ldc;
+    E.ldc = splits > 1 ? M : ep.ldc;
     E.ldg = ep.ldg;
-    E.C = ep.C;
+    E.C = splits > 1 ? work : ep.C;
     E.bias = ep.bias;
     E.G = ep.G;
-    E.mode = ep.mode;
-    E.k_blocks = Kpad / kBK;
-    E.b_exact = Blo ? 0 : 1;
+    E.mode = splits > 1 ? TcEpi::kNone : ep.mode;
+    E.k_blocks = per;
+    E.k_total = kblocks;
+    E.exact = (Alo ? 0 : 1) | (Blo ? 0 : 2);
     E.err = err;
-    cudaError_t e =
-        cudaFuncSetAttribute(self_gemm_kernel<MlpEpi>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    E.zstride = (long long)M * N;
+    // (under stream capture the attribute was set by an earlier eager call on this device)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e == cudaSuccess && cap == cudaStreamCaptureStatusNone)
+        e = cudaFuncSetAttribute(self_gemm_kernel<MlpEpi>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
-    dim3 grid((M + kBM - 1) / kBM, (N + kBN - 1) / kBN);
+    dim3 grid((M + kBM - 1) / kBM, (N + kBN - 1) / kBN, splits);
     self_gemm_kernel<MlpEpi><<<grid, 128, kSmemBytes, s>>>(ah, al, bh, bl, E);
+    if ((e = cudaGetLastError()) != cudaSuccess || splits == 1) return e;
+    const long long tot = (long long)M * N;
+    splitk_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, N, splits, work, ep);
     return cudaGetLastError();
 }
 

@@ -594,17 +594,18 @@ def run_lattice(args, sb, torch, wl, local):
 
 
 def run_near_schemes(args, sb, torch, wl, local):
-    """Close-pair stage of one FP64-accurate operator apply on dense_1024
-    (1,024 spheres, 13,940 directed close pairs) by the direct evaluation at
-    the target nodes (near_scheme 0) and by the rotated, FFT-accelerated scheme
-    of Sec. 4.2 (near_scheme 1), both in FP64, for p = 4 ... 16 and the three
-    layer operators (the far field in double-float arithmetic).  Stage times
-    are CUDA events of the library's profiler (one apply after one warm-up)
-    on a smooth density (a random rigid motion of each sphere plus four plane
-    waves with wave numbers up to 1, `workloads.smooth_density`); `rel_diff`
-    is the largest difference of the two schemes' applies relative to the
-    largest value (the rotated scheme projects each close-pair field onto
-    degree <= p on the target sphere)."""
+    """Close-pair stage of one operator apply on dense_1024 (1,024 spheres,
+    13,940 directed close pairs) by the direct evaluation at the target nodes
+    (near_scheme 0) and by the rotated, FFT-accelerated scheme of Sec. 4.2
+    (near_scheme 1), for p = 4 ... 16 and the three layer operators: in FP64
+    (the FP64-accurate operator, far field in double-float arithmetic; keys
+    without suffix) and in FP32 (the FP32 operator of the mixed path; keys
+    `_f32`).  Stage times are CUDA events of the library's profiler (one apply
+    after one warm-up) on a smooth density (a random rigid motion of each
+    sphere plus four plane waves with wave numbers up to 1,
+    `workloads.smooth_density`); `rel_diff` is the largest difference of the
+    two schemes' applies relative to the largest value (the rotated scheme
+    projects each close-pair field onto degree <= p on the target sphere)."""
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream()
     w = wl.dense_1024()
@@ -613,31 +614,37 @@ def run_near_schemes(args, sb, torch, wl, local):
         npn = (p + 1) * (2 * p + 2)
         rec = {"p": p}
         outs = {}
-        for scheme in (0, 1):
-            o = sb.make_opts(p, prec=sb.SBIE_FP64_DF, mem_kind=1, stream=stream.cuda_stream, near_scheme=scheme)
-            ctx = sb.sphere_bie_create(w["centres"], w["radii"], o)
-            if scheme == 0:
-                nodes, _, _ = sb.sphere_bie_nodes(ctx)
-                x = torch.tensor(wl.smooth_density(nodes, w["centres"], npn, seed=p), dtype=torch.float64, device=dev)
+        x = None
+        for prec, suf in ((sb.SBIE_FP64_DF, ""), (sb.SBIE_MIXED, "_f32")):
+            for scheme in (0, 1):
+                o = sb.make_opts(p, prec=prec, mem_kind=1, stream=stream.cuda_stream, near_scheme=scheme)
+                ctx = sb.sphere_bie_create(w["centres"], w["radii"], o)
+                if x is None:
+                    nodes, _, _ = sb.sphere_bie_nodes(ctx)
+                    x = torch.tensor(wl.smooth_density(nodes, w["centres"], npn, seed=p), dtype=torch.float64,
+                                     device=dev)
+                for op in ("S", "D", "K"):
+                    y = torch.zeros_like(x)
+                    sb.sphere_bie_apply_operator(ctx, op, x, y)
+                    torch.cuda.synchronize(dev)
+                    sb.sphere_bie_profile(ctx, 1)
+                    sb.sphere_bie_apply_operator(ctx, op, x, y)
+                    prof = sb.sphere_bie_profile_read(ctx)
+                    sb.sphere_bie_profile(ctx, 0)
+                    rec[f"{op}_near_ms_{'rotated' if scheme else 'direct'}{suf}"] = prof["ms"]["near"]
+                    outs[(suf, scheme, op)] = y.clone()
+                sb.sphere_bie_destroy(ctx)
             for op in ("S", "D", "K"):
-                y = torch.zeros_like(x)
-                sb.sphere_bie_apply_operator(ctx, op, x, y)
-                torch.cuda.synchronize(dev)
-                sb.sphere_bie_profile(ctx, 1)
-                sb.sphere_bie_apply_operator(ctx, op, x, y)
-                prof = sb.sphere_bie_profile_read(ctx)
-                sb.sphere_bie_profile(ctx, 0)
-                rec[f"{op}_near_ms_{'rotated' if scheme else 'direct'}"] = prof["ms"]["near"]
-                outs[(scheme, op)] = y.clone()
-            sb.sphere_bie_destroy(ctx)
-        for op in ("S", "D", "K"):
-            a, b = outs[(0, op)], outs[(1, op)]
-            rec[f"{op}_rel_diff"] = float((a - b).abs().max() / a.abs().max())
-            rec[f"{op}_speedup"] = rec[f"{op}_near_ms_direct"] / rec[f"{op}_near_ms_rotated"]
+                a, b = outs[(suf, 0, op)], outs[(suf, 1, op)]
+                rec[f"{op}_rel_diff{suf}"] = float((a - b).abs().max() / a.abs().max())
+                rec[f"{op}_speedup{suf}"] = rec[f"{op}_near_ms_direct{suf}"] / rec[f"{op}_near_ms_rotated{suf}"]
+        for op in ("S", "D", "K"):  # FP32 rotated scheme against the FP64 one
+            a, b = outs[("", 1, op)], outs[("_f32", 1, op)]
+            rec[f"{op}_rotated_f32_vs_f64"] = float((a - b).abs().max() / a.abs().max())
         rows.append(rec)
         del x, outs
-    return {"metric": "close-pair stage time per FP64-accurate operator apply, direct vs rotated scheme", "unit": "ms",
-            "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+    return {"metric": "close-pair stage time per operator apply, direct vs rotated scheme (FP64 and FP32)",
+            "unit": "ms", "higher_is_better": False, "n_gpus": 1, "dtype": "f64 / f32", "data": "synthetic",
             "config": {"workload": "near_schemes", "geometry": "dense_1024", "spheres": len(w["radii"]),
                        "p": [r["p"] for r in rows]},
             "rows": rows}

@@ -94,7 +94,7 @@ void free_all(sbie_ctx* c) {
                     c->d_rhs, c->d_res, c->d_prob_sph, c->d_sph_prob, c->d_node_prob, c->d_seg3, c->d_H, c->d_pvec,
                     c->d_ZS, c->d_ZA, c->d_modes, c->d_low, c->d_lowe, c->d_pz, c->d_ad, c->d_adi, c->d_vk,
                     c->d_sq, c->d_lcoef, c->d_rotp, c->d_rotm, c->d_fgeo, c->d_fcoef, c->d_fchan, c->d_fblk,
-                    c->d_fiota};
+                    c->d_fiota, c->d_tabf, c->d_rotpf, c->d_rotmf, c->d_fcoeff, c->d_fchanf, c->d_fblkf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (PrecState& P : c->prec)
@@ -117,7 +117,7 @@ void free_all(sbie_ctx* c) {
 // Buffers and per-entry frames of the rotated close-pair scheme (Sec. 4.2): for
 // entry e (target i, source k = near_idx[e]) the frame's pole points from c_k to
 // c_i, (sin b cos a, sin b sin a, cos b); a = 0 on the polar axis.
-sbie_status setup_near_fft(sbie_ctx* c) {
+sbie_status setup_near_fft(sbie_ctx* c, const std::vector<double>& htab) {
     const long long ne = c->n_near;
     const int P1 = c->p + 1, S = P1 * P1;
     std::vector<double> Mp, Mm;
@@ -146,8 +146,23 @@ sbie_status setup_near_fft(sbie_ctx* c) {
               dmalloc(&c->d_fcoef, (size_t)ne * 6 * S) == cudaSuccess &&
               dmalloc(&c->d_fchan, (size_t)ne * Kt * kTracChannels) == cudaSuccess &&
               dmalloc(&c->d_fblk, (size_t)ne * 6 * S) == cudaSuccess && dmalloc(&c->d_fiota, iota.size()) == cudaSuccess;
+    // FP32 copies for the FP32 operator of the mixed path
+    std::vector<float> tabf, Mpf, Mmf;
+    if (ok && c->opts.prec == SBIE_MIXED) {
+        tabf.assign(htab.begin(), htab.end());
+        Mpf.assign(Mp.begin(), Mp.end());
+        Mmf.assign(Mm.begin(), Mm.end());
+        ok = dmalloc(&c->d_tabf, tabf.size()) == cudaSuccess && dmalloc(&c->d_rotpf, Mpf.size()) == cudaSuccess &&
+             dmalloc(&c->d_rotmf, Mmf.size()) == cudaSuccess &&
+             dmalloc(&c->d_fcoeff, (size_t)ne * 6 * S) == cudaSuccess &&
+             dmalloc(&c->d_fchanf, (size_t)ne * Kt * ((kTracChannels + 3) / 4 * 4)) == cudaSuccess &&
+             dmalloc(&c->d_fblkf, (size_t)ne * 6 * S) == cudaSuccess;
+    }
     if (!ok) return fail(c, SBIE_ERR_OOM, "rotated close-pair buffers");
     cudaError_t e = h2d(c->stream, c->d_rotp, Mp.data(), Mp.size());
+    if (e == cudaSuccess && !tabf.empty()) e = h2d(c->stream, c->d_tabf, tabf.data(), tabf.size());
+    if (e == cudaSuccess && !Mpf.empty()) e = h2d(c->stream, c->d_rotpf, Mpf.data(), Mpf.size());
+    if (e == cudaSuccess && !Mmf.empty()) e = h2d(c->stream, c->d_rotmf, Mmf.data(), Mmf.size());
     if (e == cudaSuccess) e = h2d(c->stream, c->d_rotm, Mm.data(), Mm.size());
     if (e == cudaSuccess) e = h2d(c->stream, c->d_fgeo, geo.data(), geo.size());
     if (e == cudaSuccess) e = h2d(c->stream, c->d_fiota, iota.data(), iota.size());
@@ -284,8 +299,8 @@ sbie_status apply_porous(sbie_ctx* c, int mode, const double* in, double* out) {
     if (c->n_near > 0) {
         StageScope s(c, ST_NEAR);
         if (c->opts.near_scheme == 1) {
-            CK(launch_near_fft(c, Kern::S, out));
-            CK(launch_near_fft(c, Kern::D, out));
+            CK(launch_near_fft(c, Kern::S, f32, out));
+            CK(launch_near_fft(c, Kern::D, f32, out));
         } else {
             CK(launch_near(c, Kern::S, f32, out));
             CK(launch_near(c, Kern::D, f32, out));
@@ -356,7 +371,7 @@ sbie_status apply_dev(sbie_ctx* c, int op, int mode, const double* in, double* o
     }
     if (c->n_near > 0) {
         StageScope s(c, ST_NEAR);
-        CK(c->opts.near_scheme == 1 ? launch_near_fft(c, k, out) : launch_near(c, k, f32, out));
+        CK(c->opts.near_scheme == 1 ? launch_near_fft(c, k, f32, out) : launch_near(c, k, f32, out));
     }
     if (op == SBIE_OP_RESISTANCE || op == SBIE_OP_MOBILITY) {
         StageScope s(c, ST_COMPL);
@@ -1082,7 +1097,7 @@ sbie_status create_part(const sbie_opts& o, int n, const double* centres, const 
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bail(SBIE_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
     if (o.near_scheme == 1 && c->n_near > 0) {
-        sbie_status s2 = setup_near_fft(c);
+        sbie_status s2 = setup_near_fft(c, htab);
         if (s2 != SBIE_OK) return bail(s2, c->err);
     }
     c->err = "no error";

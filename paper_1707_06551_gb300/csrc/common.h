@@ -220,6 +220,13 @@ struct sbie_ctx {
     double* d_fchan = nullptr;     // [n_near][sh_count(p+2)][kTracChannels]
     double* d_fblk = nullptr;      // [n_near][3][p+1][p+1][2] target-side blocks
     int* d_fiota = nullptr;        // [n_near+1] 0, 1, ..., n_near
+    // FP32 copies for the FP32 operator of mixed-precision contexts
+    float* d_tabf = nullptr;       // the tables of d_tab
+    float* d_rotpf = nullptr;
+    float* d_rotmf = nullptr;
+    float* d_fcoeff = nullptr;     // [n_near][3][p+1][p+1][2]
+    float* d_fchanf = nullptr;     // [n_near][sh_count(p+2)][28] (rows padded to a multiple of 4)
+    float* d_fblkf = nullptr;      // [n_near][3][p+1][p+1][2]
     double mag_eta = 0.0;          // eta of the magnetic operator (Eq. 5.13) of the running solve
     double t_create_ms = 0.0;      // wall time of create (grid, tables, close pairs, preconditioner)
     bool has_solution = false;     // d_xsol holds the density of the last solve
@@ -355,12 +362,14 @@ int far_f32_builds(int tpt, int* minb);
 // near.cu
 cudaError_t launch_near(sbie_ctx* c, Kern op, bool f32, double* out);
 cudaError_t launch_near_laplace(sbie_ctx* c, int mode, double* out);
-// channels (near_prep) of `count` coefficient sets, one per entry (iota = 0..count)
-cudaError_t launch_near_prep_pairs(sbie_ctx* c, int kind, int count, const double* coef, const int* iota,
-                                   double* chan);
+// channels (near_prep) of `count` coefficient sets, one per entry (iota =
+// 0..count), from FP64 (coef) or FP32 (coeff) coefficients; FP64 channels in
+// chan and, when chanf is given, an FP32 copy with rows padded to a multiple of 4
+cudaError_t launch_near_prep_pairs(sbie_ctx* c, int kind, int count, const double* coef, const float* coeff,
+                                   const int* iota, double* chan, float* chanf);
 // nearfft.cu: close pairs by the rotated scheme of Sec. 4.2
-cudaError_t launch_near_fft(sbie_ctx* c, Kern op, double* out);
-size_t fft_eval_smem(int p, int kind);
+cudaError_t launch_near_fft(sbie_ctx* c, Kern op, bool f32, double* out);
+size_t fft_eval_smem(int p, int kind, size_t elem);
 // laplace.cu
 cudaError_t laplace_apply(sbie_ctx* c, int mode, const double* q, double* out);
 cudaError_t launch_magnetic_finalize(sbie_ctx* c, double eta, const double* in, double* out);

@@ -27,6 +27,7 @@ namespace sbie {
 struct NearArgs {
     int n, p, npn, L, nch, chunks, threads;
     const double* __restrict__ coef;   // [n][3][p+1][p+1][2]
+    const float* __restrict__ coeff;   // the same in FP32 (near_prep reads it when coef is null)
     const double* __restrict__ radius;
     const double* __restrict__ c;
     const double* __restrict__ x64;    // [N][4]
@@ -153,7 +154,8 @@ __global__ void near_prep_kernel(NearArgs A, int kind) {
     double* base = sm;            // [5][K]  Pa, Pb, Pc, Pd, Pe
     double* grad = base + 5 * K;  // [4][3][K] grad of Pa, Pb, Pc, Pd
     double* tmp = grad + 12 * K;  // [K]
-    const double* cf = A.coef + (size_t)s * 3 * P1 * P1 * 2;
+    const double* cf = A.coef ? A.coef + (size_t)s * 3 * P1 * P1 * 2 : nullptr;
+    const float* cff = A.coef ? nullptr : A.coeff + (size_t)s * 3 * P1 * P1 * 2;
     for (int q = threadIdx.x; q < 5 * K; q += blockDim.x) base[q] = 0.0;
     __syncthreads();
     for (int q = threadIdx.x; q < P1 * P1; q += blockDim.x) {
@@ -173,9 +175,10 @@ __global__ void near_prep_kernel(NearArgs A, int kind) {
             sX = 1.0 / (2 * dn + 1);
         }
         int o = n * P1 + m;
-        double Vr = cf[2 * o], Vi = cf[2 * o + 1];
-        double Wr = cf[2 * (P1 * P1 + o)], Wi = cf[2 * (P1 * P1 + o) + 1];
-        double Xr = cf[2 * (2 * P1 * P1 + o)], Xi = cf[2 * (2 * P1 * P1 + o) + 1];
+        auto co = [&](int i) { return cf ? cf[i] : (double)cff[i]; };
+        double Vr = co(2 * o), Vi = co(2 * o + 1);
+        double Wr = co(2 * (P1 * P1 + o)), Wi = co(2 * (P1 * P1 + o) + 1);
+        double Xr = co(2 * (2 * P1 * P1 + o)), Xi = co(2 * (2 * P1 * P1 + o) + 1);
         if (n == 0) { Wr = Wi = Xr = Xi = 0.0; }
         double fr[5], fi[5];
         fr[0] = sV * Vr + cW * Wr; fi[0] = sV * Vi + cW * Wi;
@@ -384,14 +387,14 @@ static cudaError_t run_eval(sbie_ctx* c, const NearArgs& A) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_near_prep_pairs(sbie_ctx* c, int kind, int count, const double* coef, const int* iota,
-                                   double* chan) {
-    NearArgs A;
+cudaError_t launch_near_prep_pairs(sbie_ctx* c, int kind, int count, const double* coef, const float* coeff,
+                                   const int* iota, double* chan, float* chanf) {
+    NearArgs A{};
     A.n = count; A.p = c->p; A.npn = c->npn;
     A.L = (kind == 2) ? c->p + 2 : c->p + 1;
     A.nch = (kind == 2) ? kTracChannels : kVelChannels;
-    A.nchf = 0;
-    A.coef = coef; A.near_ptr = iota; A.chan = chan; A.chanf = nullptr;
+    A.nchf = chanf ? (A.nch + 3) / 4 * 4 : 0;
+    A.coef = coef; A.coeff = coeff; A.near_ptr = iota; A.chan = chan; A.chanf = chanf;
     const int K = sh_count(A.L);
     const size_t sm = sizeof(double) * (size_t)(5 * K + 12 * K + K);
     cudaError_t e = cudaFuncSetAttribute(near_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -402,7 +405,7 @@ cudaError_t launch_near_prep_pairs(sbie_ctx* c, int kind, int count, const doubl
 
 cudaError_t launch_near_laplace(sbie_ctx* c, int mode, double* out) {
     if (c->n_near == 0) return cudaSuccess;
-    NearArgs A;
+    NearArgs A{};
     A.n = c->n; A.p = c->p; A.npn = c->npn;
     A.L = c->p + 1;
     A.nch = kLapChannels;
@@ -429,7 +432,7 @@ cudaError_t launch_near_laplace(sbie_ctx* c, int mode, double* out) {
 
 cudaError_t launch_near(sbie_ctx* c, Kern op, bool f32, double* out) {
     if (c->n_near == 0) return cudaSuccess;
-    NearArgs A;
+    NearArgs A{};
     A.n = c->n; A.p = c->p; A.npn = c->npn;
     int kind = (op == Kern::S) ? 0 : (op == Kern::D ? 1 : 2);
     A.L = (kind == 2) ? c->p + 2 : c->p + 1;

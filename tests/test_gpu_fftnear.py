@@ -2,8 +2,9 @@
 near_scheme = 1) on the CUDA path against the oracle's restatement of its
 three stages (oracle.fftnear): operator applies per sphere to 1e-10 on small
 suspensions with close pairs, and on sampled spheres of the dense suspension
-(1,024 spheres, 13,940 close pairs) at p = 12 and 16; solves with it converge
-to the solves of the direct scheme as p grows."""
+(1,024 spheres, 13,940 close pairs) at p = 12 and 16, in FP64 (1e-10) and in
+the FP32 operator of the mixed path (2e-5); solves with it converge to the
+solves of the direct scheme as p grows, in FP64 and in mixed precision."""
 import numpy as np
 import pytest
 
@@ -42,10 +43,11 @@ def test_rotated_scheme_matches_oracle(sb, op, geom):
         assert np.all(_per_sphere(out, ref, g.npn) < tol), (prec, _per_sphere(out, ref, g.npn).max())
 
 
-@pytest.mark.parametrize("p", [12, 16])
-def test_dense_1024_rotated_scheme_sampled(sb, p):
+@pytest.mark.parametrize("p,prec,tol", [(12, 0, 1e-10), (16, 0, 1e-10), (12, 1, 2e-5), (16, 1, 2e-5)])
+def test_dense_1024_rotated_scheme_sampled(sb, p, prec, tol):
     """The mobility operator (Eq. 5.8) of the dense suspension with the rotated
-    close-pair scheme, on its sphere with the most close partners."""
+    close-pair scheme, on its sphere with the most close partners: FP64, and
+    the FP32 operator of the mixed path (FP32 rotated scheme and far field)."""
     w = wl.dense_1024()
     g = ops.Geometry(w["centres"], w["radii"], p)
     nc = [len(x) for x in g.near]
@@ -53,22 +55,25 @@ def test_dense_1024_rotated_scheme_sampled(sb, p):
     rows = np.concatenate([np.arange(g.sl(i).start, g.sl(i).stop) for i in sample])
     dens = np.random.default_rng(p).normal(size=(g.N, 3))
     ref = fftnear.apply(g, "mobility", dens, sample)[rows]
-    with sb.SphereBIE(w["centres"], w["radii"], p, near_scheme=1) as s:
+    with sb.SphereBIE(w["centres"], w["radii"], p, prec=prec, near_scheme=1) as s:
         out = s.apply("mobility", dens)[rows]
-    assert np.all(_per_sphere(out, ref, g.npn) < 1e-10)
+    assert np.all(_per_sphere(out, ref, g.npn) < tol), _per_sphere(out, ref, g.npn).max()
 
 
-def test_rotated_scheme_solves_converge_to_direct(sb):
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-8)])
+def test_rotated_scheme_solves_converge_to_direct(sb, prec, tol):
     """Resistance solves of a suspension with gaps 0.05-0.3: the forces with the
     rotated scheme approach those of the direct scheme as p grows (the
-    scheme's projection error falls spectrally)."""
+    scheme's projection error falls spectrally), in FP64 and in mixed
+    precision (the FP32 operator with the FP32 rotated scheme inside
+    iterative refinement on the FP64-accurate operator with the FP64 one)."""
     w = wl.small_suspension(6, 4, 3)
     v = np.random.default_rng(2).normal(size=(6, 3))
     errs = []
     for p in (6, 10, 14):
         F = {}
         for scheme in (0, 1):
-            with sb.SphereBIE(w["centres"], w["radii"], p, tol=1e-12, near_scheme=scheme) as s:
+            with sb.SphereBIE(w["centres"], w["radii"], p, prec=prec, tol=tol, near_scheme=scheme) as s:
                 F[scheme], _, info = s.resistance(v, np.zeros((6, 3)))
                 assert info["status"] == 0
         errs.append(np.max(np.abs(F[1] - F[0])) / np.max(np.abs(F[0])))

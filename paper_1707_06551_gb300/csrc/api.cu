@@ -1325,25 +1325,6 @@ sbie_status aligned_blocks(int n, const double* d, const double* a_s, const doub
 }
 
 // y = Rinv * B * R for 73 x 73 matrices (R, Rinv sparse block diagonal).
-void rotate_block(const std::vector<double>& Rinv, const double* B, const std::vector<double>& R, double* out) {
-    const int n = kLowModes;
-    std::vector<double> T((size_t)n * n, 0.0);
-    // T = B R
-    for (int k = 0; k < n; ++k)
-        for (int j = 0; j < n; ++j) {
-            const double r = R[(size_t)k * n + j];
-            if (r == 0.0) continue;
-            for (int i = 0; i < n; ++i) T[(size_t)i * n + j] += B[(size_t)i * n + k] * r;
-        }
-    std::fill(out, out + (size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i)
-        for (int k = 0; k < n; ++k) {
-            const double r = Rinv[(size_t)i * n + k];
-            if (r == 0.0) continue;
-            for (int j = 0; j < n; ++j) out[(size_t)i * n + j] += r * T[(size_t)k * n + j];
-        }
-}
-
 // f(begin, end) over [0, n) split across the host's cores.
 template <typename F>
 void parallel_for(int n, F f) {
@@ -1381,6 +1362,29 @@ void pair_frame(const double* cs, const double* ct, double Q[9], double* dist) {
 }
 
 // Network blocks (pair frame, de-standardised) for inputs (0, 0, d, a_s, a_t).
+// The network's standardised outputs for inputs X5 ([n][5]) on stream s into
+// dY ([n][5329], device).
+sbie_status net_forward_dev(const PairNet& net, const std::vector<float>& X5, cudaStream_t s, float* dY) {
+    const int n = (int)(X5.size() / kMlpIn);
+    MlpLayout L = mlp_layout();
+    float *dw = nullptr, *dX = nullptr;
+    __nv_bfloat16* dwb = nullptr;
+    std::vector<float> Xs(X5.size());
+    for (int q = 0; q < n; ++q)
+        for (int j = 0; j < kMlpIn; ++j) Xs[q * kMlpIn + j] = (X5[q * kMlpIn + j] - net.in_mean[j]) / net.in_std[j];
+    cudaError_t e = cudaMalloc(&dw, sizeof(float) * L.total);
+    if (e == cudaSuccess) e = cudaMalloc(&dwb, sizeof(__nv_bfloat16) * L.total);
+    if (e == cudaSuccess) e = cudaMalloc(&dX, sizeof(float) * Xs.size());
+    if (e == cudaSuccess) e = h2d(s, dw, net.params.data(), (size_t)L.total);
+    if (e == cudaSuccess) e = h2d(s, dX, Xs.data(), Xs.size());
+    if (e == cudaSuccess) e = mlp_to_bf16(s, dw, dwb);
+    if (e == cudaSuccess) e = mlp_forward_dev(s, dw, dwb, n, dX, dY);
+    for (void* p : {(void*)dw, (void*)dwb, (void*)dX})
+        if (p) cudaFree(p);
+    if (e != cudaSuccess) return fail(nullptr, SBIE_ERR_CUDA, std::string("network: ") + cudaGetErrorString(e));
+    return SBIE_OK;
+}
+
 sbie_status net_blocks(const PairNet& net, const std::vector<float>& X5, std::vector<double>& out) {
     const int n = (int)(X5.size() / kMlpIn);
     MlpLayout L = mlp_layout();
@@ -1562,6 +1566,70 @@ sbie_status train_one(const sbie_pair_train_opts& o, int op, PairNet& net, sbie_
 
 // Builds the pair preconditioner of operator `op` on one part (kind 1:
 // network, 2: exact blocks).
+// Own low-mode blocks of operator `op` (single-sphere problems): L_i depends
+// on the sphere's radius only, so each distinct radius is probed once, G of
+// its 73 low modes per pass on G copies of the sphere (each its own problem),
+// as many passes as needed.  Lu [distinct radii][73][73], uid[i] = the block
+// of sphere i.
+sbie_status own_blocks(sbie_ctx* c, const sbie_opts& o, int op, std::vector<double>& Lu, std::vector<int>& uid) {
+    const int n = c->n, NM = kLowModes;
+    const size_t blk = (size_t)NM * NM;
+    std::vector<double> ur;  // distinct radii
+    uid.assign(n, 0);
+    {
+        std::map<double, int> seen;
+        for (int i = 0; i < n; ++i) {
+            auto it = seen.find(c->h_a[i]);
+            if (it == seen.end()) {
+                it = seen.emplace(c->h_a[i], (int)ur.size()).first;
+                ur.push_back(c->h_a[i]);
+            }
+            uid[i] = it->second;
+        }
+    }
+    const int nu = (int)ur.size();
+    const long long cap_nodes = 1LL << 22;  // nodes per pass
+    const int G = (int)std::max(1LL, std::min((long long)NM, cap_nodes / ((long long)nu * c->npn)));
+    const int ns = nu * G;
+    std::vector<double> cc((size_t)ns * 3, 0.0), aa(ns);
+    std::vector<int> ps(ns + 1);
+    for (int j = 0; j < ns; ++j) {
+        aa[j] = ur[j / G];
+        ps[j] = j;
+    }
+    ps[ns] = ns;
+    sbie_ctx* sc = nullptr;
+    CKS(create_part(o, ns, cc.data(), aa.data(), ps, c->stream, &sc));
+    std::vector<double> ZS, ZA;
+    lowmode_tables(c->p, ZS, ZA);
+    double *dZS = nullptr, *dZA = nullptr, *dB = nullptr;
+    sbie_status st = SBIE_OK;
+    if (dmalloc(&dZS, ZS.size()) != cudaSuccess || dmalloc(&dZA, ZA.size()) != cudaSuccess ||
+        dmalloc(&dB, (size_t)nu * blk) != cudaSuccess)
+        st = fail(c, SBIE_ERR_OOM, "own-block probe buffers");
+    Lu.assign((size_t)nu * blk, 0.0);
+    cudaError_t e = cudaSuccess;
+    if (st == SBIE_OK) {
+        e = h2d(sc->stream, dZS, ZS.data(), ZS.size());
+        if (e == cudaSuccess) e = h2d(sc->stream, dZA, ZA.data(), ZA.size());
+        for (int b0 = 0; b0 < NM && e == cudaSuccess && st == SBIE_OK; b0 += G) {
+            e = launch_probe_density_multi(sc, G, b0, dZS, sc->d_in);
+            if (e == cudaSuccess) {
+                st = apply_dev(sc, op, kModeF64, sc->d_in, sc->d_out);
+                if (st != SBIE_OK) c->err = sc->err;
+            }
+            if (st == SBIE_OK && e == cudaSuccess) e = launch_probe_analysis_multi(sc, G, b0, dZA, sc->d_out, dB);
+        }
+        if (e == cudaSuccess && st == SBIE_OK) e = d2h(sc->stream, Lu.data(), dB, Lu.size());
+        if (e != cudaSuccess && st == SBIE_OK) st = fail(c, SBIE_ERR_CUDA, std::string("own blocks: ") + cudaGetErrorString(e));
+    }
+    for (double* p : {dZS, dZA, dB})
+        if (p) cudaFree(p);
+    free_all(sc);
+    delete sc;
+    return st;
+}
+
 sbie_status precond_setup(sbie_ctx* c, int op, int kind, const PairNet* net) {
     auto t0 = std::chrono::steady_clock::now();
     PrecState& P = c->prec[prec_slot(op)];
@@ -1613,19 +1681,15 @@ sbie_status precond_setup(sbie_ctx* c, int op, int kind, const PairNet* net) {
     sbie_opts o = c->opts;
     o.use_learned_precond = 0;
     o.stream = nullptr;
-    std::vector<int> ps1(n + 1);
-    for (int q = 0; q <= n; ++q) ps1[q] = q;
-    sbie_ctx* sc = nullptr;
-    CKS(create_part(o, n, c->h_c.data(), c->h_a.data(), ps1, c->stream, &sc));
-    std::vector<double> Lam;
-    sbie_status st = probe_blocks(sc, op, 1, 1, Lam);
-    if (st != SBIE_OK) c->err = sc->err;
-    free_all(sc);
-    delete sc;
+    std::vector<double> Lu;
+    std::vector<int> uid;
+    sbie_status st = own_blocks(c, o, op, Lu, uid);
     CKS(st);
     // pair blocks B_ab (target a <- source b) and B_ba
-    std::vector<double> Bab((size_t)np * blk), Bba((size_t)np * blk);
+    std::vector<double> Bab, Bba;
     if (kind == 2 && np > 0) {
+        Bab.resize((size_t)np * blk);
+        Bba.resize((size_t)np * blk);
         std::vector<double> cc((size_t)np * 6), aa((size_t)np * 2);
         std::vector<int> ps(np + 1);
         for (int q = 0; q < np; ++q) {
@@ -1652,8 +1716,15 @@ sbie_status precond_setup(sbie_ctx* c, int op, int kind, const PairNet* net) {
         free_all(pc);
         delete pc;
         CKS(st);
-    } else if (kind == 1 && np > 0) {
-        std::vector<float> X((size_t)2 * np * kMlpIn, 0.f);
+    }
+    // learned blocks: the network's inputs, and per direction the pair frame's
+    // low-mode rotation as its degree blocks (R from Q, Ri from Q^T)
+    constexpr int kDc = 165;
+    std::vector<float> X, Dr, Di;
+    if (kind == 1 && np > 0) {
+        X.assign((size_t)2 * np * kMlpIn, 0.f);
+        Dr.resize((size_t)2 * np * kDc);
+        Di.resize((size_t)2 * np * kDc);
         std::vector<double> Qs((size_t)2 * np * 9);
         for (int q = 0; q < np; ++q) {
             const int a = pairs[q].first, b = pairs[q].second;
@@ -1665,40 +1736,21 @@ sbie_status precond_setup(sbie_ctx* c, int op, int kind, const PairNet* net) {
             float* x1 = &X[(2 * q + 1) * kMlpIn];
             x1[2] = (float)d; x1[3] = (float)c->h_a[b]; x1[4] = (float)c->h_a[a];
         }
-        std::vector<double> Bp;
-        CKS(net_blocks(*net, X, Bp));
-        // pair frame -> lab frame, each direction independent: host threads
         parallel_for(2 * np, [&](int t0, int t1) {
-            std::vector<double> R, Ri;
             for (int t = t0; t < t1; ++t) {
-                const int q = t / 2, dir = t % 2;
                 const double* Q = &Qs[(size_t)t * 9];
                 double Qt[9];
                 for (int r = 0; r < 3; ++r)
                     for (int s = 0; s < 3; ++s) Qt[3 * r + s] = Q[3 * s + r];
-                lowmode_rotation(Q, R);
-                lowmode_rotation(Qt, Ri);
-                rotate_block(Ri, Bp.data() + (size_t)t * blk, R, (dir == 0 ? Bba : Bab).data() + q * blk);
+                lowmode_rotation_blocks(Q, &Dr[(size_t)t * kDc]);
+                lowmode_rotation_blocks(Qt, &Di[(size_t)t * kDc]);
             }
         });
     }
-    // pair systems [[L_a, B_ab], [B_ba, L_b]] and own blocks, inverted in FP32
-    std::vector<float> A((size_t)std::max(1, np) * 4 * blk), S((size_t)n * blk);
-    for (int q = 0; q < np; ++q) {
-        const int a = pairs[q].first, b = pairs[q].second;
-        float* M = A.data() + q * 4 * blk;
-        for (int r = 0; r < NM; ++r)
-            for (int s = 0; s < NM; ++s) {
-                M[r * 2 * NM + s] = (float)Lam[a * blk + r * NM + s];
-                M[r * 2 * NM + NM + s] = (float)Bab[q * blk + r * NM + s];
-                M[(NM + r) * 2 * NM + s] = (float)Bba[q * blk + r * NM + s];
-                M[(NM + r) * 2 * NM + NM + s] = (float)Lam[b * blk + r * NM + s];
-            }
-    }
-    for (size_t i = 0; i < S.size(); ++i) S[i] = (float)Lam[i];
     bool ok = dmalloc(&P.d_pp_ptr, pp_ptr.size()) == cudaSuccess && dmalloc(&P.d_pp_idx, pp_idx.size()) == cudaSuccess &&
-              dmalloc(&P.d_pp_pair, pp_pair.size()) == cudaSuccess && dmalloc(&P.d_pinv, A.size()) == cudaSuccess &&
-              dmalloc(&P.d_sinv, S.size()) == cudaSuccess;
+              dmalloc(&P.d_pp_pair, pp_pair.size()) == cudaSuccess &&
+              dmalloc(&P.d_pinv, (size_t)std::max(1, np) * 4 * blk) == cudaSuccess &&
+              dmalloc(&P.d_sinv, (size_t)n * blk) == cudaSuccess;
     const bool tables = !c->d_ZS;
     if (tables)
         ok = ok && dmalloc(&c->d_ZS, ZS.size()) == cudaSuccess && dmalloc(&c->d_ZA, ZA.size()) == cudaSuccess &&
@@ -1716,8 +1768,66 @@ sbie_status precond_setup(sbie_ctx* c, int op, int kind, const PairNet* net) {
     CK(h2d(c->stream, P.d_pp_ptr, pp_ptr.data(), pp_ptr.size()));
     CK(h2d(c->stream, P.d_pp_idx, pp_idx.data(), pp_idx.size()));
     CK(h2d(c->stream, P.d_pp_pair, pp_pair.data(), pp_pair.size()));
-    CK(h2d(c->stream, P.d_pinv, A.data(), A.size()));
-    CK(h2d(c->stream, P.d_sinv, S.data(), S.size()));
+    if (kind == 1) {
+        // pair systems and own systems assembled on the device from the
+        // network's outputs, which never leave it
+        std::vector<float> Luf(Lu.begin(), Lu.end());
+        std::vector<int2> pr2((size_t)std::max(1, np));
+        for (int q = 0; q < np; ++q) pr2[q] = make_int2(pairs[q].first, pairs[q].second);
+        float *dLu = nullptr, *dY = nullptr, *dDr = nullptr, *dDi = nullptr, *dmean = nullptr, *dsd = nullptr;
+        int* duid = nullptr;
+        int2* dpr = nullptr;
+        cudaError_t e = cudaSuccess;
+        if (dmalloc(&dLu, Luf.size()) != cudaSuccess || dmalloc(&duid, uid.size()) != cudaSuccess) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = h2d(c->stream, dLu, Luf.data(), Luf.size());
+        if (e == cudaSuccess) e = h2d(c->stream, duid, uid.data(), uid.size());
+        if (e == cudaSuccess && np > 0) {
+            if (dmalloc(&dY, (size_t)2 * np * blk) != cudaSuccess || dmalloc(&dDr, Dr.size()) != cudaSuccess ||
+                dmalloc(&dDi, Di.size()) != cudaSuccess || dmalloc(&dmean, blk) != cudaSuccess ||
+                dmalloc(&dsd, blk) != cudaSuccess || dmalloc(&dpr, pr2.size()) != cudaSuccess)
+                e = cudaErrorMemoryAllocation;
+            if (e == cudaSuccess) e = h2d(c->stream, dDr, Dr.data(), Dr.size());
+            if (e == cudaSuccess) e = h2d(c->stream, dDi, Di.data(), Di.size());
+            if (e == cudaSuccess) e = h2d(c->stream, dmean, net->out_mean.data(), blk);
+            if (e == cudaSuccess) e = h2d(c->stream, dsd, net->out_std.data(), blk);
+            if (e == cudaSuccess) e = h2d(c->stream, dpr, pr2.data(), pr2.size());
+            if (e == cudaSuccess) {
+                const sbie_status sn = net_forward_dev(*net, X, c->stream, dY);
+                if (sn != SBIE_OK) e = cudaErrorUnknown;
+            }
+            if (e == cudaSuccess)
+                e = launch_pair_systems(c->stream, np, dpr, duid, dLu, dY, dmean, dsd, dDr, dDi, P.d_pinv);
+        }
+        if (e == cudaSuccess) e = launch_own_systems(c->stream, n, duid, dLu, P.d_sinv);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        for (void* p : {(void*)dLu, (void*)dY, (void*)dDr, (void*)dDi, (void*)dmean, (void*)dsd, (void*)duid, (void*)dpr})
+            if (p) cudaFree(p);
+        if (e != cudaSuccess) {
+            cudaFree(d_bad);
+            return fail(c, SBIE_ERR_CUDA, std::string("learned pair systems: ") + cudaGetErrorString(e));
+        }
+    } else {
+        // exact blocks: pair systems [[L_a, B_ab], [B_ba, L_b]] and own blocks assembled here
+        std::vector<float> A((size_t)std::max(1, np) * 4 * blk), S((size_t)n * blk);
+        parallel_for(np, [&](int q0, int q1) {
+            for (int q = q0; q < q1; ++q) {
+                const double* La = &Lu[(size_t)uid[pairs[q].first] * blk];
+                const double* Lb = &Lu[(size_t)uid[pairs[q].second] * blk];
+                float* M = A.data() + q * 4 * blk;
+                for (int r = 0; r < NM; ++r)
+                    for (int s = 0; s < NM; ++s) {
+                        M[r * 2 * NM + s] = (float)La[r * NM + s];
+                        M[r * 2 * NM + NM + s] = (float)Bab[q * blk + r * NM + s];
+                        M[(NM + r) * 2 * NM + s] = (float)Bba[q * blk + r * NM + s];
+                        M[(NM + r) * 2 * NM + NM + s] = (float)Lb[r * NM + s];
+                    }
+            }
+        });
+        for (int i = 0; i < n; ++i)
+            for (size_t e = 0; e < blk; ++e) S[(size_t)i * blk + e] = (float)Lu[(size_t)uid[i] * blk + e];
+        CK(h2d(c->stream, P.d_pinv, A.data(), A.size()));
+        CK(h2d(c->stream, P.d_sinv, S.data(), S.size()));
+    }
     CK(launch_gauss_jordan(c->stream, 2 * NM, np, P.d_pinv, d_bad));
     CK(launch_gauss_jordan(c->stream, NM, n, P.d_sinv, d_bad));
     int bad = 0;

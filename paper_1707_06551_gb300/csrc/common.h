@@ -342,10 +342,22 @@ void self_gemm_free(sbie_ctx* c);
 // precond.cu
 void lowmode_tables(int p, std::vector<double>& ZS, std::vector<double>& ZA);
 void lowmode_rotation(const double Q[9], std::vector<double>& R);
+// the degree blocks D_0 .. D_4 of lowmode_rotation, row-major, 165 values
+void lowmode_rotation_blocks(const double Q[9], float* Dc);
+// pair systems of the learned preconditioner assembled on the device (see precond.cu)
+cudaError_t launch_pair_systems(cudaStream_t s, int np, const int2* pairs, const int* uid, const float* Lu,
+                                const float* Y, const float* mean, const float* sd, const float* Dr, const float* Di,
+                                float* sys);
+cudaError_t launch_own_systems(cudaStream_t s, int n, const int* uid, const float* Lu, float* S);
 std::vector<int4> low_mode_table();
 cudaError_t launch_gauss_jordan(cudaStream_t s, int n, int count, float* mats, int* d_bad);
 cudaError_t launch_probe_density(sbie_ctx* c, int sph_per_prob, int side, int beta, const double* ZS, double* dens);
 cudaError_t launch_probe_analysis(sbie_ctx* c, const double* ZA, const double* u, int beta, double* blocks);
+// G low modes per pass on single-sphere problems: sphere j carries mode
+// b0 + j mod G; blocks[j / G][row][mode]
+cudaError_t launch_probe_density_multi(sbie_ctx* c, int G, int b0, const double* ZS, double* dens);
+cudaError_t launch_probe_analysis_multi(sbie_ctx* c, int G, int b0, const double* ZA, const double* u,
+                                        double* blocks);
 // M^{-1} v; f32: the FP32 inner solves' form (H and the low-mode analysis by
 // the tensor-core GEMM), else FP64 throughout
 cudaError_t precond_apply(sbie_ctx* c, int slot, const double* v, double* out, bool f32);

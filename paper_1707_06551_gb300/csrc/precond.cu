@@ -183,11 +183,14 @@ const RotGrid& rot_grid() {
 
 }  // namespace
 
-void lowmode_rotation(const double Q[9], std::vector<double>& R) {
+namespace {
+
+// D[n][row][mu]: coefficient `row` of the rotated real basis function mu
+void lowmode_d(const double Q[9], double (&D)[kRL + 1][2 * kRL + 1][2 * kRL + 1]) {
     const RotGrid& G = rot_grid();
-    const int NM = kLowModes;
-    // D[n][row][mu]: coefficient `row` of the rotated real basis function mu
-    double D[kRL + 1][2 * kRL + 1][2 * kRL + 1] = {};
+    for (int n = 0; n <= kRL; ++n)
+        for (int r = 0; r < 2 * kRL + 1; ++r)
+            for (int c = 0; c < 2 * kRL + 1; ++c) D[n][r][c] = 0.0;
     double P[kRSh], vx[2 * kRL + 1];
     for (int q = 0; q < kRNodes; ++q) {
         const double* y = G.y[q];
@@ -219,6 +222,14 @@ void lowmode_rotation(const double Q[9], std::vector<double>& R) {
             }
         }
     }
+}
+
+}  // namespace
+
+void lowmode_rotation(const double Q[9], std::vector<double>& R) {
+    const int NM = kLowModes;
+    double D[kRL + 1][2 * kRL + 1][2 * kRL + 1];
+    lowmode_d(Q, D);
     // scatter into R: the same D_n for V, W, X
     R.assign((size_t)NM * NM, 0.0);
     static const std::vector<Mode> modes = low_modes();
@@ -229,6 +240,15 @@ void lowmode_rotation(const double Q[9], std::vector<double>& R) {
             if (ma.t != mb.t || ma.n != mb.n) continue;
             R[(size_t)a * NM + b] = D[ma.n][sub(ma)][sub(mb)];
         }
+}
+
+void lowmode_rotation_blocks(const double Q[9], float* Dc) {
+    double D[kRL + 1][2 * kRL + 1][2 * kRL + 1];
+    lowmode_d(Q, D);
+    int o = 0;
+    for (int n = 0; n <= kPrecL; ++n)
+        for (int r = 0; r < 2 * n + 1; ++r)
+            for (int c = 0; c < 2 * n + 1; ++c) Dc[o++] = (float)D[n][r][c];
 }
 
 namespace {
@@ -257,6 +277,113 @@ __global__ void probe_analysis_kernel(int npn, const double* __restrict__ ZA, co
     double s = 0.0;
     for (int e = 0; e < npn * 3; ++e) s = fma(za[e], us[e], s);
     blocks[((size_t)sphere * kLowModes + row) * kLowModes + beta] = s;
+}
+
+// Probes for G low modes at once: sphere j (its own single-sphere problem)
+// carries low mode beta = b0 + j mod G of side 0 (zero when beta >= 73).
+__global__ void probe_density_multi_kernel(int npn, int G, int b0, const double* __restrict__ ZS, long long N,
+                                           double* __restrict__ dens) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const long long sphere = i / npn;
+    const int q = (int)(i - sphere * npn);
+    const int beta = b0 + (int)(sphere % G);
+    for (int c = 0; c < 3; ++c) dens[3 * i + c] = beta < kLowModes ? ZS[((size_t)q * 3 + c) * kLowModes + beta] : 0.0;
+}
+
+// out[u][row][beta] = (ZA . u_sphere)[row] for sphere j = u G + (beta - b0)
+__global__ void probe_analysis_multi_kernel(int npn, int G, int b0, const double* __restrict__ ZA,
+                                            const double* __restrict__ u, double* __restrict__ blocks) {
+    const long long sphere = blockIdx.x;
+    const int row = threadIdx.x;
+    const int beta = b0 + (int)(sphere % G);
+    if (row >= kLowModes || beta >= kLowModes) return;
+    const long long unit = sphere / G;
+    const double* us = u + (size_t)sphere * npn * 3;
+    const double* za = ZA + (size_t)row * npn * 3;
+    double s = 0.0;
+    for (int e = 0; e < npn * 3; ++e) s = fma(za[e], us[e], s);
+    blocks[((size_t)unit * kLowModes + row) * kLowModes + beta] = s;
+}
+
+// Degree, position within its (type, degree) block, and block start of low
+// mode a (the modes run type-major, then degree, then m with (Re, Im) pairs).
+__device__ __forceinline__ void mode_block(int a, int& n, int& sub, int& start) {
+    int t = 0, base = 0;
+    const int per[3] = {(kPrecL + 1) * (kPrecL + 1), (kPrecL + 1) * (kPrecL + 1) - 1, (kPrecL + 1) * (kPrecL + 1) - 1};
+    while (a - base >= per[t]) base += per[t++];
+    int r = a - base;
+    n = t == 0 ? 0 : 1;
+    while (r >= 2 * n + 1) r -= 2 * n + 1, ++n;
+    sub = r;
+    start = a - r;
+}
+
+// Pair systems [[L_a, B_ab], [B_ba, L_b]] (FP32, 146 x 146) of the learned
+// preconditioner, one CTA per pair: the network's pair-frame blocks
+// (standardised outputs Y, de-standardised here) turned to the lab frame,
+// B = Ri Bp R, with R, Ri block diagonal by (type, degree) and given per
+// direction as the compact degree blocks D_n (Dr for R, Di for Ri, 165 values
+// each); direction 2q gives B_ba, 2q + 1 gives B_ab.
+__global__ void __launch_bounds__(256) pair_system_kernel(const int2* __restrict__ pairs, const int* __restrict__ uid,
+                                                          const float* __restrict__ Lu, const float* __restrict__ Y,
+                                                          const float* __restrict__ mean, const float* __restrict__ sd,
+                                                          const float* __restrict__ Dr, const float* __restrict__ Di,
+                                                          float* __restrict__ sys) {
+    constexpr int NM = kLowModes, BLK = NM * NM, W = 2 * NM, NDC = 165;
+    __shared__ float B[BLK], T[BLK], dr[NDC], di[NDC];
+    const int q = blockIdx.x;
+    const int2 pr = pairs[q];
+    float* M = sys + (size_t)q * W * W;
+    const float* La = Lu + (size_t)uid[pr.x] * BLK;
+    const float* Lb = Lu + (size_t)uid[pr.y] * BLK;
+    for (int e = threadIdx.x; e < BLK; e += blockDim.x) {
+        const int r = e / NM, c = e - r * NM;
+        M[r * W + c] = La[e];
+        M[(NM + r) * W + NM + c] = Lb[e];
+    }
+    for (int dir = 0; dir < 2; ++dir) {
+        const size_t t = 2 * (size_t)q + dir;
+        __syncthreads();
+        for (int e = threadIdx.x; e < BLK; e += blockDim.x) B[e] = Y[t * BLK + e] * sd[e] + mean[e];
+        for (int e = threadIdx.x; e < NDC; e += blockDim.x) {
+            dr[e] = Dr[t * NDC + e];
+            di[e] = Di[t * NDC + e];
+        }
+        __syncthreads();
+        // T = B R: T[k][s] = sum over l in the block of s of B[k][l] D_n[sub l][sub s]
+        for (int e = threadIdx.x; e < BLK; e += blockDim.x) {
+            const int k = e / NM, s = e - k * NM;
+            int n, ss, st;
+            mode_block(s, n, ss, st);
+            const int d = 2 * n + 1, off = n * (2 * n - 1) * (2 * n + 1) / 3;
+            float v = 0.f;
+            for (int j = 0; j < d; ++j) v = fmaf(B[k * NM + st + j], dr[off + j * d + ss], v);
+            T[e] = v;
+        }
+        __syncthreads();
+        // out = Ri T: out[r][s] = sum over k in the block of r of Di_n[sub r][sub k] T[k][s]
+        for (int e = threadIdx.x; e < BLK; e += blockDim.x) {
+            const int r = e / NM, s = e - r * NM;
+            int n, sr, st;
+            mode_block(r, n, sr, st);
+            const int d = 2 * n + 1, off = n * (2 * n - 1) * (2 * n + 1) / 3;
+            float v = 0.f;
+            for (int j = 0; j < d; ++j) v = fmaf(di[off + sr * d + j], T[(st + j) * NM + s], v);
+            if (dir == 0) M[(NM + r) * W + s] = v;   // B_ba
+            else M[r * W + NM + s] = v;              // B_ab
+        }
+    }
+}
+
+// own systems: S[i] = L of sphere i's radius
+__global__ void own_system_kernel(int n, const int* __restrict__ uid, const float* __restrict__ Lu,
+                                  float* __restrict__ S) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int BLK = kLowModes * kLowModes;
+    if (e >= (long long)n * BLK) return;
+    const long long i = e / BLK;
+    S[e] = Lu[(size_t)uid[i] * BLK + (e - i * BLK)];
 }
 
 // In-place inverse of `count` n x n matrices (FP32, row-major, contiguous) by
@@ -507,6 +634,20 @@ __global__ void synth_add_kernel(int npn, long long N, const double* __restrict_
 
 }  // namespace
 
+cudaError_t launch_pair_systems(cudaStream_t s, int np, const int2* pairs, const int* uid, const float* Lu,
+                                const float* Y, const float* mean, const float* sd, const float* Dr, const float* Di,
+                                float* sys) {
+    if (np == 0) return cudaSuccess;
+    pair_system_kernel<<<np, 256, 0, s>>>(pairs, uid, Lu, Y, mean, sd, Dr, Di, sys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_own_systems(cudaStream_t s, int n, const int* uid, const float* Lu, float* S) {
+    const long long tot = (long long)n * kLowModes * kLowModes;
+    own_system_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, uid, Lu, S);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gauss_jordan(cudaStream_t s, int n, int count, float* mats, int* d_bad) {
     if (count == 0) return cudaSuccess;
     size_t sm = sizeof(float) * ((size_t)n * 2 * n + n);
@@ -525,6 +666,19 @@ cudaError_t launch_probe_density(sbie_ctx* c, int sph_per_prob, int side, int be
 
 cudaError_t launch_probe_analysis(sbie_ctx* c, const double* ZA, const double* u, int beta, double* blocks) {
     probe_analysis_kernel<<<c->n, 96, 0, c->stream>>>(c->npn, ZA, u, beta, blocks);
+    ++c->n_launch;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe_density_multi(sbie_ctx* c, int G, int b0, const double* ZS, double* dens) {
+    probe_density_multi_kernel<<<(unsigned)((c->N + 255) / 256), 256, 0, c->stream>>>(c->npn, G, b0, ZS, c->N, dens);
+    ++c->n_launch;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe_analysis_multi(sbie_ctx* c, int G, int b0, const double* ZA, const double* u,
+                                        double* blocks) {
+    probe_analysis_multi_kernel<<<c->n, 96, 0, c->stream>>>(c->npn, G, b0, ZA, u, blocks);
     ++c->n_launch;
     return cudaGetLastError();
 }

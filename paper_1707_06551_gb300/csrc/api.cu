@@ -188,8 +188,11 @@ void choose_tuning(sbie_ctx* c) {
                 int slots = th * tpt;
                 int chunks = (c->npn + slots - 1) / slots;
                 double waste = (double)(chunks * slots - c->npn) / c->npn;
-                double pref = f32 ? (tpt == 2 ? 0.0 : 0.03) : (tpt == 1 ? 0.0 : 0.05);
-                pref += th == 128 ? 0.0 : 0.001;
+                // FP32: 64 threads x 4 targets (the 128-register build, 8
+                // resident CTAs per SM) is what the autotuner settles on
+                double pref = f32 ? ((tpt == 4 && th == 64) ? 0.0 : (tpt == 2 ? 0.03 : 0.04))
+                                  : (tpt == 1 ? 0.0 : 0.05);
+                pref += (th == 128 || (f32 && th == 64)) ? 0.0 : 0.001;
                 double score = waste + pref;
                 if (score < best_waste - 1e-12) {
                     best_waste = score;
@@ -201,6 +204,12 @@ void choose_tuning(sbie_ctx* c) {
         long long ctas = (long long)c->n * chunks;
         long long want = (long long)c->sm_count * (f32 ? 12 : 4);
         int split = (int)std::min<long long>(32, std::max<long long>(1, (want + ctas - 1) / ctas));
+        if (f32 && best.threads == 64 && best.tpt == 4) {
+            // about three whole waves of resident CTAs
+            best.minb = 8;
+            const int occ = far_occupancy(c, Kern::D, kModeF32, best);
+            if (occ > 0) split = (int)std::min<long long>(32, std::max<long long>(1, 3LL * occ * c->sm_count / ctas));
+        }
         // small contexts: shorter tiles before fewer splits
         while (best.tile > 32 && (c->N + split - 1) / split < best.tile) best.tile /= 2;
         long long per = (c->N + split - 1) / split;

@@ -1266,7 +1266,8 @@ sbie_status net_load(const char* path, PairNetSet& set) {
 // sphere s of every problem and operator `op` (resistance or mobility)
 // applied in FP64; the low-mode analysis of every sphere's response fills
 // out[s][sphere][row][mode] (host).
-sbie_status probe_blocks(sbie_ctx* c, int op, int sph_per_prob, int nsides, std::vector<double>& out) {
+sbie_status probe_blocks(sbie_ctx* c, int op, int sph_per_prob, int nsides, std::vector<double>& out,
+                         int mode = kModeF64) {
     std::vector<double> ZS, ZA;
     lowmode_tables(c->p, ZS, ZA);
     double *dZS = nullptr, *dZA = nullptr, *dB = nullptr;
@@ -1283,7 +1284,7 @@ sbie_status probe_blocks(sbie_ctx* c, int op, int sph_per_prob, int nsides, std:
         for (int s = 0; s < nsides && e == cudaSuccess && st == SBIE_OK; ++s)
             for (int b = 0; b < kLowModes && e == cudaSuccess && st == SBIE_OK; ++b) {
                 e = launch_probe_density(c, sph_per_prob, s, b, dZS, c->d_in);
-                if (e == cudaSuccess) st = apply_dev(c, op, kModeF64, c->d_in, c->d_out);
+                if (e == cudaSuccess) st = apply_dev(c, op, mode, c->d_in, c->d_out);
                 if (st == SBIE_OK && e == cudaSuccess) e = launch_probe_analysis(c, dZA, c->d_out, b, dB + s * per);
             }
         if (e == cudaSuccess && st == SBIE_OK) {
@@ -1303,7 +1304,7 @@ sbie_status create_part(const sbie_opts& o, int n, const double* centres, const 
 // Exact aligned blocks: source sphere (radius a_s) at the origin, target
 // (radius a_t) at (0, 0, d); out [n][73][73] (target <- source).
 sbie_status aligned_blocks(int n, const double* d, const double* a_s, const double* a_t, int p, double eta, int op,
-                           std::vector<double>& out) {
+                           std::vector<double>& out, int mode = kModeF64) {
     std::vector<double> cc((size_t)n * 6, 0.0), aa((size_t)n * 2);
     std::vector<int> ps(n + 1);
     for (int q = 0; q < n; ++q) {
@@ -1320,7 +1321,7 @@ sbie_status aligned_blocks(int n, const double* d, const double* a_s, const doub
     sbie_ctx* pc = nullptr;
     CKS(create_part(o, 2 * n, cc.data(), aa.data(), ps, nullptr, &pc));
     std::vector<double> B;
-    sbie_status st = probe_blocks(pc, op, 2, 1, B);
+    sbie_status st = probe_blocks(pc, op, 2, 1, B, mode);
     if (st == SBIE_OK) {
         out.resize((size_t)n * kLowModes * kLowModes);
         const size_t blk = (size_t)kLowModes * kLowModes;
@@ -1333,7 +1334,6 @@ sbie_status aligned_blocks(int n, const double* d, const double* a_s, const doub
     return st;
 }
 
-// y = Rinv * B * R for 73 x 73 matrices (R, Rinv sparse block diagonal).
 // f(begin, end) over [0, n) split across the host's cores.
 template <typename F>
 void parallel_for(int n, F f) {
@@ -1394,33 +1394,20 @@ sbie_status net_forward_dev(const PairNet& net, const std::vector<float>& X5, cu
     return SBIE_OK;
 }
 
+// The network's blocks for inputs X5, de-standardised, on the host.
 sbie_status net_blocks(const PairNet& net, const std::vector<float>& X5, std::vector<double>& out) {
     const int n = (int)(X5.size() / kMlpIn);
-    MlpLayout L = mlp_layout();
-    float *dw = nullptr, *dX = nullptr, *dY = nullptr;
-    __nv_bfloat16* dwb = nullptr;
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(nullptr, SBIE_ERR_CUDA, "stream");
-    std::vector<float> Xs(X5.size());
-    for (int q = 0; q < n; ++q)
-        for (int j = 0; j < kMlpIn; ++j) Xs[q * kMlpIn + j] = (X5[q * kMlpIn + j] - net.in_mean[j]) / net.in_std[j];
-    cudaError_t e = cudaMalloc(&dw, sizeof(float) * L.total);
-    if (e == cudaSuccess) e = cudaMalloc(&dwb, sizeof(__nv_bfloat16) * L.total);
-    if (e == cudaSuccess) e = cudaMalloc(&dX, sizeof(float) * Xs.size());
-    if (e == cudaSuccess) e = cudaMalloc(&dY, sizeof(float) * (size_t)n * kMlpOut);
-    if (e == cudaSuccess) e = h2d(s, dw, net.params.data(), (size_t)L.total);
-    if (e == cudaSuccess) e = h2d(s, dX, Xs.data(), Xs.size());
-    if (e == cudaSuccess) e = mlp_to_bf16(s, dw, dwb);
-    if (e == cudaSuccess) e = mlp_forward_dev(s, dw, dwb, n, dX, dY);
-    std::vector<float> Y;
-    if (e == cudaSuccess) {
-        Y.resize((size_t)n * kMlpOut);
-        e = d2h(s, Y.data(), dY, Y.size());
-    }
-    for (void* p : {(void*)dw, (void*)dwb, (void*)dX, (void*)dY})
-        if (p) cudaFree(p);
+    float* dY = nullptr;
+    std::vector<float> Y((size_t)n * kMlpOut);
+    sbie_status st = SBIE_OK;
+    if (cudaMalloc(&dY, sizeof(float) * Y.size()) != cudaSuccess) st = fail(nullptr, SBIE_ERR_OOM, "network outputs");
+    if (st == SBIE_OK) st = net_forward_dev(net, X5, s, dY);
+    if (st == SBIE_OK && d2h(s, Y.data(), dY, Y.size()) != cudaSuccess) st = fail(nullptr, SBIE_ERR_CUDA, "network outputs");
+    if (dY) cudaFree(dY);
     cudaStreamDestroy(s);
-    if (e != cudaSuccess) return fail(nullptr, SBIE_ERR_CUDA, std::string("network: ") + cudaGetErrorString(e));
+    if (st != SBIE_OK) return st;
     out.resize(Y.size());
     for (size_t i = 0; i < Y.size(); ++i)
         out[i] = (double)Y[i] * net.out_std[i % kMlpOut] + net.out_mean[i % kMlpOut];
@@ -1479,7 +1466,8 @@ sbie_status train_one(const sbie_pair_train_opts& o, int op, PairNet& net, sbie_
     for (int q0 = 0; q0 < n; q0 += chunk) {
         const int m = std::min(chunk, n - q0);
         std::vector<double> out;
-        CKS(aligned_blocks(m, d.data() + q0, as.data() + q0, at.data() + q0, o.p, 1e9, op, out));
+        // the FP32 operator: blocks to about 1e-6, far below the network's error
+        CKS(aligned_blocks(m, d.data() + q0, as.data() + q0, at.data() + q0, o.p, 1e9, op, out, kModeF32));
         std::memcpy(blocks.data() + (size_t)q0 * kMlpOut, out.data(), sizeof(double) * out.size());
     }
     auto t1 = std::chrono::steady_clock::now();
@@ -1714,7 +1702,7 @@ sbie_status precond_setup(sbie_ctx* c, int op, int kind, const PairNet* net) {
         sbie_ctx* pc = nullptr;
         CKS(create_part(o, 2 * np, cc.data(), aa.data(), ps, c->stream, &pc));
         std::vector<double> PB;
-        st = probe_blocks(pc, op, 2, 2, PB);
+        st = probe_blocks(pc, op, 2, 2, PB, kModeF32);  // the pair systems are FP32
         if (st != SBIE_OK) c->err = pc->err;
         const size_t per = (size_t)2 * np * blk;
         if (st == SBIE_OK)

@@ -98,8 +98,9 @@ def layer(g, op, dens, targets=None):
 
 
 def apply(g, op, dens, targets=None):
-    """The operators of oracle.operators.apply / apply_at with the rotated
-    close-pair scheme (rows of other spheres zero when targets are given)."""
+    """The operators of oracle.operators.apply / apply_at (S, D, K, mobility,
+    resistance, porous, squirmer) with the rotated close-pair scheme (rows of
+    other spheres zero when targets are given)."""
     dens = np.asarray(dens, float).reshape(-1, 3)
     rows = np.arange(g.N) if targets is None else np.concatenate(
         [np.arange(g.sl(i).start, g.sl(i).stop) for i in targets])
@@ -111,4 +112,10 @@ def apply(g, op, dens, targets=None):
         return mask * (0.5 * dens + ops.rigid_L(g, dens)) + layer(g, "K", dens, targets)
     if op == "resistance":
         return mask * (0.5 * dens + ops.completion_N(g, dens, rows)) + layer(g, "D", dens, targets)
+    if op == "porous":
+        return mask * (0.5 * dens) + layer(g, "S", dens, targets) + layer(g, "D", dens, targets)
+    if op == "squirmer":
+        r = ops.rigid_part(g, dens)
+        q = dens - r
+        return mask * (0.5 * q - r) + layer(g, "S", q, targets) + layer(g, "D", q, targets)
     raise ValueError(op)

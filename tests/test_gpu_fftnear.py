@@ -28,7 +28,7 @@ def _per_sphere(got, ref, npn):
         np.abs(ref).reshape(-1, npn, 3), axis=(1, 2))
 
 
-@pytest.mark.parametrize("op", ["S", "D", "K", "resistance", "mobility"])
+@pytest.mark.parametrize("op", ["S", "D", "K", "resistance", "mobility", "porous", "squirmer"])
 @pytest.mark.parametrize("geom", [(6, 4, 1, (1.0, 1.0)), (7, 9, 5, (0.5, 1.5))])
 def test_rotated_scheme_matches_oracle(sb, op, geom):
     n, p, seed, rr = geom
@@ -78,3 +78,24 @@ def test_rotated_scheme_solves_converge_to_direct(sb, prec, tol):
                 assert info["status"] == 0
         errs.append(np.max(np.abs(F[1] - F[0])) / np.max(np.abs(F[0])))
     assert errs[2] < errs[0] / 10 and errs[2] < 1e-3, errs
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-6)])
+def test_batch_with_rotated_scheme_equals_separate_contexts(sb, prec, tol):
+    """A batch of suspensions of different orders with the rotated scheme
+    applies each problem's operator as a context of its own does."""
+    batch = []
+    for n, p, seed in ((4, 4, 1), (5, 6, 2), (3, 5, 3)):
+        w = wl.small_suspension(n, p, seed, radius_range=(0.8, 1.2))
+        batch.append((w["centres"], w["radii"], p))
+    rng = np.random.default_rng(11)
+    dens = [rng.normal(size=(len(r) * (p + 1) * (2 * p + 2), 3)) for (c, r, p) in batch]
+    with sb.SphereBIE(batch=batch, prec=prec, near_scheme=1) as s:
+        out = s.apply("mobility", np.concatenate(dens))
+    off = 0
+    for (c, r, p), d in zip(batch, dens):
+        with sb.SphereBIE(c, r, p, prec=prec, near_scheme=1) as s1:
+            ref = s1.apply("mobility", d)
+        got = out[off:off + len(d)]
+        off += len(d)
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < tol

@@ -99,7 +99,7 @@ typedef struct {
                                Sec. 4.2 (Fig. 2: source coefficients rotated to the pair's
                                pole, evaluation on the target's pole-aligned grid, forward
                                transform, rotation back), which projects the close-pair field
-                               onto degree <= p on the target sphere; p <= 16                */
+                               onto degree <= p on the target sphere                          */
 } sbie_opts;
 
 typedef struct {

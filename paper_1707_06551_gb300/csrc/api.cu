@@ -982,8 +982,6 @@ sbie_status check_opts(const sbie_opts* opts) {
     if (opts->use_graphs != 0 && opts->use_graphs != 1) return fail(nullptr, SBIE_ERR_ARG, "use_graphs must be 0 or 1");
     if (opts->near_scheme != 0 && opts->near_scheme != 1)
         return fail(nullptr, SBIE_ERR_ARG, "near_scheme must be 0 or 1");
-    if (opts->near_scheme == 1 && opts->p > 16)
-        return fail(nullptr, SBIE_ERR_ARG, "the rotated close-pair scheme (near_scheme 1) takes p <= 16");
     return SBIE_OK;
 }
 
@@ -1898,8 +1896,6 @@ sbie_status sphere_bie_create_batch(int n_problems, const int* n_spheres, const 
         if (p_per_problem[q] < 1 || p_per_problem[q] > kMaxP) return fail(nullptr, SBIE_ERR_ARG, "p must be in [1, 24]");
         if (opts->use_learned_precond > 0 && p_per_problem[q] < kPrecL)
             return fail(nullptr, SBIE_ERR_ARG, "the pair preconditioner needs p >= 4");
-        if (opts->near_scheme == 1 && p_per_problem[q] > 16)
-            return fail(nullptr, SBIE_ERR_ARG, "the rotated close-pair scheme (near_scheme 1) takes p <= 16");
         ntot += n_spheres[q];
     }
     if (ntot > (1LL << 30)) return fail(nullptr, SBIE_ERR_ARG, "too many spheres");

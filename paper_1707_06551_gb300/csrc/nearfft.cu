@@ -190,8 +190,10 @@ __global__ void fft_eval_kernel(FftArgs<T> A) {
     const T* mSt = tab + tl.o_mS;
     const int S = P1 * P1;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T* ch = reinterpret_cast<T*>(smraw);         // [K][NCH]
-    T* Ad = ch + (size_t)K * NCH;                // [G][L+1][NCH][2] a group of discs
+    // the pair's channels stay in global memory (read through L1): at p = 24
+    // they alone would fill the shared memory
+    const T* ch = A.chan + (size_t)e * K * nchs;  // [K][nchs]
+    T* Ad = reinterpret_cast<T*>(smraw);          // [G][L+1][NCH][2] a group of discs
     T* U = Ad + (size_t)G * (L + 1) * NCH * 2;   // [3][npn] spherical components of the samples
     T* Fh = U + 3 * npn;                         // [3][nlat][P1][2]
     T* cu = Fh + 3 * nlat * P1 * 2;              // [3][P1][P1][2]
@@ -203,10 +205,6 @@ __global__ void fft_eval_kernel(FftArgs<T> A) {
     const int tid = threadIdx.x, bd = blockDim.x;
     const double* g = A.geo + 8 * (size_t)e;
     const T D = (T)g[4], rho = (T)g[5], scale = KIND == 0 ? (T)g[6] : T(1);  // S scales by the source radius
-    for (int q = tid; q < K * NCH; q += bd) {
-        const int row = q / NCH, h = q - row * NCH;
-        ch[q] = A.chan[((size_t)e * K + row) * nchs + h];
-    }
     for (int q = tid; q < nlon; q += bd) {
         pc[q] = cph[q];
         ps[q] = sph[q];
@@ -234,8 +232,8 @@ __global__ void fft_eval_kernel(FftArgs<T> A) {
                     q1 = qn;
                 }
                 const int ire = sh_index(L, n, m, 0);
-                ar = fma(ch[(size_t)ire * NCH + h], qn, ar);
-                if (m >= 1) ai = fma(-ch[(size_t)(ire + 1) * NCH + h], qn, ai);
+                ar = fma(ch[(size_t)ire * nchs + h], qn, ar);
+                if (m >= 1) ai = fma(-ch[(size_t)(ire + 1) * nchs + h], qn, ai);
             }
             Ad[2 * q] = ar;
             Ad[2 * q + 1] = ai;
@@ -492,8 +490,8 @@ size_t fft_eval_smem(int p, int kind, size_t elem) {
     const int P1 = p + 1, L = kind == 2 ? p + 2 : p + 1, K = (L + 1) * (L + 1);
     const int nch = kind == 2 ? kTracChannels : kVelChannels;
     const int nlat = p + 1, nlon = 2 * p + 2, npn = nlat * nlon, S = P1 * P1;
-    return elem * ((size_t)K * nch + (size_t)fft_eval_group(p) * (L + 1) * nch * 2 + 3 * npn + 3 * nlat * P1 * 2 +
-                   6 * S * 4 + 2 * nlon);
+    (void)K;
+    return elem * ((size_t)fft_eval_group(p) * (L + 1) * nch * 2 + 3 * npn + 3 * nlat * P1 * 2 + 6 * S * 4 + 2 * nlon);
 }
 
 cudaError_t launch_near_fft(sbie_ctx* c, Kern op, bool f32, double* out) {

@@ -99,3 +99,18 @@ def test_batch_with_rotated_scheme_equals_separate_contexts(sb, prec, tol):
         got = out[off:off + len(d)]
         off += len(d)
         assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < tol
+
+
+@pytest.mark.parametrize("op", ["S", "D", "K", "mobility"])
+def test_rotated_scheme_at_p24(sb, op):
+    """The library's largest order: the evaluation kernel reads the pair's
+    channels from global memory and needs 210 KB of shared memory in FP64."""
+    w = wl.small_suspension(3, 24, 5, radius_range=(0.8, 1.2))
+    g = ops.Geometry(w["centres"], w["radii"], 24)
+    assert g.n_near_pairs() > 0
+    dens = np.random.default_rng(24).normal(size=(g.N, 3))
+    ref = fftnear.apply(g, op, dens)
+    for prec, tol in ((0, 1e-10), (1, 2e-5)):
+        with sb.SphereBIE(w["centres"], w["radii"], 24, prec=prec, near_scheme=1) as s:
+            out = s.apply(op, dens)
+        assert np.all(_per_sphere(out, ref, g.npn) < tol), (prec, _per_sphere(out, ref, g.npn).max())

@@ -73,10 +73,11 @@ def test_close_pair_converges_to_direct(op):
 
 def test_operator_converges_to_direct_on_a_suspension():
     """Three spheres, every pair close (gaps 1.1 to 1.4 radii), a random nodal
-    density: the rotated-scheme resistance and mobility operators approach the
-    direct ones (oracle.operators.apply) geometrically in p."""
+    density: the rotated-scheme resistance, mobility, porous-media and
+    squirmer operators approach the direct ones (oracle.operators.apply)
+    geometrically in p."""
     c = np.array([[0.0, 0.0, 0.0], [3.2, 0.4, -0.3], [-0.5, 3.3, 0.2]])
-    errs = {"resistance": [], "mobility": []}
+    errs = {"resistance": [], "mobility": [], "porous": [], "squirmer": []}
     for p in (8, 12, 16):
         g = ops.Geometry(c, [1.0, 0.9, 1.1], p, eta=2.0)
         assert g.n_near_pairs() == 6

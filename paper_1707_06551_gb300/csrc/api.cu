@@ -92,7 +92,7 @@ void free_all(sbie_ctx* c) {
                     c->d_near_idx, c->d_tab, c->d_coef, c->d_chan, c->d_chanf, c->d_mom, c->d_part, c->d_src64,
                     c->d_srcf, c->d_in, c->d_out, c->d_tmp, c->d_tmp2, c->d_small, c->d_red, c->d_V, c->d_xsol,
                     c->d_rhs, c->d_res, c->d_prob_sph, c->d_sph_prob, c->d_node_prob, c->d_seg3, c->d_H, c->d_pvec,
-                    c->d_ZS, c->d_ZA, c->d_modes, c->d_low, c->d_lowe, c->d_pz, c->d_ad, c->d_adi, c->d_vk,
+                    c->d_ZS, c->d_ZSf, c->d_ZA, c->d_modes, c->d_low, c->d_lowe, c->d_pz, c->d_ad, c->d_adi, c->d_vk,
                     c->d_sq, c->d_lcoef, c->d_rotp, c->d_rotm, c->d_fgeo, c->d_fcoef, c->d_fchan, c->d_fblk,
                     c->d_fiota, c->d_tabf, c->d_rotpf, c->d_rotmf, c->d_fcoeff, c->d_fchanf, c->d_fblkf};
     for (void* p : ptrs)
@@ -1757,6 +1757,12 @@ sbie_status precond_setup(sbie_ctx* c, int op, int kind, const PairNet* net) {
     CK(cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
     if (tables) {
         CK(h2d(c->stream, c->d_ZS, ZS.data(), ZS.size()));
+        if (c->opts.prec == SBIE_MIXED) {  // FP32 copy for the FP32 inner solves
+            std::vector<float> ZSf(ZS.begin(), ZS.end());
+            if (dmalloc(&c->d_ZSf, ZSf.size()) != cudaSuccess) return fail(c, SBIE_ERR_OOM, "preconditioner buffers");
+            CK(h2d(c->stream, c->d_ZSf, ZSf.data(), ZSf.size()));
+            CK(cudaStreamSynchronize(c->stream));
+        }
         CK(h2d(c->stream, c->d_ZA, ZA.data(), ZA.size()));
         CK(h2d(c->stream, c->d_modes, modes.data(), modes.size()));
     }

@@ -205,6 +205,7 @@ struct sbie_ctx {
     sbie::PrecState prec[2];
     std::shared_ptr<sbie::PairNetSet> nets;  // networks of opts.mlp_weights_path (top context)
     double* d_ZS = nullptr;        // [npn][3][73] low-mode synthesis
+    float* d_ZSf = nullptr;        // the same in FP32 (mixed-precision contexts)
     double* d_ZA = nullptr;        // [73][npn][3] low-mode analysis
     int4* d_modes = nullptr;       // [73] (type, n, m, part)
     double* d_low = nullptr;       // [n][73]

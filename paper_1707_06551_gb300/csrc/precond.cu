@@ -632,6 +632,38 @@ __global__ void synth_add_kernel(int npn, long long N, const double* __restrict_
     }
 }
 
+// The same in FP32 for the FP32 inner solves (FP64 would make this small
+// contraction FP64-bound on GB300): out_sphere += ZS . e_sphere
+__global__ void synth_add_f32_kernel(int npn, long long N, const float* __restrict__ ZS, const double* __restrict__ e,
+                                     double* __restrict__ out) {
+    __shared__ float es[kLowModes];
+    const long long i0 = (long long)blockIdx.x * blockDim.x;
+    const long long s0 = i0 / npn;
+    long long i = i0 + threadIdx.x;
+    const bool valid = i < N;
+    if (!valid) i = N - 1;
+    const long long s = i / npn;
+    const int q = (int)(i - s * npn);
+    float v[3] = {0.f, 0.f, 0.f};
+    const float* z = ZS + (size_t)q * 3 * kLowModes;
+    // the block's spheres one at a time through shared memory
+    const long long s1 = min((long long)(i0 + blockDim.x - 1), N - 1) / npn;
+    for (long long ss = s0; ss <= s1; ++ss) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < kLowModes; b += blockDim.x) es[b] = (float)e[(size_t)ss * kLowModes + b];
+        __syncthreads();
+        if (ss != s) continue;
+        for (int b = 0; b < kLowModes; ++b) {
+            const float eb = es[b];
+            v[0] = fmaf(z[b], eb, v[0]);
+            v[1] = fmaf(z[kLowModes + b], eb, v[1]);
+            v[2] = fmaf(z[2 * kLowModes + b], eb, v[2]);
+        }
+    }
+    if (!valid) return;
+    for (int c = 0; c < 3; ++c) out[3 * i + c] += (double)v[c];
+}
+
 }  // namespace
 
 cudaError_t launch_pair_systems(cudaStream_t s, int np, const int2* pairs, const int* uid, const float* Lu,
@@ -723,7 +755,11 @@ cudaError_t precond_apply(sbie_ctx* c, int slot, const double* v, double* out, b
                                                               P.d_sinv, c->d_low, c->d_lowe);
         ++c->n_launch;
     }
-    synth_add_kernel<<<(unsigned)((c->N + 127) / 128), 128, 0, c->stream>>>(c->npn, c->N, c->d_ZS, c->d_lowe, out);
+    if (f32 && c->d_ZSf)
+        synth_add_f32_kernel<<<(unsigned)((c->N + 127) / 128), 128, 0, c->stream>>>(c->npn, c->N, c->d_ZSf, c->d_lowe,
+                                                                                    out);
+    else
+        synth_add_kernel<<<(unsigned)((c->N + 127) / 128), 128, 0, c->stream>>>(c->npn, c->N, c->d_ZS, c->d_lowe, out);
     ++c->n_launch;
     return cudaGetLastError();
 }
